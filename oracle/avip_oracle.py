@@ -1,0 +1,425 @@
+"""Plain, slow, FP64 CPU oracle for the Poisson-coupled drift-diffusion step of AVIP
+(arXiv 2201.01291).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or links this module;
+only the tests, the smoke check and the CPU-baseline leg of the benchmark use it.  It shares
+no code with the CUDA library: it restates the paper's vertex-centred finite-volume method
+step by step with numpy/scipy, in the paper's order and notation.
+
+Structure (each function cites the passage it follows):
+  * metrics: cell volume V_tau, face normals S_f, nodal normals S_k^tau (Eq. node_normal),
+    median-dual nodal volume V_i (Fig. 2D_cells), per-cell edge normals S_ij^tau (dual face
+    from the edge midpoint to the centroid), boundary nodal normal S_i^b (Fig. bcs_normal);
+  * Poisson: matrix of Eq. coeff_matriceA with the sign of the "remark on the implementation"
+    (-lap phi = rho/eps0), right-hand side of Eq. poisson_discretization_cartesian, natural
+    Neumann rows, Dirichlet values eliminated symmetrically; solved by a sparse direct LU
+    (the paper names no linear solver; the exact solution of the linear system is the
+    definition being restated);
+  * gradients: Green-Gauss cell gradient with nodal normals (section "Cartesian geometry"),
+    nodal gradient = volume-weighted mean of the cell gradients (the "centered gradient");
+  * transport: limited Lax-Wendroff convective flux with a virtual upwind node and the
+    central diffusive flux, accumulated edge by edge (Eq. vertex_centered_flux and the LLW
+    section), node-flux boundary closure (section "Boundary conditions in AVIP");
+  * time step: cell-based CFL, Fourier, dielectric and chemical limits (section "Time step
+    computation");
+  * source: ionisation S = alpha mu_e |E| n_e added to electrons and positive ions
+    (section "Bagheri benchmark"), optional attachment;
+  * explicit update and the charge sum.
+
+Readings where the paper is silent or garbled (each also listed in the design notes):
+  * ratio of gradients: r = (u_U - u_k)/(u_W - u_U) with the virtual upwind node
+    u_k = u_W - 2 grad(u_U).(x_W - x_U); the printed R_ij is its negative;
+  * for V_ij.S_ij < 0 the roles of i and j are mirrored (the 1D form of the limited scheme);
+  * u_W == u_U gives Psi = 0;
+  * nodal velocity V_s = sign(q_s) mu_s(|E|) E, edge velocity = mean of nodal velocities;
+  * Delta x_tau = shortest edge of the cell; cell values = mean of the three nodal values;
+  * chemical time step A_tau * min over nodes of n_e/|S_e| (the printed form is not a time);
+  * Dirichlet rows eliminated symmetrically (same solution as the unit-row form).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+E_CHARGE = 1.602176634e-19
+EPS0 = 8.8541878128e-12
+
+
+# ----------------------------------------------------------------------------- metrics
+def orient_ccw(xy, tris):
+    """Return the triangles with counter-clockwise vertex order (positive signed area)."""
+    tris = np.asarray(tris, dtype=np.int64).copy()
+    p0, p1, p2 = xy[tris[:, 0]], xy[tris[:, 1]], xy[tris[:, 2]]
+    cross = (p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1]) - (p1[:, 1] - p0[:, 1]) * (p2[:, 0] - p0[:, 0])
+    flip = cross < 0
+    tris[flip, 1], tris[flip, 2] = tris[flip, 2].copy(), tris[flip, 1].copy()
+    return tris
+
+
+def cell_volumes(xy, tris):
+    """V_tau: area of each (counter-clockwise) triangle."""
+    p0, p1, p2 = xy[tris[:, 0]], xy[tris[:, 1]], xy[tris[:, 2]]
+    return 0.5 * ((p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1]) - (p1[:, 1] - p0[:, 1]) * (p2[:, 0] - p0[:, 0]))
+
+
+def face_normals(xy, tris):
+    """Outward, length-scaled normals S_f of the three faces of each triangle.
+    Face m joins local vertices m and m+1 (mod 3); shape (T, 3, 2)."""
+    T = tris.shape[0]
+    Sf = np.empty((T, 3, 2))
+    for m in range(3):
+        p = xy[tris[:, m]]
+        q = xy[tris[:, (m + 1) % 3]]
+        t = q - p
+        Sf[:, m, 0] = t[:, 1]        # right of the direction of travel = outward for CCW
+        Sf[:, m, 1] = -t[:, 0]
+    return Sf
+
+
+def nodal_normals(xy, tris):
+    """S_k^tau = -(n_d / n_v^f) * sum of the faces adjacent to k (Eq. node_normal);
+    triangles: n_d = 2, n_v^f = 2.  Shape (T, 3, 2)."""
+    Sf = face_normals(xy, tris)
+    S = np.empty_like(Sf)
+    for k in range(3):
+        # faces adjacent to local vertex k: face k (k -> k+1) and face k-1 (k-1 -> k)
+        S[:, k] = -(2.0 / 2.0) * (Sf[:, k] + Sf[:, (k - 1) % 3])
+    return S
+
+
+def nodal_volumes(tris, V_tau, n_nodes):
+    """Median-dual nodal volume V_i = sum over E(i) of V_tau / 3 (Fig. 2D_cells)."""
+    V = np.zeros(n_nodes)
+    for k in range(3):
+        np.add.at(V, tris[:, k], V_tau / 3.0)
+    return V
+
+
+def cell_edge_normals(xy, tris):
+    """S_ij^tau: length-scaled normal of the dual face inside tau that separates V_i from
+    V_j, i.e. the segment from the midpoint of edge (i,j) to the centroid, oriented from i
+    towards j (Fig. tri_cell).  Returned for local pairs (0,1), (1,2), (2,0): shape (T,3,2)."""
+    c = (xy[tris[:, 0]] + xy[tris[:, 1]] + xy[tris[:, 2]]) / 3.0
+    out = np.empty((tris.shape[0], 3, 2))
+    for m in range(3):
+        xi = xy[tris[:, m]]
+        xj = xy[tris[:, (m + 1) % 3]]
+        v = c - 0.5 * (xi + xj)
+        n = np.stack([v[:, 1], -v[:, 0]], axis=1)
+        sgn = np.sign(np.einsum("ij,ij->i", n, xj - xi))
+        out[:, m] = n * sgn[:, None]
+    return out
+
+
+def edges_and_normals(xy, tris):
+    """Global edge list (i < j) and the aggregated edge normal S_ij = sum_tau S_ij^tau,
+    oriented from i to j; also the number of cells sharing each edge."""
+    Sc = cell_edge_normals(xy, tris)
+    I = np.concatenate([tris[:, m] for m in range(3)])
+    J = np.concatenate([tris[:, (m + 1) % 3] for m in range(3)])
+    Sv = np.concatenate([Sc[:, m] for m in range(3)])
+    swap = I > J
+    lo = np.where(swap, J, I)
+    hi = np.where(swap, I, J)
+    Sv = np.where(swap[:, None], -Sv, Sv)
+    key = lo.astype(np.int64) * (int(xy.shape[0]) + 1) + hi
+    uniq, inv, counts = np.unique(key, return_inverse=True, return_counts=True)
+    S = np.zeros((uniq.size, 2))
+    np.add.at(S, inv, Sv)
+    edges = np.stack([uniq // (int(xy.shape[0]) + 1), uniq % (int(xy.shape[0]) + 1)], axis=1)
+    return edges.astype(np.int64), S, counts
+
+
+def boundary_normals(xy, tris):
+    """S_i^b = 1/2 * sum of the outward normals of the boundary faces adjacent to node i
+    (Fig. bcs_normal).  A boundary face belongs to exactly one cell."""
+    Sf = face_normals(xy, tris)
+    I = np.concatenate([tris[:, m] for m in range(3)])
+    J = np.concatenate([tris[:, (m + 1) % 3] for m in range(3)])
+    F = np.concatenate([Sf[:, m] for m in range(3)])
+    lo, hi = np.minimum(I, J), np.maximum(I, J)
+    key = lo.astype(np.int64) * (int(xy.shape[0]) + 1) + hi
+    _, inv, counts = np.unique(key, return_inverse=True, return_counts=True)
+    bnd = counts[inv] == 1
+    Sb = np.zeros((xy.shape[0], 2))
+    np.add.at(Sb, I[bnd], 0.5 * F[bnd])
+    np.add.at(Sb, J[bnd], 0.5 * F[bnd])
+    return Sb
+
+
+def min_edge_length(xy, tris):
+    """Delta x_tau read as the shortest edge of the cell."""
+    L = []
+    for m in range(3):
+        d = xy[tris[:, (m + 1) % 3]] - xy[tris[:, m]]
+        L.append(np.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2))
+    return np.minimum(np.minimum(L[0], L[1]), L[2])
+
+
+# ----------------------------------------------------------------------------- Poisson
+def poisson_matrix(tris, S, V_tau, n_nodes):
+    """K = -A with a_ik = sum_tau -S_i.S_k/(V_tau n_d^2) (Eq. coeff_matriceA), i.e. the
+    matrix of -lap phi = rho/eps0 (remark on the implementation), n_d = 2."""
+    rows, cols, vals = [], [], []
+    for a in range(3):
+        for b in range(3):
+            rows.append(tris[:, a])
+            cols.append(tris[:, b])
+            vals.append(np.einsum("ij,ij->i", S[:, a], S[:, b]) / (V_tau * 4.0))
+    K = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n_nodes, n_nodes)).tocsr()
+    K.sum_duplicates()
+    return K
+
+
+def poisson_rhs(rho, V_node):
+    """Right-hand side rho_i V_i / eps0 of Eq. poisson_discretization_cartesian; the zero
+    normal field on Neumann sides adds nothing (natural condition)."""
+    return rho * V_node / EPS0
+
+
+class DirichletSolver:
+    """Exact solution of K phi = b with phi = phi_D on Dirichlet nodes: the Dirichlet
+    columns are moved to the right-hand side and K_FF phi_F = b_F - K_FD phi_D is solved by
+    a sparse LU factorisation computed once per mesh."""
+
+    def __init__(self, K, node_bc, phi_D):
+        self.free = np.flatnonzero(node_bc == 0)
+        self.dir = np.flatnonzero(node_bc != 0)
+        self.phi_D = np.asarray(phi_D, dtype=np.float64)
+        Kc = K.tocsc()
+        self.K_FF = Kc[self.free][:, self.free].tocsc()
+        self.K_FD = K.tocsr()[self.free][:, self.dir]
+        self.lu = spla.splu(self.K_FF) if self.free.size else None
+        self.n = K.shape[0]
+
+    def solve(self, b):
+        phi = np.zeros(self.n)
+        phi[self.dir] = self.phi_D[self.dir]
+        if self.free.size:
+            rhs = b[self.free] - self.K_FD @ self.phi_D[self.dir]
+            phi[self.free] = self.lu.solve(rhs)
+        return phi
+
+
+# ----------------------------------------------------------------------------- gradients
+def cell_gradient(u, tris, S, V_tau):
+    """grad u_tau = -1/(V_tau n_d) sum_k u_k S_k (section "Cartesian geometry"), n_d = 2."""
+    g = np.zeros((tris.shape[0], 2))
+    for k in range(3):
+        g += u[tris[:, k]][:, None] * S[:, k]
+    return -g / (2.0 * V_tau)[:, None]
+
+
+def nodal_gradient(u, tris, S, V_tau, V_node):
+    """Centered nodal gradient: volume-weighted mean of the cell gradients over E(i), each
+    cell contributing its V_tau/3 share of V_i."""
+    gc = cell_gradient(u, tris, S, V_tau)
+    g = np.zeros((V_node.size, 2))
+    for k in range(3):
+        np.add.at(g, tris[:, k], gc * (V_tau / 3.0)[:, None])
+    return g / V_node[:, None]
+
+
+# ----------------------------------------------------------------------------- closures
+def mobility(sp_, Emag):
+    """Mobility of a species as a function of |E|: constant, or the local-field power law
+    mu0 (max(|E|, E_floor)/E_ref)^expo."""
+    p = sp_.mob_params
+    if sp_.mob_model == 0:
+        return np.full_like(Emag, p[0])
+    if sp_.mob_model == 1:
+        return p[0] * (np.maximum(Emag, p[3]) / p[1]) ** p[2]
+    raise ValueError("unknown mobility model")
+
+
+def townsend_alpha(A, B, Emag):
+    """alpha(|E|) = A exp(-B/|E|), zero where |E| = 0."""
+    out = np.zeros_like(Emag)
+    nz = Emag > 0
+    out[nz] = A * np.exp(-B / Emag[nz])
+    return out
+
+
+def limiter(r, beta, kind):
+    """Psi(r): Sweby(beta) = max(0, min(beta r, 1), min(r, beta)) or Van Leer (r+|r|)/(1+|r|)."""
+    if kind == 0:
+        return np.maximum(0.0, np.maximum(np.minimum(beta * r, 1.0), np.minimum(r, beta)))
+    return (r + np.abs(r)) / (1.0 + np.abs(r))
+
+
+# ----------------------------------------------------------------------------- the method
+class Oracle:
+    """The full explicit iteration on one mesh.  `problem` is any object with the fields of
+    the synthetic workload (xy, tris, node_bc, phi_D, species, source, opts)."""
+
+    def __init__(self, problem):
+        self.p = problem
+        xy = np.asarray(problem.xy, dtype=np.float64)
+        self.xy = xy
+        self.tris = orient_ccw(xy, problem.tris)
+        self.N = xy.shape[0]
+        self.V_tau = cell_volumes(xy, self.tris)
+        if np.any(self.V_tau <= 0):
+            raise ValueError("degenerate triangle")
+        self.S = nodal_normals(xy, self.tris)
+        self.V_node = nodal_volumes(self.tris, self.V_tau, self.N)
+        self.edges, self.S_edge, _ = edges_and_normals(xy, self.tris)
+        self.S_b = boundary_normals(xy, self.tris)
+        self.dx_tau = min_edge_length(xy, self.tris)
+        self.K = poisson_matrix(self.tris, self.S, self.V_tau, self.N)
+        self.node_bc = np.asarray(problem.node_bc)
+        self.solver = DirichletSolver(self.K, self.node_bc, problem.phi_D)
+        self.is_bnd = np.any(self.S_b != 0.0, axis=1)
+
+    # -- Poisson sub-step -------------------------------------------------------------
+    def charge_density(self, n):
+        rho = np.zeros(self.N)
+        for s, sp_ in enumerate(self.p.species):
+            rho += E_CHARGE * sp_.charge * n[s]
+        return rho
+
+    def poisson(self, n):
+        return self.solver.solve(poisson_rhs(self.charge_density(n), self.V_node))
+
+    # -- one explicit step -----------------------------------------------------------
+    def fields(self, n):
+        """phi, E = -grad phi, |E|, nodal velocities and density gradients."""
+        phi = self.poisson(n)
+        E = -nodal_gradient(phi, self.tris, self.S, self.V_tau, self.V_node)
+        Emag = np.sqrt(E[:, 0] ** 2 + E[:, 1] ** 2)
+        mu = [mobility(sp_, Emag) for sp_ in self.p.species]
+        vel = [np.sign(sp_.charge) * mu[s][:, None] * E for s, sp_ in enumerate(self.p.species)]
+        grad = [nodal_gradient(n[s], self.tris, self.S, self.V_tau, self.V_node)
+                for s in range(len(self.p.species))]
+        return phi, E, Emag, mu, vel, grad
+
+    def sources(self, n, Emag, mu):
+        """Per-species source rates S_s,i (m^-3 s^-1) and the net electron rate."""
+        src = self.p.source
+        out = [np.zeros(self.N) for _ in self.p.species]
+        if src.model == 0:
+            return out
+        e, pos, neg = src.idx
+        A, B, nu_att = src.params
+        alpha = townsend_alpha(A, B, Emag)
+        ion = alpha * mu[e] * Emag * n[e]
+        out[e] = out[e] + ion
+        out[pos] = out[pos] + ion
+        if src.model == 2:
+            att = nu_att * n[e]
+            out[e] = out[e] - att
+            out[neg] = out[neg] + att
+        return out
+
+    def time_step(self, n, mu, vel, S_src):
+        """Minimum over cells and species of the convective, diffusive and dielectric time
+        steps, and the chemical limit over nodes (section "Time step computation")."""
+        o = self.p.opts
+        t = self.tris
+        dts = [np.inf]
+        for s, sp_ in enumerate(self.p.species):
+            Vc = (vel[s][t[:, 0]] + vel[s][t[:, 1]] + vel[s][t[:, 2]]) / 3.0
+            Vm = np.sqrt(Vc[:, 0] ** 2 + Vc[:, 1] ** 2)
+            ok = Vm > 0
+            if np.any(ok):
+                dts.append(np.min(o.cfl * self.dx_tau[ok] / Vm[ok]))
+            if sp_.D > 0:
+                dts.append(np.min(o.fourier * self.dx_tau ** 2 / sp_.D))
+        sigma = np.zeros(t.shape[0])
+        for s, sp_ in enumerate(self.p.species):
+            nm = n[s] * mu[s]
+            cell = (nm[t[:, 0]] + nm[t[:, 1]] + nm[t[:, 2]]) / 3.0
+            sigma += np.abs(sp_.charge * E_CHARGE * cell)
+        ok = sigma > 0
+        if np.any(ok):
+            dts.append(np.min(o.a_diel * EPS0 / sigma[ok]))
+        if self.p.source.model != 0:
+            e = self.p.source.idx[0]
+            Se = S_src[e]
+            ok = Se != 0
+            if np.any(ok):
+                with np.errstate(over="ignore", divide="ignore"):
+                    dts.append(np.min(o.a_chem * n[e][ok] / np.abs(Se[ok])))
+        return float(min(dts))
+
+    def edge_flux(self, u, grad, vel, D, dt):
+        """Limited Lax-Wendroff convective flux plus central diffusive flux through the dual
+        face of every edge (i, j), i < j, counted positive from i to j (LLW section and
+        "Central difference diffusive flux integration")."""
+        o = self.p.opts
+        i, j = self.edges[:, 0], self.edges[:, 1]
+        S = self.S_edge
+        Vij = 0.5 * (vel[i] + vel[j])
+        a = np.einsum("ij,ij->i", Vij, S)
+        gij = 0.5 * (grad[i] + grad[j])
+        up_i = a >= 0
+        U = np.where(up_i, i, j)
+        W = np.where(up_i, j, i)
+        delta = u[W] - u[U]
+        d = self.xy[W] - self.xy[U]
+        nz = delta != 0
+        r = np.zeros_like(delta)
+        r[nz] = (2.0 * np.einsum("ij,ij->i", grad[U][nz], d[nz]) - delta[nz]) / delta[nz]
+        psi = np.where(nz, limiter(r, o.beta, o.limiter), 0.0)
+        lw = 0.5 * delta - 0.5 * dt * np.einsum("ij,ij->i", gij, Vij)
+        FC = (u[U] + lw * psi) * a
+        FD = -D * np.einsum("ij,ij->i", gij, S)
+        return FC + FD
+
+    def residual(self, u, grad, vel, D, bnd_mode, dt):
+        """R_i = -(sum of the fluxes leaving V_i): edge fluxes scattered to both ends
+        (Eq. vertex_centered_flux, residual computed at each edge) plus the node-flux
+        boundary closure F_i.S_i^b with F = F_C (Neumann) or F_C + F_D (outflow).
+        Returns R and the per-node boundary outflow F_i.S_i^b."""
+        F = self.edge_flux(u, grad, vel, D, dt)
+        R = np.zeros(self.N)
+        np.add.at(R, self.edges[:, 0], -F)
+        np.add.at(R, self.edges[:, 1], F)
+        Fb = u[:, None] * vel
+        if bnd_mode == 1:
+            Fb = Fb - D * grad
+        fb = np.einsum("ij,ij->i", Fb, self.S_b)
+        return R - fb, fb
+
+    def step(self, n, dt_fixed=None):
+        """One explicit step from densities n (list of (N,) arrays).  Returns the new
+        densities and a dict of diagnostics (phi, E, dt, charge, boundary ledger)."""
+        phi, E, Emag, mu, vel, grad = self.fields(n)
+        S_src = self.sources(n, Emag, mu)
+        if dt_fixed is not None and dt_fixed > 0:
+            dt = float(dt_fixed)
+        elif self.p.opts.dt_fixed > 0:
+            dt = float(self.p.opts.dt_fixed)
+        else:
+            dt = self.time_step(n, mu, vel, S_src)
+        new = []
+        outflow = []
+        for s, sp_ in enumerate(self.p.species):
+            R, fb = self.residual(n[s], grad[s], vel[s], sp_.D, sp_.bnd_mode, dt)
+            outflow.append(float(np.sum(fb)))
+            new.append(n[s] + dt * (R / self.V_node + S_src[s]))
+        info = dict(phi=phi, E=E, dt=dt, outflow=outflow,
+                    source_total=[float(np.sum(self.V_node * S_src[s])) for s in range(len(n))])
+        return new, info
+
+    def charge(self, n):
+        """Q = e sum_s q_s sum_i V_i n_s,i."""
+        return float(sum(E_CHARGE * sp_.charge * np.sum(self.V_node * n[s])
+                         for s, sp_ in enumerate(self.p.species)))
+
+    def initial_state(self):
+        return [np.asarray(sp_.n0, dtype=np.float64).copy() for sp_ in self.p.species]
+
+    def run(self, nsteps, n=None):
+        """nsteps explicit steps from the initial (or given) state.  Returns the final
+        densities, the potential of the last step, and the per-step dt list."""
+        n = self.initial_state() if n is None else [x.copy() for x in n]
+        dts = []
+        phi = None
+        for _ in range(nsteps):
+            n, info = self.step(n)
+            dts.append(info["dt"])
+            phi = info["phi"]
+        return n, phi, dts

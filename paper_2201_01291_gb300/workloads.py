@@ -1,0 +1,246 @@
+"""Seeded synthetic inputs for the Poisson-coupled drift-diffusion step.
+
+This module builds *inputs only*: node coordinates, triangles, boundary flags, Dirichlet
+values, initial densities and the physical parameters of each species.  It holds none of
+the method's arithmetic (no metrics, no fluxes, no solver), so both the CUDA path and the
+CPU oracle can be driven from it without sharing any of the method.
+
+Workload shapes follow the drift-diffusion discharge cases of the paper (AVIP, arXiv
+2201.01291): a planar domain with two electrodes (Dirichlet potential, Eq. poisson_dirichlet),
+insulating sides (zero normal field, Eq. poisson_neumann), electrons and positive ions seeded
+by a Gaussian (the initial condition shape of Eq. positive_ions_bagheri, section "Bagheri
+benchmark"), on jittered triangle meshes whose sizes span the paper's 1e4--2e6 cells.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+E_CHARGE = 1.602176634e-19      # C
+EPS0 = 8.8541878128e-12         # F/m
+K_BOLTZMANN = 1.380649e-23      # J/K
+
+# Mobility models understood by both implementations.
+MOB_CONST = 0   # mu = mu0
+MOB_POWER = 1   # mu = mu0 * (max(|E|, E_floor) / E_ref) ** expo
+
+# Source models.
+SRC_NONE = 0
+SRC_TOWNSEND = 1            # alpha(|E|) = A exp(-B/|E|);  S = alpha mu_e |E| n_e to e and +
+SRC_TOWNSEND_ATTACH = 2     # as above, plus attachment nu_a n_e moved from e to -
+
+# Transport boundary closure modes (section "Boundary conditions in AVIP").
+BND_NEUMANN = 0             # F = F_C (zero normal gradient implied)
+BND_OUTFLOW = 1             # F = F_C + F_D ("supersonic")
+
+LIM_SWEBY = 0
+LIM_VANLEER = 1
+
+
+@dataclasses.dataclass
+class Species:
+    name: str
+    charge: int                 # -1 or +1 (units of e)
+    mob_model: int
+    mob_params: List[float]     # MOB_CONST: [mu0]; MOB_POWER: [mu0, E_ref, expo, E_floor]
+    D: float                    # diffusion coefficient, m^2/s
+    bnd_mode: int
+    n0: np.ndarray              # initial density, m^-3, per node
+
+
+@dataclasses.dataclass
+class Source:
+    model: int = SRC_NONE
+    params: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])  # [A, B, nu_att]
+    idx: List[int] = dataclasses.field(default_factory=lambda: [0, 1, -1])  # [electron, positive, negative]
+
+
+@dataclasses.dataclass
+class Opts:
+    cfl: float = 0.4
+    fourier: float = 0.25
+    a_diel: float = 0.5
+    a_chem: float = 0.2
+    beta: float = 1.0           # Sweby parameter (1 = min-mod)
+    limiter: int = LIM_SWEBY
+    rtol: float = 1e-12         # PCG stop: ||b - K phi||_2 <= rtol ||b||_2
+    max_iter: int = 20000
+    dt_fixed: float = 0.0       # > 0 replaces the automatic time step
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    xy: np.ndarray              # (N, 2) float64
+    tris: np.ndarray            # (T, 3) int32, counter-clockwise
+    node_bc: np.ndarray         # (N,) int32: 0 free, 1 Dirichlet
+    phi_D: np.ndarray           # (N,) float64, used where node_bc == 1
+    species: List[Species]
+    source: Source
+    opts: Opts
+    seed: int
+    meta: dict
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+
+def jittered_rectangle(nx: int, ny: int, Lx: float, Ly: float, jitter: float, seed: int,
+                       fixed: Optional[np.ndarray] = None):
+    """Structured nx-by-ny node grid on [0,Lx]x[0,Ly], interior nodes moved uniformly in
+    +-jitter*h per coordinate, every quad split by its lower-left/upper-right diagonal.
+    Nodes are numbered i + nx*j (x fastest).  `fixed` masks extra nodes kept unjittered."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hx, hy = Lx / (nx - 1), Ly / (ny - 1)
+    xs = np.arange(nx) * hx
+    ys = np.arange(ny) * hy
+    X, Y = np.meshgrid(xs, ys)              # (ny, nx)
+    X = X.reshape(-1).copy()
+    Y = Y.reshape(-1).copy()
+    jx = rng.uniform(-jitter * hx, jitter * hx, size=X.shape)
+    jy = rng.uniform(-jitter * hy, jitter * hy, size=Y.shape)
+    ii = np.tile(np.arange(nx), ny)
+    jj = np.repeat(np.arange(ny), nx)
+    interior = (ii > 0) & (ii < nx - 1) & (jj > 0) & (jj < ny - 1)
+    if fixed is not None:
+        interior &= ~fixed
+    X[interior] += jx[interior]
+    Y[interior] += jy[interior]
+    xy = np.stack([X, Y], axis=1)
+    # triangles
+    qi, qj = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1))
+    qi = qi.reshape(-1)
+    qj = qj.reshape(-1)
+    a = qi + nx * qj
+    b = a + 1
+    c = a + 1 + nx
+    d = a + nx
+    t1 = np.stack([a, b, c], axis=1)
+    t2 = np.stack([a, c, d], axis=1)
+    tris = np.empty((2 * a.size, 3), dtype=np.int32)
+    tris[0::2] = t1
+    tris[1::2] = t2
+    return xy, tris, ii, jj
+
+
+def gaussian(xy, x0, y0, sigma, n_peak, n_back):
+    r2 = (xy[:, 0] - x0) ** 2 + (xy[:, 1] - y0) ** 2
+    return n_peak * np.exp(-r2 / sigma ** 2) + n_back
+
+
+def default_species(xy, seed_xy, sigma, n_peak, n_back, field_dependent: bool,
+                    n_species: int = 2):
+    """Electrons + positive ions (+ optional negative ions).  Constant mobility/diffusion
+    or the local-field power law mu_e = 0.04 (max(|E|,1e3)/1e6)^-0.2 m^2/Vs."""
+    ne = gaussian(xy, seed_xy[0], seed_xy[1], sigma, n_peak, n_back)
+    npos = ne.copy()
+    if field_dependent:
+        e_mob = (MOB_POWER, [0.04, 1e6, -0.2, 1e3])
+    else:
+        e_mob = (MOB_CONST, [0.04])
+    sp = [
+        Species("e", -1, e_mob[0], e_mob[1], 0.1, BND_NEUMANN, ne),
+        Species("p", +1, MOB_CONST, [2e-4], 5e-6, BND_NEUMANN, npos),
+    ]
+    if n_species == 3:
+        sp.append(Species("n", -1, MOB_CONST, [2.2e-4], 5e-6, BND_NEUMANN,
+                          np.full_like(ne, 0.0)))
+    return sp
+
+
+def townsend_air(p_torr: float = 760.0):
+    """Textbook air-like Townsend fit alpha = A p exp(-B p/|E|),
+    A = 15 /(cm Torr), B = 365 V/(cm Torr), converted to SI."""
+    A = 15.0 * 100.0 * p_torr          # 1/m
+    B = 365.0 * 100.0 * p_torr         # V/m
+    return A, B
+
+
+def plates_problem(nx: int, ny: int, Lx: float, Ly: float, voltage: float, seed: int,
+                   n_peak: float = 1e19, n_back: float = 1e13, sigma: float = 1e-3,
+                   jitter: float = 0.2, field_dependent: bool = False, source: int = SRC_NONE,
+                   n_species: int = 2, name: str = "plates", opts: Optional[Opts] = None,
+                   needle_len: float = 0.0, seed_y: Optional[float] = None) -> Problem:
+    """Parallel-plate (optionally pin-plane) discharge: phi = 0 on y = 0, phi = voltage on
+    y = Ly (and on a zero-thickness needle of length needle_len hanging from the top centre),
+    zero normal field on the sides."""
+    fixed = None
+    ic = nx // 2
+    ii = np.tile(np.arange(nx), ny)
+    jj = np.repeat(np.arange(ny), nx)
+    hy = Ly / (ny - 1)
+    needle = np.zeros(nx * ny, dtype=bool)
+    if needle_len > 0:
+        needle = (ii == ic) & (jj * hy >= Ly - needle_len - 1e-12 * Ly)
+        fixed = needle
+    xy, tris, ii, jj = jittered_rectangle(nx, ny, Lx, Ly, jitter, seed, fixed)
+    node_bc = np.zeros(nx * ny, dtype=np.int32)
+    phi_D = np.zeros(nx * ny, dtype=np.float64)
+    bottom = jj == 0
+    top = jj == ny - 1
+    node_bc[bottom | top | needle] = 1
+    phi_D[top | needle] = voltage
+    x0 = xy[ic, 0] if needle_len > 0 else 0.5 * Lx
+    if seed_y is None:
+        seed_y = (Ly - needle_len - 5e-4) if needle_len > 0 else 0.5 * Ly
+    sp = default_species(xy, (x0, seed_y), sigma, n_peak, n_back, field_dependent, n_species)
+    src = Source()
+    if source != SRC_NONE:
+        A, B = townsend_air()
+        n_gas = 101325.0 / (K_BOLTZMANN * 300.0)
+        nu_att = 1e-17 * n_gas if source == SRC_TOWNSEND_ATTACH else 0.0
+        src = Source(source, [A, B, nu_att], [0, 1, 2 if n_species == 3 else -1])
+    return Problem(name, xy, tris, node_bc, phi_D, sp, src, opts or Opts(), seed,
+                   dict(nx=nx, ny=ny, Lx=Lx, Ly=Ly, voltage=voltage, needle_len=needle_len))
+
+
+def config_small(nx: int = 17, ny: int = 17, seed: int = 7, **kw) -> Problem:
+    """Small plates case for fast tests (defaults: 17x17 nodes, 512 triangles)."""
+    kw.setdefault("voltage", 5e3)
+    return plates_problem(nx, ny, 1e-2, 1e-2, seed=seed, name=f"small{nx}x{ny}", **kw)
+
+
+def config_plates_65() -> Problem:
+    """Plain FP64 parallel plates: 1 cm x 1 cm, 65 x 65 nodes (8192 triangles), jitter +-0.2h,
+    seed 1, Gaussian 1e19 m^-3 (sigma 1 mm) at the centre on a 1e13 background, 0 V / 5 kV,
+    constant mobility and diffusion, no source, PCG rtol 1e-12, 100 steps."""
+    return plates_problem(65, 65, 1e-2, 1e-2, 5e3, seed=1, name="plates65_fp64")
+
+
+def config_pin_plane(nx: int = 500, ny: int = 1000) -> Problem:
+    """Pin-plane streamer: 1 cm x 2 cm, 500 x 1000 nodes (997,002 triangles), 20 kV needle
+    anode 2 mm long at the top centre, grounded plane at y = 0, local-field electron mobility
+    mu ~ E^-0.2, Townsend ionisation (air-like, 1 atm), Gaussian seed 0.5 mm below the tip."""
+    return plates_problem(nx, ny, 1e-2, 2e-2, 2e4, seed=2, field_dependent=True,
+                          source=SRC_TOWNSEND, name=f"pin_plane_{nx}x{ny}", needle_len=2e-3)
+
+
+def random_instances(count: int, seed: int, t_min: float = 2e3, t_max: float = 2e5):
+    """Many uneven discharge instances: triangle counts log-uniform in [t_min, t_max], aspect
+    ratio uniform in [1,4], voltage uniform in [5,25] kV, 2 or 3 charged species (the third a
+    negative ion fed by attachment, k = 1e-17 m^3/s)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        T = float(np.exp(rng.uniform(np.log(t_min), np.log(t_max))))
+        ar = float(rng.uniform(1.0, 4.0))
+        volt = float(rng.uniform(5e3, 25e3))
+        ns = int(rng.integers(2, 4))
+        # T = 2 (nx-1)(ny-1), ny-1 = ar (nx-1)
+        nq = max(1.0, np.sqrt(T / (2.0 * ar)))
+        nx = max(5, int(round(nq)) + 1)
+        ny = max(5, int(round(nq * ar)) + 1)
+        Lx = 1e-2
+        Ly = Lx * (ny - 1) / (nx - 1)
+        src = SRC_TOWNSEND_ATTACH if ns == 3 else SRC_TOWNSEND
+        p = plates_problem(nx, ny, Lx, Ly, volt, seed=seed * 100003 + k, field_dependent=True,
+                           source=src, n_species=ns, name=f"inst{k}")
+        out.append(p)
+    return out

@@ -1,0 +1,293 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix: closed forms,
+identities of the vertex-centred metrics, the textbook P1 stiffness matrix, manufactured
+Poisson solutions, a dense brute-force solve, the 1D reduction of the limited Lax-Wendroff
+scheme with real upwind nodes, and conservation.  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import avip_oracle as O
+from paper_2201_01291_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def mesh(nx=9, ny=7, Lx=1.0, Ly=0.8, jitter=0.2, seed=3):
+    xy, tris, ii, jj = W.jittered_rectangle(nx, ny, Lx, Ly, jitter, seed)
+    return xy, O.orient_ccw(xy, tris), ii, jj
+
+
+def hat_gradients(xy, tris):
+    """grad(lambda_k) of the linear hat functions, from the inverse Jacobian (independent of
+    the nodal-normal construction)."""
+    p0, p1, p2 = xy[tris[:, 0]], xy[tris[:, 1]], xy[tris[:, 2]]
+    J = np.stack([p1 - p0, p2 - p0], axis=2)          # columns: edges
+    Jinv = np.linalg.inv(J)                           # rows: d(xi,eta)/d(x,y)
+    g1, g2 = Jinv[:, 0, :], Jinv[:, 1, :]
+    return np.stack([-(g1 + g2), g1, g2], axis=1), 0.5 * np.abs(np.linalg.det(J))
+
+
+# ---------------------------------------------------------------- metrics
+def test_nodal_normals_sum_to_zero_and_match_hat_gradients():
+    xy, t, _, _ = mesh()
+    S = O.nodal_normals(xy, t)
+    V = O.cell_volumes(xy, t)
+    assert np.abs(S.sum(axis=1)).max() < 1e-14
+    G, area = hat_gradients(xy, t)
+    np.testing.assert_allclose(V, area, rtol=1e-13)
+    # S_k = -n_d V_tau grad(lambda_k): the Green-Gauss gradient is exact for linear fields
+    np.testing.assert_allclose(S, -2.0 * V[:, None, None] * G, rtol=1e-11, atol=1e-14)
+
+
+def test_cell_edge_normals_identities():
+    """Per cell: sum_j S_ij = S_i / n_d (the exact simplex identity of the Cartesian Poisson
+    section) and S_ij = (S_i - S_j)/6 (the relation quoted in the axisymmetric section)."""
+    xy, t, _, _ = mesh()
+    S = O.nodal_normals(xy, t)
+    Sc = O.cell_edge_normals(xy, t)       # pairs (0,1), (1,2), (2,0)
+    for m in range(3):
+        i, j = m, (m + 1) % 3
+        np.testing.assert_allclose(Sc[:, m], (S[:, i] - S[:, j]) / 6.0, rtol=1e-12, atol=1e-15)
+    for i in range(3):
+        out_ = Sc[:, i]                   # i -> i+1
+        in_ = -Sc[:, (i - 1) % 3]         # pair (i-1, i) reversed: i -> i-1
+        np.testing.assert_allclose(out_ + in_, S[:, i] / 2.0, rtol=1e-12, atol=1e-15)
+
+
+def test_closure_and_volumes():
+    """sum_j S_ij + S_i^b = 0 at every node (constant states are preserved) and the dual
+    volumes tile the domain."""
+    xy, t, _, _ = mesh(nx=11, ny=6, Lx=2.0, Ly=0.5)
+    edges, S, counts = O.edges_and_normals(xy, t)
+    Sb = O.boundary_normals(xy, t)
+    acc = np.zeros_like(Sb)
+    np.add.at(acc, edges[:, 0], S)
+    np.add.at(acc, edges[:, 1], -S)
+    assert np.abs(acc + Sb).max() < 1e-14
+    V = O.nodal_volumes(t, O.cell_volumes(xy, t), xy.shape[0])
+    assert abs(V.sum() - 2.0 * 0.5) < 1e-13
+    # boundary normals of a rectangle: total outward normal vanishes, perimeter is recovered
+    assert np.abs(Sb.sum(axis=0)).max() < 1e-14
+    assert abs(np.abs(Sb).sum() - 2 * (2.0 + 0.5)) < 1e-12
+
+
+def test_gradient_exact_for_linear_fields():
+    xy, t, _, _ = mesh()
+    V = O.cell_volumes(xy, t)
+    S = O.nodal_normals(xy, t)
+    Vn = O.nodal_volumes(t, V, xy.shape[0])
+    u = 3.0 - 2.0 * xy[:, 0] + 5.0 * xy[:, 1]
+    g = O.nodal_gradient(u, t, S, V, Vn)
+    np.testing.assert_allclose(g, np.tile([-2.0, 5.0], (xy.shape[0], 1)), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- Poisson
+def test_matrix_golden_reference_triangle():
+    gold = json.load(open(os.path.join(GOLDEN, "p1_reference_triangle.json")))
+    xy = np.array(gold["xy"])
+    t = O.orient_ccw(xy, np.array([[0, 1, 2]]))
+    K = O.poisson_matrix(t, O.nodal_normals(xy, t), O.cell_volumes(xy, t), 3).toarray()
+    np.testing.assert_allclose(K, np.array(gold["K"]), atol=1e-15)
+
+
+def test_matrix_equals_p1_stiffness():
+    xy, t, _, _ = mesh(nx=8, ny=9)
+    K = O.poisson_matrix(t, O.nodal_normals(xy, t), O.cell_volumes(xy, t), xy.shape[0]).toarray()
+    G, area = hat_gradients(xy, t)
+    Kf = np.zeros_like(K)
+    for a in range(3):
+        for b in range(3):
+            np.add.at(Kf, (t[:, a], t[:, b]), area * np.einsum("ij,ij->i", G[:, a], G[:, b]))
+    np.testing.assert_allclose(K, Kf, atol=1e-12 * np.abs(Kf).max())
+    # symmetric, annihilates constants, annihilates linear fields in interior rows
+    assert np.abs(K - K.T).max() < 1e-14
+    assert np.abs(K.sum(axis=1)).max() < 1e-12
+    _, _, ii, jj = mesh(nx=8, ny=9)
+    interior = (ii > 0) & (ii < 7) & (jj > 0) & (jj < 8)
+    lin = 1.0 + 0.3 * xy[:, 0] - 0.7 * xy[:, 1]
+    assert np.abs((K @ lin)[interior]).max() < 1e-12
+
+
+def all_dirichlet_problem(nx, ny, phi_fn, rho_eps, seed=5):
+    xy, t, ii, jj = W.jittered_rectangle(nx, ny, 1.0, 1.0, 0.2, seed)
+    t = O.orient_ccw(xy, t)
+    bc = ((ii == 0) | (ii == nx - 1) | (jj == 0) | (jj == ny - 1)).astype(np.int32)
+    V = O.cell_volumes(xy, t)
+    S = O.nodal_normals(xy, t)
+    K = O.poisson_matrix(t, S, V, xy.shape[0])
+    Vn = O.nodal_volumes(t, V, xy.shape[0])
+    solver = O.DirichletSolver(K, bc, phi_fn(xy))
+    phi = solver.solve(O.poisson_rhs(np.full(xy.shape[0], rho_eps * O.EPS0), Vn))
+    return np.abs(phi - phi_fn(xy)).max(), K, bc, xy, Vn, rho_eps
+
+
+@pytest.mark.parametrize("case", ["quadratic", "harmonic"])
+def test_manufactured_second_order(case):
+    if case == "quadratic":
+        f = lambda xy: xy[:, 0] ** 2 + xy[:, 1] ** 2        # -lap = -4
+        rho_eps = -4.0
+    else:
+        f = lambda xy: np.sin(np.pi * xy[:, 0]) * np.sinh(np.pi * xy[:, 1]) / np.sinh(np.pi)
+        rho_eps = 0.0
+    errs = [all_dirichlet_problem(n, n, f, rho_eps)[0] for n in (9, 17, 33, 65)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 2e-3
+    assert rates[1:].mean() > 1.6, (errs, rates)   # asymptotic range; first level is coarse
+
+
+def test_dense_bruteforce_tiny():
+    """Direct sparse solve == dense LU of the full FEM system with unit Dirichlet rows."""
+    for n in (3, 4, 5, 9):
+        xy, t, ii, jj = W.jittered_rectangle(n, n, 1.0, 1.0, 0.2, 11 + n)
+        t = O.orient_ccw(xy, t)
+        rng = np.random.default_rng(n)
+        bc = ((jj == 0) | (jj == n - 1)).astype(np.int32)
+        phiD = rng.uniform(-1, 1, xy.shape[0])
+        rho = rng.uniform(-1, 1, xy.shape[0]) * O.EPS0
+        V = O.cell_volumes(xy, t)
+        S = O.nodal_normals(xy, t)
+        Vn = O.nodal_volumes(t, V, xy.shape[0])
+        K = O.poisson_matrix(t, S, V, xy.shape[0])
+        phi = O.DirichletSolver(K, bc, phiD).solve(O.poisson_rhs(rho, Vn))
+        # dense system with the paper's unit-row Dirichlet form (Dirichlet section)
+        G, area = hat_gradients(xy, t)
+        A = np.zeros((xy.shape[0],) * 2)
+        for a in range(3):
+            for b in range(3):
+                np.add.at(A, (t[:, a], t[:, b]), area * np.einsum("ij,ij->i", G[:, a], G[:, b]))
+        b = rho * Vn / O.EPS0
+        d = bc == 1
+        A[d] = 0.0
+        A[d, d] = 1.0
+        b[d] = phiD[d]
+        ref = np.linalg.solve(A, b)
+        np.testing.assert_allclose(phi, ref, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+def test_plates_linear_potential_exact():
+    p = W.config_small(nx=13, ny=11, n_peak=0.0, n_back=0.0)
+    o = O.Oracle(p)
+    phi = o.poisson(o.initial_state())
+    np.testing.assert_allclose(phi, 5e3 * p.xy[:, 1] / 1e-2, rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- transport
+def one_d_reduction(c, D, dt, nx=24, ny=8, beta=1.0):
+    """Run the 2D residual on an unjittered strip with u = u(x) and V = (c, 0); return the
+    2D residual per unit face height and the 1D limited Lax-Wendroff residual written with
+    real upwind nodes and centred nodal gradients."""
+    h = 1.0 / (nx - 1)
+    Ly = h * (ny - 1)
+    p = W.plates_problem(nx, ny, 1.0, Ly, 0.0, seed=1, jitter=0.0, n_peak=0.0, n_back=0.0)
+    p.opts.beta = beta
+    o = O.Oracle(p)
+    x = p.xy[:, 0]
+    prof = lambda xx: 1e2 + 0.5 * (1.0 + np.tanh((xx - 0.45) / 0.08)) * 1e6 + 3e5 * np.sin(7 * xx)
+    u = prof(x)
+    grad = O.nodal_gradient(u, o.tris, o.S, o.V_tau, o.V_node)
+    vel = np.tile([c, 0.0], (p.n_nodes, 1))
+    R, _ = o.residual(u, grad, vel, D, 0, dt)
+    # 1D recurrence on the x line
+    xs = np.arange(nx) * h
+    U = prof(xs)
+    g = np.zeros(nx)
+    g[1:-1] = (U[2:] - U[:-2]) / (2 * h)
+
+    def face(i):  # flux from node i to i+1 through a face of unit height
+        if c >= 0:
+            up, dn, uu = i, i + 1, i - 1
+        else:
+            up, dn, uu = i + 1, i, i + 2
+        delta = U[dn] - U[up]
+        if delta == 0:
+            psi = 0.0
+        else:
+            r = (U[up] - U[uu]) / delta
+            psi = max(0.0, min(beta * r, 1.0), min(r, beta))
+        gf = 0.5 * (g[i] + g[i + 1])
+        fc = (U[up] + (0.5 * delta - 0.5 * dt * gf * c) * psi) * c
+        return fc - D * gf
+
+    ii = np.tile(np.arange(nx), ny)
+    jj = np.repeat(np.arange(ny), nx)
+    sel = (ii >= 3) & (ii <= nx - 4) & (jj >= 2) & (jj <= ny - 3)
+    R1 = np.array([-(face(i) - face(i - 1)) for i in ii[sel]])
+    return R[sel] / h, R1, np.abs(U).max() * abs(c)
+
+
+@pytest.mark.parametrize("c", [3.0, -2.0])
+@pytest.mark.parametrize("beta", [1.0, 2.0])
+def test_llw_reduces_to_1d_limited_lax_wendroff(c, beta):
+    R2, R1, scale = one_d_reduction(c, D=0.0, dt=0.01, beta=beta)
+    np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
+    R2, R1, scale = one_d_reduction(c, D=0.05, dt=0.01, beta=beta)
+    np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
+
+
+def test_uniform_state_and_exponential_source():
+    """A uniform neutral plasma between plates stays uniform; with Townsend ionisation each
+    species grows as n0 (1 + dt nu)^k (explicit Euler of dn/dt = nu n)."""
+    p = W.config_small(nx=9, ny=9, n_peak=0.0, n_back=1e12, source=W.SRC_TOWNSEND,
+                       voltage=3e4, jitter=0.2)
+    o = O.Oracle(p)
+    n = o.initial_state()
+    Emag = 3e4 / 1e-2
+    mu = 0.04
+    A, B = W.townsend_air()
+    nu = A * np.exp(-B / Emag) * mu * Emag
+    ref = 1e12
+    for k in range(5):
+        n, info = o.step(n)
+        ref = ref * (1.0 + info["dt"] * nu)
+        for s in range(2):
+            np.testing.assert_allclose(n[s], ref, rtol=1e-11)
+
+
+def test_charge_ledger_round_off():
+    """Q^{n+1} - Q^n = -dt e sum_s q_s (boundary outflow_s) + dt e sum_s q_s (source total_s):
+    interior fluxes cancel edge by edge, reactions are charge-neutral."""
+    p = W.config_small(nx=17, ny=17, source=W.SRC_TOWNSEND, voltage=2.5e4, n_peak=1e19)
+    o = O.Oracle(p)
+    n = o.initial_state()
+    scale = sum(O.E_CHARGE * np.sum(o.V_node * x) for x in n)
+    for _ in range(10):
+        Q0 = o.charge(n)
+        n, info = o.step(n)
+        ledger = sum(-info["dt"] * O.E_CHARGE * sp_.charge * (info["outflow"][s] - info["source_total"][s])
+                     for s, sp_ in enumerate(p.species))
+        assert abs(o.charge(n) - Q0 - ledger) <= 1e-13 * scale
+        # ionisation is neutral: the source totals of e and + are equal
+        assert abs(info["source_total"][0] - info["source_total"][1]) <= 1e-14 * abs(info["source_total"][0]) + 1e-300
+
+
+def test_time_step_closed_form():
+    """Unjittered plates, uniform field and density: dt = min(CFL h / (mu_e E),
+    F h^2 / D_e, A_D eps0 / (e n (mu_e + mu_+)))."""
+    nx = 11
+    h = 1e-2 / (nx - 1)
+    for nb, volt in ((1e12, 5e3), (1e18, 5e3), (1e10, 1e2)):
+        p = W.config_small(nx=nx, ny=nx, n_peak=0.0, n_back=nb, voltage=volt, jitter=0.0)
+        o = O.Oracle(p)
+        _, info = o.step(o.initial_state())
+        E = volt / 1e-2
+        ref = min(0.4 * h / (0.04 * E), 0.25 * h * h / 0.1, 0.5 * O.EPS0 / (O.E_CHARGE * nb * (0.04 + 2e-4)))
+        assert abs(info["dt"] - ref) <= 1e-12 * ref
+
+
+def test_electrons_drift_against_field():
+    """A weak electron cloud between plates (no space charge) moves towards the anode at
+    mu_e |E|; its centroid speed matches within 2%."""
+    p = W.config_small(nx=33, ny=33, n_peak=1e12, n_back=0.0, voltage=5e3, sigma=1.5e-3,
+                       jitter=0.2)
+    p.opts.dt_fixed = 2e-10
+    o = O.Oracle(p)
+    n = o.initial_state()
+    c0 = np.sum(o.V_node * n[0] * p.xy[:, 1]) / np.sum(o.V_node * n[0])
+    k = 20
+    for _ in range(k):
+        n, _ = o.step(n)
+    c1 = np.sum(o.V_node * n[0] * p.xy[:, 1]) / np.sum(o.V_node * n[0])
+    v = (c1 - c0) / (k * 2e-10)
+    assert abs(v - 0.04 * 5e5) < 0.02 * 0.04 * 5e5
