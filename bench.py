@@ -1,0 +1,321 @@
+"""Throughput of the Poisson-coupled drift-diffusion step on GB300 (cell-steps/s).
+
+Default workload: the pin-plane streamer, 1 cm x 2 cm, 500 x 1000 jittered nodes (997,002
+triangles), Morton-ordered, 20 kV needle anode, local-field electron mobility mu ~ E^-0.2,
+Townsend ionisation, plain FP64, PCG rtol 1e-12.  One step = Poisson (Jacobi-PCG to rtol,
+warm-started) + E + gradients + time step + fluxes + source + update, all in the CUDA library.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one independent replica per GPU (weak scaling; the path has no
+data exchange).  `--impl reference` times the FP64 CPU oracle on the host cores instead.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s (DD+Poisson) plain vs mixed/batched/served; p50/p99 latency"
+UNIT = "cell-steps/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65"])
+    ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    return ap.parse_args()
+
+
+def make_problem(name):
+    from paper_2201_01291_gb300 import workloads as W
+    if name == "pin_plane":
+        p = W.config_pin_plane()
+        desc = ("pin-plane streamer 1cm x 2cm, 500x1000 jittered nodes (997,002 tris), Morton order, "
+                "20 kV needle, mu_e ~ E^-0.2, Townsend alpha (air-like, 1 atm), e + positive ions, FP64")
+    else:
+        p = W.config_plates_65()
+        desc = "parallel plates 1cm x 1cm, 65x65 jittered nodes (8192 tris), 5 kV, constant mu/D, FP64"
+    return p, desc
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pcg_traffic_model(info, iters, solves):
+    """Algorithmic bytes and FP64 flops of the PCG launches (per the kernel design):
+    per iteration  phase A: matrix (col 4 B + value 8 B per stored entry) + row length 4 B +
+                   z gather 8 B + p, q read+write 32 B;  phase B: x, r read+write 32 B, p, q, D^-1
+                   read 24 B, z write 8 B  ->  12 nnz + 108 N bytes;
+                   flops 2 nnz + 16 N (SpMV, two axpy-recurrences, preconditioner, three dots);
+    per solve      b assembly + initial residual + final true residual: 2 x (12 nnz) + ~120 N."""
+    N, nnz = info["n_nodes"], info["nnz"]
+    per_it = 12 * nnz + 108 * N
+    per_solve = 24 * nnz + 120 * N
+    bytes_ = iters * per_it + solves * per_solve
+    flops = iters * (2 * nnz + 16 * N) + solves * (4 * nnz + 12 * N)
+    return bytes_, flops
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2201_01291_gb300 import build, avip
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+        build.build()
+    avip.load()
+    problem, desc = make_problem(args.workload)
+    T = problem.n_tris
+    stream = torch.cuda.Stream()
+    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    # warm-up (graph capture happens here too)
+    with torch.cuda.stream(stream):
+        m.run(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    kernel_ms = dict.fromkeys(avip.TIMED_KERNELS, 0.0)
+    iters = 0
+    launches = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # evict the previous step from L2
+            ms, st = m.run_timed(1)
+            for key in kernel_ms:
+                kernel_ms[key] += ms[key]
+            iters += st["pcg_iters_total"]
+            launches += 5
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * T * args.steps / elapsed
+    # ---- end to end through the public API with host buffers
+    e2e_steps = max(3, min(args.steps, 10))
+    host = m.state()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        m.set_state(host)
+        m.run(1)
+        host = m.state()
+    e2e_t = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_t], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    state_bytes = host.size * 8
+    info = m.info
+    m.close()
+    if rank != 0:
+        return None
+    # ---- roofline of the dominant kernel (PCG)
+    peaks = measured_peaks()
+    byts, flops = pcg_traffic_model(info, iters, args.steps)
+    pcg_s = kernel_ms["pcg"] / 1e3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = byts / pcg_s / 1e9
+    tfl = flops / pcg_s / 1e12
+    alu_frac = tfl / FP64_PEAK_TFLOPS
+    hbm_frac = gbs / hbm
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4), "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)",
+                "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "fp64_tflops": round(tfl, 4), "fp64_frac": round(alu_frac, 4)}
+    roof.update({"kernel": "pcg_fp64_kernel", "traffic": None,
+                 "algorithmic_bytes_per_launch": int(byts / args.steps),
+                 "pcg_iters_per_step": iters / args.steps,
+                 "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kernel_ms.items()}})
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n_nodes": info["n_nodes"], "n_tris": T, "nnz": info["nnz"],
+                   "rtol": args.rtol, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write inside the timed region)",
+                   "seed": problem.seed},
+        "e2e": {"value": world * T * e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes,
+                "how": "per step: state_set from host, run_steps(1), state_get to host"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(problem, args.cpu_steps)
+    return out
+
+
+def oracle_module():
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import avip_oracle
+    return avip_oracle
+
+
+def cpu_baseline(problem, steps):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    O = oracle_module()
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    o = O.Oracle(problem)
+    setup = time.perf_counter() - t0
+    n = o.initial_state()
+    t1 = time.perf_counter()
+    c1 = time.process_time()
+    for _ in range(steps):
+        n, _ = o.step(n)
+    wall = time.perf_counter() - t1
+    cpu = time.process_time() - c1
+    return {"value": problem.n_tris * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)),
+            "kind": "oracle",
+            "sample": f"{steps} explicit steps of the same workload after a {setup:.1f} s one-off "
+                      f"setup (metrics + sparse LU factorisation, excluded); numpy/scipy, "
+                      f"{os.cpu_count()} host cores visible"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    problem, desc = make_problem(args.workload)
+    O = oracle_module()
+    t0 = time.perf_counter()
+    o = O.Oracle(problem)
+    setup = time.perf_counter() - t0
+    n = o.initial_state()
+    for _ in range(args.warmup):
+        n, _ = o.step(n)
+    c1 = time.process_time()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        n, _ = o.step(n)
+    wall = time.perf_counter() - t1
+    cpu = time.process_time() - c1
+    value = problem.n_tris * args.steps / wall
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "n_tris": problem.n_tris, "precision": "fp64",
+                       "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+                             "sample": f"each step one explicit oracle step of the workload "
+                                       f"(setup {setup:.1f} s excluded)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

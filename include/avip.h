@@ -1,0 +1,179 @@
+/*
+ * avip.h -- C ABI of the GB300 (sm_103a) library for the Poisson-coupled drift-diffusion
+ * step of the AVIP low-temperature plasma method (arXiv 2201.01291).
+ *
+ * One explicit time step on an unstructured triangle mesh:
+ *   1. potential phi from  -lap(phi) = rho/eps0  with Dirichlet / zero-normal-field
+ *      boundaries (section "Integrating the Poisson equation", Eq. poisson, Eq.
+ *      poisson_discretization_cartesian, Eq. coeff_matriceA, "Boundary conditions"),
+ *      solved by Jacobi-preconditioned conjugate gradients on the device;
+ *   2. E = -grad(phi) with Green-Gauss cell gradients through nodal normals;
+ *   3. edge-based limited Lax-Wendroff + central diffusion fluxes of every charged species
+ *      (section "Development of TVD schemes", Eq. vertex_centered_flux) with the node-flux
+ *      boundary closure (section "Boundary conditions in AVIP");
+ *   4. field-dependent ionisation source (section "Bagheri benchmark");
+ *   5. explicit update under the cell-based time step (section "Time step computation").
+ *
+ * Conventions for every entry point:
+ *   - Return value: AVIP_OK (0) or a negative AVIP_E* status; nothing aborts, traps or exits.
+ *   - Host arrays passed in are copied; the library never keeps a caller pointer.
+ *   - Node arrays (in and out) use the caller's node numbering.  The library renumbers nodes
+ *     internally (Morton order) and hides the permutation.
+ *   - All device memory belongs to the handle.  It comes from opts->alloc/opts->free when
+ *     given (e.g. a framework's caching allocator), else from cudaMalloc/cudaFree.
+ *   - All work is queued on the handle's stream (opts->stream, or mesh_set_stream); calls
+ *     that return host data synchronise that stream.  One handle per host thread.
+ *   - SI units throughout (m, V, m^-3, m^2/(V s), m^2/s, s).
+ */
+#ifndef AVIP_H
+#define AVIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define AVIP_OK        0
+#define AVIP_EINVAL   -1  /* bad argument: index out of range, degenerate cell, unknown model */
+#define AVIP_ENOMEM   -2  /* device allocation failed */
+#define AVIP_ENOTCONV -3  /* PCG reached max_iter; phi is left at the last iterate           */
+#define AVIP_ENAN     -4  /* a non-finite density, potential or time step was detected      */
+#define AVIP_ECUDA    -5  /* a CUDA runtime call failed                                      */
+#define AVIP_ETIMEOUT -6  /* a device-side wait gave up (bounded spin); the handle is reset  */
+#define AVIP_ESTATE   -7  /* call out of order (e.g. stepping before every species is set)  */
+
+/* ---- model identifiers ------------------------------------------------------------- */
+#define AVIP_MOB_CONST 0   /* mu = p[0]                                                    */
+#define AVIP_MOB_POWER 1   /* mu = p[0] * (max(|E|, p[3]) / p[1]) ^ p[2]                  */
+#define AVIP_SRC_NONE 0
+#define AVIP_SRC_TOWNSEND 1          /* alpha(|E|) = A exp(-B/|E|); S = alpha mu_e |E| n_e  */
+#define AVIP_SRC_TOWNSEND_ATTACH 2   /* plus attachment nu_a n_e moved from e to the anion  */
+#define AVIP_BND_NEUMANN 0 /* boundary node flux F = F_C ("Neumann")                        */
+#define AVIP_BND_OUTFLOW 1 /* boundary node flux F = F_C + F_D ("supersonic")              */
+#define AVIP_LIM_SWEBY 0   /* Psi(r) = max(0, min(beta r, 1), min(r, beta))                 */
+#define AVIP_LIM_VANLEER 1 /* Psi(r) = (r + |r|)/(1 + |r|)                                  */
+#define AVIP_PREC_FP64 0   /* every stage in FP64                                           */
+#define AVIP_PREC_MIXED 1  /* FP32 inner PCG + FP64 iterative refinement of the residual    */
+#define AVIP_MAX_SPECIES 4
+
+#define AVIP_FIELD_PHI 0
+#define AVIP_FIELD_EX 1
+#define AVIP_FIELD_EY 2
+#define AVIP_FIELD_DENSITY 3  /* species index in `s`                                       */
+#define AVIP_FIELD_VOLUME 4   /* median-dual nodal volume V_i                               */
+
+typedef void* (*avip_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*avip_free_fn)(void* ptr, void* ctx);
+
+/* Run-time choices.  The paper fixes no DD constants; these defaults are project choices:
+ * CFL 0.4 (the stiff advection case), Fourier 0.25, A_D 0.5, A_tau 0.2, min-mod (beta 1). */
+typedef struct avip_opts {
+  double cfl, fourier, a_diel, a_chem; /* time-step constants (section "Time step computation") */
+  double beta;                         /* Sweby limiter parameter, 1 <= beta <= 2             */
+  int32_t limiter;                     /* AVIP_LIM_*                                          */
+  int32_t precision;                   /* AVIP_PREC_*                                         */
+  double rtol;                         /* stop when ||b - K phi||_2 <= rtol ||b||_2           */
+  int32_t max_iter;                    /* PCG iteration cap per solve                         */
+  int32_t reorder;                     /* 1 = Morton renumbering (default), 0 = keep order    */
+  double dt_fixed;                     /* > 0: use this time step instead of the automatic one */
+  double inner_rtol;                   /* mixed precision: FP32 inner reduction per refinement */
+  void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
+  avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
+  avip_free_fn free;
+  void* alloc_ctx;
+} avip_opts;
+
+/* Per-run statistics filled by run_steps / dd_step. */
+typedef struct avip_stats {
+  int32_t steps;             /* steps completed in this call                                */
+  int32_t pcg_iters_total;   /* PCG iterations summed over the call                         */
+  int32_t pcg_iters_max;     /* largest per-step PCG iteration count                        */
+  int32_t status;            /* AVIP_OK or the first error seen                             */
+  double dt_min, dt_max;     /* time steps taken                                            */
+  double t;                  /* simulated time after the call                               */
+  double charge;             /* Q = e sum_s q_s sum_i V_i n_s,i after the call (C/m)        */
+  double charge_start;       /* Q before the call                                           */
+  double relres_max;         /* largest final PCG relative residual                         */
+} avip_stats;
+
+typedef struct avip_mesh* avip_mesh_t;
+
+/* Fill `o` with the defaults above. */
+int avip_opts_default(avip_opts* o);
+
+/* Build a mesh handle.
+ *   xy[2*n_nodes]   node coordinates, interleaved (x0,y0,x1,y1,...);
+ *   tris[3*n_tris]  0-based node indices, either orientation (made counter-clockwise);
+ *   node_bc[n_nodes] 0 = free node (interior or zero-normal-field side), 1 = Dirichlet;
+ *   phi_D[n_nodes]  Dirichlet potential (read where node_bc == 1).
+ * Computes the metrics of the section "Nomenclature and notations" (cell volumes, nodal
+ * normals, median-dual volumes, edge normals, boundary nodal normals) and the Poisson matrix
+ * of Eq. coeff_matriceA, renumbers, and uploads everything.  Errors: AVIP_EINVAL for
+ * out-of-range indices, zero-area cells, a mesh with no Dirichlet node; AVIP_ENOMEM. */
+int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                const int32_t* node_bc, const double* phi_D, const avip_opts* opts,
+                avip_mesh_t* out);
+
+/* Release every device and host resource of the handle.  NULL is accepted. */
+int mesh_destroy(avip_mesh_t h);
+
+/* Queue subsequent work of the handle on `stream` (a cudaStream_t). */
+int mesh_set_stream(avip_mesh_t h, void* stream);
+
+/* Declare species s (0 <= s < AVIP_MAX_SPECIES; species must be declared 0,1,2,... in order)
+ * of the drift-diffusion system (section "Drift-diffusion equations"): charge in units of e
+ * (-1 or +1), mobility model AVIP_MOB_* with 4 parameters, diffusion coefficient D,
+ * boundary closure AVIP_BND_*, and the initial density n0[n_nodes] (host, caller order). */
+int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model,
+                const double* mob_params, double D, int32_t bnd_mode, const double* n0);
+
+/* Source model (section "Bagheri benchmark"): params = {A, B, nu_att}; idx = {electron,
+ * positive ion, negative ion (-1 if none)} species indices. */
+int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t* idx);
+
+/* Solve the Poisson problem for the current densities (warm start from the last phi).
+ * iters_out / relres_out (may be NULL) receive the PCG iteration count and the final true
+ * relative residual.  AVIP_ENOTCONV if max_iter was reached. */
+int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out);
+
+/* One explicit step: Poisson, E, gradients, time step (dt <= 0: automatic, else dt), fluxes,
+ * source, update.  dt_used may be NULL. */
+int dd_step(avip_mesh_t h, double dt, double* dt_used);
+
+/* nsteps explicit steps queued without host synchronisation (replayed as a CUDA graph);
+ * synchronises once at the end and fills `stats` (may be NULL). */
+int run_steps(avip_mesh_t h, int32_t nsteps, avip_stats* stats);
+
+/* Measurement variant of run_steps: the same kernels launched one by one (no graph) with CUDA
+ * events recorded on the handle's stream around each of them.  kernel_ms[AVIP_TIMED_KERNELS]
+ * receives the summed device time of {PCG solve, nodal fields, cell time step, fluxes +
+ * update, finalize} over the call; `stats` (may be NULL) as for run_steps. */
+#define AVIP_TIMED_KERNELS 5
+int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats* stats);
+
+/* Copy a nodal field to host memory, caller numbering: AVIP_FIELD_* (s = species index for
+ * densities).  out[n_nodes] doubles. */
+int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out);
+
+/* Checkpoint / resume.  state layout: [n_species * n_nodes densities][n_nodes phi][t],
+ * caller numbering; size = (n_species + 1) * n_nodes + 1 doubles. */
+int state_size(avip_mesh_t h, int64_t* n_doubles);
+int state_get(avip_mesh_t h, double* host_state);
+int state_set(avip_mesh_t h, const double* host_state);
+
+/* Sizes of the handle: n_nodes, n_tris, n_edges, nnz of the Poisson matrix. */
+int mesh_info(avip_mesh_t h, int64_t* info4);
+
+/* Human-readable text of a status code (static storage). */
+const char* avip_status_str(int status);
+
+/* Detail of the last AVIP_EINVAL / AVIP_ECUDA raised on this host thread (static storage). */
+const char* avip_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AVIP_H */

@@ -33,7 +33,8 @@ Readings where the paper is silent or garbled (each also listed in the design no
   * u_W == u_U gives Psi = 0;
   * nodal velocity V_s = sign(q_s) mu_s(|E|) E, edge velocity = mean of nodal velocities;
   * Delta x_tau = shortest edge of the cell; cell values = mean of the three nodal values;
-  * chemical time step A_tau * min over nodes of n_e/|S_e| (the printed form is not a time);
+  * chemical time step A_tau * min over nodes of |n_e|/|S_e| (the printed form is not a
+    time; the magnitudes keep it a positive time scale when a density undershoots below 0);
   * Dirichlet rows eliminated symmetrically (same solution as the unit-row form).
 """
 from __future__ import annotations
@@ -341,7 +342,7 @@ class Oracle:
             ok = Se != 0
             if np.any(ok):
                 with np.errstate(over="ignore", divide="ignore"):
-                    dts.append(np.min(o.a_chem * n[e][ok] / np.abs(Se[ok])))
+                    dts.append(np.min(o.a_chem * np.abs(n[e][ok]) / np.abs(Se[ok])))
         return float(min(dts))
 
     def edge_flux(self, u, grad, vel, D, dt):

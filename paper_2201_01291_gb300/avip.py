@@ -1,0 +1,319 @@
+"""Thin Python binding of the C ABI in include/avip.h (argument marshalling only).
+
+Every function of the header is exposed under the same name; `Mesh` is a convenience wrapper
+that creates a handle from a synthetic workload description and owns it.  All computation
+runs in the CUDA library; if the library is missing or cannot be loaded the import fails
+loudly (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libavip.so")
+
+AVIP_OK, AVIP_EINVAL, AVIP_ENOMEM, AVIP_ENOTCONV, AVIP_ENAN, AVIP_ECUDA, AVIP_ETIMEOUT, AVIP_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+FIELD_PHI, FIELD_EX, FIELD_EY, FIELD_DENSITY, FIELD_VOLUME = 0, 1, 2, 3, 4
+PREC_FP64, PREC_MIXED = 0, 1
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class AvipOpts(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("fourier", C.c_double), ("a_diel", C.c_double), ("a_chem", C.c_double),
+                ("beta", C.c_double), ("limiter", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double),
+                ("max_iter", C.c_int32), ("reorder", C.c_int32), ("dt_fixed", C.c_double),
+                ("inner_rtol", C.c_double), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class AvipStats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("pcg_iters_total", C.c_int32), ("pcg_iters_max", C.c_int32),
+                ("status", C.c_int32), ("dt_min", C.c_double), ("dt_max", C.c_double), ("t", C.c_double),
+                ("charge", C.c_double), ("charge_start", C.c_double), ("relres_max", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AvipError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} ({code}) {last_error()}")
+
+
+_P = C.POINTER
+_D = _P(C.c_double)
+_I = _P(C.c_int32)
+_H = C.c_void_p
+
+_SIGS = {
+    "avip_opts_default": (C.c_int, [_P(AvipOpts)]),
+    "mesh_create": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, _D, _P(AvipOpts), _P(_H)]),
+    "mesh_destroy": (C.c_int, [_H]),
+    "mesh_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "mesh_info": (C.c_int, [_H, _P(C.c_int64)]),
+    "species_set": (C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, _D, C.c_double, C.c_int32, _D]),
+    "source_set": (C.c_int, [_H, C.c_int32, _D, _I]),
+    "poisson_solve": (C.c_int, [_H, _I, _D]),
+    "dd_step": (C.c_int, [_H, C.c_double, _D]),
+    "run_steps": (C.c_int, [_H, C.c_int32, _P(AvipStats)]),
+    "run_steps_timed": (C.c_int, [_H, C.c_int32, _D, _P(AvipStats)]),
+    "field_get": (C.c_int, [_H, C.c_int32, C.c_int32, _D]),
+    "state_size": (C.c_int, [_H, _P(C.c_int64)]),
+    "state_get": (C.c_int, [_H, _D]),
+    "state_set": (C.c_int, [_H, _D]),
+    "avip_status_str": (C.c_char_p, [C.c_int]),
+    "avip_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (build it first with paper_2201_01291_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2201_01291_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_str(code: int) -> str:
+    return load().avip_status_str(code).decode()
+
+
+def last_error() -> str:
+    return load().avip_last_error().decode()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(_I)
+
+
+def _check(rc, where, ok=(AVIP_OK,)):
+    if rc not in ok:
+        raise AvipError(rc, where)
+    return rc
+
+
+# ------------------------------------------------------------------ same names as the C ABI
+def avip_opts_default() -> AvipOpts:
+    o = AvipOpts()
+    _check(load().avip_opts_default(C.byref(o)), "avip_opts_default")
+    return o
+
+
+def mesh_create(xy, tris, node_bc, phi_D, opts: AvipOpts):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    tris = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1)
+    node_bc = np.ascontiguousarray(node_bc, dtype=np.int32)
+    phi_D = np.ascontiguousarray(phi_D, dtype=np.float64)
+    h = _H()
+    rc = load().mesh_create(_dptr(xy), xy.size // 2, _iptr(tris), tris.size // 3, _iptr(node_bc), _dptr(phi_D),
+                            C.byref(opts), C.byref(h))
+    return rc, h
+
+
+def mesh_destroy(h):
+    return load().mesh_destroy(h)
+
+
+def species_set(h, s, charge, mob_model, mob_params, D, bnd_mode, n0):
+    mp = np.zeros(4)
+    mp[:len(mob_params)] = mob_params
+    n0 = np.ascontiguousarray(n0, dtype=np.float64)
+    return load().species_set(h, s, charge, mob_model, _dptr(mp), float(D), bnd_mode, _dptr(n0))
+
+
+def source_set(h, model, params, idx):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    i = np.ascontiguousarray(idx, dtype=np.int32)
+    return load().source_set(h, model, _dptr(p), _iptr(i))
+
+
+def poisson_solve(h):
+    it = C.c_int32()
+    rr = C.c_double()
+    rc = load().poisson_solve(h, C.byref(it), C.byref(rr))
+    return rc, it.value, rr.value
+
+
+def dd_step(h, dt=0.0):
+    used = C.c_double()
+    rc = load().dd_step(h, float(dt), C.byref(used))
+    return rc, used.value
+
+
+def run_steps(h, nsteps):
+    st = AvipStats()
+    rc = load().run_steps(h, int(nsteps), C.byref(st))
+    return rc, st.as_dict()
+
+
+TIMED_KERNELS = ("pcg", "node_fields", "dt_cells", "flux_update", "finalize")
+
+
+def run_steps_timed(h, nsteps):
+    ms = np.zeros(len(TIMED_KERNELS))
+    st = AvipStats()
+    rc = load().run_steps_timed(h, int(nsteps), _dptr(ms), C.byref(st))
+    return rc, dict(zip(TIMED_KERNELS, ms.tolist())), st.as_dict()
+
+
+def mesh_set_stream(h, stream):
+    return load().mesh_set_stream(h, C.c_void_p(stream))
+
+
+def field_get(h, which, s, n_nodes):
+    out = np.empty(n_nodes)
+    rc = load().field_get(h, which, s, _dptr(out))
+    return rc, out
+
+
+def mesh_info(h):
+    info = np.zeros(4, dtype=np.int64)
+    _check(load().mesh_info(h, info.ctypes.data_as(_P(C.c_int64))), "mesh_info")
+    return dict(n_nodes=int(info[0]), n_tris=int(info[1]), n_edges=int(info[2]), nnz=int(info[3]))
+
+
+def state_get(h):
+    n = C.c_int64()
+    _check(load().state_size(h, C.byref(n)), "state_size")
+    out = np.empty(n.value)
+    return load().state_get(h, _dptr(out)), out
+
+
+def state_set(h, state):
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    return load().state_set(h, _dptr(s))
+
+
+# ------------------------------------------------------------------ convenience wrapper
+def torch_allocator():
+    """(alloc, free) callbacks drawing device memory from PyTorch's caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    @ALLOC_FN
+    def _alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev))
+        except Exception:
+            return None
+
+    @FREE_FN
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _alloc, _free
+
+
+class Mesh:
+    """Owns one handle built from a synthetic workload (see workloads.Problem)."""
+
+    def __init__(self, problem, precision=PREC_FP64, rtol=None, max_iter=None, dt_fixed=None,
+                 reorder=1, use_torch_allocator=False, stream=None):
+        o = avip_opts_default()
+        po = problem.opts
+        o.cfl, o.fourier, o.a_diel, o.a_chem = po.cfl, po.fourier, po.a_diel, po.a_chem
+        o.beta, o.limiter = po.beta, po.limiter
+        o.rtol = po.rtol if rtol is None else rtol
+        o.max_iter = po.max_iter if max_iter is None else max_iter
+        o.dt_fixed = po.dt_fixed if dt_fixed is None else dt_fixed
+        o.precision = precision
+        o.reorder = reorder
+        self._cb = None
+        if use_torch_allocator:
+            self._cb = torch_allocator()
+            o.alloc, o.free = self._cb
+        if stream is not None:
+            o.stream = C.c_void_p(stream)
+        self.problem = problem
+        self.N = problem.n_nodes
+        rc, h = mesh_create(problem.xy, problem.tris, problem.node_bc, problem.phi_D, o)
+        _check(rc, "mesh_create")
+        self.h = h
+        for s, sp in enumerate(problem.species):
+            _check(species_set(h, s, sp.charge, sp.mob_model, sp.mob_params, sp.D, sp.bnd_mode, sp.n0),
+                   "species_set")
+        src = problem.source
+        if src.model != 0:
+            _check(source_set(h, src.model, src.params, src.idx), "source_set")
+        self.info = mesh_info(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def poisson_solve(self, allow=(AVIP_OK,)):
+        rc, it, rr = poisson_solve(self.h)
+        _check(rc, "poisson_solve", allow)
+        return it, rr
+
+    def step(self, dt=0.0):
+        rc, used = dd_step(self.h, dt)
+        _check(rc, "dd_step")
+        return used
+
+    def run(self, nsteps, allow=(AVIP_OK,)):
+        rc, st = run_steps(self.h, nsteps)
+        _check(rc, "run_steps", allow)
+        return st
+
+    def run_timed(self, nsteps, allow=(AVIP_OK,)):
+        rc, ms, st = run_steps_timed(self.h, nsteps)
+        _check(rc, "run_steps_timed", allow)
+        return ms, st
+
+    def set_stream(self, stream):
+        _check(mesh_set_stream(self.h, stream), "mesh_set_stream")
+
+    def field(self, which, s=0):
+        rc, out = field_get(self.h, which, s, self.N)
+        _check(rc, "field_get")
+        return out
+
+    def density(self, s):
+        return self.field(FIELD_DENSITY, s)
+
+    def phi(self):
+        return self.field(FIELD_PHI)
+
+    def state(self):
+        rc, st = state_get(self.h)
+        _check(rc, "state_get")
+        return st
+
+    def set_state(self, st):
+        _check(state_set(self.h, st), "state_set")

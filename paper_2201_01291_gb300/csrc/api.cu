@@ -1,0 +1,635 @@
+// C ABI entry points (include/avip.h): handle life cycle, device memory, launch sequencing
+// of one explicit step, CUDA-graph replay of the time loop, host <-> device field copies.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "avip_internal.h"
+
+namespace avip {
+cudaError_t launch_pcg_fp64(const PcgArgs& args, int blocks, cudaStream_t st);
+int pcg_fp64_max_blocks();
+cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
+cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
+cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
+cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st);
+cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st);
+int flux_blocks(int N);
+}  // namespace avip
+
+using namespace avip;
+
+struct avip_mesh {
+  avip_opts opts;
+  HostMesh hm;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  // device arrays
+  int32_t *sl_ptr = nullptr, *sl_w = nullptr, *rlen = nullptr, *col = nullptr, *tri = nullptr;
+  double *aval = nullptr, *gx = nullptr, *gy = nullptr, *sx = nullptr, *sy = nullptr;
+  double *x = nullptr, *y = nullptr, *vol = nullptr, *dinv = nullptr, *lift = nullptr, *rhs_scale = nullptr;
+  double* dxmin = nullptr;
+  double *phi = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
+  double* partials = nullptr;   // PCG grid-reduction partials
+  double* qpart = nullptr;      // per-block charge partials of the flux kernel
+  GridSync* sync = nullptr;
+  DevScalars* sc = nullptr;
+  int32_t Npad = 0;
+  int pcg_blocks = 0;
+  int nparts = 0;
+  Physics ph;
+  int species_declared = 0;
+  // graph of one step
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+};
+
+namespace {
+
+thread_local char g_err[256];
+
+void* dev_alloc(avip_mesh* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->opts.alloc) {
+    p = h->opts.alloc(bytes, h->opts.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->allocs.push_back(p);
+  return p;
+}
+
+void dev_free_all(avip_mesh* h) {
+  for (void* p : h->allocs) {
+    if (h->opts.free)
+      h->opts.free(p, h->opts.alloc_ctx);
+    else
+      cudaFree(p);
+  }
+  h->allocs.clear();
+}
+
+template <typename T>
+bool upload(avip_mesh* h, T*& dst, const std::vector<T>& src, size_t min_count = 0) {
+  size_t n = std::max(src.size(), min_count);
+  dst = static_cast<T*>(dev_alloc(h, n * sizeof(T)));
+  if (!dst) return false;
+  if (cudaMemsetAsync(dst, 0, n * sizeof(T), h->stream) != cudaSuccess) return false;
+  if (!src.empty() && cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                      h->stream) != cudaSuccess)
+    return false;
+  return true;
+}
+
+template <typename T>
+bool zalloc(avip_mesh* h, T*& dst, size_t count) {
+  dst = static_cast<T*>(dev_alloc(h, count * sizeof(T)));
+  if (!dst) return false;
+  return cudaMemsetAsync(dst, 0, count * sizeof(T), h->stream) == cudaSuccess;
+}
+
+SellView sell_view(const avip_mesh* h) {
+  SellView v;
+  v.sl_ptr = h->sl_ptr;
+  v.sl_w = h->sl_w;
+  v.rlen = h->rlen;
+  v.col = h->col;
+  v.aval = h->aval;
+  v.gx = h->gx;
+  v.gy = h->gy;
+  v.sx = h->sx;
+  v.sy = h->sy;
+  v.N = h->hm.N;
+  v.nslices = h->hm.nslices;
+  return v;
+}
+
+PcgArgs pcg_args(const avip_mesh* h) {
+  PcgArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = sell_view(h);
+  a.dinv = h->dinv;
+  a.rhs_scale = h->rhs_scale;
+  a.lift = h->lift;
+  a.nbuf = h->nbuf;
+  a.Npad = h->Npad;
+  a.ns = h->ph.ns;
+  for (int s = 0; s < AVIP_MAX_SPECIES; ++s) a.q[s] = h->ph.sp[s].q;
+  a.x = h->phi;
+  a.b = h->b;
+  a.r = h->r;
+  a.z = h->z;
+  a.p = h->p;
+  a.q_ap = h->q;
+  a.partials = h->partials;
+  a.sync = h->sync;
+  a.sc = h->sc;
+  a.rtol = h->opts.rtol;
+  a.max_iter = h->opts.max_iter;
+  a.use_density_rhs = 1;
+  return a;
+}
+
+DDArgs dd_args(const avip_mesh* h) {
+  DDArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = sell_view(h);
+  a.ph = h->ph;
+  a.x = h->x;
+  a.y = h->y;
+  a.vol = h->vol;
+  a.phi = h->phi;
+  a.nbuf = h->nbuf;
+  a.ndat = h->ndat;
+  a.nm = h->nm;
+  a.src = h->src;
+  a.Ex = h->Ex;
+  a.Ey = h->Ey;
+  a.tri = h->tri;
+  a.dxmin = h->dxmin;
+  a.T = h->hm.T;
+  a.Npad = h->Npad;
+  a.partials = h->qpart;
+  a.sc = h->sc;
+  return a;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return AVIP_OK;
+  std::snprintf(g_err, sizeof(g_err), "CUDA: %s", cudaGetErrorString(e));
+  cudaGetLastError();
+  return AVIP_ECUDA;
+}
+
+// Queue one Poisson solve (cooperative PCG launch).
+cudaError_t enqueue_poisson(avip_mesh* h) {
+  cudaError_t e = cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+  if (e != cudaSuccess) return e;
+  return launch_pcg_fp64(pcg_args(h), h->pcg_blocks, h->stream);
+}
+
+// Queue one explicit step (no host synchronisation).
+cudaError_t enqueue_step(avip_mesh* h) {
+  cudaError_t e = enqueue_poisson(h);
+  if (e != cudaSuccess) return e;
+  DDArgs a = dd_args(h);
+  const bool auto_dt = !(h->ph.dt_fixed > 0.0);
+  if ((e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream)) != cudaSuccess) return e;
+  if (auto_dt && (e = launch_dt_cells(a, h->stream)) != cudaSuccess) return e;
+  if ((e = launch_flux_update(a, h->stream)) != cudaSuccess) return e;
+  return launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
+}
+
+int read_scalars(avip_mesh* h, DevScalars& out) {
+  cudaError_t e = cudaMemcpyAsync(&out, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+bool ready(const avip_mesh* h) { return h && h->ph.ns > 0 && h->species_declared == h->ph.ns; }
+
+void invalidate_graph(avip_mesh* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_valid = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int avip_opts_default(avip_opts* o) {
+  if (!o) return AVIP_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->cfl = 0.4;
+  o->fourier = 0.25;
+  o->a_diel = 0.5;
+  o->a_chem = 0.2;
+  o->beta = 1.0;
+  o->limiter = AVIP_LIM_SWEBY;
+  o->precision = AVIP_PREC_FP64;
+  o->rtol = 1e-12;
+  o->max_iter = 20000;
+  o->reorder = 1;
+  o->dt_fixed = 0.0;
+  o->inner_rtol = 1e-4;
+  return AVIP_OK;
+}
+
+const char* avip_status_str(int s) {
+  switch (s) {
+    case AVIP_OK: return "ok";
+    case AVIP_EINVAL: return "invalid argument";
+    case AVIP_ENOMEM: return "device allocation failed";
+    case AVIP_ENOTCONV: return "PCG did not converge within max_iter";
+    case AVIP_ENAN: return "non-finite value detected";
+    case AVIP_ECUDA: return "CUDA runtime error";
+    case AVIP_ETIMEOUT: return "device wait timed out";
+    case AVIP_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* avip_last_error(void) { return g_err; }
+
+int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                const int32_t* node_bc, const double* phi_D, const avip_opts* opts, avip_mesh_t* out) {
+  if (!out) return AVIP_EINVAL;
+  *out = nullptr;
+  avip_mesh* h = new (std::nothrow) avip_mesh();
+  if (!h) return AVIP_ENOMEM;
+  if (opts)
+    h->opts = *opts;
+  else
+    avip_opts_default(&h->opts);
+  if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
+      h->opts.precision != AVIP_PREC_FP64) {
+    delete h;
+    return AVIP_EINVAL;
+  }
+  // host-side validation and metrics first: bad meshes are rejected without touching the GPU
+  int st = prepare_mesh(xy, n_nodes, tris, n_tris, node_bc, phi_D, h->opts.reorder, h->hm, g_err, sizeof(g_err));
+  if (st != AVIP_OK) {
+    delete h;
+    return st;
+  }
+  h->stream = static_cast<cudaStream_t>(h->opts.stream);
+  if (!h->stream) {
+    // a private stream keeps the step graph-capturable
+    cudaError_t ce = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+      int rc = cuda_status(ce);
+      delete h;
+      return rc;
+    }
+    h->own_stream = true;
+  }
+  HostMesh& m = h->hm;
+  h->Npad = m.nslices * kSlice;
+  const size_t Np = (size_t)h->Npad;
+  bool ok = upload(h, h->sl_ptr, m.sl_ptr) && upload(h, h->sl_w, m.sl_w) && upload(h, h->rlen, m.rlen) &&
+            upload(h, h->col, m.col) && upload(h, h->aval, m.aval) && upload(h, h->gx, m.gx) &&
+            upload(h, h->gy, m.gy) && upload(h, h->sx, m.sx) && upload(h, h->sy, m.sy) &&
+            upload(h, h->tri, m.tri) && upload(h, h->dxmin, m.dxmin) && upload(h, h->x, m.x, Np) &&
+            upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dinv, m.dinv, Np) &&
+            upload(h, h->lift, m.lift, Np) && upload(h, h->rhs_scale, m.rhs_scale, Np);
+  // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere
+  std::vector<double> phi0(Np, 0.0);
+  for (int32_t i = 0; i < m.N; ++i)
+    if (m.bc[i] == 1) phi0[i] = m.lift[i];
+  ok = ok && upload(h, h->phi, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->z, Np) &&
+       zalloc(h, h->p, Np) && zalloc(h, h->q, Np) && zalloc(h, h->nbuf, 2 * AVIP_MAX_SPECIES * Np) &&
+       zalloc(h, h->ndat, 4 * AVIP_MAX_SPECIES * Np) && zalloc(h, h->nm, AVIP_MAX_SPECIES * Np) &&
+       zalloc(h, h->src, AVIP_MAX_SPECIES * Np) && zalloc(h, h->Ex, Np) && zalloc(h, h->Ey, Np);
+  if (!ok) {
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return AVIP_ENOMEM;
+  }
+  // persistent PCG grid: co-resident blocks, but no more than there are slices to share
+  const int maxb = pcg_fp64_max_blocks();
+  const int want = (m.nslices + 7) / 8;  // one slice per warp of a 256-thread block
+  h->pcg_blocks = std::max(1, std::min(maxb, want));
+  h->nparts = flux_blocks(m.N);
+  ok = zalloc(h, h->partials, (size_t)h->pcg_blocks * 4) && zalloc(h, h->qpart, (size_t)h->nparts) && zalloc(h, h->sync, 1) && zalloc(h, h->sc, 1);
+  if (!ok) {
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return AVIP_ENOMEM;
+  }
+  DevScalars s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.dt_bits = 0x7ff0000000000000ULL;  // +inf
+  s0.run_dt_min = INFINITY;
+  cudaError_t e = cudaMemcpyAsync(h->sc, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    int rc = cuda_status(e);
+    dev_free_all(h);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return rc;
+  }
+  std::memset(&h->ph, 0, sizeof(h->ph));
+  h->ph.beta = h->opts.beta;
+  h->ph.limiter = h->opts.limiter;
+  h->ph.cfl = h->opts.cfl;
+  h->ph.fourier = h->opts.fourier;
+  h->ph.a_diel = h->opts.a_diel;
+  h->ph.a_chem = h->opts.a_chem;
+  h->ph.dt_fixed = h->opts.dt_fixed;
+  h->ph.src_idx[0] = 0;
+  h->ph.src_idx[1] = 1;
+  h->ph.src_idx[2] = -1;
+  *out = h;
+  return AVIP_OK;
+}
+
+int mesh_destroy(avip_mesh_t h) {
+  if (!h) return AVIP_OK;
+  cudaStreamSynchronize(h->stream);
+  invalidate_graph(h);
+  dev_free_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return AVIP_OK;
+}
+
+int mesh_set_stream(avip_mesh_t h, void* stream) {
+  if (!h) return AVIP_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  if (!stream) return AVIP_OK;  // keep the current (private or given) stream
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  h->stream = static_cast<cudaStream_t>(stream);
+  invalidate_graph(h);
+  return AVIP_OK;
+}
+
+int mesh_info(avip_mesh_t h, int64_t* info) {
+  if (!h || !info) return AVIP_EINVAL;
+  info[0] = h->hm.N;
+  info[1] = h->hm.T;
+  info[2] = h->hm.E;
+  info[3] = h->hm.nnz;
+  return AVIP_OK;
+}
+
+int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model, const double* mob_params, double D,
+                int32_t bnd_mode, const double* n0) {
+  if (!h || s < 0 || s >= AVIP_MAX_SPECIES || !mob_params || !n0) return AVIP_EINVAL;
+  if (s > h->species_declared) return AVIP_ESTATE;
+  if ((charge != -1 && charge != 1) || (mob_model != AVIP_MOB_CONST && mob_model != AVIP_MOB_POWER) ||
+      (bnd_mode != AVIP_BND_NEUMANN && bnd_mode != AVIP_BND_OUTFLOW) || !(D >= 0) || !std::isfinite(D))
+    return AVIP_EINVAL;
+  if (mob_model == AVIP_MOB_POWER && !(mob_params[1] > 0 && mob_params[3] > 0)) return AVIP_EINVAL;
+  const HostMesh& m = h->hm;
+  std::vector<double> nn(m.N);
+  for (int32_t i = 0; i < m.N; ++i) {
+    nn[i] = n0[m.perm[i]];
+    if (!std::isfinite(nn[i])) return AVIP_ENAN;
+  }
+  SpeciesParams& sp = h->ph.sp[s];
+  sp.q = (double)charge;
+  for (int k = 0; k < 4; ++k) sp.mob[k] = mob_params[k];
+  sp.D = D;
+  sp.mob_model = mob_model;
+  sp.bnd_mode = bnd_mode;
+  if (s == h->species_declared) h->species_declared++;
+  h->ph.ns = h->species_declared;
+  // density into the current parity buffer
+  DevScalars sc;
+  int rc = read_scalars(h, sc);
+  if (rc) return rc;
+  double* dst = h->nbuf + ((size_t)sc.parity * AVIP_MAX_SPECIES + s) * h->Npad;
+  cudaError_t e = cudaMemcpyAsync(dst, nn.data(), nn.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  invalidate_graph(h);
+  return cuda_status(e);
+}
+
+int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t* idx) {
+  if (!h) return AVIP_EINVAL;
+  if (model == AVIP_SRC_NONE) {
+    h->ph.src_model = 0;
+    invalidate_graph(h);
+    return AVIP_OK;
+  }
+  if (!params || !idx || (model != AVIP_SRC_TOWNSEND && model != AVIP_SRC_TOWNSEND_ATTACH)) return AVIP_EINVAL;
+  if (idx[0] < 0 || idx[0] >= AVIP_MAX_SPECIES || idx[1] < 0 || idx[1] >= AVIP_MAX_SPECIES) return AVIP_EINVAL;
+  if (model == AVIP_SRC_TOWNSEND_ATTACH && (idx[2] < 0 || idx[2] >= AVIP_MAX_SPECIES)) return AVIP_EINVAL;
+  if (!(params[0] >= 0) || !(params[1] >= 0) || !(params[2] >= 0)) return AVIP_EINVAL;
+  h->ph.src_model = model;
+  for (int k = 0; k < 3; ++k) {
+    h->ph.src_params[k] = params[k];
+    h->ph.src_idx[k] = idx[k];
+  }
+  invalidate_graph(h);
+  return AVIP_OK;
+}
+
+int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out) {
+  if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
+  cudaError_t e = enqueue_poisson(h);
+  if (e == cudaSuccess) e = launch_node_fields(dd_args(h), 0, h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  DevScalars sc;
+  int rc = read_scalars(h, sc);
+  if (rc) return rc;
+  if (iters_out) *iters_out = sc.pcg_iters;
+  if (relres_out) *relres_out = sc.pcg_relres;
+  return sc.pcg_status;
+}
+
+static int run_impl(avip_mesh_t h, int32_t nsteps, double dt, avip_stats* stats, bool use_graph) {
+  if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
+  if (nsteps < 0) return AVIP_EINVAL;
+  DevScalars s0;
+  int rc = read_scalars(h, s0);
+  if (rc) return rc;
+  const double saved_dt = h->ph.dt_fixed;
+  if (dt > 0.0) {
+    if (h->ph.dt_fixed != dt) invalidate_graph(h);
+    h->ph.dt_fixed = dt;
+  }
+  cudaError_t e = launch_run_reset(h->sc, h->stream);
+  if (use_graph && nsteps > 1 && e == cudaSuccess) {
+    if (!h->graph_valid) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_step(h);
+        e = cudaStreamEndCapture(h->stream, &g);
+        if (e2 != cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) {
+        h->graph_valid = true;
+      } else {
+        cudaGetLastError();
+        h->graph = nullptr;
+        use_graph = false;  // capture unsupported here: launch the same kernels directly
+        e = cudaSuccess;
+      }
+    }
+    for (int32_t k = 0; k < nsteps && e == cudaSuccess && use_graph; ++k) e = cudaGraphLaunch(h->graph, h->stream);
+    if (!use_graph)
+      for (int32_t k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(h);
+  } else {
+    for (int32_t k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(h);
+  }
+  h->ph.dt_fixed = saved_dt;
+  if (dt > 0.0 && saved_dt != dt) invalidate_graph(h);
+  if (e != cudaSuccess) return cuda_status(e);
+  DevScalars sc;
+  rc = read_scalars(h, sc);
+  if (rc) return rc;
+  if (stats) {
+    stats->steps = sc.run_steps;
+    stats->pcg_iters_total = sc.run_iters_total;
+    stats->pcg_iters_max = sc.run_iters_max;
+    stats->status = sc.status;
+    stats->dt_min = sc.run_dt_min;
+    stats->dt_max = sc.run_dt_max;
+    stats->t = sc.t;
+    stats->charge = sc.charge;
+    stats->charge_start = s0.charge;
+    stats->relres_max = sc.run_relres_max;
+  }
+  if (sc.status == AVIP_ETIMEOUT) {
+    // leave the handle usable: clear the barrier state
+    cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+    cudaStreamSynchronize(h->stream);
+  }
+  return sc.status;
+}
+
+int dd_step(avip_mesh_t h, double dt, double* dt_used) {
+  avip_stats st;
+  int rc = run_impl(h, 1, dt, &st, false);
+  if (dt_used) *dt_used = st.dt_max;
+  return rc;
+}
+
+int run_steps(avip_mesh_t h, int32_t nsteps, avip_stats* stats) { return run_impl(h, nsteps, 0.0, stats, true); }
+
+// Eager launches with CUDA events around every kernel on the handle's stream.
+int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats* stats) {
+  if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
+  if (nsteps < 0 || !kernel_ms) return AVIP_EINVAL;
+  for (int k = 0; k < AVIP_TIMED_KERNELS; ++k) kernel_ms[k] = 0.0;
+  DevScalars s0;
+  int rc = read_scalars(h, s0);
+  if (rc) return rc;
+  cudaEvent_t ev[AVIP_TIMED_KERNELS + 1];
+  for (auto& e : ev) cudaEventCreate(&e);
+  cudaError_t e = launch_run_reset(h->sc, h->stream);
+  const bool auto_dt = !(h->ph.dt_fixed > 0.0);
+  for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    DDArgs a = dd_args(h);
+    e = cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) e = launch_pcg_fp64(pcg_args(h), h->pcg_blocks, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess) e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess && auto_dt) e = launch_dt_cells(a, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+    if (e == cudaSuccess) e = launch_flux_update(a, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+    if (e == cudaSuccess) e = launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
+    for (int k = 0; k < AVIP_TIMED_KERNELS && e == cudaSuccess; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      kernel_ms[k] += ms;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return cuda_status(e);
+  DevScalars sc;
+  rc = read_scalars(h, sc);
+  if (rc) return rc;
+  if (stats) {
+    stats->steps = sc.run_steps;
+    stats->pcg_iters_total = sc.run_iters_total;
+    stats->pcg_iters_max = sc.run_iters_max;
+    stats->status = sc.status;
+    stats->dt_min = sc.run_dt_min;
+    stats->dt_max = sc.run_dt_max;
+    stats->t = sc.t;
+    stats->charge = sc.charge;
+    stats->charge_start = s0.charge;
+    stats->relres_max = sc.run_relres_max;
+  }
+  return sc.status;
+}
+
+static int to_host_perm(avip_mesh_t h, const double* dev, double* host_out) {
+  std::vector<double> tmp(h->hm.N);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), dev, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int32_t i = 0; i < h->hm.N; ++i) host_out[h->hm.perm[i]] = tmp[i];
+  return AVIP_OK;
+}
+
+int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out) {
+  if (!h || !host_out) return AVIP_EINVAL;
+  switch (which) {
+    case AVIP_FIELD_PHI: return to_host_perm(h, h->phi, host_out);
+    case AVIP_FIELD_EX: return to_host_perm(h, h->Ex, host_out);
+    case AVIP_FIELD_EY: return to_host_perm(h, h->Ey, host_out);
+    case AVIP_FIELD_VOLUME: return to_host_perm(h, h->vol, host_out);
+    case AVIP_FIELD_DENSITY: {
+      if (s < 0 || s >= h->ph.ns) return AVIP_EINVAL;
+      DevScalars sc;
+      int rc = read_scalars(h, sc);
+      if (rc) return rc;
+      return to_host_perm(h, h->nbuf + ((size_t)sc.parity * AVIP_MAX_SPECIES + s) * h->Npad, host_out);
+    }
+    default: return AVIP_EINVAL;
+  }
+}
+
+int state_size(avip_mesh_t h, int64_t* n) {
+  if (!h || !n) return AVIP_EINVAL;
+  *n = (int64_t)(h->ph.ns + 1) * h->hm.N + 1;
+  return AVIP_OK;
+}
+
+int state_get(avip_mesh_t h, double* out) {
+  if (!ready(h) || !out) return AVIP_EINVAL;
+  const int32_t N = h->hm.N;
+  for (int s = 0; s < h->ph.ns; ++s) {
+    int rc = field_get(h, AVIP_FIELD_DENSITY, s, out + (size_t)s * N);
+    if (rc) return rc;
+  }
+  int rc = field_get(h, AVIP_FIELD_PHI, 0, out + (size_t)h->ph.ns * N);
+  if (rc) return rc;
+  DevScalars sc;
+  rc = read_scalars(h, sc);
+  if (rc) return rc;
+  out[(size_t)(h->ph.ns + 1) * N] = sc.t;
+  return AVIP_OK;
+}
+
+int state_set(avip_mesh_t h, const double* in) {
+  if (!ready(h) || !in) return AVIP_EINVAL;
+  const int32_t N = h->hm.N;
+  DevScalars sc;
+  int rc = read_scalars(h, sc);
+  if (rc) return rc;
+  std::vector<double> tmp(N);
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s <= h->ph.ns && e == cudaSuccess; ++s) {
+    const double* src = in + (size_t)s * N;
+    for (int32_t i = 0; i < N; ++i) {
+      tmp[i] = src[h->hm.perm[i]];
+      if (!std::isfinite(tmp[i])) return AVIP_ENAN;
+    }
+    double* dst = s < h->ph.ns ? h->nbuf + ((size_t)sc.parity * AVIP_MAX_SPECIES + s) * h->Npad : h->phi;
+    e = cudaMemcpyAsync(dst, tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  const double t = in[(size_t)(h->ph.ns + 1) * N];
+  e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+}  // extern "C"

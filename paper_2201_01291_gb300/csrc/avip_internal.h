@@ -1,0 +1,157 @@
+// Internal layout shared by the host mesh preparation, the kernels and the C ABI.
+//
+// Device data layout (nodes renumbered in Morton order, SELL-32 sparse storage):
+//   * rows are grouped in slices of 32 consecutive nodes; slice s owns the element range
+//     [sl_ptr[s], sl_ptr[s] + 32 * sl_w[s]) with element (lane, k) at sl_ptr[s] + 32 k + lane,
+//     so a warp reading slot k of its 32 rows issues one fully coalesced load;
+//   * slot 0 of every row is the diagonal (column = row); slots 1..rlen-1 are the neighbours
+//     in ascending column order; slots >= rlen are padding and never read;
+//   * per element: col (int32), aval (Poisson matrix after Dirichlet elimination), gx/gy
+//     (nodal-gradient weights G_ik), sx/sy (edge normal S_ij oriented row -> col; in slot 0
+//     the boundary nodal normal S_i^b).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/avip.h"
+
+namespace avip {
+
+constexpr double kECharge = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr int kSlice = 32;
+
+struct HostMesh {
+  int32_t N = 0, T = 0, E = 0;        // nodes, triangles, undirected edges
+  int32_t nslices = 0;
+  int64_t nnz = 0;                    // structural nonzeros (diag + 2 E)
+  int64_t nelem = 0;                  // SELL elements incl. padding
+  std::vector<int32_t> perm;          // new -> caller index
+  std::vector<int32_t> iperm;         // caller -> new index
+  std::vector<double> x, y, vol;      // new order
+  std::vector<int32_t> bc;            // new order
+  std::vector<int32_t> tri;           // 3*T, new indices, counter-clockwise (SoA: a[T], b[T], c[T])
+  std::vector<double> dxmin;          // T, shortest edge
+  std::vector<int32_t> rlen;          // N (padded to nslices*32 with 0)
+  std::vector<int32_t> sl_ptr, sl_w;  // nslices
+  std::vector<int32_t> col;           // nelem
+  std::vector<double> aval, gx, gy, sx, sy;  // nelem
+  std::vector<double> dinv;           // N: 1 / diagonal
+  std::vector<double> lift;           // N: free rows -sum_{k in D} K_ik phi_D,k ; Dirichlet rows phi_D
+  std::vector<double> rhs_scale;      // N: free rows e V_i / eps0 ; Dirichlet rows 0
+};
+
+// Builds every metric and sparse structure; returns AVIP_OK or AVIP_EINVAL.
+int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                 const int32_t* node_bc, const double* phi_D, int reorder, HostMesh& out,
+                 char* err, size_t errlen);
+
+// ----------------------------------------------------------------- kernel argument blocks
+struct SellView {  // device pointers of the SELL-32 structure
+  const int32_t* sl_ptr;
+  const int32_t* sl_w;
+  const int32_t* rlen;
+  const int32_t* col;
+  const double* aval;
+  const double* gx;
+  const double* gy;
+  const double* sx;
+  const double* sy;
+  int32_t N;
+  int32_t nslices;
+};
+
+struct SpeciesParams {
+  double q;           // charge number (-1, +1)
+  double mob[4];
+  double D;
+  int32_t mob_model;
+  int32_t bnd_mode;
+};
+
+struct Physics {
+  int32_t ns;
+  int32_t src_model;
+  int32_t src_idx[3];
+  int32_t limiter;
+  double src_params[3];
+  double beta, cfl, fourier, a_diel, a_chem;
+  double dt_fixed;
+  SpeciesParams sp[AVIP_MAX_SPECIES];
+};
+
+// Grid-wide barrier / reduction state (device memory, zeroed before each cooperative launch).
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+  int pad;
+  double red[8];
+};
+
+// Device scalars of a handle (one block of device memory).
+struct DevScalars {
+  unsigned long long dt_bits;   // running min of candidate time steps (bit pattern of a
+                                // positive double orders like the integer)
+  double dt;                    // time step used by the current step
+  double t;                     // simulated time
+  double charge;                // Q after the last step
+  int32_t parity;               // which density buffer is current
+  int32_t status;               // first error of the current run (AVIP_*)
+  int32_t pcg_iters;            // iterations of the last solve
+  int32_t pcg_status;
+  double pcg_relres;            // final true relative residual of the last solve
+  double pcg_bnorm;
+  // run statistics (accumulated by the finalize kernel)
+  int32_t run_steps;
+  int32_t run_iters_total;
+  int32_t run_iters_max;
+  int32_t pad;
+  double run_dt_min, run_dt_max, run_relres_max;
+};
+
+struct PcgArgs {
+  SellView A;
+  const double* dinv;
+  const double* rhs_scale;
+  const double* lift;
+  const double* nbuf;     // density buffers: nbuf[(parity * ns + s) * Npad + i]
+  int32_t Npad;
+  int32_t ns;
+  double q[AVIP_MAX_SPECIES];
+  double* x;              // phi (warm start in, solution out)
+  double* b;
+  double* r;
+  double* z;
+  double* p;
+  double* q_ap;           // A p
+  double* partials;       // per-block partial sums (gridDim.x * 4)
+  GridSync* sync;
+  DevScalars* sc;
+  double rtol;
+  int32_t max_iter;
+  int32_t use_density_rhs;  // 1: b from densities; 0: b already in `b`
+};
+
+struct DDArgs {
+  SellView A;
+  Physics ph;
+  const double* x;        // node coordinates
+  const double* y;
+  const double* vol;
+  const double* phi;
+  double* nbuf;           // density ping-pong buffers
+  double* ndat;           // per species per node: gx, gy, vx, vy (4 doubles)
+  double* nm;             // per species per node: n * mu
+  double* src;            // per species per node: source rate
+  double* Ex;
+  double* Ey;
+  const int32_t* tri;     // SoA a[T], b[T], c[T]
+  const double* dxmin;
+  int32_t T;
+  int32_t Npad;
+  double* partials;       // per-block charge partials
+  DevScalars* sc;
+};
+
+}  // namespace avip

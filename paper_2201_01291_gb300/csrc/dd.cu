@@ -1,0 +1,347 @@
+// Drift-diffusion part of the explicit step, FP64, node-centric and atomic-free.
+//
+//   node_fields_kernel  E = -grad(phi), grad(n_s), nodal velocities V_s = sign(q_s) mu_s E,
+//                       n_s mu_s, source rates, chemical time-step candidates
+//   dt_cells_kernel     cell-based CFL / Fourier / dielectric candidates (section "Time step
+//                       computation"); global minimum by an integer atomicMin on the bits of
+//                       the positive doubles (exact and order independent)
+//   flux_update_kernel  for each node, every incident edge flux (limited Lax-Wendroff +
+//                       central diffusion) and the node-flux boundary closure, then source
+//                       and explicit update into the other density buffer; per-block charge
+//   finalize_kernel     charge sum in fixed order, time, parity flip, run statistics
+//
+// The residual of Eq. vertex_centered_flux is a sum over the edges of each dual cell.  Here
+// every node gathers its own edges (each flux is evaluated at both ends), so no scatter and
+// no atomics are needed and the result is deterministic.  Each edge flux is evaluated from the
+// (lower index, higher index) ordered pair, so both ends compute bit-identical values and the
+// scheme stays exactly conservative.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "avip_internal.h"
+
+namespace avip {
+
+constexpr int kDDThreads = 256;
+
+__device__ __forceinline__ double mobility(const SpeciesParams& sp, double Emag) {
+  if (sp.mob_model == AVIP_MOB_POWER) return sp.mob[0] * pow(fmax(Emag, sp.mob[3]) / sp.mob[1], sp.mob[2]);
+  return sp.mob[0];
+}
+
+__device__ __forceinline__ double limiter(double r, double beta, int kind) {
+  if (kind == AVIP_LIM_VANLEER) return (r + fabs(r)) / (1.0 + fabs(r));
+  return fmax(0.0, fmax(fmin(beta * r, 1.0), fmin(r, beta)));
+}
+
+__device__ __forceinline__ void block_min_to_global(double v, unsigned long long* dst) {
+  __shared__ double sm[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? sm[lane] : INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (lane == 0 && t < INFINITY && t > 0.0)
+      atomicMin(dst, (unsigned long long)__double_as_longlong(t));
+  }
+}
+
+// ------------------------------------------------------------------------ nodal fields
+__global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int with_dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = a.A.N;
+  const int ns = a.ph.ns;
+  double chem = INFINITY;
+  if (i < N) {
+    const int slice = i / kSlice, lane = i % kSlice;
+    const double* n = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+    const int base = __ldg(a.A.sl_ptr + slice) + lane;
+    const int rl = __ldg(a.A.rlen + i);
+    double gpx = 0.0, gpy = 0.0;
+    double gnx[AVIP_MAX_SPECIES], gny[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) gnx[s] = gny[s] = 0.0;
+    for (int k = 0; k < rl; ++k) {
+      const int e = base + k * kSlice;
+      const int j = __ldg(a.A.col + e);
+      const double wx = __ldg(a.A.gx + e), wy = __ldg(a.A.gy + e);
+      const double pj = a.phi[j];
+      gpx = fma(wx, pj, gpx);
+      gpy = fma(wy, pj, gpy);
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s < ns) {
+          const double u = n[(size_t)s * a.Npad + j];
+          gnx[s] = fma(wx, u, gnx[s]);
+          gny[s] = fma(wy, u, gny[s]);
+        }
+      }
+    }
+    const double Ex = -gpx, Ey = -gpy;
+    const double Emag = sqrt(Ex * Ex + Ey * Ey);
+    a.Ex[i] = Ex;
+    a.Ey[i] = Ey;
+    double mu[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      if (s < ns) {
+        const SpeciesParams& sp = a.ph.sp[s];
+        mu[s] = mobility(sp, Emag);
+        const double sg = sp.q > 0 ? 1.0 : -1.0;
+        const double vx = sg * mu[s] * Ex, vy = sg * mu[s] * Ey;
+        double2* d = reinterpret_cast<double2*>(a.ndat + ((size_t)s * a.Npad + i) * 4);
+        d[0] = make_double2(gnx[s], gny[s]);
+        d[1] = make_double2(vx, vy);
+        a.nm[(size_t)s * a.Npad + i] = n[(size_t)s * a.Npad + i] * mu[s];
+      }
+    }
+    double src[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) src[s] = 0.0;
+    if (a.ph.src_model != AVIP_SRC_NONE) {
+      const int ie = a.ph.src_idx[0], ip = a.ph.src_idx[1], ineg = a.ph.src_idx[2];
+      const double ne = n[(size_t)ie * a.Npad + i];
+      const double alpha = Emag > 0.0 ? a.ph.src_params[0] * exp(-a.ph.src_params[1] / Emag) : 0.0;
+      double mue = 0.0;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+        if (s == ie) mue = mu[s];
+      const double ion = alpha * mue * Emag * ne;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s == ie) src[s] += ion;
+        if (s == ip) src[s] += ion;
+      }
+      if (a.ph.src_model == AVIP_SRC_TOWNSEND_ATTACH) {
+        const double att = a.ph.src_params[2] * ne;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ie) src[s] -= att;
+          if (s == ineg) src[s] += att;
+        }
+      }
+      double se = 0.0;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+        if (s == ie) se = src[s];
+      if (se != 0.0) chem = a.ph.a_chem * fabs(ne) / fabs(se);
+    }
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+      if (s < ns) a.src[(size_t)s * a.Npad + i] = src[s];
+  }
+  if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
+}
+
+// ------------------------------------------------------------------------ time step
+__global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double cand = INFINITY;
+  if (c < a.T) {
+    const int n0 = a.tri[c], n1 = a.tri[a.T + c], n2 = a.tri[2 * a.T + c];
+    const double dx = a.dxmin[c];
+    const int ns = a.ph.ns;
+    double sigma = 0.0;
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      if (s < ns) {
+        const SpeciesParams& sp = a.ph.sp[s];
+        const double* d = a.ndat + (size_t)s * a.Npad * 4;
+        const double vx = (d[4 * n0 + 2] + d[4 * n1 + 2] + d[4 * n2 + 2]) / 3.0;
+        const double vy = (d[4 * n0 + 3] + d[4 * n1 + 3] + d[4 * n2 + 3]) / 3.0;
+        const double vm = sqrt(vx * vx + vy * vy);
+        if (vm > 0.0) cand = fmin(cand, a.ph.cfl * dx / vm);
+        if (sp.D > 0.0) cand = fmin(cand, a.ph.fourier * (dx * dx) / sp.D);
+        const double* nm = a.nm + (size_t)s * a.Npad;
+        const double cell = (nm[n0] + nm[n1] + nm[n2]) / 3.0;
+        sigma += fabs(sp.q * kECharge * cell);
+      }
+    }
+    if (sigma > 0.0) cand = fmin(cand, a.ph.a_diel * kEps0 / sigma);
+  }
+  block_min_to_global(cand, &a.sc->dt_bits);
+}
+
+// ------------------------------------------------------------------------ fluxes + update
+struct EdgeEnd {
+  double u, gx, gy, vx, vy, x, y;
+};
+
+// Flux from `lo` to `hi` through the dual face with normal (Sx, Sy) oriented lo -> hi:
+// limited Lax-Wendroff convective part with a virtual upwind node plus central diffusion.
+__device__ __forceinline__ double edge_flux(const EdgeEnd& lo, const EdgeEnd& hi, double Sx, double Sy,
+                                            double D, double dt, double beta, int lim) {
+  const double Vx = 0.5 * (lo.vx + hi.vx), Vy = 0.5 * (lo.vy + hi.vy);
+  const double av = Vx * Sx + Vy * Sy;
+  const double gx = 0.5 * (lo.gx + hi.gx), gy = 0.5 * (lo.gy + hi.gy);
+  const bool up_lo = av >= 0.0;
+  const EdgeEnd& U = up_lo ? lo : hi;
+  const EdgeEnd& W = up_lo ? hi : lo;
+  const double delta = W.u - U.u;
+  double psi = 0.0;
+  if (delta != 0.0) {
+    const double dx = W.x - U.x, dy = W.y - U.y;
+    const double r = (2.0 * (U.gx * dx + U.gy * dy) - delta) / delta;
+    psi = limiter(r, beta, lim);
+  }
+  const double lw = 0.5 * delta - 0.5 * dt * (gx * Vx + gy * Vy);
+  const double fc = (U.u + lw * psi) * av;
+  const double fd = -D * (gx * Sx + gy * Sy);
+  return fc + fd;
+}
+
+__global__ void __launch_bounds__(kDDThreads) flux_update_kernel(DDArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = a.A.N;
+  const int ns = a.ph.ns;
+  const double dt = a.ph.dt_fixed > 0.0 ? a.ph.dt_fixed : __longlong_as_double((long long)a.sc->dt_bits);
+  double qsum = 0.0;
+  if (i < N) {
+    const int par = a.sc->parity;
+    const double* n = a.nbuf + (size_t)par * AVIP_MAX_SPECIES * a.Npad;
+    double* nn = a.nbuf + (size_t)(par ^ 1) * AVIP_MAX_SPECIES * a.Npad;
+    const int slice = i / kSlice, lane = i % kSlice;
+    const int base = __ldg(a.A.sl_ptr + slice) + lane;
+    const int rl = __ldg(a.A.rlen + i);
+    const double xi = a.x[i], yi = a.y[i];
+    double R[AVIP_MAX_SPECIES];
+    EdgeEnd me[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      R[s] = 0.0;
+      if (s < ns) {
+        const double2* d = reinterpret_cast<const double2*>(a.ndat + ((size_t)s * a.Npad + i) * 4);
+        const double2 g = d[0], v = d[1];
+        me[s] = EdgeEnd{n[(size_t)s * a.Npad + i], g.x, g.y, v.x, v.y, xi, yi};
+      }
+    }
+    for (int k = 1; k < rl; ++k) {
+      const int e = base + k * kSlice;
+      const int j = __ldg(a.A.col + e);
+      const double Sx = __ldg(a.A.sx + e), Sy = __ldg(a.A.sy + e);
+      const bool lo_is_me = i < j;
+      const double xj = a.x[j], yj = a.y[j];
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s < ns) {
+          const double2* d = reinterpret_cast<const double2*>(a.ndat + ((size_t)s * a.Npad + j) * 4);
+          const double2 g = d[0], v = d[1];
+          const EdgeEnd other{n[(size_t)s * a.Npad + j], g.x, g.y, v.x, v.y, xj, yj};
+          const EdgeEnd& lo = lo_is_me ? me[s] : other;
+          const EdgeEnd& hi = lo_is_me ? other : me[s];
+          // the stored normal is oriented i -> j; the canonical one lo -> hi
+          const double sgn = lo_is_me ? 1.0 : -1.0;
+          const double F = edge_flux(lo, hi, sgn * Sx, sgn * Sy, a.ph.sp[s].D, dt, a.ph.beta, a.ph.limiter);
+          R[s] = lo_is_me ? R[s] - F : R[s] + F;
+        }
+      }
+    }
+    // boundary closure through the boundary nodal normal kept in the diagonal slot
+    const double Sbx = __ldg(a.A.sx + base), Sby = __ldg(a.A.sy + base);
+    const double Vi = a.vol[i];
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      if (s < ns) {
+        const SpeciesParams& sp = a.ph.sp[s];
+        double Fx = me[s].u * me[s].vx, Fy = me[s].u * me[s].vy;
+        if (sp.bnd_mode == AVIP_BND_OUTFLOW) {
+          Fx -= sp.D * me[s].gx;
+          Fy -= sp.D * me[s].gy;
+        }
+        const double rs = R[s] - (Fx * Sbx + Fy * Sby);
+        const double un = me[s].u + dt * (rs / Vi + a.src[(size_t)s * a.Npad + i]);
+        nn[(size_t)s * a.Npad + i] = un;
+        bad |= !isfinite(un);
+        qsum += sp.q * (Vi * un);
+      }
+    }
+    if (bad) atomicCAS(&a.sc->status, AVIP_OK, AVIP_ENAN);
+  }
+  // per-block charge partial (fixed order)
+  __shared__ double sm[32];
+  const int ln = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, o);
+  if (ln == 0) sm[warp] = qsum;
+  __syncthreads();
+  if (warp == 0) {
+    double t = ln < nw ? sm[ln] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (ln == 0) a.partials[blockIdx.x] = t;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->dt = dt;
+}
+
+// Single block: charge in block order, time, parity, statistics; re-arm the dt minimum.
+__global__ void finalize_kernel(DevScalars* sc, const double* partials, int nparts) {
+  __shared__ double sm[32];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) t += partials[b];
+  const int ln = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (ln == 0) sm[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = 0.0;
+    for (int w = 0; w < nw; ++w) q += sm[w];
+    sc->charge = kECharge * q;
+    const double dt = sc->dt;
+    if (!(dt > 0.0) || !isfinite(dt)) {
+      if (sc->status == AVIP_OK) sc->status = AVIP_ENAN;
+    }
+    sc->t += dt;
+    sc->parity ^= 1;
+    sc->run_steps += 1;
+    sc->run_iters_total += sc->pcg_iters;
+    sc->run_iters_max = max(sc->run_iters_max, sc->pcg_iters);
+    sc->run_dt_min = fmin(sc->run_dt_min, dt);
+    sc->run_dt_max = fmax(sc->run_dt_max, dt);
+    sc->run_relres_max = fmax(sc->run_relres_max, sc->pcg_relres);
+    sc->dt_bits = (unsigned long long)__double_as_longlong(INFINITY);
+  }
+}
+
+__global__ void run_reset_kernel(DevScalars* sc) {
+  sc->run_steps = 0;
+  sc->run_iters_total = 0;
+  sc->run_iters_max = 0;
+  sc->run_dt_min = INFINITY;
+  sc->run_dt_max = 0.0;
+  sc->run_relres_max = 0.0;
+  sc->status = AVIP_OK;
+}
+
+// ------------------------------------------------------------------------ host launchers
+static inline int nblk(int n) { return (n + kDDThreads - 1) / kDDThreads; }
+
+cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st) {
+  node_fields_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
+  return cudaGetLastError();
+}
+cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
+  dt_cells_kernel<<<nblk(a.T), kDDThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st) {
+  flux_update_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st) {
+  finalize_kernel<<<1, 256, 0, st>>>(sc, partials, nparts);
+  return cudaGetLastError();
+}
+cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st) {
+  run_reset_kernel<<<1, 1, 0, st>>>(sc);
+  return cudaGetLastError();
+}
+int flux_blocks(int N) { return nblk(N); }
+
+}  // namespace avip

@@ -1,0 +1,295 @@
+// Host-side mesh preparation: validation, Morton renumbering, vertex-centred metrics and the
+// SELL-32 sparse structures consumed by the kernels.
+//
+// Metrics (section "Nomenclature and notations" and "Cartesian geometry"):
+//   * V_tau = signed area of the counter-clockwise triangle;
+//   * nodal normal S_k^tau (Eq. node_normal) = minus the sum of the two faces adjacent to k,
+//     which for a triangle is the outward length-normal of the face opposite k;
+//   * median-dual volume V_i = sum over E(i) of V_tau / 3;
+//   * edge normal S_ij^tau = (S_i^tau - S_j^tau) / 6, oriented i -> j (the relation quoted in
+//     the axisymmetric section; it satisfies sum_j S_ij^tau = S_i^tau / n_d), summed over the
+//     cells sharing the edge;
+//   * boundary nodal normal S_i^b = 1/2 sum of the outward normals of the boundary faces at
+//     i (Fig. bcs_normal);
+//   * Poisson matrix K_ik = sum_tau S_i.S_k / (n_d^2 V_tau) (Eq. coeff_matriceA with the sign
+//     of -lap phi = rho/eps0), Dirichlet unknowns eliminated symmetrically;
+//   * nodal gradient weights: grad u_i = (1/V_i) sum_tau (V_tau/3) grad u_tau with
+//     grad u_tau = -1/(n_d V_tau) sum_k u_k S_k, i.e. grad u_i = sum_k G_ik u_k with
+//     G_ik = -(1 / (6 V_i)) sum_{tau containing i and k} S_k^tau.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "avip_internal.h"
+
+namespace avip {
+
+namespace {
+
+uint64_t spread_bits(uint64_t v) {  // 21 bits -> every other bit
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+
+void morton_order(const double* xy, int32_t n, std::vector<int32_t>& perm) {
+  double xmin = xy[0], xmax = xy[0], ymin = xy[1], ymax = xy[1];
+  for (int32_t i = 0; i < n; ++i) {
+    xmin = std::min(xmin, xy[2 * i]);
+    xmax = std::max(xmax, xy[2 * i]);
+    ymin = std::min(ymin, xy[2 * i + 1]);
+    ymax = std::max(ymax, xy[2 * i + 1]);
+  }
+  double ext = std::max(xmax - xmin, ymax - ymin);
+  if (!(ext > 0)) ext = 1.0;
+  const double scale = double((1u << 21) - 1) / ext;
+  std::vector<uint64_t> key(n);
+  for (int32_t i = 0; i < n; ++i) {
+    uint64_t qx = (uint64_t)std::llround((xy[2 * i] - xmin) * scale);
+    uint64_t qy = (uint64_t)std::llround((xy[2 * i + 1] - ymin) * scale);
+    key[i] = spread_bits(qx) | (spread_bits(qy) << 1);
+  }
+  perm.resize(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+}
+
+}  // namespace
+
+int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                 const int32_t* node_bc, const double* phi_D, int reorder, HostMesh& m,
+                 char* err, size_t errlen) {
+  auto fail = [&](const char* msg) {
+    if (err && errlen) std::snprintf(err, errlen, "%s", msg);
+    return AVIP_EINVAL;
+  };
+  if (!xy || !tris || !node_bc || !phi_D) return fail("null input array");
+  if (n_nodes < 3 || n_tris < 1) return fail("mesh needs at least 3 nodes and 1 triangle");
+  const int32_t N = n_nodes, T = n_tris;
+  for (int64_t k = 0; k < 3LL * T; ++k)
+    if (tris[k] < 0 || tris[k] >= N) return fail("triangle index out of range");
+  int ndir = 0;
+  for (int32_t i = 0; i < N; ++i) {
+    if (node_bc[i] != 0 && node_bc[i] != 1) return fail("node_bc must be 0 or 1");
+    if (!std::isfinite(xy[2 * i]) || !std::isfinite(xy[2 * i + 1])) return fail("non-finite coordinate");
+    if (node_bc[i] == 1) {
+      ++ndir;
+      if (!std::isfinite(phi_D[i])) return fail("non-finite Dirichlet value");
+    }
+  }
+  if (ndir == 0) return fail("at least one Dirichlet node is required (pure Neumann problem is singular)");
+
+  // ---- renumbering
+  if (reorder) {
+    morton_order(xy, N, m.perm);
+  } else {
+    m.perm.resize(N);
+    std::iota(m.perm.begin(), m.perm.end(), 0);
+  }
+  m.iperm.assign(N, 0);
+  for (int32_t i = 0; i < N; ++i) m.iperm[m.perm[i]] = i;
+  m.N = N;
+  m.T = T;
+  m.x.resize(N);
+  m.y.resize(N);
+  m.bc.resize(N);
+  for (int32_t i = 0; i < N; ++i) {
+    m.x[i] = xy[2 * m.perm[i]];
+    m.y[i] = xy[2 * m.perm[i] + 1];
+    m.bc[i] = node_bc[m.perm[i]];
+  }
+
+  // ---- cells: orientation, volume, nodal normals, shortest edge
+  std::vector<int32_t> tv(3 * (size_t)T);
+  std::vector<double> Vt(T), Sn(6 * (size_t)T);  // Sn[6c + 2k + {0,1}]
+  m.dxmin.resize(T);
+  for (int32_t c = 0; c < T; ++c) {
+    int32_t a = m.iperm[tris[3 * c]], b = m.iperm[tris[3 * c + 1]], d = m.iperm[tris[3 * c + 2]];
+    double cr = (m.x[b] - m.x[a]) * (m.y[d] - m.y[a]) - (m.y[b] - m.y[a]) * (m.x[d] - m.x[a]);
+    if (cr < 0) {
+      std::swap(b, d);
+      cr = -cr;
+    }
+    if (!(cr > 0)) return fail("degenerate (zero-area) triangle");
+    tv[3 * c] = a;
+    tv[3 * c + 1] = b;
+    tv[3 * c + 2] = d;
+    Vt[c] = 0.5 * cr;
+    for (int k = 0; k < 3; ++k) {
+      int32_t p = tv[3 * c + (k + 1) % 3], q = tv[3 * c + (k + 2) % 3];
+      // outward length-normal of the opposite face p -> q (right-hand side of travel)
+      Sn[6 * c + 2 * k] = m.y[q] - m.y[p];
+      Sn[6 * c + 2 * k + 1] = -(m.x[q] - m.x[p]);
+    }
+    double l0 = std::hypot(m.x[b] - m.x[a], m.y[b] - m.y[a]);
+    double l1 = std::hypot(m.x[d] - m.x[b], m.y[d] - m.y[b]);
+    double l2 = std::hypot(m.x[a] - m.x[d], m.y[a] - m.y[d]);
+    m.dxmin[c] = std::min(std::min(l0, l1), l2);
+  }
+  m.tri.resize(3 * (size_t)T);
+  for (int32_t c = 0; c < T; ++c)
+    for (int k = 0; k < 3; ++k) m.tri[(size_t)k * T + c] = tv[3 * c + k];
+
+  // ---- node -> cells
+  std::vector<int32_t> ncell(N + 1, 0);
+  for (size_t k = 0; k < tv.size(); ++k) ncell[tv[k] + 1]++;
+  for (int32_t i = 0; i < N; ++i) ncell[i + 1] += ncell[i];
+  std::vector<int32_t> cells(tv.size());
+  {
+    std::vector<int32_t> fillp(ncell.begin(), ncell.end() - 1);
+    for (int32_t c = 0; c < T; ++c)
+      for (int k = 0; k < 3; ++k) cells[fillp[tv[3 * c + k]]++] = c;
+  }
+  m.vol.assign(N, 0.0);
+  for (int32_t i = 0; i < N; ++i)
+    for (int32_t e = ncell[i]; e < ncell[i + 1]; ++e) m.vol[i] += Vt[cells[e]] / 3.0;
+  for (int32_t i = 0; i < N; ++i)
+    if (!(m.vol[i] > 0)) return fail("node not used by any triangle");
+
+  // ---- rows: diagonal first then neighbours ascending
+  std::vector<int32_t> rowptr(N + 1, 0);
+  std::vector<int32_t> cols;
+  cols.reserve((size_t)N * 8);
+  {
+    std::vector<int32_t> nb;
+    for (int32_t i = 0; i < N; ++i) {
+      nb.clear();
+      for (int32_t e = ncell[i]; e < ncell[i + 1]; ++e) {
+        int32_t c = cells[e];
+        for (int k = 0; k < 3; ++k)
+          if (tv[3 * c + k] != i) nb.push_back(tv[3 * c + k]);
+      }
+      std::sort(nb.begin(), nb.end());
+      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+      cols.push_back(i);
+      cols.insert(cols.end(), nb.begin(), nb.end());
+      rowptr[i + 1] = (int32_t)cols.size();
+    }
+  }
+  const int64_t nnz = (int64_t)cols.size();
+  m.nnz = nnz;
+  m.E = (int32_t)((nnz - N) / 2);
+  std::vector<double> K(nnz, 0.0), Gx(nnz, 0.0), Gy(nnz, 0.0), Sx(nnz, 0.0), Sy(nnz, 0.0);
+  std::vector<int32_t> shared(nnz, 0);
+  auto slot = [&](int32_t i, int32_t k) -> int64_t {
+    if (k == i) return rowptr[i];
+    const int32_t* b = cols.data() + rowptr[i] + 1;
+    const int32_t* e = cols.data() + rowptr[i + 1];
+    const int32_t* p = std::lower_bound(b, e, k);
+    return (int64_t)(p - cols.data());
+  };
+  for (int32_t i = 0; i < N; ++i) {
+    for (int32_t e = ncell[i]; e < ncell[i + 1]; ++e) {
+      int32_t c = cells[e];
+      int li = (tv[3 * c] == i) ? 0 : (tv[3 * c + 1] == i ? 1 : 2);
+      const double six = Sn[6 * c + 2 * li], siy = Sn[6 * c + 2 * li + 1];
+      for (int k = 0; k < 3; ++k) {
+        int32_t j = tv[3 * c + k];
+        int64_t s = slot(i, j);
+        const double skx = Sn[6 * c + 2 * k], sky = Sn[6 * c + 2 * k + 1];
+        K[s] += (six * skx + siy * sky) / (4.0 * Vt[c]);
+        Gx[s] += -skx / (6.0 * m.vol[i]);
+        Gy[s] += -sky / (6.0 * m.vol[i]);
+        if (j != i) {
+          Sx[s] += (six - skx) / 6.0;
+          Sy[s] += (siy - sky) / 6.0;
+          shared[s] += 1;
+        }
+      }
+    }
+  }
+  // boundary faces: edges with a single adjacent cell; their outward normal is split between
+  // the two end nodes (stored in the diagonal slot)
+  for (int32_t c = 0; c < T; ++c) {
+    for (int k = 0; k < 3; ++k) {
+      int32_t p = tv[3 * c + k], q = tv[3 * c + (k + 1) % 3];
+      if (shared[slot(p, q)] == 1) {
+        double nx = m.y[q] - m.y[p], ny = -(m.x[q] - m.x[p]);
+        Sx[rowptr[p]] += 0.5 * nx;
+        Sy[rowptr[p]] += 0.5 * ny;
+        Sx[rowptr[q]] += 0.5 * nx;
+        Sy[rowptr[q]] += 0.5 * ny;
+      }
+    }
+  }
+
+  // ---- Dirichlet elimination
+  m.dinv.assign(N, 0.0);
+  m.lift.assign(N, 0.0);
+  m.rhs_scale.assign(N, 0.0);
+  std::vector<double> Ael(K);
+  for (int32_t i = 0; i < N; ++i) {
+    if (m.bc[i] == 1) {
+      for (int32_t s = rowptr[i]; s < rowptr[i + 1]; ++s) Ael[s] = 0.0;
+      Ael[rowptr[i]] = 1.0;
+      m.lift[i] = phi_D[m.perm[i]];
+      m.rhs_scale[i] = 0.0;
+    } else {
+      double l = 0.0;
+      for (int32_t s = rowptr[i] + 1; s < rowptr[i + 1]; ++s) {
+        int32_t k = cols[s];
+        if (m.bc[k] == 1) {
+          l -= K[s] * phi_D[m.perm[k]];
+          Ael[s] = 0.0;
+        }
+      }
+      m.lift[i] = l;
+      m.rhs_scale[i] = kECharge * m.vol[i] / kEps0;
+    }
+    if (!(Ael[rowptr[i]] > 0)) return fail("non-positive Poisson diagonal");
+    m.dinv[i] = 1.0 / Ael[rowptr[i]];
+  }
+
+  // ---- SELL-32 layout
+  m.nslices = (N + kSlice - 1) / kSlice;
+  const int32_t Npad = m.nslices * kSlice;
+  m.rlen.assign(Npad, 0);
+  for (int32_t i = 0; i < N; ++i) m.rlen[i] = rowptr[i + 1] - rowptr[i];
+  m.sl_ptr.resize(m.nslices + 1);
+  m.sl_w.resize(m.nslices);
+  int64_t off = 0;
+  for (int32_t s = 0; s < m.nslices; ++s) {
+    int32_t w = 0;
+    for (int l = 0; l < kSlice; ++l) w = std::max(w, m.rlen[s * kSlice + l]);
+    m.sl_w[s] = w;
+    m.sl_ptr[s] = (int32_t)off;
+    off += (int64_t)w * kSlice;
+    if (off > INT32_MAX) return fail("mesh too large for 32-bit sparse offsets");
+  }
+  m.sl_ptr[m.nslices] = (int32_t)off;
+  m.nelem = off;
+  m.col.assign(off, 0);
+  m.aval.assign(off, 0.0);
+  m.gx.assign(off, 0.0);
+  m.gy.assign(off, 0.0);
+  m.sx.assign(off, 0.0);
+  m.sy.assign(off, 0.0);
+  for (int32_t s = 0; s < m.nslices; ++s) {
+    for (int l = 0; l < kSlice; ++l) {
+      int32_t i = s * kSlice + l;
+      for (int32_t k = 0; k < m.sl_w[s]; ++k) {
+        int64_t e = (int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l;
+        if (i < N && k < m.rlen[i]) {
+          int64_t src = rowptr[i] + k;
+          m.col[e] = cols[src];
+          m.aval[e] = Ael[src];
+          m.gx[e] = Gx[src];
+          m.gy[e] = Gy[src];
+          m.sx[e] = Sx[src];
+          m.sy[e] = Sy[src];
+        } else {
+          m.col[e] = (i < N) ? i : 0;
+        }
+      }
+    }
+  }
+  return AVIP_OK;
+}
+
+}  // namespace avip

@@ -1,0 +1,66 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every function that
+include/avip.h declares; host-only entry points behave.  No GPU compute is called."""
+import os
+
+import pytest
+
+from helpers import header_functions
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_01291_gb300 import build
+    build.build()
+    from paper_2201_01291_gb300 import avip
+    return avip.load()
+
+
+def test_header_symbols_exported(lib):
+    names = header_functions(os.path.join(ROOT, "include", "avip.h"))
+    assert "mesh_create" in names and "run_steps" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_2201_01291_gb300 import avip
+    names = header_functions(os.path.join(ROOT, "include", "avip.h"))
+    assert set(names) <= set(avip.exported_symbols())
+
+
+def test_host_only_entry_points(lib):
+    from paper_2201_01291_gb300 import avip
+    o = avip.avip_opts_default()
+    assert o.cfl == 0.4 and o.rtol == 1e-12 and o.reorder == 1 and o.precision == 0
+    assert avip.status_str(avip.AVIP_ENOTCONV).startswith("PCG")
+    assert avip.status_str(12345) == "unknown status"
+    assert lib.mesh_destroy(None) == 0
+
+
+def test_mesh_validation_on_host(lib):
+    """mesh_create rejects bad meshes in host code before any CUDA call (runs without a GPU)."""
+    import numpy as np
+    from paper_2201_01291_gb300 import avip, workloads as W
+    p = W.config_small(nx=9, ny=9)
+    o = avip.avip_opts_default()
+    bad = p.tris.copy()
+    bad[0, 0] = p.n_nodes + 5
+    assert avip.mesh_create(p.xy, bad, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "out of range" in avip.last_error()
+    deg = p.tris.copy()
+    deg[0, 1] = deg[0, 0]
+    assert avip.mesh_create(p.xy, deg, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "zero-area" in avip.last_error()
+    assert avip.mesh_create(p.xy, p.tris, np.zeros_like(p.node_bc), p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "Dirichlet" in avip.last_error()
+    bc = p.node_bc.copy()
+    bc[0] = 7
+    assert avip.mesh_create(p.xy, p.tris, bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    xy = p.xy.copy()
+    xy[4, 0] = np.inf
+    assert avip.mesh_create(xy, p.tris, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    o2 = avip.avip_opts_default()
+    o2.rtol = -1.0
+    assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o2)[0] == avip.AVIP_EINVAL

@@ -291,3 +291,22 @@ def test_electrons_drift_against_field():
     c1 = np.sum(o.V_node * n[0] * p.xy[:, 1]) / np.sum(o.V_node * n[0])
     v = (c1 - c0) / (k * 2e-10)
     assert abs(v - 0.04 * 5e5) < 0.02 * 0.04 * 5e5
+
+
+def test_chemical_time_step_closed_form():
+    """Uniform field and density with Townsend ionisation: the chemical limit is
+    A_tau / nu with nu = alpha(|E|) mu_e |E|, also where the density is negative (a time
+    scale, section "Time step computation")."""
+    nx = 9
+    for nb in (1e8, -1e8):
+        p = W.config_small(nx=nx, ny=nx, n_peak=0.0, n_back=nb, voltage=3e4, jitter=0.0,
+                           source=W.SRC_TOWNSEND)
+        p.opts.cfl = p.opts.fourier = 1e9          # leave only the chemical limit active
+        o = O.Oracle(p)
+        _, info = o.step(o.initial_state())
+        E = 3e4 / 1e-2
+        A, B = W.townsend_air()
+        nu = A * np.exp(-B / E) * 0.04 * E
+        ref = min(0.2 / nu, 0.5 * O.EPS0 / (O.E_CHARGE * abs(nb) * (0.04 + 2e-4)))
+        assert info["dt"] > 0
+        assert abs(info["dt"] - ref) <= 1e-12 * ref
