@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi sampling (diagnosis only)")
+    ap.add_argument("--pcg-max-iter", type=int, default=0,
+                    help="cap PCG iterations per solve (profiling captures only; not a bench setting)")
     return ap.parse_args()
 
 
@@ -143,13 +147,15 @@ def run_ours(args, rank, world, local_rank):
     problem, desc = make_problem(args.workload)
     T = problem.n_tris
     stream = torch.cuda.Stream()
-    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream)
+    kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
+    allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
+    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, **kw)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     # warm-up (graph capture happens here too)
     with torch.cuda.stream(stream):
-        m.run(args.warmup)
+        m.run(args.warmup, allow=allow)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local_rank) if rank == 0 else None
+    sampler = ClockSampler(local_rank) if rank == 0 and not args.no_clocks else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
@@ -164,7 +170,7 @@ def run_ours(args, rank, world, local_rank):
         ev0.record(stream)
         for k in range(args.steps):
             flush.fill_(float(k))                 # evict the previous step from L2
-            ms, st = m.run_timed(1)
+            ms, st = m.run_timed(1, allow=allow)
             for key in kernel_ms:
                 kernel_ms[key] += ms[key]
             iters += st["pcg_iters_total"]
@@ -181,15 +187,15 @@ def run_ours(args, rank, world, local_rank):
         elapsed = float(t.item())
     value = world * T * args.steps / elapsed
     # ---- end to end through the public API with host buffers
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
     host = m.state()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         m.set_state(host)
-        m.run(1)
+        m.run(1, allow=allow)
         host = m.state()
-    e2e_t = time.perf_counter() - t0
+    e2e_t = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
         t = torch.tensor([e2e_t], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
