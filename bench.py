@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi sampling (diagnosis only)")
+    ap.add_argument("--pcg-threads", type=int, default=0, help="PCG block size (0 = library default)")
     ap.add_argument("--pcg-max-iter", type=int, default=0,
                     help="cap PCG iterations per solve (profiling captures only; not a bench setting)")
     return ap.parse_args()
@@ -149,7 +150,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
     allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
-    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, **kw)
+    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads, **kw)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     # warm-up (graph capture happens here too)
     with torch.cuda.stream(stream):

@@ -80,6 +80,8 @@ typedef struct avip_opts {
   int32_t reorder;                     /* 1 = Morton renumbering (default), 0 = keep order    */
   double dt_fixed;                     /* > 0: use this time step instead of the automatic one */
   double inner_rtol;                   /* mixed precision: FP32 inner reduction per refinement */
+  int32_t pcg_threads;                 /* streaming PCG block size (256/512/768/1024; 0 = 768) */
+  int32_t pcg_kind;                    /* PCG kernel: 0 auto, 1 streaming, 2 register-resident */
   void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
   avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
   avip_free_fn free;

@@ -29,7 +29,8 @@ class AvipOpts(C.Structure):
     _fields_ = [("cfl", C.c_double), ("fourier", C.c_double), ("a_diel", C.c_double), ("a_chem", C.c_double),
                 ("beta", C.c_double), ("limiter", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double),
                 ("max_iter", C.c_int32), ("reorder", C.c_int32), ("dt_fixed", C.c_double),
-                ("inner_rtol", C.c_double), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -236,7 +237,7 @@ class Mesh:
     """Owns one handle built from a synthetic workload (see workloads.Problem)."""
 
     def __init__(self, problem, precision=PREC_FP64, rtol=None, max_iter=None, dt_fixed=None,
-                 reorder=1, use_torch_allocator=False, stream=None):
+                 reorder=1, use_torch_allocator=False, stream=None, pcg_threads=0, pcg_kind=0):
         o = avip_opts_default()
         po = problem.opts
         o.cfl, o.fourier, o.a_diel, o.a_chem = po.cfl, po.fourier, po.a_diel, po.a_chem
@@ -246,6 +247,8 @@ class Mesh:
         o.dt_fixed = po.dt_fixed if dt_fixed is None else dt_fixed
         o.precision = precision
         o.reorder = reorder
+        o.pcg_threads = pcg_threads
+        o.pcg_kind = pcg_kind
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()

@@ -11,8 +11,7 @@
 #include "avip_internal.h"
 
 namespace avip {
-cudaError_t launch_pcg_fp64(const PcgArgs& args, int blocks, cudaStream_t st);
-int pcg_fp64_max_blocks();
+cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
@@ -32,16 +31,19 @@ struct avip_mesh {
   // device arrays
   int32_t *sl_ptr = nullptr, *sl_w = nullptr, *rlen = nullptr, *col = nullptr, *tri = nullptr;
   double *aval = nullptr, *gx = nullptr, *gy = nullptr, *sx = nullptr, *sy = nullptr;
-  double *x = nullptr, *y = nullptr, *vol = nullptr, *dinv = nullptr, *lift = nullptr, *rhs_scale = nullptr;
+  double *x = nullptr, *y = nullptr, *vol = nullptr, *dsq = nullptr, *dsqinv = nullptr, *lift = nullptr,
+         *rhs_scale = nullptr;
   double* dxmin = nullptr;
-  double *phi = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
-  double* partials = nullptr;   // PCG grid-reduction partials
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
-  GridSync* sync = nullptr;
+  GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
+  unsigned* flags = nullptr;
+  double* parts = nullptr;
+  size_t sync_bytes = 0;
   DevScalars* sc = nullptr;
   int32_t Npad = 0;
-  int pcg_blocks = 0;
+  PcgPlan plan;
   int nparts = 0;
   Physics ph;
   int species_declared = 0;
@@ -117,20 +119,22 @@ PcgArgs pcg_args(const avip_mesh* h) {
   PcgArgs a;
   std::memset(&a, 0, sizeof(a));
   a.A = sell_view(h);
-  a.dinv = h->dinv;
+  a.dsq = h->dsq;
+  a.dsqinv = h->dsqinv;
   a.rhs_scale = h->rhs_scale;
   a.lift = h->lift;
   a.nbuf = h->nbuf;
   a.Npad = h->Npad;
   a.ns = h->ph.ns;
   for (int s = 0; s < AVIP_MAX_SPECIES; ++s) a.q[s] = h->ph.sp[s].q;
-  a.x = h->phi;
+  a.phi = h->phi;
+  a.x = h->xs;
   a.b = h->b;
   a.r = h->r;
-  a.z = h->z;
   a.p = h->p;
   a.q_ap = h->q;
-  a.partials = h->partials;
+  a.flags = h->flags;
+  a.parts = h->parts;
   a.sync = h->sync;
   a.sc = h->sc;
   a.rtol = h->opts.rtol;
@@ -172,9 +176,9 @@ int cuda_status(cudaError_t e) {
 
 // Queue one Poisson solve (cooperative PCG launch).
 cudaError_t enqueue_poisson(avip_mesh* h) {
-  cudaError_t e = cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+  cudaError_t e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
   if (e != cudaSuccess) return e;
-  return launch_pcg_fp64(pcg_args(h), h->pcg_blocks, h->stream);
+  return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
 
 // Queue one explicit step (no host synchronisation).
@@ -280,13 +284,13 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
             upload(h, h->col, m.col) && upload(h, h->aval, m.aval) && upload(h, h->gx, m.gx) &&
             upload(h, h->gy, m.gy) && upload(h, h->sx, m.sx) && upload(h, h->sy, m.sy) &&
             upload(h, h->tri, m.tri) && upload(h, h->dxmin, m.dxmin) && upload(h, h->x, m.x, Np) &&
-            upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dinv, m.dinv, Np) &&
+            upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dsq, m.dsq, Np) && upload(h, h->dsqinv, m.dsqinv, Np) &&
             upload(h, h->lift, m.lift, Np) && upload(h, h->rhs_scale, m.rhs_scale, Np);
   // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere
   std::vector<double> phi0(Np, 0.0);
   for (int32_t i = 0; i < m.N; ++i)
     if (m.bc[i] == 1) phi0[i] = m.lift[i];
-  ok = ok && upload(h, h->phi, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->z, Np) &&
+  ok = ok && upload(h, h->phi, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
        zalloc(h, h->p, Np) && zalloc(h, h->q, Np) && zalloc(h, h->nbuf, 2 * AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->ndat, 4 * AVIP_MAX_SPECIES * Np) && zalloc(h, h->nm, AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->src, AVIP_MAX_SPECIES * Np) && zalloc(h, h->Ex, Np) && zalloc(h, h->Ey, Np);
@@ -297,11 +301,13 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     return AVIP_ENOMEM;
   }
   // persistent PCG grid: co-resident blocks, but no more than there are slices to share
-  const int maxb = pcg_fp64_max_blocks();
-  const int want = (m.nslices + 7) / 8;  // one slice per warp of a 256-thread block
-  h->pcg_blocks = std::max(1, std::min(maxb, want));
+  // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
+  h->plan = pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
   h->nparts = flux_blocks(m.N);
-  ok = zalloc(h, h->partials, (size_t)h->pcg_blocks * 4) && zalloc(h, h->qpart, (size_t)h->nparts) && zalloc(h, h->sync, 1) && zalloc(h, h->sc, 1);
+  h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)h->plan.blocks;
+  ok = zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
+       zalloc(h, h->sync, (h->sync_bytes + sizeof(GridSync) - 1) / sizeof(GridSync)) && zalloc(h, h->sc, 1);
+  if (ok) h->flags = reinterpret_cast<unsigned*>(h->sync + 1);
   if (!ok) {
     dev_free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -490,7 +496,7 @@ static int run_impl(avip_mesh_t h, int32_t nsteps, double dt, avip_stats* stats,
   }
   if (sc.status == AVIP_ETIMEOUT) {
     // leave the handle usable: clear the barrier state
-    cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+    cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
     cudaStreamSynchronize(h->stream);
   }
   return sc.status;
@@ -519,9 +525,9 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
   for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
     DDArgs a = dd_args(h);
-    e = cudaMemsetAsync(h->sync, 0, sizeof(GridSync), h->stream);
+    e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) e = launch_pcg_fp64(pcg_args(h), h->pcg_blocks, h->stream);
+    if (e == cudaSuccess) e = launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess) e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);

@@ -35,10 +35,10 @@ struct HostMesh {
   std::vector<int32_t> rlen;          // N (padded to nslices*32 with 0)
   std::vector<int32_t> sl_ptr, sl_w;  // nslices
   std::vector<int32_t> col;           // nelem
-  std::vector<double> aval, gx, gy, sx, sy;  // nelem
-  std::vector<double> dinv;           // N: 1 / diagonal
-  std::vector<double> lift;           // N: free rows -sum_{k in D} K_ik phi_D,k ; Dirichlet rows phi_D
-  std::vector<double> rhs_scale;      // N: free rows e V_i / eps0 ; Dirichlet rows 0
+  std::vector<double> aval, gx, gy, sx, sy;  // nelem (aval: D^-1/2 K D^-1/2)
+  std::vector<double> dsq, dsqinv;    // N: sqrt(K_ii) and its inverse (symmetric Jacobi scaling)
+  std::vector<double> lift;           // N: free rows -sum_{k in D} K_ik phi_D,k ; Dirichlet rows phi_D (scaled by 1/sqrt(K_ii))
+  std::vector<double> rhs_scale;      // N: free rows e V_i / eps0 ; Dirichlet rows 0 (scaled by 1/sqrt(K_ii))
 };
 
 // Builds every metric and sparse structure; returns AVIP_OK or AVIP_EINVAL.
@@ -110,28 +110,43 @@ struct DevScalars {
   double run_dt_min, run_dt_max, run_relres_max;
 };
 
+// Jacobi-PCG is run on the symmetrically scaled system
+//   (D^-1/2 K D^-1/2) x = D^-1/2 b,   phi = D^-1/2 x,
+// whose CG iterates are those of Jacobi-preconditioned CG on K phi = b; the preconditioned
+// residual z = D^-1 r becomes the plain residual of the scaled system.
 struct PcgArgs {
-  SellView A;
-  const double* dinv;
-  const double* rhs_scale;
-  const double* lift;
-  const double* nbuf;     // density buffers: nbuf[(parity * ns + s) * Npad + i]
+  SellView A;             // A.aval holds the scaled matrix D^-1/2 K D^-1/2
+  const double* dsq;      // sqrt(K_ii)
+  const double* dsqinv;   // 1 / sqrt(K_ii)
+  const double* rhs_scale;  // scaled: e V_i / (eps0 sqrt(K_ii)) on free rows, 0 on Dirichlet rows
+  const double* lift;       // scaled Dirichlet lift
+  const double* nbuf;     // density buffers: nbuf[(parity * AVIP_MAX_SPECIES + s) * Npad + i]
   int32_t Npad;
   int32_t ns;
   double q[AVIP_MAX_SPECIES];
-  double* x;              // phi (warm start in, solution out)
-  double* b;
+  double* phi;            // potential (warm start in, solution out)
+  double* x;              // scaled iterate
+  double* b;              // scaled right-hand side
   double* r;
-  double* z;
   double* p;
-  double* q_ap;           // A p
-  double* partials;       // per-block partial sums (gridDim.x * 4)
+  double* q_ap;           // scaled A p
+  unsigned* flags;        // grid barrier flags (zeroed before each launch)
+  double* parts;          // grid barrier partials, 2 * gridDim.x * 4
   GridSync* sync;
   DevScalars* sc;
   double rtol;
   int32_t max_iter;
   int32_t use_density_rhs;  // 1: b from densities; 0: b already in `b`
 };
+
+// Kernel and grid of a PCG launch.
+struct PcgPlan {
+  int kind = 1;    // 1 streaming, 2 register-resident
+  int tpb = 768;
+  int maxs = 0;    // slices per warp (register-resident)
+  int blocks = 1;
+};
+PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 
 struct DDArgs {
   SellView A;

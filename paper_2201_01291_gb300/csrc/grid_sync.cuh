@@ -1,10 +1,12 @@
 // Deterministic block and grid reductions for persistent (cooperatively launched) kernels.
 //
-// The grid reduction doubles as the grid-wide barrier: every block publishes its partial
-// sums, the last block to arrive adds all partials in block order (so the result does not
-// depend on arrival order) and releases the others by bumping a generation counter.  Every
-// wait is bounded: after kSpinLimitNs of polling a block raises `abort`, every waiter leaves,
-// and the kernel reports AVIP_ETIMEOUT instead of hanging.
+// Grid reduction = grid barrier: every block publishes its partial sums, every block reads all
+// partials in block order once everybody has arrived, so every block obtains bit-identical
+// totals (deterministic, independent of arrival order).  An optional epilogue derives scalars
+// from the totals (e.g. the CG step alpha = r.r / p.q) once per block.
+//
+// Every wait is bounded: after kSpinLimitNs of polling a block raises `abort`, every waiter
+// leaves, and the kernel reports a timeout instead of hanging.
 #pragma once
 #include <cstdint>
 
@@ -13,6 +15,7 @@
 namespace avip {
 
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;  // 2 s
+constexpr int kPollUnroll = 8;  // partial loads per lane kept in flight (grids up to 256 blocks)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -22,6 +25,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long global_timer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -29,7 +38,7 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
 }
 
 // Sum NV values over the block; the result is valid in every thread.  Fixed shuffle/smem
-// order, so identical inputs give identical bits.  smem must hold 32*NV doubles + NV.
+// order, so identical inputs give identical bits.  smem must hold 32*NV + NV doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -58,66 +67,139 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
   for (int k = 0; k < NV; ++k) v[k] = smem[32 * NV + k];
 }
 
-// Grid-wide sum of NV (<= 8, <= warps per block) values; also a grid barrier.  Returns false
-// if the wait was abandoned (timeout or another block aborted); the caller must then leave.
-template <int NV>
-__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, GridSync* gs,
-                                         double* smem) {
-  block_sum<NV>(v, smem);
+// Barrier state of one cooperative launch.  `flags[0]` (the arrival counter) must be zero at
+// launch; `parts` holds 2 * gridDim.x * 4 doubles.
+struct FlagSync {
+  unsigned* flags;
+  double* parts;  // [2][gridDim.x][4]
+  GridSync* gs;   // abort flag
+  unsigned seq;   // reductions passed so far (identical in every thread)
+};
+
+struct NoEpilogue {
+  __device__ void operator()(const double*, double*) const {}
+};
+
+__device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide sum of NV (<= 4) values; NE (<= 4) scalars are then derived from the totals by
+// `epi` on one thread per block.  On return v[] holds the totals and out[] the epilogue
+// results, identical in every thread of the grid.  Returns false if the wait was abandoned
+// (timeout or another block aborted); the caller must leave.
+//
+// Protocol (measured fastest on GB300 among flag-per-block, last-block and counter schemes):
+// warp sums -> shared memory -> warp 0 adds the block partial, stores it in the block's slot
+// and announces it with one release reduction on a monotone arrival counter; every lane of
+// warp 0 waits (acquire) until the counter reaches seq * gridDim.x and then reads all
+// partials in block order.  Partials are double-buffered by the parity of seq because a fast
+// block may publish reduction k+1 while a slow one is still reading reduction k.
+template <int NV, int NE, typename Epi>
+__device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 0 ? NE : 1], FlagSync& fs,
+                                            double* smem, Epi epi) {
+  static_assert(NV <= 4 && NE <= 4, "grid_allsum: at most 4 sums and 4 derived scalars");
   const int nb = gridDim.x;
-  if (nb == 1) return true;
-  __shared__ int s_last;
-  __shared__ unsigned s_gen;
+  const unsigned seq = ++fs.seq;
+  const int par = seq & 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_res[8];
   __shared__ int s_ok;
-  if (threadIdx.x == 0) {
+  // warp sums into a parity-indexed shared buffer (no guard barrier needed)
+  double* sw = smem + par * (32 * 4);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) __stcg(partials + (size_t)blockIdx.x * NV + k, v[k]);
-    unsigned g = ld_acquire_u32(&gs->gen);
-    __threadfence();
-    unsigned arrived = atomicAdd(&gs->count, 1u);
-    __threadfence();
-    s_last = (arrived == (unsigned)nb - 1);
-    s_gen = g;
-    s_ok = 1;
+  for (int k = 0; k < NV; ++k) {
+    double t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sw[k * 32 + warp] = t;
   }
   __syncthreads();
-  if (s_last) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < NV) {
-      double t = 0.0;
-      for (int b = lane; b < nb; b += 32) t += __ldcg(partials + (size_t)b * NV + warp);
+  if (warp == 0) {
+    double bt[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sw[k * 32 + lane] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) __stcg(&gs->red[warp], t);
+      bt[k] = t;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicExch(&gs->count, 0u);
-      __threadfence();
-      st_release_u32(&gs->gen, s_gen + 1);
-    }
-  } else if (threadIdx.x == 0) {
-    const unsigned long long t0 = global_timer_ns();
-    unsigned spins = 0;
-    while (ld_acquire_u32(&gs->gen) == s_gen) {
-      if ((++spins & 255u) == 0) {
-        if (*((volatile int*)&gs->abort)) {
-          s_ok = 0;
-          break;
-        }
-        if (global_timer_ns() - t0 > kSpinLimitNs) {
-          atomicExch(&gs->abort, 1);
-          s_ok = 0;
-          break;
+    int ok = 1;
+    if (nb > 1) {
+      if (lane == 0) {
+        double* mine = fs.parts + ((size_t)par * nb + blockIdx.x) * 4;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) __stcg(mine + k, bt[k]);
+        red_add_release_u32(fs.flags, 1u);
+      }
+      const unsigned target = seq * (unsigned)nb;
+      const unsigned long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(fs.flags) < target) {
+        if ((++spins & 63u) == 0) {
+          if (*((volatile int*)&fs.gs->abort) || global_timer_ns() - t0 > kSpinLimitNs) {
+            ok = 0;
+            break;
+          }
         }
       }
+      ok = __all_sync(0xffffffffu, ok);
+      double acc[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+      if (ok) {
+        if (nb <= 32 * kPollUnroll) {
+          const int mine = (nb - lane + 31) / 32;
+          double pv[kPollUnroll][NV];
+#pragma unroll
+          for (int q = 0; q < kPollUnroll; ++q) {
+            const double* pb = fs.parts + ((size_t)par * nb + lane + 32 * q) * 4;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) pv[q][k] = (q < mine) ? __ldcg(pb + k) : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < kPollUnroll; ++q)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += pv[q][k];
+        } else {
+          for (int b = lane; b < nb; b += 32) {
+            const double* pb = fs.parts + ((size_t)par * nb + b) * 4;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(pb + k);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        bt[k] = acc[k];
+      }
+    }
+    if (lane == 0) {
+      s_ok = ok;
+      if (!ok) atomicExch(&fs.gs->abort, 1);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s_res[k] = bt[k];
+      double e[NE > 0 ? NE : 1];
+      epi(s_res, e);
+#pragma unroll
+      for (int k = 0; k < NE; ++k) s_res[NV + k] = e[k];
     }
   }
   __syncthreads();
   if (!s_ok) return false;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = __ldcg(&gs->red[k]);
+  for (int k = 0; k < NV; ++k) v[k] = s_res[k];
+#pragma unroll
+  for (int k = 0; k < NE; ++k) out[k] = s_res[NV + k];
   return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_allsum(double (&v)[NV], FlagSync& fs, double* smem) {
+  double dummy[1];
+  return grid_allsum<NV, 0>(v, dummy, fs, smem, NoEpilogue());
 }
 
 }  // namespace avip

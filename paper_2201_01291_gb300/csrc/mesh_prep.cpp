@@ -12,7 +12,8 @@
 //   * boundary nodal normal S_i^b = 1/2 sum of the outward normals of the boundary faces at
 //     i (Fig. bcs_normal);
 //   * Poisson matrix K_ik = sum_tau S_i.S_k / (n_d^2 V_tau) (Eq. coeff_matriceA with the sign
-//     of -lap phi = rho/eps0), Dirichlet unknowns eliminated symmetrically;
+//     of -lap phi = rho/eps0), Dirichlet unknowns eliminated symmetrically, then scaled
+//     symmetrically by its diagonal (D^-1/2 K D^-1/2) for Jacobi-preconditioned CG;
 //   * nodal gradient weights: grad u_i = (1/V_i) sum_tau (V_tau/3) grad u_tau with
 //     grad u_tau = -1/(n_d V_tau) sum_k u_k S_k, i.e. grad u_i = sum_k G_ik u_k with
 //     G_ik = -(1 / (6 V_i)) sum_{tau containing i and k} S_k^tau.
@@ -220,7 +221,6 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
   }
 
   // ---- Dirichlet elimination
-  m.dinv.assign(N, 0.0);
   m.lift.assign(N, 0.0);
   m.rhs_scale.assign(N, 0.0);
   std::vector<double> Ael(K);
@@ -243,7 +243,18 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
       m.rhs_scale[i] = kECharge * m.vol[i] / kEps0;
     }
     if (!(Ael[rowptr[i]] > 0)) return fail("non-positive Poisson diagonal");
-    m.dinv[i] = 1.0 / Ael[rowptr[i]];
+  }
+  // symmetric Jacobi scaling: Jacobi-PCG on K is plain CG on D^-1/2 K D^-1/2
+  m.dsq.assign(N, 1.0);
+  m.dsqinv.assign(N, 1.0);
+  for (int32_t i = 0; i < N; ++i) {
+    m.dsq[i] = std::sqrt(Ael[rowptr[i]]);
+    m.dsqinv[i] = 1.0 / m.dsq[i];
+  }
+  for (int32_t i = 0; i < N; ++i) {
+    for (int32_t s = rowptr[i]; s < rowptr[i + 1]; ++s) Ael[s] = Ael[s] / (m.dsq[i] * m.dsq[cols[s]]);
+    m.lift[i] *= m.dsqinv[i];
+    m.rhs_scale[i] *= m.dsqinv[i];
   }
 
   // ---- SELL-32 layout
