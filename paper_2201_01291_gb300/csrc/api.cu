@@ -304,7 +304,7 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
   h->plan = pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
   h->nparts = flux_blocks(m.N);
-  h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)h->plan.blocks;
+  h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
   ok = zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
        zalloc(h, h->sync, (h->sync_bytes + sizeof(GridSync) - 1) / sizeof(GridSync)) && zalloc(h, h->sc, 1);
   if (ok) h->flags = reinterpret_cast<unsigned*>(h->sync + 1);

@@ -130,7 +130,7 @@ struct PcgArgs {
   double* r;
   double* p;
   double* q_ap;           // scaled A p
-  unsigned* flags;        // grid barrier flags (zeroed before each launch)
+  unsigned* flags;        // [0] grid-reduction arrival counter (zeroed before each launch)
   double* parts;          // grid barrier partials, 2 * gridDim.x * 4
   GridSync* sync;
   DevScalars* sc;
@@ -143,7 +143,7 @@ struct PcgArgs {
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident
   int tpb = 768;
-  int maxs = 0;    // slices per warp (register-resident)
+  int maxs = 0;    // slices per warp (register-resident kinds)
   int blocks = 1;
 };
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);

@@ -32,6 +32,7 @@
 namespace avip {
 
 constexpr int kMaxRestarts = 8;
+constexpr int kResTPB = 512;  // block size of the register-resident kernels (one block per SM)
 
 // One row of y = A v over the SELL-32 structure (diagonal first, then ascending columns).
 // Slots are fetched in groups of 8 so that the column loads, the value loads and the
@@ -328,14 +329,20 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
         if (!grid_allsum<1, 1>(pq, one, fs, smem, [rr_now](const double* t, double* e) { e[0] = rr_now / t[0]; }))
           goto timeout;
         const double alpha = one[0];
-        // ---- phase B
+        // ---- phase B: all loads of r issued before the first store (no aliasing stall)
         double rn[1] = {0.0};
+        double rv[MAXS];
+#pragma unroll
+        for (int j = 0; j < MAXS; ++j) {
+          const int i = (gwarp * MAXS + j) * kSlice + lane;
+          rv[j] = rl[j] != 0 ? __ldcg(a.r + i) : 0.0;
+        }
 #pragma unroll
         for (int j = 0; j < MAXS; ++j) {
           const int i = (gwarp * MAXS + j) * kSlice + lane;
           if (rl[j] == 0) continue;
           x[j] = fma(alpha, p[j], x[j]);
-          const double r = fma(-alpha, q[j], a.r[i]);
+          const double r = fma(-alpha, q[j], rv[j]);
           a.r[i] = r;
           rn[0] = fma(r, r, rn[0]);
         }
@@ -396,7 +403,6 @@ static const void* pcg_kernel_ptr(int tpb) {
   }
 }
 
-constexpr int kResTPB = 512;
 static const void* pcg_res_kernel_ptr(int maxs) {
   switch (maxs) {
     case 1: return (const void*)pcg_fp64_res_kernel<kResTPB, 1>;
@@ -419,16 +425,17 @@ static int occupancy(const void* k, int tpb) {
   return occ;
 }
 
-// Choose the kernel and grid.  kind: 0 = automatic, 1 = streaming, 2 = register-resident.
+// Choose the kernel and grid.  kind: 0 = automatic (register-resident when the mesh fits in
+// one block per SM, else streaming), 1 = streaming, 2 = register-resident.
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb) {
   PcgPlan pl;
   const int sms = sm_count();
-  if (kind != 1) {
+  if (kind == 0 || kind == 2) {
     constexpr int wpb = kResTPB / kSlice;
     for (int maxs : {1, 2, 4, 8}) {
       const int blocks = (nslices + wpb * maxs - 1) / (wpb * maxs);
       const int occ = occupancy(pcg_res_kernel_ptr(maxs), kResTPB);
-      if (blocks <= sms * std::max(occ, 0) && occ > 0) {
+      if (occ > 0 && blocks <= sms * occ) {
         pl.kind = 2;
         pl.tpb = kResTPB;
         pl.maxs = maxs;
