@@ -169,6 +169,26 @@ int state_set(avip_mesh_t h, const double* host_state);
 /* Sizes of the handle: n_nodes, n_tris, n_edges, nnz of the Poisson matrix. */
 int mesh_info(avip_mesh_t h, int64_t* info4);
 
+/* No-allocation Jacobi-preconditioned CG for callers that cannot allocate device memory.
+ * The paper has no counterpart: it exists for code that must not call cudaMalloc or any
+ * allocating routine (for example while a CUDA stream is being captured, in a real-time loop
+ * with a fixed memory budget, or under a framework that owns all device memory), which also
+ * rules out mesh_create.  Such a caller places the Dirichlet-eliminated Poisson matrix (or any
+ * symmetric positive definite matrix) in device memory as CSR and solves A x = b:
+ *   row_ptr[n+1], col[nnz], val[nnz], b[n]  device pointers, read only;
+ *   x[n]  device pointer: initial guess in, solution out;
+ *   stop when ||b - A x||_2 <= rtol ||b||_2 (true residual), at most max_iter iterations;
+ *   stream: cudaStream_t the solve is queued on (NULL = default); the call waits for it.
+ * Work vectors live in one fixed array compiled into the library (AVIP_STATIC_PCG_MAX_ROWS
+ * rows, about 10.5 MB, present on every GPU that loads the library until exit).  The first
+ * call on a device looks up that array's device address; make it before any stream capture.
+ * Calls that overlap on the GPU share the array and race: order them on one stream.
+ * Returns AVIP_EINVAL for n > AVIP_STATIC_PCG_MAX_ROWS or bad arguments, AVIP_ENOTCONV when
+ * max_iter was reached (x holds the last iterate).  Allocates nothing. */
+#define AVIP_STATIC_PCG_MAX_ROWS 262144
+int pcg_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val, const double* b,
+                   double* x, double rtol, int32_t max_iter, void* stream, int32_t* iters_out, double* relres_out);
+
 /* Human-readable text of a status code (static storage). */
 const char* avip_status_str(int status);
 

@@ -70,6 +70,8 @@ _SIGS = {
     "state_size": (C.c_int, [_H, _P(C.c_int64)]),
     "state_get": (C.c_int, [_H, _D]),
     "state_set": (C.c_int, [_H, _D]),
+    "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_double, C.c_int32, C.c_void_p, _I, _D]),
     "avip_status_str": (C.c_char_p, [C.c_int]),
     "avip_last_error": (C.c_char_p, []),
 }
@@ -210,6 +212,18 @@ def state_get(h):
 def state_set(h, state):
     s = np.ascontiguousarray(state, dtype=np.float64)
     return load().state_set(h, _dptr(s))
+
+
+def pcg_csr_static(n, row_ptr, col, val, b, x, rtol, max_iter, stream=0):
+    """Jacobi-PCG on a CSR matrix already in device memory, using only the library's
+    compiled-in scratch array (no allocation).  Pointer arguments are device addresses (ints,
+    e.g. torch tensor .data_ptr()).  Returns (status, iterations, relative residual)."""
+    it = C.c_int32()
+    rr = C.c_double()
+    rc = load().pcg_csr_static(int(n), C.c_void_p(row_ptr), C.c_void_p(col), C.c_void_p(val), C.c_void_p(b),
+                               C.c_void_p(x), float(rtol), int(max_iter), C.c_void_p(stream), C.byref(it),
+                               C.byref(rr))
+    return rc, it.value, rr.value
 
 
 # ------------------------------------------------------------------ convenience wrapper
