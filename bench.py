@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65"])
     ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed = FP32 inner PCG with FP64 refinement of the Poisson residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
@@ -83,7 +85,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "500"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -150,7 +152,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
     allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
-    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads, **kw)
+    prec = avip.PREC_MIXED if args.precision == "mixed" else avip.PREC_FP64
+    m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads,
+                  precision=prec, **kw)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     # warm-up (graph capture happens here too)
     with torch.cuda.stream(stream):
@@ -230,9 +234,10 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": desc, "n_nodes": info["n_nodes"], "n_tris": T, "nnz": info["nnz"],
-                   "rtol": args.rtol, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "rtol": args.rtol, "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write inside the timed region)",
                    "seed": problem.seed},
         "e2e": {"value": world * T * e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,

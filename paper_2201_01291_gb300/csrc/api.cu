@@ -12,6 +12,7 @@
 
 namespace avip {
 cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
@@ -37,6 +38,7 @@ struct avip_mesh {
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
+  float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
   unsigned* flags = nullptr;
   double* parts = nullptr;
@@ -140,6 +142,12 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.rtol = h->opts.rtol;
   a.max_iter = h->opts.max_iter;
   a.use_density_rhs = 1;
+  a.aval32 = h->aval32;
+  a.e32 = h->e32;
+  a.r32 = h->r32;
+  a.p32 = h->p32;
+  a.q32 = h->q32;
+  a.inner_rtol = h->opts.inner_rtol;
   return a;
 }
 
@@ -178,6 +186,7 @@ int cuda_status(cudaError_t e) {
 cudaError_t enqueue_poisson(avip_mesh* h) {
   cudaError_t e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
   if (e != cudaSuccess) return e;
+  if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
 
@@ -256,7 +265,8 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   else
     avip_opts_default(&h->opts);
   if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
-      h->opts.precision != AVIP_PREC_FP64) {
+      (h->opts.precision != AVIP_PREC_FP64 && h->opts.precision != AVIP_PREC_MIXED) ||
+      (h->opts.precision == AVIP_PREC_MIXED && !(h->opts.inner_rtol > 0 && h->opts.inner_rtol < 1))) {
     delete h;
     return AVIP_EINVAL;
   }
@@ -302,10 +312,16 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   }
   // persistent PCG grid: co-resident blocks, but no more than there are slices to share
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
-  h->plan = pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
+  h->plan = h->opts.precision == AVIP_PREC_MIXED ? pcg_mixed_plan(m.nslices, h->opts.pcg_threads)
+                                                 : pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
+  if (h->opts.precision == AVIP_PREC_MIXED) {
+    std::vector<float> a32(m.aval.begin(), m.aval.end());
+    ok = upload(h, h->aval32, a32) && zalloc(h, h->e32, Np) && zalloc(h, h->r32, Np) && zalloc(h, h->p32, Np) &&
+         zalloc(h, h->q32, Np);
+  }
   h->nparts = flux_blocks(m.N);
   h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
-  ok = zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
+  ok = ok && zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
        zalloc(h, h->sync, (h->sync_bytes + sizeof(GridSync) - 1) / sizeof(GridSync)) && zalloc(h, h->sc, 1);
   if (ok) h->flags = reinterpret_cast<unsigned*>(h->sync + 1);
   if (!ok) {
@@ -527,7 +543,9 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
     DDArgs a = dd_args(h);
     e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) e = launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
+    if (e == cudaSuccess)
+      e = h->plan.kind == 4 ? launch_pcg_mixed(pcg_args(h), h->plan, h->stream)
+                            : launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess) e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);

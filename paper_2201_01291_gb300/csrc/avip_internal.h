@@ -106,7 +106,7 @@ struct DevScalars {
   int32_t run_steps;
   int32_t run_iters_total;
   int32_t run_iters_max;
-  int32_t pad;
+  int32_t pcg_outer;            // refinement steps of the last mixed-precision solve
   double run_dt_min, run_dt_max, run_relres_max;
 };
 
@@ -137,16 +137,24 @@ struct PcgArgs {
   double rtol;
   int32_t max_iter;
   int32_t use_density_rhs;  // 1: b from densities; 0: b already in `b`
+  // mixed precision: FP32 copy of the scaled matrix and FP32 inner-CG vectors
+  const float* aval32;
+  float* e32;
+  float* r32;
+  float* p32;
+  float* q32;
+  double inner_rtol;
 };
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
-  int kind = 1;    // 1 streaming, 2 register-resident
+  int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision (streaming)
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident kinds)
   int blocks = 1;
 };
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
+PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 
 struct DDArgs {
   SellView A;

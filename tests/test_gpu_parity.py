@@ -190,3 +190,33 @@ def test_tiny_and_single_slice_meshes(avip):
         for s in range(2):
             assert normwise(m.density(s), n_ref[s]) <= TOL
         assert normwise(m.phi(), phi_ref) <= TOL
+
+
+# ---------------------------------------------------------------- mixed precision
+MIXED_TOL = 1e-6
+
+
+def test_mixed_poisson_matches_oracle(avip):
+    """FP32 inner PCG + FP64 refinement reaches the FP64 answer (rtol 1e-12 on the residual)."""
+    p = W.config_small(nx=40, ny=33, seed=5)
+    o = O.Oracle(p)
+    phi_ref = o.poisson(o.initial_state())
+    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-12)
+    it, rr = m.poisson_solve()
+    assert rr <= 1e-12
+    assert normwise(m.phi(), phi_ref) <= 1e-10
+
+
+def test_mixed_plates65_2000_steps_within_1e6(avip):
+    """Mixed precision on the 65 x 65 plates mesh and physics (FP32 inner PCG with FP64
+    refinement of the Poisson residual to 1e-10): phi, n_e and n_+ within 1e-6 (norm-wise) of
+    the FP64 oracle after 2000 steps."""
+    p = W.config_plates_65()
+    o = O.Oracle(p)
+    n_ref, phi_ref, dts = o.run(2000)
+    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-10)
+    st = m.run(2000)
+    assert st["steps"] == 2000 and st["status"] == 0
+    errs = [normwise(m.density(s), n_ref[s]) for s in range(2)] + [normwise(m.phi(), phi_ref)]
+    print("mixed-precision 2000-step norm-wise errors (n_e, n_+, phi):", errs)
+    assert max(errs) <= MIXED_TOL
