@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi sampling (diagnosis only)")
     ap.add_argument("--pcg-threads", type=int, default=0, help="PCG block size (0 = library default)")
+    ap.add_argument("--pcg-kind", type=int, default=0,
+                    help="PCG kernel: 0 auto, 1 streaming, 2 register-resident, 5 cluster-resident")
     ap.add_argument("--pcg-max-iter", type=int, default=0,
                     help="cap PCG iterations per solve (profiling captures only; not a bench setting)")
     return ap.parse_args()
@@ -154,7 +156,7 @@ def run_ours(args, rank, world, local_rank):
     allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
     prec = avip.PREC_MIXED if args.precision == "mixed" else avip.PREC_FP64
     m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads,
-                  precision=prec, **kw)
+                  pcg_kind=args.pcg_kind, precision=prec, **kw)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     # warm-up (graph capture happens here too)
     with torch.cuda.stream(stream):

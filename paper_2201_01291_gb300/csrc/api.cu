@@ -13,6 +13,7 @@
 namespace avip {
 cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
@@ -46,6 +47,7 @@ struct avip_mesh {
   DevScalars* sc = nullptr;
   int32_t Npad = 0;
   PcgPlan plan;
+  ClusterLayout clay{};
   int nparts = 0;
   Physics ph;
   int species_declared = 0;
@@ -57,6 +59,7 @@ struct avip_mesh {
 namespace {
 
 thread_local char g_err[256];
+constexpr int kClusterAutoRows = 20000;  // cluster-resident PCG below this many nodes
 
 void* dev_alloc(avip_mesh* h, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -182,12 +185,17 @@ int cuda_status(cudaError_t e) {
   return AVIP_ECUDA;
 }
 
+cudaError_t enqueue_pcg_only(avip_mesh* h) {
+  if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind == 5) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
+  return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
+}
+
 // Queue one Poisson solve (cooperative PCG launch).
 cudaError_t enqueue_poisson(avip_mesh* h) {
   cudaError_t e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
   if (e != cudaSuccess) return e;
-  if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
-  return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
+  return enqueue_pcg_only(h);
 }
 
 // Queue one explicit step (no host synchronisation).
@@ -314,6 +322,19 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
   h->plan = h->opts.precision == AVIP_PREC_MIXED ? pcg_mixed_plan(m.nslices, h->opts.pcg_threads)
                                                  : pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
+  if (h->opts.precision == AVIP_PREC_FP64 && (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5)) {
+    // small meshes: one thread-block cluster with everything in shared memory
+    ClusterHost chd;
+    PcgPlan cp = pcg_cluster_plan(m, h->opts.pcg_kind == 5 ? (1 << 30) : kClusterAutoRows, &h->clay, &chd);
+    if (cp.kind == 5) {
+      int32_t *colL = nullptr, *pptr = nullptr, *pdst = nullptr;
+      ok = ok && upload(h, colL, chd.colL) && upload(h, pptr, chd.push_ptr) && upload(h, pdst, chd.push_dst, 1);
+      h->clay.colL = colL;
+      h->clay.push_ptr = pptr;
+      h->clay.push_dst = pdst;
+      h->plan = cp;
+    }
+  }
   if (h->opts.precision == AVIP_PREC_MIXED) {
     std::vector<float> a32(m.aval.begin(), m.aval.end());
     ok = upload(h, h->aval32, a32) && zalloc(h, h->e32, Np) && zalloc(h, h->r32, Np) && zalloc(h, h->p32, Np) &&
@@ -543,9 +564,7 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
     DDArgs a = dd_args(h);
     e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess)
-      e = h->plan.kind == 4 ? launch_pcg_mixed(pcg_args(h), h->plan, h->stream)
-                            : launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
+    if (e == cudaSuccess) e = enqueue_pcg_only(h);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess) e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);

@@ -148,13 +148,30 @@ struct PcgArgs {
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
-  int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision (streaming)
+  int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident
   int tpb = 768;
-  int maxs = 0;    // slices per warp (register-resident kinds)
+  int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
 };
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
+
+// Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
+struct ClusterLayout {
+  int32_t spc;        // slices per CTA
+  int32_t rows;       // spc * 32
+  int32_t hmax;       // largest halo (rows of other CTAs read by one CTA)
+  int32_t max_elems;  // largest SELL element count of one CTA's slices
+  int32_t mat_smem;   // 1: the CTA copies its matrix slices into shared memory
+  int32_t pad;
+  const int32_t* colL;      // per SELL element: local index (own row, or rows + halo slot)
+  const int32_t* push_ptr;  // per row: range of push_dst
+  const int32_t* push_dst;  // (reader rank << 24) | halo slot
+};
+struct ClusterHost {
+  std::vector<int32_t> colL, push_ptr, push_dst;
+};
+PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd);
 
 struct DDArgs {
   SellView A;

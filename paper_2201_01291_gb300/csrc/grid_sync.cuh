@@ -105,21 +105,21 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ double s_res[8];
   __shared__ int s_ok;
-  // warp sums into a parity-indexed shared buffer (no guard barrier needed)
-  double* sw = smem + par * (32 * 4);
+  // Block partial: every thread stores its values, then warp 0 adds them (lane l takes
+  // threads l, l+32, ...) and finishes with a shuffle tree.  On GB300 an FP64 add costs a
+  // warp ~16 cycles of the SM's FP64 pipe, so this uses blockDim/32 + 5 warp-wide adds per
+  // value instead of the 5 * blockDim/32 + 5 of a shuffle tree in every warp.
+  __shared__ double s_thr[4 * 1024];
+  (void)smem;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sw[k * 32 + warp] = t;
-  }
+  for (int k = 0; k < NV; ++k) s_thr[k * 1024 + threadIdx.x] = v[k];
   __syncthreads();
   if (warp == 0) {
     double bt[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double t = lane < nw ? sw[k * 32 + lane] : 0.0;
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += s_thr[k * 1024 + w * 32 + lane];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       bt[k] = t;

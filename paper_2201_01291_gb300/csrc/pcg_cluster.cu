@@ -1,0 +1,365 @@
+// Cluster-resident Jacobi-PCG (FP64) for meshes that fit in the shared memory of one
+// thread-block cluster.
+//
+// One cluster of C CTAs (C = 16 when the device allows non-portable clusters, else 8) solves
+// the whole system.  CTA `rank` owns a contiguous range of SELL-32 slices; its rows' vectors
+// x, r, p, q, b and (when it fits) its slice of the matrix stay in that CTA's shared memory
+// for the whole solve.  Each CTA also keeps a halo: the x and r entries of rows owned by other
+// CTAs that its rows reference.  Halo entries are *pushed*: when a row updates r (or x) it
+// stores the new value straight into the halo slots of the CTAs that read it, through
+// distributed shared memory (fire-and-forget stores), and the cluster barrier that follows
+// makes them visible.  Every read of an iteration is therefore a local shared-memory read.
+// Reductions are pushed the same way: every CTA writes its partial into every CTA's slot
+// table, one cluster barrier, then each CTA adds the C partials locally in rank order
+// (identical totals everywhere; deterministic).  A reduction costs one hardware cluster
+// barrier (~0.3 us on GB300) instead of the ~3.5 us of a grid-wide reduction, which is what
+// bounds small meshes with the persistent grid kernels.
+//
+// The same symmetric Jacobi scaling and CG recurrences as the grid-wide kernel are used.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "avip_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace avip {
+
+constexpr int kClusterTPB = 512;
+constexpr size_t kClusterSmemMax = 200 * 1024;
+
+// Shared memory per CTA: xs[R + H], rs[R + H], ps[R], qs[R], bs[R] (FP64), then, when the
+// matrix fits, vals[max_elems] (FP64) and cols[max_elems] (int32 local indices).
+__global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, ClusterLayout L) {
+  extern __shared__ __align__(16) double dsm[];
+  __shared__ double s_part[2][16][4];  // [parity][source rank][value]
+  __shared__ double s_thr[2 * kClusterTPB];
+  __shared__ double s_res[8];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int C = (int)cl.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int R = L.rows, H = L.hmax;
+  double* xs = dsm;
+  double* rs = xs + R + H;
+  double* ps = rs + R + H;
+  double* qs = ps + R;
+  double* bs = qs + R;
+  double* vals = bs + R;
+  int32_t* cols = reinterpret_cast<int32_t*>(vals + (L.mat_smem ? L.max_elems : 0));
+  const int N = a.A.N, nsl = a.A.nslices;
+  const int s0 = rank * L.spc, s1 = min(nsl, s0 + L.spc);
+  const int e0 = s0 < nsl ? __ldg(a.A.sl_ptr + s0) : 0;
+  const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+  unsigned seq = 0;
+
+  // one row of A v, all reads local (own rows and pushed halo)
+  auto row_dot = [&](int s, int l, int i, const double* v) -> double {
+    const int w = __ldg(a.A.sl_w + s);
+    const int rl = __ldg(a.A.rlen + i);
+    const int base = __ldg(a.A.sl_ptr + s) + l - e0;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) {
+      if (k < rl) {
+        const int e = base + k * kSlice;
+        const int c = L.mat_smem ? cols[e] : __ldg(L.colL + e0 + e);
+        const double av = L.mat_smem ? vals[e] : __ldg(a.A.aval + e0 + e);
+        acc = fma(av, v[c], acc);
+      }
+    }
+    return acc;
+  };
+  // push the value of own row i into the halo slots of the CTAs that read it
+  auto push = [&](double* v, int i, double val) {
+    const int p1 = __ldg(L.push_ptr + i + 1);
+    for (int k = __ldg(L.push_ptr + i); k < p1; ++k) {
+      const unsigned d = (unsigned)__ldg(L.push_dst + k);
+      *cl.map_shared_rank(v + R + (int)(d & 0xffffffu), (int)(d >> 24)) = val;
+    }
+  };
+  // cluster-wide sum of NV values with an epilogue evaluated once per CTA
+  auto csum = [&](int NV, double* v, auto epi) {
+    const int par = (++seq) & 1;
+    // per-thread values -> shared memory -> warp 0 adds them (few warp-wide FP64 adds)
+    for (int k = 0; k < NV; ++k) s_thr[k * kClusterTPB + threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+      double bt[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += s_thr[k * kClusterTPB + w * 32 + lane];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        bt[k] = t;
+      }
+      // lane d pushes this CTA's partial into CTA d's table
+      if (lane < C) {
+        double* dst = cl.map_shared_rank(&s_part[par][rank][0], lane);
+        for (int k = 0; k < NV; ++k) dst[k] = bt[k];
+      }
+    }
+    cl.sync();  // all partials (and all pushed halo values) are visible
+    if (warp == 0) {
+      for (int k = 0; k < NV; ++k) {
+        double t = lane < C ? s_part[par][lane][k] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_res[k] = t;
+      }
+      if (lane == 0) epi(s_res, s_res + 4);
+    }
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) v[k] = s_res[k];
+  };
+  auto none = [](const double*, double*) {};
+
+  // ---- load the matrix slices, x = D^1/2 phi (pushed to the halos), b'
+  if (L.mat_smem && s0 < nsl) {
+    const int e1 = __ldg(a.A.sl_ptr + s1);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      cols[e - e0] = __ldg(L.colL + e);
+      vals[e - e0] = __ldg(a.A.aval + e);
+    }
+  }
+  double bb[1] = {0.0};
+  for (int li = threadIdx.x; li < R; li += blockDim.x) {
+    const int i = s0 * kSlice + li;
+    double x = 0.0, b = 0.0;
+    if (i < N) {
+      x = a.dsq[i] * a.phi[i];
+      if (a.use_density_rhs) {
+        double rho = 0.0;
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+        b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      } else {
+        b = a.b[i];
+      }
+      bb[0] = fma(b, b, bb[0]);
+      push(xs, i, x);
+    }
+    xs[li] = x;
+    bs[li] = b;
+    rs[li] = ps[li] = qs[li] = 0.0;
+  }
+  csum(1, bb, none);  // also the barrier after which x (own and halo) may be read
+  const double thresh = a.rtol * a.rtol * bb[0];
+  double rr = 0.0, beta = 0.0, rr_true = 0.0;
+  bool check = true;
+  int it = 0, restarts = 0, status = AVIP_OK;
+  if (bb[0] == 0.0) {
+    for (int li = threadIdx.x; li < R; li += blockDim.x) xs[li] = 0.0;
+  } else {
+    while (true) {
+      if (check || it >= a.max_iter) {
+        // ---- true residual r = b' - A x
+        double r2[1] = {0.0};
+        for (int s = s0 + warp; s < s1; s += nw) {
+          const int i = s * kSlice + lane;
+          const int li = i - s0 * kSlice;
+          if (i >= N) continue;
+          const double r = bs[li] - row_dot(s, lane, i, xs);
+          rs[li] = r;
+          ps[li] = 0.0;
+          qs[li] = 0.0;
+          push(rs, i, r);
+          r2[0] = fma(r, r, r2[0]);
+        }
+        csum(1, r2, none);
+        rr_true = r2[0];
+        if (rr_true <= thresh) break;
+        if (it >= a.max_iter || (it > 0 && restarts >= 8)) {
+          status = AVIP_ENOTCONV;
+          break;
+        }
+        if (it > 0) ++restarts;
+        rr = rr_true;
+        beta = 0.0;
+        check = false;
+      }
+      // ---- phase A: q = A r + beta q, p = r + beta p, p.q
+      double pq[1] = {0.0};
+      for (int s = s0 + warp; s < s1; s += nw) {
+        const int i = s * kSlice + lane;
+        const int li = i - s0 * kSlice;
+        if (i >= N) continue;
+        const double w = row_dot(s, lane, i, rs);
+        const double qn = fma(beta, qs[li], w);
+        const double pn = fma(beta, ps[li], rs[li]);
+        qs[li] = qn;
+        ps[li] = pn;
+        pq[0] = fma(pn, qn, pq[0]);
+      }
+      const double rr_now = rr;
+      csum(1, pq, [rr_now](const double* t, double* e) { e[0] = rr_now / t[0]; });
+      const double alpha = s_res[4];
+      // ---- phase B: update own rows, push r to the halos that read it
+      double rn[1] = {0.0};
+      for (int s = s0 + warp; s < s1; s += nw) {
+        const int i = s * kSlice + lane;
+        const int li = i - s0 * kSlice;
+        if (i >= N) continue;
+        xs[li] = fma(alpha, ps[li], xs[li]);
+        const double r = fma(-alpha, qs[li], rs[li]);
+        rs[li] = r;
+        push(rs, i, r);
+        rn[0] = fma(r, r, rn[0]);
+      }
+      csum(1, rn, [rr_now, thresh](const double* t, double* e) {
+        e[0] = t[0] / rr_now;
+        e[1] = t[0] <= thresh ? 1.0 : 0.0;
+      });
+      beta = s_res[4];
+      check = s_res[5] != 0.0;
+      rr = rn[0];
+      ++it;
+      if (check || it >= a.max_iter) {
+        // the true residual reads x of the halo: push it, then a barrier
+        for (int s = s0 + warp; s < s1; s += nw) {
+          const int i = s * kSlice + lane;
+          if (i < N) push(xs, i, xs[i - s0 * kSlice]);
+        }
+        cl.sync();
+      }
+    }
+  }
+  // ---- phi = D^-1/2 x
+  for (int li = threadIdx.x; li < R; li += blockDim.x) {
+    const int i = s0 * kSlice + li;
+    if (i < N) {
+      a.phi[i] = a.dsqinv[i] * xs[li];
+      a.x[i] = xs[li];
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    a.sc->pcg_iters = it;
+    a.sc->pcg_status = status;
+    a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+    a.sc->pcg_bnorm = sqrt(bb[0]);
+    if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
+  }
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+// Largest cluster (16 or 8 CTAs) the device schedules for this kernel with `smem` bytes of
+// dynamic shared memory per CTA; 0 if none.
+static int cluster_size_supported(size_t smem) {
+  cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kClusterTPB);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, pcg_cluster_kernel, &cfg) == cudaSuccess && n > 0) return c;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+// Plan a cluster solve for the mesh, or return kind 0 if it does not fit.  The cluster kernel
+// runs on C SMs only, so it is chosen only for meshes small enough that the grid-wide
+// reduction latency, not FP64 throughput, would dominate (n_rows <= max_rows).  Fills the
+// host arrays of the layout: local column indices, halo push lists.
+PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd) {
+  PcgPlan pl;
+  pl.kind = 0;
+  if (m.N > max_rows) return pl;
+  for (int C : {16, 8}) {
+    const int spc = (m.nslices + C - 1) / C;
+    const int R = spc * kSlice;
+    auto owner = [&](int c) { return (c / kSlice) / spc; };
+    // halo slots per CTA: sorted distinct remote columns
+    std::vector<std::vector<int32_t>> halo(C);
+    int max_elems = 0;
+    for (int r = 0; r < C; ++r) {
+      const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
+      if (s0 >= s1) continue;
+      max_elems = std::max(max_elems, m.sl_ptr[s1] - m.sl_ptr[s0]);
+      for (int s = s0; s < s1; ++s)
+        for (int l = 0; l < kSlice; ++l) {
+          const int i = s * kSlice + l;
+          if (i >= m.N) continue;
+          for (int k = 0; k < m.rlen[i]; ++k) {
+            const int c = m.col[(int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l];
+            if (owner(c) != r) halo[r].push_back(c);
+          }
+        }
+      std::sort(halo[r].begin(), halo[r].end());
+      halo[r].erase(std::unique(halo[r].begin(), halo[r].end()), halo[r].end());
+    }
+    int H = 0;
+    for (auto& h : halo) H = std::max<int>(H, (int)h.size());
+    const size_t vec = sizeof(double) * (5 * (size_t)R + 2 * (size_t)H);
+    const size_t mat = (sizeof(double) + sizeof(int32_t)) * (size_t)max_elems;
+    const int mat_smem = vec + mat <= kClusterSmemMax ? 1 : 0;
+    const size_t smem = vec + (mat_smem ? mat : 0);
+    if (smem > kClusterSmemMax) continue;
+    if (cluster_size_supported(smem) < C) continue;
+    // local column indices and push lists
+    hd->colL.assign(m.col.size(), 0);
+    std::vector<std::vector<uint32_t>> dst(m.N);
+    for (int r = 0; r < C; ++r) {
+      const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
+      for (int s = s0; s < s1; ++s)
+        for (int l = 0; l < kSlice; ++l) {
+          const int i = s * kSlice + l;
+          if (i >= m.N) continue;
+          for (int k = 0; k < m.rlen[i]; ++k) {
+            const int64_t e = (int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l;
+            const int c = m.col[e];
+            if (owner(c) == r) {
+              hd->colL[e] = c - r * R;
+            } else {
+              const int slot = (int)(std::lower_bound(halo[r].begin(), halo[r].end(), c) - halo[r].begin());
+              hd->colL[e] = R + slot;
+            }
+          }
+        }
+      for (size_t h = 0; h < halo[r].size(); ++h) dst[halo[r][h]].push_back(((uint32_t)r << 24) | (uint32_t)h);
+    }
+    hd->push_ptr.assign(m.N + 1, 0);
+    hd->push_dst.clear();
+    for (int i = 0; i < m.N; ++i) {
+      for (uint32_t d : dst[i]) hd->push_dst.push_back((int32_t)d);
+      hd->push_ptr[i + 1] = (int32_t)hd->push_dst.size();
+    }
+    out->spc = spc;
+    out->rows = R;
+    out->hmax = H;
+    out->max_elems = max_elems;
+    out->mat_smem = mat_smem;
+    pl.kind = 5;
+    pl.tpb = kClusterTPB;
+    pl.blocks = C;
+    pl.maxs = (int)smem;  // dynamic shared memory bytes
+    return pl;
+  }
+  return pl;
+}
+
+cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.blocks);
+  cfg.blockDim = dim3(pl.tpb);
+  cfg.dynamicSmemBytes = (size_t)pl.maxs;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.blocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel, args, L);
+}
+
+}  // namespace avip

@@ -220,3 +220,17 @@ def test_mixed_plates65_2000_steps_within_1e6(avip):
     errs = [normwise(m.density(s), n_ref[s]) for s in range(2)] + [normwise(m.phi(), phi_ref)]
     print("mixed-precision 2000-step norm-wise errors (n_e, n_+, phi):", errs)
     assert max(errs) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("kind", [1, 2, 5])
+def test_every_pcg_kernel_matches_oracle(avip, kind):
+    """Streaming (1), register-resident (2) and cluster-resident (5) FP64 solvers, forced on a
+    mesh of 71 x 53 nodes (ragged last slice), give the oracle's step."""
+    p = W.plates_problem(71, 53, 1e-2, 0.8e-2, 1.5e4, seed=31, field_dependent=True, source=W.SRC_TOWNSEND)
+    o = O.Oracle(p)
+    n_ref, phi_ref, _ = o.run(6)
+    m = avip.Mesh(p, rtol=1e-13, pcg_kind=kind)
+    m.run(6)
+    for s in range(2):
+        assert normwise(m.density(s), n_ref[s]) <= TOL
+    assert normwise(m.phi(), phi_ref) <= TOL
