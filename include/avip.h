@@ -169,6 +169,26 @@ int state_set(avip_mesh_t h, const double* host_state);
 /* Sizes of the handle: n_nodes, n_tris, n_edges, nnz of the Poisson matrix. */
 int mesh_info(avip_mesh_t h, int64_t* info4);
 
+/* ---- batches (many independent instances per step) -------------------------------------
+ * A batch advances several mesh handles together: per step, one persistent launch solves the
+ * Poisson system of every instance (one thread-block cluster per instance at a time, largest
+ * instances first), then one launch per drift-diffusion stage covers every instance; the step
+ * is captured as a CUDA graph and replayed.  Each instance keeps its own state, time step and
+ * statistics, and gives the same result alone and in the batch (tests check it).
+ *   meshes[count]: FP64 handles with every species set; they must outlive the batch and must
+ *                  not be stepped on their own while the batch runs;
+ *   cluster_size:  8 or 16 CTAs per cluster, or 0 to pick by timing both on the batch (the
+ *                  instances' state is saved and restored around the trial).
+ * AVIP_EINVAL if an instance does not fit one cluster's shared memory (the cluster kernel holds
+ * every vector of its instance there; about 100k nodes at most). */
+typedef struct avip_batch* avip_batch_t;
+int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size, avip_batch_t* out);
+/* nsteps steps of every instance; stats[count] (may be NULL) receives per-instance statistics. */
+int batch_run_steps(avip_batch_t b, int32_t nsteps, avip_stats* stats);
+/* info[4] = {cluster size, resident clusters, dynamic shared memory bytes per CTA, count}. */
+int batch_info(avip_batch_t b, int64_t* info);
+int batch_destroy(avip_batch_t b);
+
 /* No-allocation Jacobi-preconditioned CG for callers that cannot allocate device memory.
  * The paper has no counterpart: it exists for code that must not call cudaMalloc or any
  * allocating routine (for example while a CUDA stream is being captured, in a real-time loop

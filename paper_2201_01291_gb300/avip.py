@@ -70,6 +70,10 @@ _SIGS = {
     "state_size": (C.c_int, [_H, _P(C.c_int64)]),
     "state_get": (C.c_int, [_H, _D]),
     "state_set": (C.c_int, [_H, _D]),
+    "batch_create": (C.c_int, [_P(_H), C.c_int32, C.c_int32, _P(_H)]),
+    "batch_run_steps": (C.c_int, [_H, C.c_int32, C.c_void_p]),
+    "batch_info": (C.c_int, [_H, _P(C.c_int64)]),
+    "batch_destroy": (C.c_int, [_H]),
     "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_int32, C.c_void_p, _I, _D]),
     "avip_status_str": (C.c_char_p, [C.c_int]),
@@ -226,6 +230,29 @@ def pcg_csr_static(n, row_ptr, col, val, b, x, rtol, max_iter, stream=0):
     return rc, it.value, rr.value
 
 
+def batch_create(handles, cluster_size=0):
+    arr = (_H * len(handles))(*[h.value if isinstance(h, _H) else h for h in handles])
+    b = _H()
+    rc = load().batch_create(arr, len(handles), int(cluster_size), C.byref(b))
+    return rc, b
+
+
+def batch_run_steps(b, nsteps, count):
+    st = (AvipStats * count)()
+    rc = load().batch_run_steps(b, int(nsteps), C.cast(st, C.c_void_p))
+    return rc, [x.as_dict() for x in st]
+
+
+def batch_info(b):
+    info = np.zeros(4, dtype=np.int64)
+    _check(load().batch_info(b, info.ctypes.data_as(_P(C.c_int64))), "batch_info")
+    return dict(cluster_size=int(info[0]), clusters=int(info[1]), smem_bytes=int(info[2]), count=int(info[3]))
+
+
+def batch_destroy(b):
+    return load().batch_destroy(b)
+
+
 # ------------------------------------------------------------------ convenience wrapper
 def torch_allocator():
     """(alloc, free) callbacks drawing device memory from PyTorch's caching allocator."""
@@ -334,3 +361,31 @@ class Mesh:
 
     def set_state(self, st):
         _check(state_set(self.h, st), "state_set")
+
+
+class Batch:
+    """Several Mesh objects advanced together (see batch_create in the C header).  The meshes
+    must stay alive, and must not be stepped on their own, while the batch exists."""
+
+    def __init__(self, meshes, cluster_size=0):
+        self.meshes = list(meshes)
+        rc, b = batch_create([m.h for m in self.meshes], cluster_size)
+        _check(rc, "batch_create")
+        self.b = b
+        self.info = batch_info(b)
+
+    def run(self, nsteps, allow=(AVIP_OK,)):
+        rc, st = batch_run_steps(self.b, nsteps, len(self.meshes))
+        _check(rc, "batch_run_steps", allow)
+        return st
+
+    def close(self):
+        if getattr(self, "b", None):
+            batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

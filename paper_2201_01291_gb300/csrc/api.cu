@@ -2,6 +2,7 @@
 // of one explicit step, CUDA-graph replay of the time loop, host <-> device field copies.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -673,6 +674,294 @@ int state_set(avip_mesh_t h, const double* in) {
   e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return cuda_status(e);
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Batches: many independent discharge instances advanced together.  One step of a batch is
+// one persistent cluster-resident PCG launch for every instance (each resident cluster solves
+// instances in decreasing-size order) followed by one launch per drift-diffusion stage that
+// covers every instance's nodes or cells; the step is captured once as a CUDA graph and
+// replayed.  The cluster size is either given or picked by timing the candidates on the
+// batch itself (state saved and restored around the trial).
+namespace avip {
+int cluster_batch_capacity(int C, size_t smem);
+PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd);
+cudaError_t launch_pcg_cluster_batch(const PcgArgs* args, const ClusterLayout* lays, const int32_t* order, int count,
+                                     int C, int nclusters, size_t smem, cudaStream_t st);
+cudaError_t launch_dd_batch(const DDArgs* args, const int32_t* node_pref, const int32_t* cell_pref, int count,
+                            int node_blocks, int cell_blocks, cudaStream_t st);
+cudaError_t launch_run_reset_batch(const DDArgs* args, int count, cudaStream_t st);
+int dd_threads();
+}  // namespace avip
+
+struct avip_batch {
+  std::vector<avip_mesh*> m;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  int C = 16, nclusters = 0;
+  size_t smem = 0;
+  PcgArgs* d_pargs = nullptr;
+  ClusterLayout* d_lays = nullptr;
+  DDArgs* d_dargs = nullptr;
+  int32_t *d_order = nullptr, *d_npref = nullptr, *d_cpref = nullptr;
+  int node_blocks = 0, cell_blocks = 0;
+  cudaGraphExec_t graph = nullptr;
+  // per candidate cluster size: layouts (device arrays owned by the batch)
+  std::vector<ClusterLayout> lays;
+};
+
+namespace {
+
+void* batch_alloc(avip_batch* b, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  b->allocs.push_back(p);
+  return p;
+}
+
+template <typename T>
+T* batch_upload(avip_batch* b, const std::vector<T>& v) {
+  T* d = static_cast<T*>(batch_alloc(b, v.size() * sizeof(T)));
+  if (d && !v.empty() && cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+void batch_free(avip_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+}
+
+// Build the device tables for cluster size C; false if some instance does not fit.
+bool batch_configure(avip_batch* b, int C) {
+  const int n = (int)b->m.size();
+  std::vector<ClusterLayout> lays(n);
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    ClusterHost hd;
+    PcgPlan p = pcg_cluster_plan_fixed(b->m[k]->hm, C, &lays[k], &hd);
+    if (p.kind != 5) return false;
+    smem = std::max(smem, (size_t)p.maxs);
+    lays[k].colL = batch_upload(b, hd.colL);
+    lays[k].push_ptr = batch_upload(b, hd.push_ptr);
+    std::vector<int32_t> pd = hd.push_dst;
+    if (pd.empty()) pd.push_back(0);
+    lays[k].push_dst = batch_upload(b, pd);
+    if (!lays[k].colL || !lays[k].push_ptr || !lays[k].push_dst) return false;
+  }
+  const int cap = cluster_batch_capacity(C, smem);
+  if (cap < 1) return false;
+  b->C = C;
+  b->smem = smem;
+  b->nclusters = std::min(cap, n);
+  b->lays = lays;
+  b->d_lays = batch_upload(b, lays);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  return b->d_lays != nullptr;
+}
+
+cudaError_t batch_enqueue_step(avip_batch* b) {
+  cudaError_t e = launch_pcg_cluster_batch(b->d_pargs, b->d_lays, b->d_order, (int)b->m.size(), b->C, b->nclusters,
+                                           b->smem, b->stream);
+  if (e != cudaSuccess) return e;
+  return launch_dd_batch(b->d_dargs, b->d_npref, b->d_cpref, (int)b->m.size(), b->node_blocks, b->cell_blocks,
+                         b->stream);
+}
+
+// Save (dir = 0) or restore (dir = 1) every instance's densities, potential and scalars.
+cudaError_t batch_snapshot(avip_batch* b, std::vector<void*>& buf, int dir) {
+  cudaError_t e = cudaSuccess;
+  size_t j = 0;
+  for (avip_mesh* h : b->m) {
+    const size_t nb = (size_t)2 * AVIP_MAX_SPECIES * h->Npad * sizeof(double);
+    const size_t pb = (size_t)h->Npad * sizeof(double);
+    struct Item { void* dev; size_t bytes; } items[3] = {{h->nbuf, nb}, {h->phi, pb}, {h->sc, sizeof(DevScalars)}};
+    for (auto& it : items) {
+      if (dir == 0) {
+        void* p = batch_alloc(b, it.bytes);
+        if (!p) return cudaErrorMemoryAllocation;
+        buf.push_back(p);
+        e = cudaMemcpyAsync(p, it.dev, it.bytes, cudaMemcpyDeviceToDevice, b->stream);
+      } else {
+        e = cudaMemcpyAsync(it.dev, buf[j++], it.bytes, cudaMemcpyDeviceToDevice, b->stream);
+      }
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size, avip_batch_t* out) {
+  if (!meshes || count < 1 || !out || (cluster_size != 0 && cluster_size != 8 && cluster_size != 16))
+    return AVIP_EINVAL;
+  *out = nullptr;
+  avip_batch* b = new (std::nothrow) avip_batch();
+  if (!b) return AVIP_ENOMEM;
+  for (int k = 0; k < count; ++k) {
+    avip_mesh* h = meshes[k];
+    if (!ready(h) || h->opts.precision != AVIP_PREC_FP64) {
+      delete b;
+      return h ? AVIP_ESTATE : AVIP_EINVAL;
+    }
+    cudaStreamSynchronize(h->stream);
+    b->m.push_back(h);
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return AVIP_ECUDA;
+  }
+  // argument tables, decreasing-size order, block prefix sums
+  std::vector<PcgArgs> pa(count);
+  std::vector<DDArgs> da(count);
+  std::vector<int32_t> order(count), npref(count + 1, 0), cpref(count + 1, 0);
+  const int T = dd_threads();
+  for (int k = 0; k < count; ++k) {
+    pa[k] = pcg_args(b->m[k]);
+    da[k] = dd_args(b->m[k]);
+    da[k].partials = b->m[k]->qpart;
+    order[k] = k;
+    npref[k + 1] = npref[k] + (b->m[k]->hm.N + T - 1) / T;
+    cpref[k + 1] = cpref[k] + (b->m[k]->hm.T + T - 1) / T;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->m[x]->hm.N > b->m[y]->hm.N; });
+  b->node_blocks = npref[count];
+  b->cell_blocks = cpref[count];
+  b->d_pargs = batch_upload(b, pa);
+  b->d_dargs = batch_upload(b, da);
+  b->d_order = batch_upload(b, order);
+  b->d_npref = batch_upload(b, npref);
+  b->d_cpref = batch_upload(b, cpref);
+  if (!b->d_pargs || !b->d_dargs || !b->d_order || !b->d_npref || !b->d_cpref) {
+    batch_free(b);
+    cudaStreamDestroy(b->stream);
+    delete b;
+    return AVIP_ENOMEM;
+  }
+  bool ok = false;
+  if (cluster_size != 0) {
+    ok = batch_configure(b, cluster_size);
+  } else {
+    // autotune: time two steps per feasible cluster size on the batch itself, then restore
+    std::vector<void*> snap;
+    cudaError_t e = batch_snapshot(b, snap, 0);
+    float best = 0.f;
+    int bestC = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int C : {16, 8}) {
+      if (e != cudaSuccess || !batch_configure(b, C)) continue;
+      e = cudaEventRecord(e0, b->stream);
+      for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = batch_enqueue_step(b);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (bestC == 0 || ms < best)) {
+        best = ms;
+        bestC = C;
+      }
+      if (e == cudaSuccess) e = batch_snapshot(b, snap, 1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess && bestC != 0) ok = batch_configure(b, bestC);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) ok = false;
+  }
+  if (!ok) {
+    std::snprintf(g_err, sizeof(g_err), "batch: an instance does not fit the cluster shared memory");
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    cudaStreamDestroy(b->stream);
+    delete b;
+    return AVIP_EINVAL;
+  }
+  *out = b;
+  return AVIP_OK;
+}
+
+int batch_destroy(avip_batch_t b) {
+  if (!b) return AVIP_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  cudaStreamDestroy(b->stream);
+  delete b;
+  return AVIP_OK;
+}
+
+int batch_info(avip_batch_t b, int64_t* info) {
+  if (!b || !info) return AVIP_EINVAL;
+  info[0] = b->C;
+  info[1] = b->nclusters;
+  info[2] = (int64_t)b->smem;
+  info[3] = (int64_t)b->m.size();
+  return AVIP_OK;
+}
+
+int batch_run_steps(avip_batch_t b, int32_t nsteps, avip_stats* stats) {
+  if (!b || nsteps < 0) return AVIP_EINVAL;
+  const int n = (int)b->m.size();
+  std::vector<DevScalars> s0(n);
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e = cudaMemcpyAsync(&s0[k], b->m[k]->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  cudaError_t e = launch_run_reset_batch(b->d_dargs, n, b->stream);
+  if (e == cudaSuccess && !b->graph && nsteps > 1) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = batch_enqueue_step(b);
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->graph = nullptr;
+      e = cudaSuccess;
+    }
+  }
+  for (int32_t s = 0; s < nsteps && e == cudaSuccess; ++s)
+    e = b->graph ? cudaGraphLaunch(b->graph, b->stream) : batch_enqueue_step(b);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::vector<DevScalars> sc(n);
+  for (int k = 0; k < n && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(&sc[k], b->m[k]->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int status = AVIP_OK;
+  for (int k = 0; k < n; ++k) {
+    if (stats) {
+      stats[k].steps = sc[k].run_steps;
+      stats[k].pcg_iters_total = sc[k].run_iters_total;
+      stats[k].pcg_iters_max = sc[k].run_iters_max;
+      stats[k].status = sc[k].status;
+      stats[k].dt_min = sc[k].run_dt_min;
+      stats[k].dt_max = sc[k].run_dt_max;
+      stats[k].t = sc[k].t;
+      stats[k].charge = sc[k].charge;
+      stats[k].charge_start = s0[k].charge;
+      stats[k].relres_max = sc[k].run_relres_max;
+    }
+    if (status == AVIP_OK && sc[k].status != AVIP_OK) status = sc[k].status;
+  }
+  return status;
 }
 
 }  // extern "C"

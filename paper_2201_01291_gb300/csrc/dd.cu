@@ -52,8 +52,8 @@ __device__ __forceinline__ void block_min_to_global(double v, unsigned long long
 }
 
 // ------------------------------------------------------------------------ nodal fields
-__global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int with_dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, int bid) {
+  const int i = bid * blockDim.x + threadIdx.x;
   const int N = a.A.N;
   const int ns = a.ph.ns;
   double chem = INFINITY;
@@ -138,9 +138,13 @@ __global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int w
   if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
 }
 
+__global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int with_dt) {
+  node_fields_body(a, with_dt, blockIdx.x);
+}
+
 // ------------------------------------------------------------------------ time step
-__global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
+  const int c = bid * blockDim.x + threadIdx.x;
   double cand = INFINITY;
   if (c < a.T) {
     const int n0 = a.tri[c], n1 = a.tri[a.T + c], n2 = a.tri[2 * a.T + c];
@@ -166,6 +170,8 @@ __global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) {
   }
   block_min_to_global(cand, &a.sc->dt_bits);
 }
+
+__global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) { dt_cells_body(a, blockIdx.x); }
 
 // ------------------------------------------------------------------------ fluxes + update
 struct EdgeEnd {
@@ -195,8 +201,8 @@ __device__ __forceinline__ double edge_flux(const EdgeEnd& lo, const EdgeEnd& hi
   return fc + fd;
 }
 
-__global__ void __launch_bounds__(kDDThreads) flux_update_kernel(DDArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
+  const int i = bid * blockDim.x + threadIdx.x;
   const int N = a.A.N;
   const int ns = a.ph.ns;
   const double dt = a.ph.dt_fixed > 0.0 ? a.ph.dt_fixed : __longlong_as_double((long long)a.sc->dt_bits);
@@ -274,13 +280,15 @@ __global__ void __launch_bounds__(kDDThreads) flux_update_kernel(DDArgs a) {
     double t = ln < nw ? sm[ln] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (ln == 0) a.partials[blockIdx.x] = t;
+    if (ln == 0) a.partials[bid] = t;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->dt = dt;
+  if (bid == 0 && threadIdx.x == 0) a.sc->dt = dt;
 }
 
+__global__ void __launch_bounds__(kDDThreads) flux_update_kernel(DDArgs a) { flux_update_body(a, blockIdx.x); }
+
 // Single block: charge in block order, time, parity, statistics; re-arm the dt minimum.
-__global__ void finalize_kernel(DevScalars* sc, const double* partials, int nparts) {
+__device__ __forceinline__ void finalize_body(DevScalars* sc, const double* partials, int nparts) {
   __shared__ double sm[32];
   double t = 0.0;
   for (int b = threadIdx.x; b < nparts; b += blockDim.x) t += partials[b];
@@ -309,7 +317,58 @@ __global__ void finalize_kernel(DevScalars* sc, const double* partials, int npar
   }
 }
 
+__global__ void finalize_kernel(DevScalars* sc, const double* partials, int nparts) {
+  finalize_body(sc, partials, nparts);
+}
+
 __global__ void run_reset_kernel(DevScalars* sc) {
+  sc->run_steps = 0;
+  sc->run_iters_total = 0;
+  sc->run_iters_max = 0;
+  sc->run_dt_min = INFINITY;
+  sc->run_dt_max = 0.0;
+  sc->run_relres_max = 0.0;
+  sc->status = AVIP_OK;
+}
+
+// ------------------------------------------------------------------------ batched forms
+// One launch covers every instance of a batch: block b belongs to the instance k with
+// bpref[k] <= b < bpref[k + 1] and runs that instance's block b - bpref[k].
+__device__ __forceinline__ int batch_instance(const int32_t* __restrict__ bpref, int count, int b) {
+  int lo = 0, hi = count;  // largest k with bpref[k] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(bpref + mid) <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kDDThreads) node_fields_batch_kernel(const DDArgs* __restrict__ args,
+                                                                        const int32_t* __restrict__ bpref, int count) {
+  const int k = batch_instance(bpref, count, blockIdx.x);
+  const DDArgs& a = args[k];
+  node_fields_body(a, a.ph.dt_fixed > 0.0 ? 0 : 1, blockIdx.x - __ldg(bpref + k));
+}
+__global__ void __launch_bounds__(kDDThreads) dt_cells_batch_kernel(const DDArgs* __restrict__ args,
+                                                                     const int32_t* __restrict__ bpref, int count) {
+  const int k = batch_instance(bpref, count, blockIdx.x);
+  const DDArgs& a = args[k];
+  if (a.ph.dt_fixed > 0.0) return;
+  dt_cells_body(a, blockIdx.x - __ldg(bpref + k));
+}
+__global__ void __launch_bounds__(kDDThreads) flux_update_batch_kernel(const DDArgs* __restrict__ args,
+                                                                        const int32_t* __restrict__ bpref, int count) {
+  const int k = batch_instance(bpref, count, blockIdx.x);
+  flux_update_body(args[k], blockIdx.x - __ldg(bpref + k));
+}
+__global__ void finalize_batch_kernel(const DDArgs* __restrict__ args, int count) {
+  const DDArgs& a = args[blockIdx.x];
+  finalize_body(a.sc, a.partials, (a.A.N + kDDThreads - 1) / kDDThreads);
+}
+__global__ void run_reset_batch_kernel(const DDArgs* __restrict__ args, int count) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  DevScalars* sc = args[k].sc;
   sc->run_steps = 0;
   sc->run_iters_total = 0;
   sc->run_iters_max = 0;
@@ -343,5 +402,19 @@ cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st) {
   return cudaGetLastError();
 }
 int flux_blocks(int N) { return nblk(N); }
+
+cudaError_t launch_dd_batch(const DDArgs* args, const int32_t* node_pref, const int32_t* cell_pref, int count,
+                            int node_blocks, int cell_blocks, cudaStream_t st) {
+  node_fields_batch_kernel<<<node_blocks, kDDThreads, 0, st>>>(args, node_pref, count);
+  dt_cells_batch_kernel<<<cell_blocks, kDDThreads, 0, st>>>(args, cell_pref, count);
+  flux_update_batch_kernel<<<node_blocks, kDDThreads, 0, st>>>(args, node_pref, count);
+  finalize_batch_kernel<<<count, 256, 0, st>>>(args, count);
+  return cudaGetLastError();
+}
+cudaError_t launch_run_reset_batch(const DDArgs* args, int count, cudaStream_t st) {
+  run_reset_batch_kernel<<<(count + 127) / 128, 128, 0, st>>>(args, count);
+  return cudaGetLastError();
+}
+int dd_threads() { return kDDThreads; }
 
 }  // namespace avip

@@ -33,7 +33,8 @@ constexpr size_t kClusterSmemMax = 200 * 1024;
 
 // Shared memory per CTA: xs[R + H], rs[R + H], ps[R], qs[R], bs[R] (FP64), then, when the
 // matrix fits, vals[max_elems] (FP64) and cols[max_elems] (int32 local indices).
-__global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, ClusterLayout L) {
+// One complete solve of the system described by (a, L) by the calling cluster.
+__device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
   extern __shared__ __align__(16) double dsm[];
   __shared__ double s_part[2][16][4];  // [parity][source rank][value]
   __shared__ double s_thr[2 * kClusterTPB];
@@ -254,6 +255,27 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, 
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
+__global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, ClusterLayout L) {
+  cluster_solve(a, L);
+}
+
+// Batched, persistent: every resident cluster solves instances order[c], order[c + nclusters],
+// ... (the order is sorted by decreasing size, so the largest solves start first).
+__global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const PcgArgs* __restrict__ args,
+                                                                            const ClusterLayout* __restrict__ lays,
+                                                                            const int32_t* __restrict__ order,
+                                                                            int count) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+  for (int j = cid; j < count; j += ncl) {
+    const int k = order[j];
+    const PcgArgs a = args[k];
+    const ClusterLayout L = lays[k];
+    cluster_solve(a, L);
+  }
+}
+
 // Largest cluster (16 or 8 CTAs) the device schedules for this kernel with `smem` bytes of
 // dynamic shared memory per CTA; 0 if none.
 static int cluster_size_supported(size_t smem) {
@@ -282,79 +304,90 @@ static int cluster_size_supported(size_t smem) {
 // runs on C SMs only, so it is chosen only for meshes small enough that the grid-wide
 // reduction latency, not FP64 throughput, would dominate (n_rows <= max_rows).  Fills the
 // host arrays of the layout: local column indices, halo push lists.
+PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd) {
+  PcgPlan pl;
+  pl.kind = 0;
+  const int spc = (m.nslices + C - 1) / C;
+  const int R = spc * kSlice;
+  auto owner = [&](int c) { return (c / kSlice) / spc; };
+  // halo slots per CTA: sorted distinct remote columns
+  std::vector<std::vector<int32_t>> halo(C);
+  int max_elems = 0;
+  for (int r = 0; r < C; ++r) {
+    const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
+    if (s0 >= s1) continue;
+    max_elems = std::max(max_elems, m.sl_ptr[s1] - m.sl_ptr[s0]);
+    for (int s = s0; s < s1; ++s)
+      for (int l = 0; l < kSlice; ++l) {
+        const int i = s * kSlice + l;
+        if (i >= m.N) continue;
+        for (int k = 0; k < m.rlen[i]; ++k) {
+          const int c = m.col[(int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l];
+          if (owner(c) != r) halo[r].push_back(c);
+        }
+      }
+    std::sort(halo[r].begin(), halo[r].end());
+    halo[r].erase(std::unique(halo[r].begin(), halo[r].end()), halo[r].end());
+  }
+  int H = 0;
+  for (auto& h : halo) H = std::max<int>(H, (int)h.size());
+  const size_t vec = sizeof(double) * (5 * (size_t)R + 2 * (size_t)H);
+  const size_t mat = (sizeof(double) + sizeof(int32_t)) * (size_t)max_elems;
+  const int mat_smem = vec + mat <= kClusterSmemMax ? 1 : 0;
+  const size_t smem = vec + (mat_smem ? mat : 0);
+  if (smem > kClusterSmemMax) return pl;
+  // local column indices and push lists
+  hd->colL.assign(m.col.size(), 0);
+  std::vector<std::vector<uint32_t>> dst(m.N);
+  for (int r = 0; r < C; ++r) {
+    const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
+    for (int s = s0; s < s1; ++s)
+      for (int l = 0; l < kSlice; ++l) {
+        const int i = s * kSlice + l;
+        if (i >= m.N) continue;
+        for (int k = 0; k < m.rlen[i]; ++k) {
+          const int64_t e = (int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l;
+          const int c = m.col[e];
+          if (owner(c) == r) {
+            hd->colL[e] = c - r * R;
+          } else {
+            const int slot = (int)(std::lower_bound(halo[r].begin(), halo[r].end(), c) - halo[r].begin());
+            hd->colL[e] = R + slot;
+          }
+        }
+      }
+    for (size_t h = 0; h < halo[r].size(); ++h) dst[halo[r][h]].push_back(((uint32_t)r << 24) | (uint32_t)h);
+  }
+  hd->push_ptr.assign(m.N + 1, 0);
+  hd->push_dst.clear();
+  for (int i = 0; i < m.N; ++i) {
+    for (uint32_t d : dst[i]) hd->push_dst.push_back((int32_t)d);
+    hd->push_ptr[i + 1] = (int32_t)hd->push_dst.size();
+  }
+  out->spc = spc;
+  out->rows = R;
+  out->hmax = H;
+  out->max_elems = max_elems;
+  out->mat_smem = mat_smem;
+  pl.kind = 5;
+  pl.tpb = kClusterTPB;
+  pl.blocks = C;
+  pl.maxs = (int)smem;  // dynamic shared memory bytes
+  return pl;
+}
+
 PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd) {
   PcgPlan pl;
   pl.kind = 0;
   if (m.N > max_rows) return pl;
   for (int C : {16, 8}) {
-    const int spc = (m.nslices + C - 1) / C;
-    const int R = spc * kSlice;
-    auto owner = [&](int c) { return (c / kSlice) / spc; };
-    // halo slots per CTA: sorted distinct remote columns
-    std::vector<std::vector<int32_t>> halo(C);
-    int max_elems = 0;
-    for (int r = 0; r < C; ++r) {
-      const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
-      if (s0 >= s1) continue;
-      max_elems = std::max(max_elems, m.sl_ptr[s1] - m.sl_ptr[s0]);
-      for (int s = s0; s < s1; ++s)
-        for (int l = 0; l < kSlice; ++l) {
-          const int i = s * kSlice + l;
-          if (i >= m.N) continue;
-          for (int k = 0; k < m.rlen[i]; ++k) {
-            const int c = m.col[(int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l];
-            if (owner(c) != r) halo[r].push_back(c);
-          }
-        }
-      std::sort(halo[r].begin(), halo[r].end());
-      halo[r].erase(std::unique(halo[r].begin(), halo[r].end()), halo[r].end());
-    }
-    int H = 0;
-    for (auto& h : halo) H = std::max<int>(H, (int)h.size());
-    const size_t vec = sizeof(double) * (5 * (size_t)R + 2 * (size_t)H);
-    const size_t mat = (sizeof(double) + sizeof(int32_t)) * (size_t)max_elems;
-    const int mat_smem = vec + mat <= kClusterSmemMax ? 1 : 0;
-    const size_t smem = vec + (mat_smem ? mat : 0);
-    if (smem > kClusterSmemMax) continue;
-    if (cluster_size_supported(smem) < C) continue;
-    // local column indices and push lists
-    hd->colL.assign(m.col.size(), 0);
-    std::vector<std::vector<uint32_t>> dst(m.N);
-    for (int r = 0; r < C; ++r) {
-      const int s0 = r * spc, s1 = std::min(m.nslices, s0 + spc);
-      for (int s = s0; s < s1; ++s)
-        for (int l = 0; l < kSlice; ++l) {
-          const int i = s * kSlice + l;
-          if (i >= m.N) continue;
-          for (int k = 0; k < m.rlen[i]; ++k) {
-            const int64_t e = (int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l;
-            const int c = m.col[e];
-            if (owner(c) == r) {
-              hd->colL[e] = c - r * R;
-            } else {
-              const int slot = (int)(std::lower_bound(halo[r].begin(), halo[r].end(), c) - halo[r].begin());
-              hd->colL[e] = R + slot;
-            }
-          }
-        }
-      for (size_t h = 0; h < halo[r].size(); ++h) dst[halo[r][h]].push_back(((uint32_t)r << 24) | (uint32_t)h);
-    }
-    hd->push_ptr.assign(m.N + 1, 0);
-    hd->push_dst.clear();
-    for (int i = 0; i < m.N; ++i) {
-      for (uint32_t d : dst[i]) hd->push_dst.push_back((int32_t)d);
-      hd->push_ptr[i + 1] = (int32_t)hd->push_dst.size();
-    }
-    out->spc = spc;
-    out->rows = R;
-    out->hmax = H;
-    out->max_elems = max_elems;
-    out->mat_smem = mat_smem;
-    pl.kind = 5;
-    pl.tpb = kClusterTPB;
-    pl.blocks = C;
-    pl.maxs = (int)smem;  // dynamic shared memory bytes
-    return pl;
+    ClusterLayout L{};
+    ClusterHost H;
+    PcgPlan p = pcg_cluster_plan_fixed(m, C, &L, &H);
+    if (p.kind != 5 || cluster_size_supported((size_t)p.maxs) < C) continue;
+    *out = L;
+    *hd = std::move(H);
+    return p;
   }
   return pl;
 }
@@ -373,6 +406,49 @@ cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const Clu
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel, args, L);
+}
+
+// Clusters of size C that can be resident at once with `smem` bytes per CTA.
+int cluster_batch_capacity(int C, size_t smem) {
+  cudaFuncSetAttribute(pcg_cluster_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(pcg_cluster_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kClusterTPB);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, pcg_cluster_batch_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// Layout of one instance for a batch with cluster size C (kind 0 if it does not fit).
+PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd);
+
+cudaError_t launch_pcg_cluster_batch(const PcgArgs* args, const ClusterLayout* lays, const int32_t* order, int count,
+                                     int C, int nclusters, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * nclusters);
+  cfg.blockDim = dim3(kClusterTPB);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pcg_cluster_batch_kernel, args, lays, order, count);
 }
 
 }  // namespace avip

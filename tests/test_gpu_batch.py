@@ -1,0 +1,60 @@
+"""Batched instances: every instance gives the same result alone and inside a batch of
+uneven sizes and species counts, and matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+import avip_oracle as O
+from helpers import normwise
+from paper_2201_01291_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def avip():
+    from paper_2201_01291_gb300 import build
+    build.build()
+    from paper_2201_01291_gb300 import avip as A
+    A.load()
+    return A
+
+
+def _instances():
+    ps = W.random_instances(6, seed=4, t_min=500, t_max=6000)
+    return ps
+
+
+@pytest.mark.parametrize("cluster_size", [16, 8, 0])
+def test_batch_equals_alone(avip, cluster_size):
+    ps = _instances()
+    nsteps = 8
+    batch_meshes = [avip.Mesh(p, rtol=1e-13) for p in ps]
+    b = avip.Batch(batch_meshes, cluster_size=cluster_size)
+    st = b.run(nsteps)
+    assert all(s["steps"] == nsteps for s in st)
+    C = b.info["cluster_size"]
+    for k, p in enumerate(ps):
+        alone = avip.Mesh(p, rtol=1e-13, pcg_kind=5)
+        alone.run(nsteps)
+        for s in range(len(p.species)):
+            a = alone.density(s)
+            m = batch_meshes[k].density(s)
+            assert normwise(m, a) <= 1e-12, (k, s, C)
+        assert normwise(batch_meshes[k].phi(), alone.phi()) <= 1e-12
+        alone.close()
+    b.close()
+
+
+def test_batch_matches_oracle(avip):
+    ps = _instances()[:3]
+    nsteps = 6
+    meshes = [avip.Mesh(p, rtol=1e-13) for p in ps]
+    b = avip.Batch(meshes)
+    b.run(nsteps)
+    for k, p in enumerate(ps):
+        o = O.Oracle(p)
+        n_ref, phi_ref, _ = o.run(nsteps)
+        for s in range(len(p.species)):
+            assert normwise(meshes[k].density(s), n_ref[s]) <= 1e-10, (k, s)
+        assert normwise(meshes[k].phi(), phi_ref) <= 1e-10
+    b.close()
