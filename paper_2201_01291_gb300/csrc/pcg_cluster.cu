@@ -29,10 +29,11 @@ namespace cg = cooperative_groups;
 namespace avip {
 
 constexpr int kClusterTPB = 512;
-constexpr size_t kClusterSmemMax = 200 * 1024;
+constexpr size_t kClusterSmemMax = 212 * 1024;  // dynamic part; static arrays use ~10 KB
 
-// Shared memory per CTA: xs[R + H], rs[R + H], ps[R], qs[R], bs[R] (FP64), then, when the
-// matrix fits, vals[max_elems] (FP64) and cols[max_elems] (int32 local indices).
+// Shared memory per CTA: xs[R + H], rs[R + H], ps[R], qs[R] (FP64), then, when the matrix
+// fits, vals[max_elems] (FP64) and cols[max_elems] (int32 local indices).  b' stays in global
+// memory (read only at the start and by the true-residual passes).
 // One complete solve of the system described by (a, L) by the calling cluster.
 __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
   extern __shared__ __align__(16) double dsm[];
@@ -48,8 +49,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
   double* rs = xs + R + H;
   double* ps = rs + R + H;
   double* qs = ps + R;
-  double* bs = qs + R;
-  double* vals = bs + R;
+  double* vals = qs + R;
   int32_t* cols = reinterpret_cast<int32_t*>(vals + (L.mat_smem ? L.max_elems : 0));
   const int N = a.A.N, nsl = a.A.nslices;
   const int s0 = rank * L.spc, s1 = min(nsl, s0 + L.spc);
@@ -151,9 +151,9 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
       }
       bb[0] = fma(b, b, bb[0]);
       push(xs, i, x);
+      a.b[i] = b;
     }
     xs[li] = x;
-    bs[li] = b;
     rs[li] = ps[li] = qs[li] = 0.0;
   }
   csum(1, bb, none);  // also the barrier after which x (own and halo) may be read
@@ -172,7 +172,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
           const int i = s * kSlice + lane;
           const int li = i - s0 * kSlice;
           if (i >= N) continue;
-          const double r = bs[li] - row_dot(s, lane, i, xs);
+          const double r = a.b[i] - row_dot(s, lane, i, xs);
           rs[li] = r;
           ps[li] = 0.0;
           qs[li] = 0.0;
@@ -331,7 +331,7 @@ PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, Clu
   }
   int H = 0;
   for (auto& h : halo) H = std::max<int>(H, (int)h.size());
-  const size_t vec = sizeof(double) * (5 * (size_t)R + 2 * (size_t)H);
+  const size_t vec = sizeof(double) * (4 * (size_t)R + 2 * (size_t)H);
   const size_t mat = (sizeof(double) + sizeof(int32_t)) * (size_t)max_elems;
   const int mat_smem = vec + mat <= kClusterSmemMax ? 1 : 0;
   const size_t smem = vec + (mat_smem ? mat : 0);
