@@ -37,8 +37,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "batch256"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "batch256", "served"])
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
+    ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
+    ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
     ap.add_argument("--rtol", type=float, default=1e-12)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed = FP32 inner PCG with FP64 refinement of the Poisson residual")
@@ -325,6 +327,51 @@ def run_batch(args, rank, world, local_rank):
     }
 
 
+def run_served(args, rank, world, local_rank):
+    """Poisson arrivals at 50 requests/s of discharge solves (triangles lognormal, median 1e5,
+    clipped to [5e3, 2e6]; 5-25 kV; steps uniform in --req-steps), served with continuous
+    batching (admission by free HBM, resident state, overlapping work), against the same
+    requests run one by one on the plain FP64 path."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2201_01291_gb300 import build, avip, serve
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    avip.load()
+    lo, hi = args.req_steps
+    reqs = serve.poisson_requests(args.requests, 50.0, seed=5 + 1000 * rank, steps_min=lo, steps_max=hi)
+    # warm-up: compile paths, first-touch
+    warm = serve.poisson_requests(2, 50.0, seed=999, t_max=2e4, steps_min=5, steps_max=5)
+    serve.Server(keep_state=False).run(warm, realtime=False)
+    sampler = ClockSampler(local_rank) if rank == 0 and not args.no_clocks else None
+    if sampler:
+        sampler.start()
+    srv = serve.Server(chunk=25, keep_state=False)
+    served = srv.run(reqs)
+    clocks = sampler.stop() if sampler else None
+    seq_reqs = serve.poisson_requests(args.requests, 50.0, seed=5 + 1000 * rank, steps_min=lo, steps_max=hi)
+    seq = serve.run_sequential(seq_reqs, keep_state=False)
+    if rank != 0:
+        return None
+    T = sum(r.problem.n_tris for r in reqs)
+    return {
+        "metric": METRIC, "value": served["cell_steps_per_s"] * world, "unit": UNIT, "n_gpus": world,
+        "steps": sum(r.nsteps for r in reqs), "warmup": 1, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"served: {args.requests} Poisson arrivals at 50 req/s, triangles lognormal "
+                               f"(median 1e5, clipped to [5e3, 2e6]; this sample {T} in total), 5-25 kV, "
+                               f"steps uniform in [{lo}, {hi}], FP64",
+                   "requests": args.requests, "precision": "fp64", "parallelism": f"replicas x{world}"},
+        "served": served, "sequential_fp64": seq,
+        "p50_latency_s": served["p50_latency_s"], "p99_latency_s": served["p99_latency_s"],
+        "e2e": {"value": served["cell_steps_per_s"] * world, "unit": UNIT,
+                "how": "requests from host problem descriptions to host results, wall clock"},
+        "clocks": clocks,
+    }
+
+
 def oracle_module():
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import avip_oracle
@@ -394,7 +441,8 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        out = (run_batch if args.workload == "batch256" else run_ours)(args, rank, world, local_rank)
+        fn = {"batch256": run_batch, "served": run_served}.get(args.workload, run_ours)
+        out = fn(args, rank, world, local_rank)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()
