@@ -127,6 +127,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(elapsed, units_per_rank, world, device="cuda"):
+    """Whole-job figures of a replicated run: the slowest rank's elapsed time (max over ranks)
+    and the units of all ranks divided by it."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return elapsed, world * units_per_rank / elapsed
+
+
 def pcg_traffic_model(info, iters, solves):
     """Algorithmic bytes and FP64 flops of the PCG launches (per the kernel design):
     per iteration  phase A: matrix (col 4 B + value 8 B per stored entry) + row length 4 B +
@@ -191,11 +202,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clocks = sampler.stop() if sampler else None
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * T * args.steps / elapsed
+    elapsed, value = aggregate(elapsed, T * args.steps, world)
     # ---- end to end through the public API with host buffers
     e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
     host = m.state()
@@ -205,11 +212,7 @@ def run_ours(args, rank, world, local_rank):
         m.set_state(host)
         m.run(1, allow=allow)
         host = m.state()
-    e2e_t = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        t = torch.tensor([e2e_t], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t, _ = aggregate(max(time.perf_counter() - t0, 1e-9), 1, world)
     state_bytes = host.size * 8
     info = m.info
     m.close()
@@ -287,10 +290,7 @@ def run_batch(args, rank, world, local_rank):
     st = b.run(args.steps)          # graph replays; the call returns after the device finished
     elapsed = time.perf_counter() - t1
     clocks = sampler.stop() if sampler else None
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed, _ = aggregate(elapsed, 1, world)
     iters = sum(x["pcg_iters_total"] for x in st)
     # end to end: per step every instance's state in from host, one batch step, state back
     e2e_steps = 0 if args.no_e2e else 2
