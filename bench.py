@@ -138,18 +138,29 @@ def aggregate(elapsed, units_per_rank, world, device="cuda"):
     return elapsed, world * units_per_rank / elapsed
 
 
+KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (register-resident)",
+                4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)"}
+
+# DRAM bytes per PCG iteration measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of
+# a 300-iteration capture of the pin-plane 500x1000 solve, divided by 300): the working set
+# stays in L2.  Keyed by kernel kind; valid for the kernel revision the capture was taken on.
+NCU_DRAM_BYTES_PER_ITER = {2: (72.372224e6 + 2.023936e6) / 300.0}
+
+
 def pcg_traffic_model(info, iters, solves):
-    """Algorithmic bytes and FP64 flops of the PCG launches (per the kernel design):
-    per iteration  phase A: matrix (col 4 B + value 8 B per stored entry) + row length 4 B +
-                   z gather 8 B + p, q read+write 32 B;  phase B: x, r read+write 32 B, p, q, D^-1
-                   read 24 B, z write 8 B  ->  12 nnz + 108 N bytes;
-                   flops 2 nnz + 16 N (SpMV, two axpy-recurrences, preconditioner, three dots);
-    per solve      b assembly + initial residual + final true residual: 2 x (12 nnz) + ~120 N."""
-    N, nnz = info["n_nodes"], info["nnz"]
-    per_it = 12 * nnz + 108 * N
-    per_solve = 24 * nnz + 120 * N
+    """Algorithmic bytes and flops of one step's PCG launch, per the kernel that runs:
+    streaming (1): per iteration 12 B per stored entry (int32 column + FP64 value) + 4 B row
+        length + r gather 8 + p, q read/write 32 (phase A) + x, r read/write 32, p, q reads 16
+        (phase B) = 12 nnz + 92 N bytes;
+    register-resident (2): p, q, x in registers: 12 nnz + r gather 8 + r read/write 16
+        = 12 nnz + 24 N bytes;
+    mixed (4): FP32 inner iteration 8 nnz + 48 N bytes (FP64 outer residuals not counted);
+    flops: 2 nnz + 12 N per iteration (SpMV, 3 recurrences, 2 dots, x update)."""
+    N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
+    per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N}.get(kind, 0)
+    per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N}.get(kind, 0)
     bytes_ = iters * per_it + solves * per_solve
-    flops = iters * (2 * nnz + 16 * N) + solves * (4 * nnz + 12 * N)
+    flops = iters * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
     return bytes_, flops
 
 
@@ -225,19 +236,24 @@ def run_ours(args, rank, world, local_rank):
     hbm = peaks.get("hbm_gbs", 6800.0)
     gbs = byts / pcg_s / 1e9
     tfl = flops / pcg_s / 1e12
-    alu_frac = tfl / FP64_PEAK_TFLOPS
-    hbm_frac = gbs / hbm
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(alu_frac, 4), "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)",
-                "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4)}
+    kind = info["pcg_kind"]
+    if kind == 4:
+        # FP32 inner solve: bandwidth/latency bound, compare with HBM
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                "fp64_tflops": round(tfl, 4), "fp64_frac": round(alu_frac, 4)}
-    roof.update({"kernel": "pcg_fp64_kernel", "traffic": None,
+        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(tfl / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (FMA-chain probe measured 1.197)",
+                "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm, 4)}
+    per_launch_iters = iters / args.steps
+    traffic = NCU_DRAM_BYTES_PER_ITER.get(kind)
+    roof.update({"kernel": KERNEL_NAMES.get(kind, str(kind)),
+                 "traffic": int(traffic * per_launch_iters) if traffic else None,
+                 "traffic_note": ("ncu DRAM read+write of a 300-iteration capture scaled to the launch's "
+                                  "iterations (L2-resident working set)") if traffic else None,
                  "algorithmic_bytes_per_launch": int(byts / args.steps),
-                 "pcg_iters_per_step": iters / args.steps,
+                 "pcg_iters_per_step": per_launch_iters,
                  "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kernel_ms.items()}})
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -166,8 +166,10 @@ int state_size(avip_mesh_t h, int64_t* n_doubles);
 int state_get(avip_mesh_t h, double* host_state);
 int state_set(avip_mesh_t h, const double* host_state);
 
-/* Sizes of the handle: n_nodes, n_tris, n_edges, nnz of the Poisson matrix. */
-int mesh_info(avip_mesh_t h, int64_t* info4);
+/* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
+ * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident), PCG blocks,
+ * PCG threads per block, device bytes held by the handle}. */
+int mesh_info(avip_mesh_t h, int64_t* info8);
 
 /* ---- batches (many independent instances per step) -------------------------------------
  * A batch advances several mesh handles together: per step, one persistent launch solves the

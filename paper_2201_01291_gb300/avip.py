@@ -200,10 +200,15 @@ def field_get(h, which, s, n_nodes):
     return rc, out
 
 
+PCG_KINDS = {1: "streaming", 2: "register-resident", 4: "mixed", 5: "cluster-resident"}
+
+
 def mesh_info(h):
-    info = np.zeros(4, dtype=np.int64)
+    info = np.zeros(8, dtype=np.int64)
     _check(load().mesh_info(h, info.ctypes.data_as(_P(C.c_int64))), "mesh_info")
-    return dict(n_nodes=int(info[0]), n_tris=int(info[1]), n_edges=int(info[2]), nnz=int(info[3]))
+    return dict(n_nodes=int(info[0]), n_tris=int(info[1]), n_edges=int(info[2]), nnz=int(info[3]),
+                pcg_kind=int(info[4]), pcg_blocks=int(info[5]), pcg_threads=int(info[6]),
+                device_bytes=int(info[7]))
 
 
 def state_get(h):

@@ -31,6 +31,7 @@ struct avip_mesh {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<void*> allocs;
+  size_t bytes = 0;  // device bytes held
   // device arrays
   int32_t *sl_ptr = nullptr, *sl_w = nullptr, *rlen = nullptr, *col = nullptr, *tri = nullptr;
   double *aval = nullptr, *gx = nullptr, *gy = nullptr, *sx = nullptr, *sy = nullptr;
@@ -72,7 +73,10 @@ void* dev_alloc(avip_mesh* h, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
-  if (p) h->allocs.push_back(p);
+  if (p) {
+    h->allocs.push_back(p);
+    h->bytes += bytes;
+  }
   return p;
 }
 
@@ -407,6 +411,10 @@ int mesh_info(avip_mesh_t h, int64_t* info) {
   info[1] = h->hm.T;
   info[2] = h->hm.E;
   info[3] = h->hm.nnz;
+  info[4] = h->plan.kind;
+  info[5] = h->plan.blocks;
+  info[6] = h->plan.tpb;
+  info[7] = (int64_t)h->bytes;
   return AVIP_OK;
 }
 
