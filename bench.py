@@ -290,7 +290,8 @@ def run_batch(args, rank, world, local_rank):
     avip.load()
     t0 = time.perf_counter()
     probs = W.random_instances(args.instances, seed=4 + 1000 * rank)
-    meshes = [avip.Mesh(p, rtol=args.rtol) for p in probs]
+    prec = avip.PREC_MIXED if args.precision == "mixed" else avip.PREC_FP64
+    meshes = [avip.Mesh(p, rtol=args.rtol, precision=prec) for p in probs]
     b = avip.Batch(meshes, cluster_size=0)
     setup = time.perf_counter() - t0
     T = sum(p.n_tris for p in probs)
@@ -328,11 +329,11 @@ def run_batch(args, rank, world, local_rank):
     return {
         "metric": METRIC, "value": world * T * args.steps / elapsed, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"batched: {args.instances} instances, triangles log-uniform in [2e3, 2e5] "
-                               f"(total {T}), aspect 1-4, 5-25 kV, 2 or 3 species, FP64",
-                   "instances": args.instances, "n_tris_total": T, "rtol": args.rtol, "precision": "fp64",
+                               f"(total {T}), aspect 1-4, 5-25 kV, 2 or 3 species, {args.precision}",
+                   "instances": args.instances, "n_tris_total": T, "rtol": args.rtol, "precision": args.precision,
                    "cluster": info, "setup_s": round(setup, 1), "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2", "timing": "host clock around synchronous graph replays"},
         "pcg_iters_per_step": iters / args.steps,

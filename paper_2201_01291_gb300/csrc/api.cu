@@ -192,7 +192,7 @@ int cuda_status(cudaError_t e) {
 
 cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 5) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
+  if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
 
@@ -327,11 +327,12 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
   h->plan = h->opts.precision == AVIP_PREC_MIXED ? pcg_mixed_plan(m.nslices, h->opts.pcg_threads)
                                                  : pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
-  if (h->opts.precision == AVIP_PREC_FP64 && (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5)) {
+  if (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5 || h->opts.pcg_kind == 6) {
     // small meshes: one thread-block cluster with everything in shared memory
+    const int mixed = h->opts.precision == AVIP_PREC_MIXED ? 1 : 0;
     ClusterHost chd;
-    PcgPlan cp = pcg_cluster_plan(m, h->opts.pcg_kind == 5 ? (1 << 30) : kClusterAutoRows, &h->clay, &chd);
-    if (cp.kind == 5) {
+    PcgPlan cp = pcg_cluster_plan(m, h->opts.pcg_kind >= 5 ? (1 << 30) : kClusterAutoRows, &h->clay, &chd, mixed);
+    if (cp.kind == 5 || cp.kind == 6) {
       int32_t *colL = nullptr, *pptr = nullptr, *pdst = nullptr;
       ok = ok && upload(h, colL, chd.colL) && upload(h, pptr, chd.push_ptr) && upload(h, pdst, chd.push_dst, 1);
       h->clay.colL = colL;
@@ -695,7 +696,7 @@ int state_set(avip_mesh_t h, const double* in) {
 // batch itself (state saved and restored around the trial).
 namespace avip {
 int cluster_batch_capacity(int C, size_t smem);
-PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd);
+PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd, int mixed);
 cudaError_t launch_pcg_cluster_batch(const PcgArgs* args, const ClusterLayout* lays, const int32_t* order, int count,
                                      int C, int nclusters, size_t smem, cudaStream_t st);
 cudaError_t launch_dd_batch(const DDArgs* args, const int32_t* node_pref, const int32_t* cell_pref, int count,
@@ -754,8 +755,9 @@ bool batch_configure(avip_batch* b, int C) {
   size_t smem = 0;
   for (int k = 0; k < n; ++k) {
     ClusterHost hd;
-    PcgPlan p = pcg_cluster_plan_fixed(b->m[k]->hm, C, &lays[k], &hd);
-    if (p.kind != 5) return false;
+    PcgPlan p = pcg_cluster_plan_fixed(b->m[k]->hm, C, &lays[k], &hd,
+                                       b->m[k]->opts.precision == AVIP_PREC_MIXED ? 1 : 0);
+    if (p.kind == 0) return false;
     smem = std::max(smem, (size_t)p.maxs);
     lays[k].colL = batch_upload(b, hd.colL);
     lays[k].push_ptr = batch_upload(b, hd.push_ptr);
@@ -819,7 +821,7 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
   if (!b) return AVIP_ENOMEM;
   for (int k = 0; k < count; ++k) {
     avip_mesh* h = meshes[k];
-    if (!ready(h) || h->opts.precision != AVIP_PREC_FP64) {
+    if (!ready(h)) {
       delete b;
       return h ? AVIP_ESTATE : AVIP_EINVAL;
     }

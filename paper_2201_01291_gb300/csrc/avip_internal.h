@@ -148,7 +148,8 @@ struct PcgArgs {
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
-  int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident
+  int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
+                   // 6 cluster-resident mixed precision
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
@@ -163,7 +164,7 @@ struct ClusterLayout {
   int32_t hmax;       // largest halo (rows of other CTAs read by one CTA)
   int32_t max_elems;  // largest SELL element count of one CTA's slices
   int32_t mat_smem;   // 1: the CTA copies its matrix slices into shared memory
-  int32_t pad;
+  int32_t mixed;      // 1: FP32 inner CG + FP64 refinement (matrix slices kept in FP32)
   const int32_t* colL;      // per SELL element: local index (own row, or rows + halo slot)
   const int32_t* push_ptr;  // per row: range of push_dst
   const int32_t* push_dst;  // (reader rank << 24) | halo slot
@@ -171,7 +172,7 @@ struct ClusterLayout {
 struct ClusterHost {
   std::vector<int32_t> colL, push_ptr, push_dst;
 };
-PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd);
+PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd, int mixed = 0);
 
 struct DDArgs {
   SellView A;

@@ -29,17 +29,24 @@ namespace cg = cooperative_groups;
 namespace avip {
 
 constexpr int kClusterTPB = 512;
-constexpr size_t kClusterSmemMax = 212 * 1024;  // dynamic part; static arrays use ~10 KB
+constexpr size_t kClusterSmemMax = 212 * 1024;  // dynamic part; the static part below is ~9 KB
+
+// Static shared memory of the cluster solves (declared once per kernel).
+struct ClusterShared {
+  double part[2][16][4];        // reduction partials [parity][source rank][value]
+  double thr[2 * kClusterTPB];  // per-thread values of a block reduction
+  double res[8];                // reduced totals and epilogue results
+};
 
 // Shared memory per CTA: xs[R + H], rs[R + H], ps[R], qs[R] (FP64), then, when the matrix
 // fits, vals[max_elems] (FP64) and cols[max_elems] (int32 local indices).  b' stays in global
 // memory (read only at the start and by the true-residual passes).
 // One complete solve of the system described by (a, L) by the calling cluster.
-__device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
+__device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterShared& sh) {
   extern __shared__ __align__(16) double dsm[];
-  __shared__ double s_part[2][16][4];  // [parity][source rank][value]
-  __shared__ double s_thr[2 * kClusterTPB];
-  __shared__ double s_res[8];
+  auto& s_part = sh.part;
+  auto& s_thr = sh.thr;
+  auto& s_res = sh.res;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int C = (int)cl.num_blocks();
@@ -255,8 +262,269 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L) {
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Mixed precision in one cluster: FP32 inner CG (FP32 matrix slices and vectors in shared
+// memory, Kahan-compensated FP32 dot products), FP64 iterative refinement (FP64 iterate in
+// shared memory, FP64 residual with the FP64 matrix read from global memory).
+// Shared memory per CTA: x64[R + H] (FP64), r64[R] (FP64), r32[R + H], e32[R], p32[R], q32[R]
+// (FP32), then vals32[max_elems] (FP32) and cols[max_elems] (int32) when the matrix fits.
+__device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, ClusterShared& sh) {
+  extern __shared__ __align__(16) double dsm[];
+  auto& s_part = sh.part;
+  auto& s_thr = sh.thr;
+  auto& s_res = sh.res;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int C = (int)cl.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int R = L.rows, H = L.hmax;
+  double* x64 = dsm;
+  double* r64 = x64 + R + H;
+  float* r32 = reinterpret_cast<float*>(r64 + R);
+  float* e32 = r32 + R + H;
+  float* p32 = e32 + R;
+  float* q32 = p32 + R;
+  float* vals = q32 + R;
+  int32_t* cols = reinterpret_cast<int32_t*>(vals + (L.mat_smem ? L.max_elems : 0));
+  const int N = a.A.N, nsl = a.A.nslices;
+  const int s0 = rank * L.spc, s1 = min(nsl, s0 + L.spc);
+  const int e0 = s0 < nsl ? __ldg(a.A.sl_ptr + s0) : 0;
+  const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+  unsigned seq = 0;
+
+  auto colof = [&](int e) -> int { return L.mat_smem ? cols[e] : __ldg(L.colL + e0 + e); };
+  auto row_dot32 = [&](int s, int l, int i, const float* v) -> float {
+    const int w = __ldg(a.A.sl_w + s);
+    const int rl = __ldg(a.A.rlen + i);
+    const int base = __ldg(a.A.sl_ptr + s) + l - e0;
+    float acc = 0.f;
+    for (int k = 0; k < w; ++k) {
+      if (k < rl) {
+        const int e = base + k * kSlice;
+        const float av = L.mat_smem ? vals[e] : __ldg(a.aval32 + e0 + e);
+        acc = fmaf(av, v[colof(e)], acc);
+      }
+    }
+    return acc;
+  };
+  auto row_dot64 = [&](int s, int l, int i, const double* v) -> double {
+    const int w = __ldg(a.A.sl_w + s);
+    const int rl = __ldg(a.A.rlen + i);
+    const int base = __ldg(a.A.sl_ptr + s) + l - e0;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) {
+      if (k < rl) {
+        const int e = base + k * kSlice;
+        acc = fma(__ldg(a.A.aval + e0 + e), v[colof(e)], acc);
+      }
+    }
+    return acc;
+  };
+  auto push64 = [&](double* v, int i, double val) {
+    const int p1 = __ldg(L.push_ptr + i + 1);
+    for (int k = __ldg(L.push_ptr + i); k < p1; ++k) {
+      const unsigned d = (unsigned)__ldg(L.push_dst + k);
+      *cl.map_shared_rank(v + R + (int)(d & 0xffffffu), (int)(d >> 24)) = val;
+    }
+  };
+  auto push32 = [&](float* v, int i, float val) {
+    const int p1 = __ldg(L.push_ptr + i + 1);
+    for (int k = __ldg(L.push_ptr + i); k < p1; ++k) {
+      const unsigned d = (unsigned)__ldg(L.push_dst + k);
+      *cl.map_shared_rank(v + R + (int)(d & 0xffffffu), (int)(d >> 24)) = val;
+    }
+  };
+  auto csum = [&](int NV, double* v, auto epi) {
+    const int par = (++seq) & 1;
+    for (int k = 0; k < NV; ++k) s_thr[k * kClusterTPB + threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+      double bt[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < NV; ++k) {
+        constexpr int W = kClusterTPB / 32;
+        double t[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) t[w] = s_thr[k * kClusterTPB + w * 32 + lane];
+#pragma unroll
+        for (int h = W / 2; h > 0; h >>= 1)
+#pragma unroll
+          for (int w = 0; w < h; ++w) t[w] += t[w + h];
+        double u = t[0];
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        bt[k] = u;
+      }
+      if (lane < C) {
+        double* dst = cl.map_shared_rank(&s_part[par][rank][0], lane);
+        for (int k = 0; k < NV; ++k) dst[k] = bt[k];
+      }
+    }
+    cl.sync();
+    if (warp == 0) {
+      for (int k = 0; k < NV; ++k) {
+        double t = lane < C ? s_part[par][lane][k] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_res[k] = t;
+      }
+      if (lane == 0) epi(s_res, s_res + 4);
+    }
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) v[k] = s_res[k];
+  };
+  auto none = [](const double*, double*) {};
+
+  if (L.mat_smem && s0 < nsl) {
+    const int e1 = __ldg(a.A.sl_ptr + s1);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      cols[e - e0] = __ldg(L.colL + e);
+      vals[e - e0] = __ldg(a.aval32 + e);
+    }
+  }
+  double bb[1] = {0.0};
+  for (int li = threadIdx.x; li < R; li += blockDim.x) {
+    const int i = s0 * kSlice + li;
+    double x = 0.0;
+    if (i < N) {
+      x = a.dsq[i] * a.phi[i];
+      double b;
+      if (a.use_density_rhs) {
+        double rho = 0.0;
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+        b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      } else {
+        b = a.b[i];
+      }
+      a.b[i] = b;
+      bb[0] = fma(b, b, bb[0]);
+      push64(x64, i, x);
+    }
+    x64[li] = x;
+    r64[li] = 0.0;
+    r32[li] = e32[li] = p32[li] = q32[li] = 0.f;
+  }
+  csum(1, bb, none);
+  const double thresh = a.rtol * a.rtol * bb[0];
+  int it = 0, outer = 0, status = AVIP_OK;
+  double rr64 = 0.0;
+  while (bb[0] != 0.0) {
+    // ---- FP64 residual of the FP64 iterate
+    double r2[1] = {0.0};
+    for (int s = s0 + warp; s < s1; s += nw) {
+      const int i = s * kSlice + lane;
+      const int li = i - s0 * kSlice;
+      if (i >= N) continue;
+      const double r = a.b[i] - row_dot64(s, lane, i, x64);
+      r64[li] = r;
+      r2[0] = fma(r, r, r2[0]);
+    }
+    csum(1, r2, none);
+    rr64 = r2[0];
+    if (rr64 <= thresh) break;
+    if (it >= a.max_iter) {
+      status = AVIP_ENOTCONV;
+      break;
+    }
+    ++outer;
+    const double rnorm = sqrt(rr64), rscale = 1.0 / rnorm;
+    double g0[1];
+    {
+      KahanF k;
+      for (int s = s0 + warp; s < s1; s += nw) {
+        const int i = s * kSlice + lane;
+        const int li = i - s0 * kSlice;
+        if (i >= N) continue;
+        const float r = (float)(r64[li] * rscale);
+        r32[li] = r;
+        e32[li] = p32[li] = q32[li] = 0.f;
+        push32(r32, i, r);
+        k.add(r * r);
+      }
+      g0[0] = k.value();
+    }
+    csum(1, g0, none);
+    const double inner_thresh = a.inner_rtol * a.inner_rtol * g0[0];
+    double rr = g0[0];
+    float beta = 0.f;
+    while (rr > inner_thresh && it < a.max_iter) {
+      KahanF kpq;
+      for (int s = s0 + warp; s < s1; s += nw) {
+        const int i = s * kSlice + lane;
+        const int li = i - s0 * kSlice;
+        if (i >= N) continue;
+        const float w = row_dot32(s, lane, i, r32);
+        const float qn = fmaf(beta, q32[li], w);
+        const float pn = fmaf(beta, p32[li], r32[li]);
+        q32[li] = qn;
+        p32[li] = pn;
+        kpq.add(pn * qn);
+      }
+      double pq[1] = {kpq.value()};
+      const double rr_now = rr;
+      csum(1, pq, [rr_now](const double* t, double* e) { e[0] = rr_now / t[0]; });
+      const float alpha = (float)s_res[4];
+      KahanF krr;
+      for (int s = s0 + warp; s < s1; s += nw) {
+        const int i = s * kSlice + lane;
+        const int li = i - s0 * kSlice;
+        if (i >= N) continue;
+        e32[li] = fmaf(alpha, p32[li], e32[li]);
+        const float r = fmaf(-alpha, q32[li], r32[li]);
+        r32[li] = r;
+        push32(r32, i, r);
+        krr.add(r * r);
+      }
+      double rn[1] = {krr.value()};
+      csum(1, rn, [rr_now](const double* t, double* e) { e[0] = t[0] / rr_now; });
+      beta = (float)s_res[4];
+      rr = rn[0];
+      ++it;
+    }
+    // ---- FP64 correction, pushed to the halos before the next residual
+    for (int s = s0 + warp; s < s1; s += nw) {
+      const int i = s * kSlice + lane;
+      const int li = i - s0 * kSlice;
+      if (i >= N) continue;
+      const double x = fma(rnorm, (double)e32[li], x64[li]);
+      x64[li] = x;
+      push64(x64, i, x);
+    }
+    cl.sync();
+  }
+  for (int li = threadIdx.x; li < R; li += blockDim.x) {
+    const int i = s0 * kSlice + li;
+    if (i < N) {
+      a.phi[i] = a.dsqinv[i] * x64[li];
+      a.x[i] = x64[li];
+    }
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    a.sc->pcg_iters = it;
+    a.sc->pcg_outer = outer;
+    a.sc->pcg_status = status;
+    a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
+    a.sc->pcg_bnorm = sqrt(bb[0]);
+    if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
+  }
+  cl.sync();
+}
+
+__global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_mixed_kernel(PcgArgs a, ClusterLayout L) {
+  __shared__ ClusterShared sh;
+  cluster_solve_mixed(a, L, sh);
+}
+
 __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, ClusterLayout L) {
-  cluster_solve(a, L);
+  __shared__ ClusterShared sh;
+  cluster_solve(a, L, sh);
 }
 
 // Batched, persistent: every resident cluster solves instances order[c], order[c + nclusters],
@@ -265,6 +533,7 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
                                                                             const ClusterLayout* __restrict__ lays,
                                                                             const int32_t* __restrict__ order,
                                                                             int count) {
+  __shared__ ClusterShared sh;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -272,7 +541,10 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
     const int k = order[j];
     const PcgArgs a = args[k];
     const ClusterLayout L = lays[k];
-    cluster_solve(a, L);
+    if (L.mixed)
+      cluster_solve_mixed(a, L, sh);
+    else
+      cluster_solve(a, L, sh);
   }
 }
 
@@ -281,6 +553,8 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
 static int cluster_size_supported(size_t smem) {
   cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
+  cudaFuncSetAttribute(pcg_cluster_mixed_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(pcg_cluster_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
   for (int c : {16, 8}) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);
@@ -304,7 +578,7 @@ static int cluster_size_supported(size_t smem) {
 // runs on C SMs only, so it is chosen only for meshes small enough that the grid-wide
 // reduction latency, not FP64 throughput, would dominate (n_rows <= max_rows).  Fills the
 // host arrays of the layout: local column indices, halo push lists.
-PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd) {
+PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd, int mixed) {
   PcgPlan pl;
   pl.kind = 0;
   const int spc = (m.nslices + C - 1) / C;
@@ -331,8 +605,9 @@ PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, Clu
   }
   int H = 0;
   for (auto& h : halo) H = std::max<int>(H, (int)h.size());
-  const size_t vec = sizeof(double) * (4 * (size_t)R + 2 * (size_t)H);
-  const size_t mat = (sizeof(double) + sizeof(int32_t)) * (size_t)max_elems;
+  const size_t vec = mixed ? (sizeof(double) * (2 * (size_t)R + (size_t)H) + sizeof(float) * (4 * (size_t)R + (size_t)H))
+                           : sizeof(double) * (4 * (size_t)R + 2 * (size_t)H);
+  const size_t mat = ((mixed ? sizeof(float) : sizeof(double)) + sizeof(int32_t)) * (size_t)max_elems;
   const int mat_smem = vec + mat <= kClusterSmemMax ? 1 : 0;
   const size_t smem = vec + (mat_smem ? mat : 0);
   if (smem > kClusterSmemMax) return pl;
@@ -369,22 +644,23 @@ PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, Clu
   out->hmax = H;
   out->max_elems = max_elems;
   out->mat_smem = mat_smem;
-  pl.kind = 5;
+  out->mixed = mixed;
+  pl.kind = mixed ? 6 : 5;
   pl.tpb = kClusterTPB;
   pl.blocks = C;
   pl.maxs = (int)smem;  // dynamic shared memory bytes
   return pl;
 }
 
-PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd) {
+PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd, int mixed) {
   PcgPlan pl;
   pl.kind = 0;
   if (m.N > max_rows) return pl;
   for (int C : {16, 8}) {
     ClusterLayout L{};
     ClusterHost H;
-    PcgPlan p = pcg_cluster_plan_fixed(m, C, &L, &H);
-    if (p.kind != 5 || cluster_size_supported((size_t)p.maxs) < C) continue;
+    PcgPlan p = pcg_cluster_plan_fixed(m, C, &L, &H, mixed);
+    if (p.kind == 0 || cluster_size_supported((size_t)p.maxs) < C) continue;
     *out = L;
     *hd = std::move(H);
     return p;
@@ -405,6 +681,7 @@ cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const Clu
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (L.mixed) return cudaLaunchKernelEx(&cfg, pcg_cluster_mixed_kernel, args, L);
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel, args, L);
 }
 
@@ -431,8 +708,6 @@ int cluster_batch_capacity(int C, size_t smem) {
   return n;
 }
 
-// Layout of one instance for a batch with cluster size C (kind 0 if it does not fit).
-PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, ClusterHost* hd);
 
 cudaError_t launch_pcg_cluster_batch(const PcgArgs* args, const ClusterLayout* lays, const int32_t* order, int count,
                                      int C, int nclusters, size_t smem, cudaStream_t st) {

@@ -58,3 +58,25 @@ def test_batch_matches_oracle(avip):
             assert normwise(meshes[k].density(s), n_ref[s]) <= 1e-10, (k, s)
         assert normwise(meshes[k].phi(), phi_ref) <= 1e-10
     b.close()
+
+
+def test_mixed_batch_equals_alone_and_oracle(avip):
+    """Mixed-precision instances (FP32 inner CG + FP64 refinement inside each cluster) give the
+    same result in a batch as alone, and stay within 1e-6 of the FP64 oracle."""
+    ps = _instances()[:4]
+    nsteps = 6
+    meshes = [avip.Mesh(p, rtol=1e-11, precision=avip.PREC_MIXED) for p in ps]
+    b = avip.Batch(meshes, cluster_size=16)   # the cluster size the single-instance plan picks
+    b.run(nsteps)
+    for k, p in enumerate(ps):
+        alone = avip.Mesh(p, rtol=1e-11, precision=avip.PREC_MIXED)
+        assert alone.info["pcg_kind"] == 6
+        alone.run(nsteps)
+        o = O.Oracle(p)
+        n_ref, phi_ref, _ = o.run(nsteps)
+        for s in range(len(p.species)):
+            assert normwise(meshes[k].density(s), alone.density(s)) <= 1e-12
+            assert normwise(meshes[k].density(s), n_ref[s]) <= 1e-6
+        assert normwise(meshes[k].phi(), phi_ref) <= 1e-6
+        alone.close()
+    b.close()

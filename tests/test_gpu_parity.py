@@ -196,12 +196,15 @@ def test_tiny_and_single_slice_meshes(avip):
 MIXED_TOL = 1e-6
 
 
-def test_mixed_poisson_matches_oracle(avip):
-    """FP32 inner PCG + FP64 refinement reaches the FP64 answer (rtol 1e-12 on the residual)."""
+@pytest.mark.parametrize("kind", [0, 1])
+def test_mixed_poisson_matches_oracle(avip, kind):
+    """FP32 inner PCG + FP64 refinement reaches the FP64 answer (rtol 1e-12 on the residual),
+    in one cluster (kind 0 picks it for this size) and with the grid-wide kernel (kind 1)."""
     p = W.config_small(nx=40, ny=33, seed=5)
     o = O.Oracle(p)
     phi_ref = o.poisson(o.initial_state())
-    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-12)
+    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-12, pcg_kind=kind)
+    assert m.info["pcg_kind"] == (6 if kind == 0 else 4)
     it, rr = m.poisson_solve()
     assert rr <= 1e-12
     assert normwise(m.phi(), phi_ref) <= 1e-10
