@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "batch256", "served"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "batch256", "served", "sweep"])
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
     ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
@@ -389,6 +389,41 @@ def run_served(args, rank, world, local_rank):
     }
 
 
+def run_sweep(args, rank, world, local_rank):
+    """PCG throughput across mesh sizes, from L2-resident to far past L2 (pin-plane shape,
+    1 cm x 2 cm, FP64): per size the kernel chosen by the library, iterations, us per
+    iteration, algorithmic GB/s and FP64 TFLOP/s against the peaks."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2201_01291_gb300 import build, avip, workloads as W
+    build.build()
+    avip.load()
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rows = []
+    for nx in (160, 320, 500, 1000, 1415, 2000):
+        ny = 2 * nx
+        p = W.plates_problem(nx, ny, 1e-2, 2e-2, 2e4, seed=2, field_dependent=True, source=W.SRC_TOWNSEND,
+                             needle_len=2e-3)
+        m = avip.Mesh(p, rtol=args.rtol)
+        m.run(2)
+        ms, st = m.run_timed(2)
+        info = m.info
+        m.close()
+        it = st["pcg_iters_total"]
+        byts, flops = pcg_traffic_model(info, it, 2)
+        s_ = ms["pcg"] / 1e3
+        rows.append({"n_nodes": info["n_nodes"], "n_tris": info["n_tris"], "kernel": KERNEL_NAMES.get(info["pcg_kind"]),
+                     "iters_per_step": it / 2, "us_per_iter": 1e6 * s_ / it,
+                     "gbs": round(byts / s_ / 1e9, 1), "hbm_frac": round(byts / s_ / 1e9 / hbm, 3),
+                     "fp64_tflops": round(flops / s_ / 1e12, 3),
+                     "cell_steps_per_s": p.n_tris * 2 / (sum(ms.values()) / 1e3)})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "workload": "size sweep (PCG roofline)", "rows": rows, "unit": UNIT}
+
+
 def oracle_module():
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import avip_oracle
@@ -458,7 +493,7 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        fn = {"batch256": run_batch, "served": run_served}.get(args.workload, run_ours)
+        fn = {"batch256": run_batch, "served": run_served, "sweep": run_sweep}.get(args.workload, run_ours)
         out = fn(args, rank, world, local_rank)
         if world > 1:
             import torch
