@@ -24,7 +24,10 @@ Structure (each function cites the passage it follows):
     computation");
   * source: ionisation S = alpha mu_e |E| n_e added to electrons and positive ions
     (section "Bagheri benchmark"), optional attachment;
-  * explicit update and the charge sum.
+  * explicit update and the charge sum;
+  * axisymmetric (x, r) variant (section "Axisymmetric configuration" and the axisymmetric
+    flux form): r-weighted Poisson rows (closed-form dual-contour integral), r-weighted edge
+    and boundary normals, dual volumes of revolution; gradients stay two-dimensional.
 
 Readings where the paper is silent or garbled (each also listed in the design notes):
   * ratio of gradients: r = (u_U - u_k)/(u_W - u_U) with the virtual upwind node
@@ -35,7 +38,10 @@ Readings where the paper is silent or garbled (each also listed in the design no
   * Delta x_tau = shortest edge of the cell; cell values = mean of the three nodal values;
   * chemical time step A_tau * min over nodes of |n_e|/|S_e| (the printed form is not a
     time; the magnitudes keep it a positive time scale when a density undershoots below 0);
-  * Dirichlet rows eliminated symmetrically (same solution as the unit-row form).
+  * Dirichlet rows eliminated symmetrically (same solution as the unit-row form);
+  * axisymmetric dual volume: the integral of r over the median-dual cell (the centroid
+    radius of the dual cell in the Pappus relation; the node radius would give zero volume to
+    nodes on the axis); the nodal gradient keeps the planar area weights.
 """
 from __future__ import annotations
 
@@ -158,6 +164,95 @@ def min_edge_length(xy, tris):
     return np.minimum(np.minimum(L[0], L[1]), L[2])
 
 
+# ----------------------------------------------------------------------------- axisymmetry
+# Axisymmetric (x, r) configuration: the second coordinate is the radius r >= 0 and every
+# volume or face integral carries the weight r (per radian; the common factor 2 pi cancels).
+def axi_half_face_integral(xy, tris):
+    """Integral of r n dl over the part of the dual contour of vertex k inside each triangle,
+    in the closed form of the axisymmetric Poisson section:
+      1/24 [(4 r_tau + 2 r_k + r_j + r_l) n_k - (2 r_tau + r_k + r_j) n_j - (2 r_tau + r_k + r_l) n_l]
+    with n the nodal normals and r_tau the centroid radius.  Shape (T, 3, 2)."""
+    S = nodal_normals(xy, tris)
+    r = xy[:, 1][tris]                         # (T, 3)
+    rt = r.sum(axis=1) / 3.0
+    out = np.empty_like(S)
+    for k in range(3):
+        j, l = (k + 1) % 3, (k + 2) % 3
+        out[:, k] = ((4 * rt + 2 * r[:, k] + r[:, j] + r[:, l])[:, None] * S[:, k]
+                     - (2 * rt + r[:, k] + r[:, j])[:, None] * S[:, j]
+                     - (2 * rt + r[:, k] + r[:, l])[:, None] * S[:, l]) / 24.0
+    return out
+
+
+def axi_poisson_matrix(xy, tris, V_tau, n_nodes):
+    """K_ik = sum_tau (1/(n_d A_tau)) n_k . (integral of r n dl over the dual contour of i in
+    tau): the axisymmetric counterpart of Eq. coeff_matriceA for -lap phi = rho/eps0.  Not
+    symmetric (the radius breaks the symmetry)."""
+    S = nodal_normals(xy, tris)
+    I = axi_half_face_integral(xy, tris)
+    rows, cols, vals = [], [], []
+    for a in range(3):
+        for b in range(3):
+            rows.append(tris[:, a])
+            cols.append(tris[:, b])
+            vals.append(np.einsum("ij,ij->i", S[:, b], I[:, a]) / (2.0 * V_tau))
+    K = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n_nodes, n_nodes)).tocsr()
+    K.sum_duplicates()
+    return K
+
+
+def axi_nodal_volumes(xy, tris, V_tau):
+    """V_i / 2 pi = integral of r over the median-dual cell (second Pappus theorem with the
+    centroid radius of the dual cell): per triangle A_tau (22 r_i + 7 r_j + 7 r_k) / 108."""
+    r = xy[:, 1][tris]
+    V = np.zeros(xy.shape[0])
+    for k in range(3):
+        j, l = (k + 1) % 3, (k + 2) % 3
+        np.add.at(V, tris[:, k], V_tau * (22 * r[:, k] + 7 * r[:, j] + 7 * r[:, l]) / 108.0)
+    return V
+
+
+def axi_edges_and_normals(xy, tris):
+    """Edge normals weighted by the radius of their dual face: sum over the cells sharing the
+    edge of r_ij^tau S_ij^tau, r_ij^tau the radius at the middle of the dual face (the flux
+    form F_ij r_ij^tau S_ij^tau of the axisymmetric flux section)."""
+    Sc = cell_edge_normals(xy, tris)
+    c = (xy[tris[:, 0], 1] + xy[tris[:, 1], 1] + xy[tris[:, 2], 1]) / 3.0
+    I = np.concatenate([tris[:, m] for m in range(3)])
+    J = np.concatenate([tris[:, (m + 1) % 3] for m in range(3)])
+    rf = np.concatenate([0.5 * (0.5 * (xy[tris[:, m], 1] + xy[tris[:, (m + 1) % 3], 1]) + c) for m in range(3)])
+    Sv = np.concatenate([Sc[:, m] for m in range(3)]) * rf[:, None]
+    swap = I > J
+    lo = np.where(swap, J, I)
+    hi = np.where(swap, I, J)
+    Sv = np.where(swap[:, None], -Sv, Sv)
+    key = lo.astype(np.int64) * (int(xy.shape[0]) + 1) + hi
+    uniq, inv = np.unique(key, return_inverse=True)
+    S = np.zeros((uniq.size, 2))
+    np.add.at(S, inv, Sv)
+    edges = np.stack([uniq // (int(xy.shape[0]) + 1), uniq % (int(xy.shape[0]) + 1)], axis=1)
+    return edges.astype(np.int64), S
+
+
+def axi_boundary_normals(xy, tris):
+    """Boundary nodal normal weighted by the radius: each boundary face gives its end nodes half
+    of its outward normal times the radius at the middle of that half (3 r_p + r_q)/4."""
+    Sf = face_normals(xy, tris)
+    I = np.concatenate([tris[:, m] for m in range(3)])
+    J = np.concatenate([tris[:, (m + 1) % 3] for m in range(3)])
+    F = np.concatenate([Sf[:, m] for m in range(3)])
+    lo, hi = np.minimum(I, J), np.maximum(I, J)
+    key = lo.astype(np.int64) * (int(xy.shape[0]) + 1) + hi
+    _, inv, counts = np.unique(key, return_inverse=True, return_counts=True)
+    bnd = counts[inv] == 1
+    rI, rJ = xy[I, 1], xy[J, 1]
+    Sb = np.zeros((xy.shape[0], 2))
+    np.add.at(Sb, I[bnd], 0.5 * F[bnd] * ((3 * rI[bnd] + rJ[bnd]) / 4.0)[:, None])
+    np.add.at(Sb, J[bnd], 0.5 * F[bnd] * ((3 * rJ[bnd] + rI[bnd]) / 4.0)[:, None])
+    return Sb
+
+
 # ----------------------------------------------------------------------------- Poisson
 def poisson_matrix(tris, S, V_tau, n_nodes):
     """K = -A with a_ik = sum_tau -S_i.S_k/(V_tau n_d^2) (Eq. coeff_matriceA), i.e. the
@@ -265,11 +360,22 @@ class Oracle:
         if np.any(self.V_tau <= 0):
             raise ValueError("degenerate triangle")
         self.S = nodal_normals(xy, self.tris)
-        self.V_node = nodal_volumes(self.tris, self.V_tau, self.N)
-        self.edges, self.S_edge, _ = edges_and_normals(xy, self.tris)
-        self.S_b = boundary_normals(xy, self.tris)
+        # planar dual areas: the weights of the (two-dimensional) nodal gradient
+        self.A_node = nodal_volumes(self.tris, self.V_tau, self.N)
         self.dx_tau = min_edge_length(xy, self.tris)
-        self.K = poisson_matrix(self.tris, self.S, self.V_tau, self.N)
+        self.axisymmetric = bool(getattr(problem, "axisymmetric", False))
+        if self.axisymmetric:
+            if np.any(xy[:, 1] < 0):
+                raise ValueError("axisymmetric meshes need r = y >= 0")
+            self.V_node = axi_nodal_volumes(xy, self.tris, self.V_tau)
+            self.edges, self.S_edge = axi_edges_and_normals(xy, self.tris)
+            self.S_b = axi_boundary_normals(xy, self.tris)
+            self.K = axi_poisson_matrix(xy, self.tris, self.V_tau, self.N)
+        else:
+            self.V_node = self.A_node
+            self.edges, self.S_edge, _ = edges_and_normals(xy, self.tris)
+            self.S_b = boundary_normals(xy, self.tris)
+            self.K = poisson_matrix(self.tris, self.S, self.V_tau, self.N)
         self.node_bc = np.asarray(problem.node_bc)
         self.solver = DirichletSolver(self.K, self.node_bc, problem.phi_D)
         self.is_bnd = np.any(self.S_b != 0.0, axis=1)
@@ -288,11 +394,11 @@ class Oracle:
     def fields(self, n):
         """phi, E = -grad phi, |E|, nodal velocities and density gradients."""
         phi = self.poisson(n)
-        E = -nodal_gradient(phi, self.tris, self.S, self.V_tau, self.V_node)
+        E = -nodal_gradient(phi, self.tris, self.S, self.V_tau, self.A_node)
         Emag = np.sqrt(E[:, 0] ** 2 + E[:, 1] ** 2)
         mu = [mobility(sp_, Emag) for sp_ in self.p.species]
         vel = [np.sign(sp_.charge) * mu[s][:, None] * E for s, sp_ in enumerate(self.p.species)]
-        grad = [nodal_gradient(n[s], self.tris, self.S, self.V_tau, self.V_node)
+        grad = [nodal_gradient(n[s], self.tris, self.S, self.V_tau, self.A_node)
                 for s in range(len(self.p.species))]
         return phi, E, Emag, mu, vel, grad
 

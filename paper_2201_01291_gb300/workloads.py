@@ -82,6 +82,7 @@ class Problem:
     opts: Opts
     seed: int
     meta: dict
+    axisymmetric: bool = False   # True: y is the radius r >= 0, x the axis
 
     @property
     def n_nodes(self) -> int:
@@ -244,3 +245,29 @@ def random_instances(count: int, seed: int, t_min: float = 2e3, t_max: float = 2
                            source=src, n_species=ns, name=f"inst{k}")
         out.append(p)
     return out
+
+
+def axisym_problem(nx: int, nr: int, Lx: float, Lr: float, voltage: float, seed: int,
+                   n_peak: float = 1e19, n_back: float = 1e13, sigma: float = 1e-3, jitter: float = 0.2,
+                   field_dependent: bool = False, source: int = SRC_NONE, n_species: int = 2,
+                   x0: Optional[float] = None, name: str = "axisym", opts: Optional[Opts] = None) -> Problem:
+    """Axisymmetric (x, r) plane-to-plane gap: x is the axis, y = r the radius (the axis y = 0
+    and the outer radius carry no condition: zero normal field), phi = 0 on x = 0 and
+    phi = voltage on x = Lx; Gaussian seed on the axis at x0 (default mid-gap)."""
+    xy, tris, ii, jj = jittered_rectangle(nx, nr, Lx, Lr, jitter, seed)
+    node_bc = np.zeros(nx * nr, dtype=np.int32)
+    phi_D = np.zeros(nx * nr, dtype=np.float64)
+    left = ii == 0
+    right = ii == nx - 1
+    node_bc[left | right] = 1
+    phi_D[right] = voltage
+    x0 = 0.5 * Lx if x0 is None else x0
+    sp = default_species(xy, (x0, 0.0), sigma, n_peak, n_back, field_dependent, n_species)
+    src = Source()
+    if source != SRC_NONE:
+        A, B = townsend_air()
+        n_gas = 101325.0 / (K_BOLTZMANN * 300.0)
+        nu_att = 1e-17 * n_gas if source == SRC_TOWNSEND_ATTACH else 0.0
+        src = Source(source, [A, B, nu_att], [0, 1, 2 if n_species == 3 else -1])
+    return Problem(name, xy, tris, node_bc, phi_D, sp, src, opts or Opts(), seed,
+                   dict(nx=nx, nr=nr, Lx=Lx, Lr=Lr, voltage=voltage), axisymmetric=True)
