@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "batch256", "served", "sweep"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "axisym", "batch256", "served", "sweep"])
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
     ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip nvidia-smi sampling (diagnosis only)")
     ap.add_argument("--pcg-threads", type=int, default=0, help="PCG block size (0 = library default)")
     ap.add_argument("--pcg-kind", type=int, default=0,
-                    help="PCG kernel: 0 auto, 1 streaming, 2 register-resident, 5 cluster-resident")
+                    help="PCG kernel: 0 auto, 1 streaming, 2 register-resident, 5 cluster-resident, 7 BiCGStab")
     ap.add_argument("--pcg-max-iter", type=int, default=0,
                     help="cap PCG iterations per solve (profiling captures only; not a bench setting)")
     return ap.parse_args()
@@ -62,6 +62,11 @@ def make_problem(name):
         p = W.config_pin_plane()
         desc = ("pin-plane streamer 1cm x 2cm, 500x1000 jittered nodes (997,002 tris), Morton order, "
                 "20 kV needle, mu_e ~ E^-0.2, Townsend alpha (air-like, 1 atm), e + positive ions, FP64")
+    elif name == "axisym":
+        p = W.config_axisym_streamer()
+        desc = ("axisymmetric (x, r) streamer gap 1.25cm x 1.25cm, 701x701 jittered nodes (980,000 tris), "
+                "Morton order, 18.75 kV (1.5 MV/m), seed 5e18 m^-3 on the axis at x = 1 cm, mu_e ~ E^-0.2, "
+                "Townsend alpha, e + positive ions, r-weighted Poisson solved by BiCGStab, FP64")
     else:
         p = W.config_plates_65()
         desc = "parallel plates 1cm x 1cm, 65x65 jittered nodes (8192 tris), 5 kV, constant mu/D, FP64"
@@ -139,7 +144,8 @@ def aggregate(elapsed, units_per_rank, world, device="cuda"):
 
 
 KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (register-resident)",
-                4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)"}
+                4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)",
+                7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)"}
 
 # DRAM bytes per PCG iteration measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of
 # a 300-iteration capture of the pin-plane 500x1000 solve, divided by 300): the working set
@@ -155,12 +161,20 @@ def pcg_traffic_model(info, iters, solves):
     register-resident (2): p, q, x in registers: 12 nnz + r gather 8 + r read/write 16
         = 12 nnz + 24 N bytes;
     mixed (4): FP32 inner iteration 8 nnz + 48 N bytes (FP64 outer residuals not counted);
-    flops: 2 nnz + 12 N per iteration (SpMV, 3 recurrences, 2 dots, x update)."""
+    flops: 2 nnz + 12 N per iteration (SpMV, 3 recurrences, 2 dots, x update);
+    BiCGStab (7): two gathers per iteration, 12 B per stored entry each; phase S gathers v
+        (8 + 4 B row length), reads r, A r, rh (24), writes z, s, t (24); phase R gathers t
+        (8 + 4), reads s, p, v, z, rh, x (48), writes x, r, A r, p, v (40): 24 nnz + 160 N bytes;
+        flops 4 nnz + 32 N per iteration."""
     N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
-    per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N}.get(kind, 0)
-    per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N}.get(kind, 0)
+    per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
+    per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
+                 7: 24 * nnz + 170 * N}.get(kind, 0)
     bytes_ = iters * per_it + solves * per_solve
-    flops = iters * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
+    if kind == 7:
+        flops = iters * (4 * nnz + 32 * N) + solves * (4 * nnz + 20 * N)
+    else:
+        flops = iters * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
     return bytes_, flops
 
 

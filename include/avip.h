@@ -58,12 +58,20 @@ extern "C" {
 #define AVIP_PREC_FP64 0   /* every stage in FP64                                           */
 #define AVIP_PREC_MIXED 1  /* FP32 inner PCG + FP64 iterative refinement of the residual    */
 #define AVIP_MAX_SPECIES 4
+/* Geometry of the (x, y) plane.  AXISYMMETRIC: y is the radius r >= 0 about the x axis and
+ * every volume and face integral carries the weight r (sections "Axisymmetric configuration"
+ * of the Poisson chapter and the axisymmetric flux form of the transport chapter): r-weighted
+ * Poisson rows, which make the matrix non-symmetric (solved by Jacobi-scaled BiCGStab),
+ * r-weighted edge and boundary normals, dual volumes of revolution.  Volumes, charges and the
+ * VOLUME field are then per radian (the common factor 2 pi is left out). */
+#define AVIP_GEOM_PLANAR 0
+#define AVIP_GEOM_AXISYMMETRIC 1
 
 #define AVIP_FIELD_PHI 0
 #define AVIP_FIELD_EX 1
 #define AVIP_FIELD_EY 2
 #define AVIP_FIELD_DENSITY 3  /* species index in `s`                                       */
-#define AVIP_FIELD_VOLUME 4   /* median-dual nodal volume V_i                               */
+#define AVIP_FIELD_VOLUME 4   /* median-dual nodal volume V_i (per radian if axisymmetric)  */
 
 typedef void* (*avip_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*avip_free_fn)(void* ptr, void* ctx);
@@ -75,17 +83,21 @@ typedef struct avip_opts {
   double beta;                         /* Sweby limiter parameter, 1 <= beta <= 2             */
   int32_t limiter;                     /* AVIP_LIM_*                                          */
   int32_t precision;                   /* AVIP_PREC_*                                         */
-  double rtol;                         /* stop when ||b - K phi||_2 <= rtol ||b||_2           */
+  double rtol;                         /* stop when ||b - K phi||_2 <= rtol ||b||_2 over the
+                                          free rows of the diagonally scaled system (Dirichlet
+                                          rows hold their value exactly and are not counted) */
   int32_t max_iter;                    /* PCG iteration cap per solve                         */
   int32_t reorder;                     /* 1 = Morton renumbering (default), 0 = keep order    */
   double dt_fixed;                     /* > 0: use this time step instead of the automatic one */
   double inner_rtol;                   /* mixed precision: FP32 inner reduction per refinement */
   int32_t pcg_threads;                 /* streaming PCG block size (256/512/768/1024; 0 = 768) */
-  int32_t pcg_kind;                    /* PCG kernel: 0 auto, 1 streaming, 2 register-resident */
+  int32_t pcg_kind;                    /* solver kernel: 0 auto, 1 streaming, 2 register-resident,
+                                          5 cluster, 7 BiCGStab (the only one for AXISYMMETRIC) */
   void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
   avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
   avip_free_fn free;
   void* alloc_ctx;
+  int32_t geometry;                    /* AVIP_GEOM_* (default PLANAR)                          */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */
@@ -113,8 +125,11 @@ int avip_opts_default(avip_opts* o);
  *   phi_D[n_nodes]  Dirichlet potential (read where node_bc == 1).
  * Computes the metrics of the section "Nomenclature and notations" (cell volumes, nodal
  * normals, median-dual volumes, edge normals, boundary nodal normals) and the Poisson matrix
- * of Eq. coeff_matriceA, renumbers, and uploads everything.  Errors: AVIP_EINVAL for
- * out-of-range indices, zero-area cells, a mesh with no Dirichlet node; AVIP_ENOMEM. */
+ * of Eq. coeff_matriceA (with opts->geometry AXISYMMETRIC: their r-weighted forms of the
+ * axisymmetric sections), renumbers, and uploads everything.  Errors: AVIP_EINVAL for
+ * out-of-range indices, zero-area cells, a mesh with no Dirichlet node, a negative radius or
+ * a non-positive Poisson diagonal (AXISYMMETRIC), AXISYMMETRIC with AVIP_PREC_MIXED or with
+ * a pcg_kind other than 0 or 7; AVIP_ENOMEM. */
 int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
                 const int32_t* node_bc, const double* phi_D, const avip_opts* opts,
                 avip_mesh_t* out);
@@ -167,7 +182,8 @@ int state_get(avip_mesh_t h, double* host_state);
 int state_set(avip_mesh_t h, const double* host_state);
 
 /* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
- * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident), PCG blocks,
+ * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident, 6 cluster mixed,
+ * 7 BiCGStab), solver blocks,
  * PCG threads per block, device bytes held by the handle}. */
 int mesh_info(avip_mesh_t h, int64_t* info8);
 

@@ -14,6 +14,7 @@
 namespace avip {
 cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_bicgstab(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
@@ -41,6 +42,7 @@ struct avip_mesh {
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
+  double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
   unsigned* flags = nullptr;
@@ -156,6 +158,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.p32 = h->p32;
   a.q32 = h->q32;
   a.inner_rtol = h->opts.inner_rtol;
+  a.bcg = h->bcg;
   return a;
 }
 
@@ -192,6 +195,7 @@ int cuda_status(cudaError_t e) {
 
 cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
@@ -283,8 +287,20 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     delete h;
     return AVIP_EINVAL;
   }
+  // the axisymmetric matrix is not symmetric: only BiCGStab (kind 7, FP64) applies
+  const bool axi = h->opts.geometry == AVIP_GEOM_AXISYMMETRIC;
+  if (axi && (h->opts.precision != AVIP_PREC_FP64 || (h->opts.pcg_kind != 0 && h->opts.pcg_kind != 7))) {
+    std::snprintf(g_err, sizeof(g_err), "axisymmetric meshes need precision FP64 and pcg_kind 0 or 7 (BiCGStab)");
+    delete h;
+    return AVIP_EINVAL;
+  }
+  if (h->opts.pcg_kind == 7 && h->opts.precision != AVIP_PREC_FP64) {
+    delete h;
+    return AVIP_EINVAL;
+  }
   // host-side validation and metrics first: bad meshes are rejected without touching the GPU
-  int st = prepare_mesh(xy, n_nodes, tris, n_tris, node_bc, phi_D, h->opts.reorder, h->hm, g_err, sizeof(g_err));
+  int st = prepare_mesh(xy, n_nodes, tris, n_tris, node_bc, phi_D, h->opts.reorder, h->opts.geometry, h->hm, g_err,
+                        sizeof(g_err));
   if (st != AVIP_OK) {
     delete h;
     return st;
@@ -327,7 +343,11 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
   h->plan = h->opts.precision == AVIP_PREC_MIXED ? pcg_mixed_plan(m.nslices, h->opts.pcg_threads)
                                                  : pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
-  if (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5 || h->opts.pcg_kind == 6) {
+  const bool bicg = axi || h->opts.pcg_kind == 7;
+  if (bicg) {
+    h->plan = bicgstab_plan(m.nslices, h->opts.pcg_threads);
+    ok = ok && zalloc(h, h->bcg, 3 * Np);
+  } else if (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5 || h->opts.pcg_kind == 6) {
     // small meshes: one thread-block cluster with everything in shared memory
     const int mixed = h->opts.precision == AVIP_PREC_MIXED ? 1 : 0;
     ClusterHost chd;
@@ -824,6 +844,11 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
     if (!ready(h)) {
       delete b;
       return h ? AVIP_ESTATE : AVIP_EINVAL;
+    }
+    if (h->plan.kind == 7) {  // the batched solver is conjugate gradients (symmetric matrices)
+      std::snprintf(g_err, sizeof(g_err), "batches take planar meshes solved by CG only");
+      delete b;
+      return AVIP_EINVAL;
     }
     cudaStreamSynchronize(h->stream);
     b->m.push_back(h);

@@ -28,7 +28,8 @@ struct HostMesh {
   int64_t nelem = 0;                  // SELL elements incl. padding
   std::vector<int32_t> perm;          // new -> caller index
   std::vector<int32_t> iperm;         // caller -> new index
-  std::vector<double> x, y, vol;      // new order
+  int32_t geometry = 0;               // AVIP_GEOM_*
+  std::vector<double> x, y, vol;      // new order; vol = dual volume (per radian when axisymmetric)
   std::vector<int32_t> bc;            // new order
   std::vector<int32_t> tri;           // 3*T, new indices, counter-clockwise (SoA: a[T], b[T], c[T])
   std::vector<double> dxmin;          // T, shortest edge
@@ -42,8 +43,9 @@ struct HostMesh {
 };
 
 // Builds every metric and sparse structure; returns AVIP_OK or AVIP_EINVAL.
+// geometry: AVIP_GEOM_PLANAR or AVIP_GEOM_AXISYMMETRIC (second coordinate = radius >= 0).
 int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
-                 const int32_t* node_bc, const double* phi_D, int reorder, HostMesh& out,
+                 const int32_t* node_bc, const double* phi_D, int reorder, int geometry, HostMesh& out,
                  char* err, size_t errlen);
 
 // ----------------------------------------------------------------- kernel argument blocks
@@ -144,18 +146,22 @@ struct PcgArgs {
   float* p32;
   float* q32;
   double inner_rtol;
+  // BiCGStab (non-symmetric systems): three more vectors s, t and the shadow residual, each
+  // Npad long, at bcg + k * Npad (v = A p lives in q_ap)
+  double* bcg;
 };
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
-                   // 6 cluster-resident mixed precision
+                   // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix)
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
 };
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
+PcgPlan bicgstab_plan(int nslices, int requested_tpb);
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

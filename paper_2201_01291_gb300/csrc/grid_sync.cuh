@@ -76,6 +76,20 @@ struct FlagSync {
   unsigned seq;   // reductions passed so far (identical in every thread)
 };
 
+// Shared-memory scratch of grid_allsum.  A __shared__ variable declared inside a function
+// template exists once per instantiation, so a kernel that reduces with several (NV, NE)
+// combinations would reserve the scratch several times over (less L1 for the gathers, fewer
+// co-resident blocks); declared in this one non-template function it exists once per kernel.
+struct AllsumScratch {
+  double thr[4 * 1024];  // per-thread values, [value k][thread]
+  double res[8];         // totals, then epilogue results
+  int ok;
+};
+__device__ __forceinline__ AllsumScratch& allsum_scratch() {
+  __shared__ AllsumScratch s;
+  return s;
+}
+
 struct NoEpilogue {
   __device__ void operator()(const double*, double*) const {}
 };
@@ -103,13 +117,14 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 
   const unsigned seq = ++fs.seq;
   const int par = seq & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ double s_res[8];
-  __shared__ int s_ok;
+  AllsumScratch& scr = allsum_scratch();
+  double* s_res = scr.res;
+  int& s_ok = scr.ok;
+  double* s_thr = scr.thr;
   // Block partial: every thread stores its values, then warp 0 adds them (lane l takes
   // threads l, l+32, ...) and finishes with a shuffle tree.  On GB300 an FP64 add costs a
   // warp ~16 cycles of the SM's FP64 pipe, so this uses blockDim/32 + 5 warp-wide adds per
   // value instead of the 5 * blockDim/32 + 5 of a shuffle tree in every warp.
-  __shared__ double s_thr[4 * 1024];
   (void)smem;
 #pragma unroll
   for (int k = 0; k < NV; ++k) s_thr[k * 1024 + threadIdx.x] = v[k];

@@ -17,6 +17,19 @@
 //   * nodal gradient weights: grad u_i = (1/V_i) sum_tau (V_tau/3) grad u_tau with
 //     grad u_tau = -1/(n_d V_tau) sum_k u_k S_k, i.e. grad u_i = sum_k G_ik u_k with
 //     G_ik = -(1 / (6 V_i)) sum_{tau containing i and k} S_k^tau.
+//
+// Axisymmetric geometry (second coordinate = radius r; every integral per radian):
+//   * Poisson row i: K_ik = sum_tau S_k . I_i^tau / (n_d V_tau), with I_i^tau the integral of
+//     r n dl over the dual contour of i inside tau in the closed form of the axisymmetric
+//     Poisson section, 1/24 [(4 r_tau + 2 r_i + r_j + r_l) S_i - (2 r_tau + r_i + r_j) S_j
+//     - (2 r_tau + r_i + r_l) S_l]; the radius makes K non-symmetric;
+//   * dual volume = integral of r over the median-dual cell, per triangle
+//     V_tau (22 r_i + 7 r_j + 7 r_l) / 108 (the centroid radius of the dual cell in the
+//     second Pappus theorem; the node radius would give nodes on the axis no volume);
+//   * edge normal S_ij^tau times the radius at the middle of its dual face,
+//     ((r_i + r_j)/2 + r_tau)/2 (first Pappus theorem, axisymmetric flux form);
+//   * boundary normal: each half face times the radius at its middle, (3 r_p + r_q)/4;
+//   * the gradient is two-dimensional: G_ik keeps the planar dual areas.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -64,7 +77,7 @@ void morton_order(const double* xy, int32_t n, std::vector<int32_t>& perm) {
 }  // namespace
 
 int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
-                 const int32_t* node_bc, const double* phi_D, int reorder, HostMesh& m,
+                 const int32_t* node_bc, const double* phi_D, int reorder, int geometry, HostMesh& m,
                  char* err, size_t errlen) {
   auto fail = [&](const char* msg) {
     if (err && errlen) std::snprintf(err, errlen, "%s", msg);
@@ -85,6 +98,12 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
     }
   }
   if (ndir == 0) return fail("at least one Dirichlet node is required (pure Neumann problem is singular)");
+  if (geometry != AVIP_GEOM_PLANAR && geometry != AVIP_GEOM_AXISYMMETRIC) return fail("unknown geometry");
+  const bool axi = geometry == AVIP_GEOM_AXISYMMETRIC;
+  if (axi)
+    for (int32_t i = 0; i < N; ++i)
+      if (xy[2 * i + 1] < 0) return fail("axisymmetric mesh with a negative radius (y < 0)");
+  m.geometry = geometry;
 
   // ---- renumbering
   if (reorder) {
@@ -147,11 +166,24 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
     for (int32_t c = 0; c < T; ++c)
       for (int k = 0; k < 3; ++k) cells[fillp[tv[3 * c + k]]++] = c;
   }
-  m.vol.assign(N, 0.0);
+  // planar dual areas (gradient weights) and the dual volumes of the transport update
+  std::vector<double> area(N, 0.0);
   for (int32_t i = 0; i < N; ++i)
-    for (int32_t e = ncell[i]; e < ncell[i + 1]; ++e) m.vol[i] += Vt[cells[e]] / 3.0;
+    for (int32_t e = ncell[i]; e < ncell[i + 1]; ++e) area[i] += Vt[cells[e]] / 3.0;
   for (int32_t i = 0; i < N; ++i)
-    if (!(m.vol[i] > 0)) return fail("node not used by any triangle");
+    if (!(area[i] > 0)) return fail("node not used by any triangle");
+  if (axi) {
+    m.vol.assign(N, 0.0);
+    for (int32_t c = 0; c < T; ++c)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t i = tv[3 * c + k], j = tv[3 * c + (k + 1) % 3], l = tv[3 * c + (k + 2) % 3];
+        m.vol[i] += Vt[c] * (22.0 * m.y[i] + 7.0 * m.y[j] + 7.0 * m.y[l]) / 108.0;
+      }
+    for (int32_t i = 0; i < N; ++i)
+      if (!(m.vol[i] > 0)) return fail("axisymmetric dual volume is not positive");
+  } else {
+    m.vol = area;
+  }
 
   // ---- rows: diagonal first then neighbours ascending
   std::vector<int32_t> rowptr(N + 1, 0);
@@ -190,16 +222,30 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
       int32_t c = cells[e];
       int li = (tv[3 * c] == i) ? 0 : (tv[3 * c + 1] == i ? 1 : 2);
       const double six = Sn[6 * c + 2 * li], siy = Sn[6 * c + 2 * li + 1];
+      // axisymmetric: integral of r n dl over the dual contour of i inside c
+      double Ix = 0.0, Iy = 0.0, rc = 0.0;
+      if (axi) {
+        const int lj = (li + 1) % 3, ll = (li + 2) % 3;
+        const double ri = m.y[i], rj = m.y[tv[3 * c + lj]], rl = m.y[tv[3 * c + ll]];
+        rc = (ri + rj + rl) / 3.0;
+        const double wi = 4.0 * rc + 2.0 * ri + rj + rl, wj = 2.0 * rc + ri + rj, wl = 2.0 * rc + ri + rl;
+        Ix = (wi * six - wj * Sn[6 * c + 2 * lj] - wl * Sn[6 * c + 2 * ll]) / 24.0;
+        Iy = (wi * siy - wj * Sn[6 * c + 2 * lj + 1] - wl * Sn[6 * c + 2 * ll + 1]) / 24.0;
+      }
       for (int k = 0; k < 3; ++k) {
         int32_t j = tv[3 * c + k];
         int64_t s = slot(i, j);
         const double skx = Sn[6 * c + 2 * k], sky = Sn[6 * c + 2 * k + 1];
-        K[s] += (six * skx + siy * sky) / (4.0 * Vt[c]);
-        Gx[s] += -skx / (6.0 * m.vol[i]);
-        Gy[s] += -sky / (6.0 * m.vol[i]);
+        if (axi)
+          K[s] += (Ix * skx + Iy * sky) / (2.0 * Vt[c]);
+        else
+          K[s] += (six * skx + siy * sky) / (4.0 * Vt[c]);
+        Gx[s] += -skx / (6.0 * area[i]);
+        Gy[s] += -sky / (6.0 * area[i]);
         if (j != i) {
-          Sx[s] += (six - skx) / 6.0;
-          Sy[s] += (siy - sky) / 6.0;
+          const double rf = axi ? 0.5 * (0.5 * (m.y[i] + m.y[j]) + rc) : 1.0;
+          Sx[s] += rf * (six - skx) / 6.0;
+          Sy[s] += rf * (siy - sky) / 6.0;
           shared[s] += 1;
         }
       }
@@ -212,10 +258,13 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
       int32_t p = tv[3 * c + k], q = tv[3 * c + (k + 1) % 3];
       if (shared[slot(p, q)] == 1) {
         double nx = m.y[q] - m.y[p], ny = -(m.x[q] - m.x[p]);
-        Sx[rowptr[p]] += 0.5 * nx;
-        Sy[rowptr[p]] += 0.5 * ny;
-        Sx[rowptr[q]] += 0.5 * nx;
-        Sy[rowptr[q]] += 0.5 * ny;
+        // axisymmetric: each half face weighted by the radius at its middle
+        const double wp = axi ? 0.25 * (3.0 * m.y[p] + m.y[q]) : 1.0;
+        const double wq = axi ? 0.25 * (3.0 * m.y[q] + m.y[p]) : 1.0;
+        Sx[rowptr[p]] += 0.5 * nx * wp;
+        Sy[rowptr[p]] += 0.5 * ny * wp;
+        Sx[rowptr[q]] += 0.5 * nx * wq;
+        Sy[rowptr[q]] += 0.5 * ny * wq;
       }
     }
   }

@@ -6,7 +6,8 @@
 // preconditioned residual is the residual itself, so one vector, one multiply and one dot
 // product per row and iteration disappear; on GB300, where the FP64 pipe issues one warp-wide
 // FMA per ~16 cycles per SM, that is a direct saving.  The stopping test is on the scaled
-// residual: ||b' - A x||_2 <= rtol ||b'||_2.
+// residual of the free rows: ||b' - A x||_2 <= rtol ||b'||_2, both norms over the rows that
+// are not Dirichlet rows (those are unit rows whose residual is zero from the start).
 //
 // One cooperative, persistent launch runs the whole solve: assembly of b' from the densities,
 // the initial residual, every iteration, the final true-residual check and phi = D^-1/2 x.
@@ -28,44 +29,12 @@
 
 #include "avip_internal.h"
 #include "grid_sync.cuh"
+#include "sell.cuh"
 
 namespace avip {
 
 constexpr int kMaxRestarts = 8;
 constexpr int kResTPB = 512;  // block size of the register-resident kernels (one block per SM)
-
-// One row of y = A v over the SELL-32 structure (diagonal first, then ascending columns).
-// Slots are fetched in groups of 8 so that the column loads, the value loads and the
-// dependent gathers of a group are all in flight together.
-__device__ __forceinline__ double sell_row_dot(const SellView& A, int slice, int lane, int row,
-                                               const double* __restrict__ v) {
-  constexpr int U = 8;
-  const int base = __ldg(A.sl_ptr + slice) + lane;
-  const int w = __ldg(A.sl_w + slice);
-  const int rl = __ldg(A.rlen + row);
-  double acc = 0.0;
-  for (int k0 = 0; k0 < w; k0 += U) {
-    int c[U];
-    double av[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u;
-      c[u] = row;
-      av[u] = 0.0;
-      if (k < rl) {
-        c[u] = __ldg(A.col + base + k * kSlice);
-        av[u] = __ldg(A.aval + base + k * kSlice);
-      }
-    }
-    double xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = (k0 + u < rl) ? __ldcg(v + c[u]) : 0.0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (k0 + u < rl) acc = fma(av[u], xv[u], acc);
-  }
-  return acc;
-}
 
 template <int TPB>
 __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_kernel(PcgArgs a) {
@@ -94,7 +63,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
     } else {
       b = a.b[i];
     }
-    bb[0] = fma(b, b, bb[0]);
+    if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
   }
   // x must be complete before the residual gathers it: this reduction is also the barrier
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
@@ -104,10 +73,10 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
     bool check = true;  // the first pass computes the initial (true) residual
     int it = 0, restarts = 0, status = AVIP_OK;
     if (bb[0] == 0.0) {
-      // b == 0: the solution is phi = 0
+      // free b == 0: the solution is x = b (0 on free rows, the value on Dirichlet rows)
       for (int s = gwarp; s < nsl; s += nwarps) {
         const int i = s * kSlice + lane;
-        if (i < N) a.x[i] = 0.0;
+        if (i < N) a.x[i] = a.b[i];
       }
     } else {
       while (true) {
@@ -274,7 +243,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
     } else {
       b = a.b[i];
     }
-    bb[0] = fma(b, b, bb[0]);
+    if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
   }
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
   {
@@ -284,7 +253,8 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
     int it = 0, restarts = 0, status = AVIP_OK;
     if (bb[0] == 0.0) {
 #pragma unroll
-      for (int j = 0; j < MAXS; ++j) x[j] = 0.0;
+      for (int j = 0; j < MAXS; ++j)
+        if (rl[j] != 0) x[j] = a.b[(gwarp * MAXS + j) * kSlice + lane];  // free b == 0: x = b
     } else {
       while (true) {
         if (check || it >= a.max_iter) {

@@ -156,7 +156,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
       } else {
         b = a.b[i];
       }
-      bb[0] = fma(b, b, bb[0]);
+      if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
       push(xs, i, x);
       a.b[i] = b;
     }
@@ -169,7 +169,10 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
   bool check = true;
   int it = 0, restarts = 0, status = AVIP_OK;
   if (bb[0] == 0.0) {
-    for (int li = threadIdx.x; li < R; li += blockDim.x) xs[li] = 0.0;
+    for (int li = threadIdx.x; li < R; li += blockDim.x) {  // free b == 0: x = b
+      const int i = s0 * kSlice + li;
+      xs[li] = i < N ? a.b[i] : 0.0;
+    }
   } else {
     while (true) {
       if (check || it >= a.max_iter) {
@@ -404,7 +407,7 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
         b = a.b[i];
       }
       a.b[i] = b;
-      bb[0] = fma(b, b, bb[0]);
+      if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
       push64(x64, i, x);
     }
     x64[li] = x;
@@ -415,6 +418,11 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
   const double thresh = a.rtol * a.rtol * bb[0];
   int it = 0, outer = 0, status = AVIP_OK;
   double rr64 = 0.0;
+  if (bb[0] == 0.0)
+    for (int li = threadIdx.x; li < R; li += blockDim.x) {  // free b == 0: x = b
+      const int i = s0 * kSlice + li;
+      x64[li] = i < N ? a.b[i] : 0.0;
+    }
   while (bb[0] != 0.0) {
     // ---- FP64 residual of the FP64 iterate
     double r2[1] = {0.0};

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
     } else {
       b = a.b[i];
     }
-    bb[0] = fma(b, b, bb[0]);
+    if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
   }
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
   {
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
     }
     for (int s = gwarp; s < nsl; s += nwarps) {
       const int i = s * kSlice + lane;
-      if (i < N) a.phi[i] = a.dsqinv[i] * a.x[i];
+      if (i < N) a.phi[i] = a.dsqinv[i] * (bb[0] == 0.0 ? a.b[i] : a.x[i]);  // free b == 0: x = b
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.sc->pcg_iters = it;

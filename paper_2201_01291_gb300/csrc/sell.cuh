@@ -1,0 +1,40 @@
+// SELL-32 row product shared by the FP64 Krylov kernels.
+#pragma once
+#include "avip_internal.h"
+
+namespace avip {
+
+// One row of y = A v over the SELL-32 structure (diagonal first, then ascending columns).
+// Slots are fetched in groups of 8 so that the column loads, the value loads and the
+// dependent gathers of a group are all in flight together.
+__device__ __forceinline__ double sell_row_dot(const SellView& A, int slice, int lane, int row,
+                                               const double* __restrict__ v) {
+  constexpr int U = 8;
+  const int base = __ldg(A.sl_ptr + slice) + lane;
+  const int w = __ldg(A.sl_w + slice);
+  const int rl = __ldg(A.rlen + row);
+  double acc = 0.0;
+  for (int k0 = 0; k0 < w; k0 += U) {
+    int c[U];
+    double av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      c[u] = row;
+      av[u] = 0.0;
+      if (k < rl) {
+        c[u] = __ldg(A.col + base + k * kSlice);
+        av[u] = __ldg(A.aval + base + k * kSlice);
+      }
+    }
+    double xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = (k0 + u < rl) ? __ldcg(v + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k0 + u < rl) acc = fma(av[u], xv[u], acc);
+  }
+  return acc;
+}
+
+}  // namespace avip

@@ -271,3 +271,14 @@ def axisym_problem(nx: int, nr: int, Lx: float, Lr: float, voltage: float, seed:
         src = Source(source, [A, B, nu_att], [0, 1, 2 if n_species == 3 else -1])
     return Problem(name, xy, tris, node_bc, phi_D, sp, src, opts or Opts(), seed,
                    dict(nx=nx, nr=nr, Lx=Lx, Lr=Lr, voltage=voltage), axisymmetric=True)
+
+
+def config_axisym_streamer(nx: int = 701, nr: int = 701, seed: int = 2201) -> Problem:
+    """Axisymmetric streamer gap in the geometry of the paper's axisymmetric streamer benchmark
+    (section "Bagheri benchmark"): 1.25 cm x 1.25 cm, 1.5 MV/m background field (18.75 kV),
+    Gaussian seed of 5e18 m^-3 (sigma 0.4 mm) on the axis at x = 1 cm over a 1e13 m^-3
+    background; local-field electron mobility and Townsend ionisation of this library's models
+    (the benchmark's tabulated transport data are not used).  701 x 701 nodes: 980,000
+    triangles, the size class of the pin-plane workload."""
+    return axisym_problem(nx, nr, 1.25e-2, 1.25e-2, 18750.0, seed, n_peak=5e18, n_back=1e13, sigma=4e-4,
+                          field_dependent=True, source=SRC_TOWNSEND, x0=1e-2, name="axisym_streamer")

@@ -64,3 +64,26 @@ def test_mesh_validation_on_host(lib):
     o2 = avip.avip_opts_default()
     o2.rtol = -1.0
     assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o2)[0] == avip.AVIP_EINVAL
+
+
+def test_axisymmetric_validation_on_host(lib):
+    """Axisymmetric options are checked on the host: negative radius, unknown geometry, and
+    solvers that need a symmetric matrix (CG kinds, mixed precision) are rejected."""
+    from paper_2201_01291_gb300 import avip, workloads as W
+    p = W.axisym_problem(9, 7, 1e-2, 0.5e-2, 1e4, seed=1)
+    o = avip.avip_opts_default()
+    assert o.geometry == avip.GEOM_PLANAR
+    o.geometry = avip.GEOM_AXISYMMETRIC
+    xy = p.xy.copy()
+    xy[3, 1] = -1e-3
+    assert avip.mesh_create(xy, p.tris, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "negative radius" in avip.last_error()
+    for kind, prec in ((2, avip.PREC_FP64), (1, avip.PREC_FP64), (0, avip.PREC_MIXED)):
+        o2 = avip.avip_opts_default()
+        o2.geometry, o2.pcg_kind, o2.precision = avip.GEOM_AXISYMMETRIC, kind, prec
+        assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o2)[0] == avip.AVIP_EINVAL
+        assert "BiCGStab" in avip.last_error()
+    o3 = avip.avip_opts_default()
+    o3.geometry = 5
+    assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o3)[0] == avip.AVIP_EINVAL
+    assert "geometry" in avip.last_error()
