@@ -24,6 +24,9 @@ Structure (each function cites the passage it follows):
     computation");
   * source: ionisation S = alpha mu_e |E| n_e added to electrons and positive ions
     (section "Bagheri benchmark"), optional attachment;
+  * Scharfetter-Gummel edge flux as the alternative scheme (section "Scharfetter Gummel
+    scheme": exponential fitting on the edge-tangential part of the face normal, centred
+    scheme on the normal part);
   * explicit update and the charge sum;
   * axisymmetric (x, r) variant (section "Axisymmetric configuration" and the axisymmetric
     flux form): r-weighted Poisson rows (closed-form dual-contour integral), r-weighted edge
@@ -345,6 +348,41 @@ def limiter(r, beta, kind):
     return (r + np.abs(r)) / (1.0 + np.abs(r))
 
 
+def bernoulli(x):
+    """B(x) = x / (e^x - 1), B(0) = 1 (0 for x beyond the overflow of e^x)."""
+    out = np.ones_like(x)
+    nz = x != 0
+    with np.errstate(over="ignore"):
+        out[nz] = x[nz] / np.expm1(x[nz])
+    return out
+
+
+def sg_edge_flux(u_i, u_j, x_i, x_j, S, V, D, g):
+    """Scharfetter-Gummel edge flux through the dual face S (oriented i -> j), section
+    "Scharfetter Gummel scheme": S is split along the edge direction e = ij/|ij| into
+    S_par = (S.e) e and S_perp = S - S_par;
+      tangential  V.S_par (u_j - e^a u_i) / (1 - e^a),  a = h V.e / D,  h = |ij|,
+      normal      V.S_perp (u_i + u_j)/2 - D g.S_perp   (centred),
+    with V the edge velocity and g the mean of the two nodal gradients.  The tangential part
+    is evaluated as (D (S.e) / h) (B(-a) u_i - B(a) u_j) with the Bernoulli function B,
+    which is the same quantity without the overflow of e^a for |a| > 709 and the 0/0 at a = 0;
+    for D = 0 it is the upwind limit (S.e)(max(V.e, 0) u_i + min(V.e, 0) u_j)."""
+    d = x_j - x_i
+    h = np.sqrt(np.einsum("ij,ij->i", d, d))
+    e = d / h[:, None]
+    s = np.einsum("ij,ij->i", S, e)
+    S_par = s[:, None] * e
+    S_perp = S - S_par
+    Vt = np.einsum("ij,ij->i", V, e)
+    if D > 0:
+        a = h * Vt / D
+        F_par = (D * s / h) * (bernoulli(-a) * u_i - bernoulli(a) * u_j)
+    else:
+        F_par = s * (np.maximum(Vt, 0.0) * u_i + np.minimum(Vt, 0.0) * u_j)
+    F_perp = np.einsum("ij,ij->i", V, S_perp) * 0.5 * (u_i + u_j) - D * np.einsum("ij,ij->i", g, S_perp)
+    return F_par + F_perp
+
+
 # ----------------------------------------------------------------------------- the method
 class Oracle:
     """The full explicit iteration on one mesh.  `problem` is any object with the fields of
@@ -454,11 +492,14 @@ class Oracle:
     def edge_flux(self, u, grad, vel, D, dt):
         """Limited Lax-Wendroff convective flux plus central diffusive flux through the dual
         face of every edge (i, j), i < j, counted positive from i to j (LLW section and
-        "Central difference diffusive flux integration")."""
+        "Central difference diffusive flux integration"); or, with opts.scheme = 1, the
+        Scharfetter-Gummel flux of sg_edge_flux."""
         o = self.p.opts
         i, j = self.edges[:, 0], self.edges[:, 1]
         S = self.S_edge
         Vij = 0.5 * (vel[i] + vel[j])
+        if getattr(o, "scheme", 0) == 1:
+            return sg_edge_flux(u[i], u[j], self.xy[i], self.xy[j], S, Vij, D, 0.5 * (grad[i] + grad[j]))
         a = np.einsum("ij,ij->i", Vij, S)
         gij = 0.5 * (grad[i] + grad[j])
         up_i = a >= 0

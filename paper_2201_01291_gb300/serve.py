@@ -30,6 +30,7 @@ from . import avip
 BYTES_PER_NODE = 1400
 BYTES_PER_TRI = 24
 CLUSTER_NODES = 20000  # meshes up to this size use the cluster-resident solver (shared slots)
+CLUSTER_KINDS = (5, 6)  # solver kinds that occupy one thread-block cluster, not the whole GPU
 
 
 def estimate_bytes(problem) -> int:
@@ -99,9 +100,10 @@ class Server:
         self.admit_log: List[tuple] = []
 
     def _work(self, req: Request, t0: float, release):
-        ex = req.problem.n_nodes > CLUSTER_NODES
         try:
             m = avip.Mesh(req.problem, rtol=self.rtol)
+            # cluster-resident solves share the GPU; whole-GPU cooperative solves run exclusively
+            ex = m.info["pcg_kind"] not in CLUSTER_KINDS
             left = req.nsteps
             while left > 0:
                 k = min(self.chunk, left)

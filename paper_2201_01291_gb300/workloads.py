@@ -38,6 +38,9 @@ BND_OUTFLOW = 1             # F = F_C + F_D ("supersonic")
 LIM_SWEBY = 0
 LIM_VANLEER = 1
 
+FLUX_LLW = 0                # limited Lax-Wendroff convection + central diffusion
+FLUX_SG = 1                 # Scharfetter-Gummel on the edge-tangential part, centred normal part
+
 
 @dataclasses.dataclass
 class Species:
@@ -68,6 +71,7 @@ class Opts:
     rtol: float = 1e-12         # PCG stop: ||b - K phi||_2 <= rtol ||b||_2
     max_iter: int = 20000
     dt_fixed: float = 0.0       # > 0 replaces the automatic time step
+    scheme: int = FLUX_LLW      # edge flux scheme
 
 
 @dataclasses.dataclass
