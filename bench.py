@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-12)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed = FP32 inner PCG with FP64 refinement of the Poisson residual")
+    ap.add_argument("--scheme", default="llw", choices=["llw", "sg"],
+                    help="edge flux: limited Lax-Wendroff (default) or Scharfetter-Gummel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
@@ -56,7 +58,16 @@ def parse():
     return ap.parse_args()
 
 
-def make_problem(name):
+def make_problem(name, scheme="llw"):
+    p, desc = _make_problem(name)
+    if scheme == "sg":
+        from paper_2201_01291_gb300 import workloads as W
+        p.opts.scheme = W.FLUX_SG
+        desc += ", Scharfetter-Gummel edge flux"
+    return p, desc
+
+
+def _make_problem(name):
     from paper_2201_01291_gb300 import workloads as W
     if name == "pin_plane":
         p = W.config_pin_plane()
@@ -98,6 +109,11 @@ class ClockSampler:
                  "-lms", "500"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (driver/NVML initialisation) can stall the GPU's work
+            # submission for a few hundred ms: let it finish before the timed region starts
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -188,7 +204,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
         build.build()
     avip.load()
-    problem, desc = make_problem(args.workload)
+    problem, desc = make_problem(args.workload, args.scheme)
     T = problem.n_tris
     stream = torch.cuda.Stream()
     kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
@@ -468,7 +484,7 @@ def cpu_baseline(problem, steps):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    problem, desc = make_problem(args.workload)
+    problem, desc = make_problem(args.workload, args.scheme)
     O = oracle_module()
     t0 = time.perf_counter()
     o = O.Oracle(problem)

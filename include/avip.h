@@ -55,8 +55,13 @@ extern "C" {
 #define AVIP_BND_OUTFLOW 1 /* boundary node flux F = F_C + F_D ("supersonic")              */
 #define AVIP_LIM_SWEBY 0   /* Psi(r) = max(0, min(beta r, 1), min(r, beta))                 */
 #define AVIP_LIM_VANLEER 1 /* Psi(r) = (r + |r|)/(1 + |r|)                                  */
+#define AVIP_FLUX_LLW 0    /* limited Lax-Wendroff convection + central diffusion (default)   */
+#define AVIP_FLUX_SG 1     /* Scharfetter-Gummel on the edge-tangential part of S_ij, centred
+                              scheme on its normal part (section "Scharfetter Gummel scheme") */
 #define AVIP_PREC_FP64 0   /* every stage in FP64                                           */
-#define AVIP_PREC_MIXED 1  /* FP32 inner PCG + FP64 iterative refinement of the residual    */
+#define AVIP_PREC_MIXED 1  /* FP32 inner PCG + FP64 iterative refinement of the residual;
+                              FP32 gradients, velocities, sources and edge fluxes; the state,
+                              the update, the time-step reduction and the charge sum in FP64 */
 #define AVIP_MAX_SPECIES 4
 /* Geometry of the (x, y) plane.  AXISYMMETRIC: y is the radius r >= 0 about the x axis and
  * every volume and face integral carries the weight r (sections "Axisymmetric configuration"
@@ -98,6 +103,7 @@ typedef struct avip_opts {
   avip_free_fn free;
   void* alloc_ctx;
   int32_t geometry;                    /* AVIP_GEOM_* (default PLANAR)                          */
+  int32_t scheme;                      /* AVIP_FLUX_* edge flux (default LLW)                   */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */

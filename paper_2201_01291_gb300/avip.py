@@ -21,6 +21,7 @@ AVIP_OK, AVIP_EINVAL, AVIP_ENOMEM, AVIP_ENOTCONV, AVIP_ENAN, AVIP_ECUDA, AVIP_ET
 FIELD_PHI, FIELD_EX, FIELD_EY, FIELD_DENSITY, FIELD_VOLUME = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 GEOM_PLANAR, GEOM_AXISYMMETRIC = 0, 1
+FLUX_LLW, FLUX_SG = 0, 1
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -32,7 +33,7 @@ class AvipOpts(C.Structure):
                 ("max_iter", C.c_int32), ("reorder", C.c_int32), ("dt_fixed", C.c_double),
                 ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32)]
 
 
 class AvipStats(C.Structure):
@@ -298,6 +299,7 @@ class Mesh:
         o.pcg_threads = pcg_threads
         o.pcg_kind = pcg_kind
         o.geometry = GEOM_AXISYMMETRIC if getattr(problem, "axisymmetric", False) else GEOM_PLANAR
+        o.scheme = getattr(po, "scheme", FLUX_LLW)
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()

@@ -44,6 +44,7 @@ struct avip_mesh {
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
   double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
+  float *gx32 = nullptr, *gy32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *ndat32 = nullptr;  // FP32 DD
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
   unsigned* flags = nullptr;
   double* parts = nullptr;
@@ -183,6 +184,11 @@ DDArgs dd_args(const avip_mesh* h) {
   a.Npad = h->Npad;
   a.partials = h->qpart;
   a.sc = h->sc;
+  a.gx32 = h->gx32;
+  a.gy32 = h->gy32;
+  a.sx32 = h->sx32;
+  a.sy32 = h->sy32;
+  a.ndat32 = h->ndat32;
   return a;
 }
 
@@ -282,6 +288,7 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   else
     avip_opts_default(&h->opts);
   if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
+      (h->opts.scheme != AVIP_FLUX_LLW && h->opts.scheme != AVIP_FLUX_SG) ||
       (h->opts.precision != AVIP_PREC_FP64 && h->opts.precision != AVIP_PREC_MIXED) ||
       (h->opts.precision == AVIP_PREC_MIXED && !(h->opts.inner_rtol > 0 && h->opts.inner_rtol < 1))) {
     delete h;
@@ -365,6 +372,15 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     std::vector<float> a32(m.aval.begin(), m.aval.end());
     ok = upload(h, h->aval32, a32) && zalloc(h, h->e32, Np) && zalloc(h, h->r32, Np) && zalloc(h, h->p32, Np) &&
          zalloc(h, h->q32, Np);
+    // FP32 drift-diffusion stage: gradient weights and edge normals rounded once
+    std::vector<float> f(m.gx.begin(), m.gx.end());
+    ok = ok && upload(h, h->gx32, f);
+    f.assign(m.gy.begin(), m.gy.end());
+    ok = ok && upload(h, h->gy32, f);
+    f.assign(m.sx.begin(), m.sx.end());
+    ok = ok && upload(h, h->sx32, f);
+    f.assign(m.sy.begin(), m.sy.end());
+    ok = ok && upload(h, h->sy32, f) && zalloc(h, h->ndat32, 4 * AVIP_MAX_SPECIES * Np);
   }
   h->nparts = flux_blocks(m.N);
   h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
@@ -393,6 +409,8 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   std::memset(&h->ph, 0, sizeof(h->ph));
   h->ph.beta = h->opts.beta;
   h->ph.limiter = h->opts.limiter;
+  h->ph.scheme = h->opts.scheme;
+  h->ph.dd_fp32 = h->opts.precision == AVIP_PREC_MIXED ? 1 : 0;
   h->ph.cfl = h->opts.cfl;
   h->ph.fourier = h->opts.fourier;
   h->ph.a_diel = h->opts.a_diel;

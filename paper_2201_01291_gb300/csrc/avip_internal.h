@@ -76,6 +76,8 @@ struct Physics {
   int32_t src_model;
   int32_t src_idx[3];
   int32_t limiter;
+  int32_t scheme;     // AVIP_FLUX_*
+  int32_t dd_fp32;    // 1: gradients, velocities, sources and fluxes in FP32 (mixed precision)
   double src_params[3];
   double beta, cfl, fourier, a_diel, a_chem;
   double dt_fixed;
@@ -180,6 +182,16 @@ struct ClusterHost {
 };
 PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd, int mixed = 0);
 
+#ifdef __CUDACC__
+// A solve is skipped when an earlier stage of the run left non-finite data (AVIP_ENAN) or a
+// device wait gave up (AVIP_ETIMEOUT): every block (or CTA of a cluster) reads the same value
+// at entry, so all leave together.
+__device__ __forceinline__ bool solve_skipped(const DevScalars* sc) {
+  const int st = *((volatile const int*)&sc->status);
+  return st == AVIP_ENAN || st == AVIP_ETIMEOUT;
+}
+#endif
+
 struct DDArgs {
   SellView A;
   Physics ph;
@@ -199,6 +211,13 @@ struct DDArgs {
   int32_t Npad;
   double* partials;       // per-block charge partials
   DevScalars* sc;
+  // mixed precision (ph.dd_fp32): FP32 copies of the gradient weights and edge normals, and
+  // the FP32 per-species node records gx, gy, vx, vy (float4)
+  const float* gx32;
+  const float* gy32;
+  const float* sx32;
+  const float* sy32;
+  float* ndat32;
 };
 
 }  // namespace avip

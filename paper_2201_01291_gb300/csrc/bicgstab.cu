@@ -43,6 +43,7 @@ constexpr int kBcgTPB = 768;
 }  // namespace
 
 __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   const int lane = threadIdx.x & 31;
   constexpr int wpb = kBcgTPB / 32;
@@ -106,6 +107,10 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
           if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
           rr_true = r2[0];
           if (rr_true <= thresh) break;
+          if (!isfinite(rr_true)) {  // non-finite data: stop at once
+            status = AVIP_ENAN;
+            break;
+          }
           if (it >= a.max_iter || (it > 0 && restarts >= kBcgMaxRestarts)) {
             status = AVIP_ENOTCONV;
             break;
@@ -198,7 +203,8 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
         if (!grid_allsum<1>(rn2, fs, smem)) goto timeout;
         ++it;
         rho = rho_new;
-        if (rn2[0] <= thresh || omega == 0.0 || rho_new == 0.0 || it >= a.max_iter) restart = true;
+        if (rn2[0] <= thresh || !isfinite(rn2[0]) || omega == 0.0 || rho_new == 0.0 || it >= a.max_iter)
+          restart = true;
       }
     }
     // ---- phi = D^-1/2 x

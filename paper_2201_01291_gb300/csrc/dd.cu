@@ -9,6 +9,7 @@
 //                       central diffusion) and the node-flux boundary closure, then source
 //                       and explicit update into the other density buffer; per-block charge
 //   finalize_kernel     charge sum in fixed order, time, parity flip, run statistics
+//   *32 forms           the same in FP32 arithmetic for the mixed-precision path
 //
 // The residual of Eq. vertex_centered_flux is a sum over the edges of each dual cell.  Here
 // every node gathers its own edges (each flux is evaluated at both ends), so no scatter and
@@ -155,9 +156,16 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
       if (s < ns) {
         const SpeciesParams& sp = a.ph.sp[s];
-        const double* d = a.ndat + (size_t)s * a.Npad * 4;
-        const double vx = (d[4 * n0 + 2] + d[4 * n1 + 2] + d[4 * n2 + 2]) / 3.0;
-        const double vy = (d[4 * n0 + 3] + d[4 * n1 + 3] + d[4 * n2 + 3]) / 3.0;
+        double vx, vy;
+        if (a.ph.dd_fp32) {  // FP32 velocities, FP64 candidate and reduction
+          const float* d = a.ndat32 + (size_t)s * a.Npad * 4;
+          vx = ((double)d[4 * n0 + 2] + (double)d[4 * n1 + 2] + (double)d[4 * n2 + 2]) / 3.0;
+          vy = ((double)d[4 * n0 + 3] + (double)d[4 * n1 + 3] + (double)d[4 * n2 + 3]) / 3.0;
+        } else {
+          const double* d = a.ndat + (size_t)s * a.Npad * 4;
+          vx = (d[4 * n0 + 2] + d[4 * n1 + 2] + d[4 * n2 + 2]) / 3.0;
+          vy = (d[4 * n0 + 3] + d[4 * n1 + 3] + d[4 * n2 + 3]) / 3.0;
+        }
         const double vm = sqrt(vx * vx + vy * vy);
         if (vm > 0.0) cand = fmin(cand, a.ph.cfl * dx / vm);
         if (sp.D > 0.0) cand = fmin(cand, a.ph.fourier * (dx * dx) / sp.D);
@@ -178,13 +186,58 @@ struct EdgeEnd {
   double u, gx, gy, vx, vy, x, y;
 };
 
+// Bernoulli function B(x) = x / (e^x - 1) for x >= 0 (B(0) = 1; 0 once e^x overflows).
+// B(-x) = x + B(x), so one expm1 gives both values without cancellation.
+__device__ __forceinline__ double bernoulli_pos(double x) { return x != 0.0 ? x / expm1(x) : 1.0; }
+
+// Geometry of one edge for the Scharfetter-Gummel split (species independent), canonical
+// orientation lo -> hi: unit direction e, length h, s = S.e and S_perp = S - s e.
+struct SgGeo {
+  double ex, ey, h, rh, s, spx, spy;
+};
+__device__ __forceinline__ SgGeo sg_geometry(double dx, double dy, double Sx, double Sy) {
+  SgGeo g;
+  g.h = sqrt(dx * dx + dy * dy);
+  g.rh = 1.0 / g.h;
+  g.ex = dx * g.rh;
+  g.ey = dy * g.rh;
+  g.s = Sx * g.ex + Sy * g.ey;
+  g.spx = Sx - g.s * g.ex;
+  g.spy = Sy - g.s * g.ey;
+  return g;
+}
+
+// Scharfetter-Gummel flux (section "Scharfetter Gummel scheme"): S is split along the edge
+// direction e into S_par = (S.e) e and S_perp; the tangential part is the exponentially fitted
+// V.S_par (u_hi - e^a u_lo)/(1 - e^a), a = h V.e / D, evaluated as
+// (D (S.e)/h)(B(-a) u_lo - B(a) u_hi) (no overflow for large |a|, no 0/0 at a = 0; D = 0 is
+// the upwind limit); the normal part is centred: V.S_perp (u_lo + u_hi)/2 - D g.S_perp.
+__device__ __forceinline__ double sg_flux(double ulo, double uhi, const SgGeo& G, double Vx, double Vy, double gx,
+                                          double gy, double D) {
+  const double Vt = Vx * G.ex + Vy * G.ey;
+  double fpar;
+  if (D > 0.0) {
+    const double a = G.h * Vt / D;
+    const double aa = fabs(a);
+    const double Bp = bernoulli_pos(aa), Bm = aa + Bp;  // B(|a|), B(-|a|)
+    const double B_neg_a = a >= 0.0 ? Bm : Bp, B_a = a >= 0.0 ? Bp : Bm;
+    fpar = (D * G.s * G.rh) * (B_neg_a * ulo - B_a * uhi);
+  } else {
+    fpar = G.s * (fmax(Vt, 0.0) * ulo + fmin(Vt, 0.0) * uhi);
+  }
+  const double fperp = (Vx * G.spx + Vy * G.spy) * (0.5 * (ulo + uhi)) - D * (gx * G.spx + gy * G.spy);
+  return fpar + fperp;
+}
+
 // Flux from `lo` to `hi` through the dual face with normal (Sx, Sy) oriented lo -> hi:
-// limited Lax-Wendroff convective part with a virtual upwind node plus central diffusion.
+// limited Lax-Wendroff convective part with a virtual upwind node plus central diffusion, or
+// (sg != nullptr) the Scharfetter-Gummel flux.
 __device__ __forceinline__ double edge_flux(const EdgeEnd& lo, const EdgeEnd& hi, double Sx, double Sy,
-                                            double D, double dt, double beta, int lim) {
+                                            double D, double dt, double beta, int lim, const SgGeo* sg) {
   const double Vx = 0.5 * (lo.vx + hi.vx), Vy = 0.5 * (lo.vy + hi.vy);
-  const double av = Vx * Sx + Vy * Sy;
   const double gx = 0.5 * (lo.gx + hi.gx), gy = 0.5 * (lo.gy + hi.gy);
+  if (sg) return sg_flux(lo.u, hi.u, *sg, Vx, Vy, gx, gy, D);
+  const double av = Vx * Sx + Vy * Sy;
   const bool up_lo = av >= 0.0;
   const EdgeEnd& U = up_lo ? lo : hi;
   const EdgeEnd& W = up_lo ? hi : lo;
@@ -232,6 +285,10 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
       const double Sx = __ldg(a.A.sx + e), Sy = __ldg(a.A.sy + e);
       const bool lo_is_me = i < j;
       const double xj = a.x[j], yj = a.y[j];
+      SgGeo geo;
+      const bool use_sg = a.ph.scheme == AVIP_FLUX_SG;
+      if (use_sg)  // canonical lo -> hi, like the flux itself
+        geo = lo_is_me ? sg_geometry(xj - xi, yj - yi, Sx, Sy) : sg_geometry(xi - xj, yi - yj, -Sx, -Sy);
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
         if (s < ns) {
@@ -242,7 +299,8 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
           const EdgeEnd& hi = lo_is_me ? other : me[s];
           // the stored normal is oriented i -> j; the canonical one lo -> hi
           const double sgn = lo_is_me ? 1.0 : -1.0;
-          const double F = edge_flux(lo, hi, sgn * Sx, sgn * Sy, a.ph.sp[s].D, dt, a.ph.beta, a.ph.limiter);
+          const double F = edge_flux(lo, hi, sgn * Sx, sgn * Sy, a.ph.sp[s].D, dt, a.ph.beta, a.ph.limiter,
+                                     use_sg ? &geo : nullptr);
           R[s] = lo_is_me ? R[s] - F : R[s] + F;
         }
       }
@@ -285,7 +343,7 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
   if (bid == 0 && threadIdx.x == 0) a.sc->dt = dt;
 }
 
-__global__ void __launch_bounds__(kDDThreads) flux_update_kernel(DDArgs a) { flux_update_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kDDThreads, 2) flux_update_kernel(DDArgs a) { flux_update_body(a, blockIdx.x); }
 
 // Single block: charge in block order, time, parity, statistics; re-arm the dt minimum.
 __device__ __forceinline__ void finalize_body(DevScalars* sc, const double* partials, int nparts) {
@@ -331,6 +389,248 @@ __global__ void run_reset_kernel(DevScalars* sc) {
   sc->status = AVIP_OK;
 }
 
+
+// ------------------------------------------------------------------------ FP32 forms
+// Mixed precision (ph.dd_fp32): gradients, velocities, sources and fluxes in FP32 with FP32
+// accumulation; the density state, the explicit update n += dt (R/V + S), the time-step
+// candidates and reduction and the charge sum stay FP64.  Two differences are formed in FP64
+// before rounding, because FP32 cannot resolve them from the absolute values: the potential
+// differences phi_k - phi_i of the gradient (phi ~ 1e4 V varies by ~10 V between neighbours,
+// so E from absolute values would lose 4 digits), using sum_k G_ik = 0 (each cell's nodal
+// normals sum to zero), and the edge vectors x_j - x_i (coordinates ~1e-2 m, edges ~1e-5 m).
+__device__ __forceinline__ float mobility32(const SpeciesParams& sp, float Emag) {
+  if (sp.mob_model == AVIP_MOB_POWER)
+    return (float)sp.mob[0] * powf(fmaxf(Emag, (float)sp.mob[3]) / (float)sp.mob[1], (float)sp.mob[2]);
+  return (float)sp.mob[0];
+}
+
+__device__ __forceinline__ float limiter32(float r, float beta, int kind) {
+  if (kind == AVIP_LIM_VANLEER) return (r + fabsf(r)) / (1.0f + fabsf(r));
+  return fmaxf(0.0f, fmaxf(fminf(beta * r, 1.0f), fminf(r, beta)));
+}
+
+__device__ __forceinline__ void node_fields32_body(const DDArgs& a, int with_dt, int bid) {
+  const int i = bid * blockDim.x + threadIdx.x;
+  const int N = a.A.N;
+  const int ns = a.ph.ns;
+  double chem = INFINITY;
+  if (i < N) {
+    const int slice = i / kSlice, lane = i % kSlice;
+    const double* n = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+    const int base = __ldg(a.A.sl_ptr + slice) + lane;
+    const int rl = __ldg(a.A.rlen + i);
+    const double phii = a.phi[i];
+    float ui[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) ui[s] = s < ns ? (float)n[(size_t)s * a.Npad + i] : 0.0f;
+    float gpx = 0.0f, gpy = 0.0f;
+    float gnx[AVIP_MAX_SPECIES], gny[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) gnx[s] = gny[s] = 0.0f;
+    for (int k = 1; k < rl; ++k) {  // slot 0 is the row itself: zero difference
+      const int e = base + k * kSlice;
+      const int j = __ldg(a.A.col + e);
+      const float wx = __ldg(a.gx32 + e), wy = __ldg(a.gy32 + e);
+      const float dp = (float)(a.phi[j] - phii);
+      gpx = fmaf(wx, dp, gpx);
+      gpy = fmaf(wy, dp, gpy);
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s < ns) {
+          const float du = (float)n[(size_t)s * a.Npad + j] - ui[s];
+          gnx[s] = fmaf(wx, du, gnx[s]);
+          gny[s] = fmaf(wy, du, gny[s]);
+        }
+      }
+    }
+    const float Ex = -gpx, Ey = -gpy;
+    const float Emag = sqrtf(Ex * Ex + Ey * Ey);
+    a.Ex[i] = Ex;
+    a.Ey[i] = Ey;
+    float mu[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      if (s < ns) {
+        const SpeciesParams& sp = a.ph.sp[s];
+        mu[s] = mobility32(sp, Emag);
+        const float sg = sp.q > 0 ? 1.0f : -1.0f;
+        reinterpret_cast<float4*>(a.ndat32)[(size_t)s * a.Npad + i] =
+            make_float4(gnx[s], gny[s], sg * mu[s] * Ex, sg * mu[s] * Ey);
+        a.nm[(size_t)s * a.Npad + i] = n[(size_t)s * a.Npad + i] * (double)mu[s];
+      } else {
+        mu[s] = 0.0f;
+      }
+    }
+    float src[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) src[s] = 0.0f;
+    if (a.ph.src_model != AVIP_SRC_NONE) {
+      const int ie = a.ph.src_idx[0], ip = a.ph.src_idx[1], ineg = a.ph.src_idx[2];
+      const float ne = (float)n[(size_t)ie * a.Npad + i];
+      const float alpha = Emag > 0.0f ? (float)a.ph.src_params[0] * expf(-(float)a.ph.src_params[1] / Emag) : 0.0f;
+      float mue = 0.0f;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+        if (s == ie) mue = mu[s];
+      const float ion = alpha * mue * Emag * ne;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s == ie) src[s] += ion;
+        if (s == ip) src[s] += ion;
+      }
+      if (a.ph.src_model == AVIP_SRC_TOWNSEND_ATTACH) {
+        const float att = (float)a.ph.src_params[2] * ne;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ie) src[s] -= att;
+          if (s == ineg) src[s] += att;
+        }
+      }
+      float se = 0.0f;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+        if (s == ie) se = src[s];
+      // chemical time-step candidate in FP64 (part of the time-step reduction)
+      if (se != 0.0f) chem = a.ph.a_chem * fabs(n[(size_t)ie * a.Npad + i]) / fabs((double)se);
+    }
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
+      if (s < ns) a.src[(size_t)s * a.Npad + i] = src[s];
+  }
+  if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
+}
+
+__global__ void __launch_bounds__(kDDThreads) node_fields32_kernel(DDArgs a, int with_dt) {
+  node_fields32_body(a, with_dt, blockIdx.x);
+}
+
+struct EdgeEnd32 {
+  float u, gx, gy, vx, vy;
+};
+
+// FP32 edge flux lo -> hi through (Sx, Sy) oriented lo -> hi; (dx, dy) = x_hi - x_lo.
+__device__ __forceinline__ float edge_flux32(const EdgeEnd32& lo, const EdgeEnd32& hi, float dx, float dy, float Sx,
+                                             float Sy, float D, float dt, float beta, int lim, int scheme) {
+  const float Vx = 0.5f * (lo.vx + hi.vx), Vy = 0.5f * (lo.vy + hi.vy);
+  const float gx = 0.5f * (lo.gx + hi.gx), gy = 0.5f * (lo.gy + hi.gy);
+  if (scheme == AVIP_FLUX_SG) {
+    const float h = sqrtf(dx * dx + dy * dy);
+    const float rh = 1.0f / h;
+    const float ex = dx * rh, ey = dy * rh;
+    const float s = Sx * ex + Sy * ey;
+    const float spx = Sx - s * ex, spy = Sy - s * ey;
+    const float Vt = Vx * ex + Vy * ey;
+    float fpar;
+    if (D > 0.0f) {
+      const float aa = h * Vt / D, ab = fabsf(aa);
+      const float Bp = ab != 0.0f ? ab / expm1f(ab) : 1.0f, Bm = ab + Bp;  // B(|a|), B(-|a|)
+      fpar = (D * s * rh) * ((aa >= 0.0f ? Bm : Bp) * lo.u - (aa >= 0.0f ? Bp : Bm) * hi.u);
+    } else {
+      fpar = s * (fmaxf(Vt, 0.0f) * lo.u + fminf(Vt, 0.0f) * hi.u);
+    }
+    return fpar + (Vx * spx + Vy * spy) * (0.5f * (lo.u + hi.u)) - D * (gx * spx + gy * spy);
+  }
+  const float av = Vx * Sx + Vy * Sy;
+  const bool up_lo = av >= 0.0f;
+  const EdgeEnd32& U = up_lo ? lo : hi;
+  const float delta = (up_lo ? hi.u : lo.u) - U.u;
+  float psi = 0.0f;
+  if (delta != 0.0f) {
+    const float ux = up_lo ? dx : -dx, uy = up_lo ? dy : -dy;  // x_W - x_U
+    const float r = (2.0f * (U.gx * ux + U.gy * uy) - delta) / delta;
+    psi = limiter32(r, beta, lim);
+  }
+  const float lw = 0.5f * delta - 0.5f * dt * (gx * Vx + gy * Vy);
+  return (U.u + lw * psi) * av - D * (gx * Sx + gy * Sy);
+}
+
+__device__ __forceinline__ void flux_update32_body(const DDArgs& a, int bid) {
+  const int i = bid * blockDim.x + threadIdx.x;
+  const int N = a.A.N;
+  const int ns = a.ph.ns;
+  const double dt = a.ph.dt_fixed > 0.0 ? a.ph.dt_fixed : __longlong_as_double((long long)a.sc->dt_bits);
+  const float dtf = (float)dt, betaf = (float)a.ph.beta;
+  double qsum = 0.0;
+  if (i < N) {
+    const int par = a.sc->parity;
+    const double* n = a.nbuf + (size_t)par * AVIP_MAX_SPECIES * a.Npad;
+    double* nn = a.nbuf + (size_t)(par ^ 1) * AVIP_MAX_SPECIES * a.Npad;
+    const float4* nd = reinterpret_cast<const float4*>(a.ndat32);
+    const int slice = i / kSlice, lane = i % kSlice;
+    const int base = __ldg(a.A.sl_ptr + slice) + lane;
+    const int rl = __ldg(a.A.rlen + i);
+    const double xi = a.x[i], yi = a.y[i];
+    float R[AVIP_MAX_SPECIES];
+    EdgeEnd32 me[AVIP_MAX_SPECIES];
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      R[s] = 0.0f;
+      if (s < ns) {
+        const float4 d = nd[(size_t)s * a.Npad + i];
+        me[s] = EdgeEnd32{(float)n[(size_t)s * a.Npad + i], d.x, d.y, d.z, d.w};
+      }
+    }
+    for (int k = 1; k < rl; ++k) {
+      const int e = base + k * kSlice;
+      const int j = __ldg(a.A.col + e);
+      const float Sx = __ldg(a.sx32 + e), Sy = __ldg(a.sy32 + e);
+      const bool lo_is_me = i < j;
+      // canonical lo -> hi edge vector, formed in FP64 so that both ends round the same value
+      const float dx = lo_is_me ? (float)(a.x[j] - xi) : (float)(xi - a.x[j]);
+      const float dy = lo_is_me ? (float)(a.y[j] - yi) : (float)(yi - a.y[j]);
+      const float cSx = lo_is_me ? Sx : -Sx, cSy = lo_is_me ? Sy : -Sy;
+#pragma unroll
+      for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+        if (s < ns) {
+          const float4 d = nd[(size_t)s * a.Npad + j];
+          const EdgeEnd32 other{(float)n[(size_t)s * a.Npad + j], d.x, d.y, d.z, d.w};
+          const EdgeEnd32& lo = lo_is_me ? me[s] : other;
+          const EdgeEnd32& hi = lo_is_me ? other : me[s];
+          const float F = edge_flux32(lo, hi, dx, dy, cSx, cSy, (float)a.ph.sp[s].D, dtf, betaf, a.ph.limiter,
+                                      a.ph.scheme);
+          R[s] = lo_is_me ? R[s] - F : R[s] + F;
+        }
+      }
+    }
+    const float Sbx = __ldg(a.sx32 + base), Sby = __ldg(a.sy32 + base);
+    const double Vi = a.vol[i];
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+      if (s < ns) {
+        const SpeciesParams& sp = a.ph.sp[s];
+        float Fx = me[s].u * me[s].vx, Fy = me[s].u * me[s].vy;
+        if (sp.bnd_mode == AVIP_BND_OUTFLOW) {
+          Fx -= (float)sp.D * me[s].gx;
+          Fy -= (float)sp.D * me[s].gy;
+        }
+        const float rs = R[s] - (Fx * Sbx + Fy * Sby);
+        // FP64 update of the FP64 state
+        const double un = n[(size_t)s * a.Npad + i] + dt * ((double)rs / Vi + a.src[(size_t)s * a.Npad + i]);
+        nn[(size_t)s * a.Npad + i] = un;
+        bad |= !isfinite(un);
+        qsum += sp.q * (Vi * un);
+      }
+    }
+    if (bad) atomicCAS(&a.sc->status, AVIP_OK, AVIP_ENAN);
+  }
+  __shared__ double sm[32];
+  const int ln = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, o);
+  if (ln == 0) sm[warp] = qsum;
+  __syncthreads();
+  if (warp == 0) {
+    double t = ln < nw ? sm[ln] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (ln == 0) a.partials[bid] = t;
+  }
+  if (bid == 0 && threadIdx.x == 0) a.sc->dt = dt;
+}
+
+__global__ void __launch_bounds__(kDDThreads, 2) flux_update32_kernel(DDArgs a) { flux_update32_body(a, blockIdx.x); }
+
 // ------------------------------------------------------------------------ batched forms
 // One launch covers every instance of a batch: block b belongs to the instance k with
 // bpref[k] <= b < bpref[k + 1] and runs that instance's block b - bpref[k].
@@ -347,7 +647,10 @@ __global__ void __launch_bounds__(kDDThreads) node_fields_batch_kernel(const DDA
                                                                         const int32_t* __restrict__ bpref, int count) {
   const int k = batch_instance(bpref, count, blockIdx.x);
   const DDArgs& a = args[k];
-  node_fields_body(a, a.ph.dt_fixed > 0.0 ? 0 : 1, blockIdx.x - __ldg(bpref + k));
+  if (a.ph.dd_fp32)
+    node_fields32_body(a, a.ph.dt_fixed > 0.0 ? 0 : 1, blockIdx.x - __ldg(bpref + k));
+  else
+    node_fields_body(a, a.ph.dt_fixed > 0.0 ? 0 : 1, blockIdx.x - __ldg(bpref + k));
 }
 __global__ void __launch_bounds__(kDDThreads) dt_cells_batch_kernel(const DDArgs* __restrict__ args,
                                                                      const int32_t* __restrict__ bpref, int count) {
@@ -356,10 +659,13 @@ __global__ void __launch_bounds__(kDDThreads) dt_cells_batch_kernel(const DDArgs
   if (a.ph.dt_fixed > 0.0) return;
   dt_cells_body(a, blockIdx.x - __ldg(bpref + k));
 }
-__global__ void __launch_bounds__(kDDThreads) flux_update_batch_kernel(const DDArgs* __restrict__ args,
+__global__ void __launch_bounds__(kDDThreads, 2) flux_update_batch_kernel(const DDArgs* __restrict__ args,
                                                                         const int32_t* __restrict__ bpref, int count) {
   const int k = batch_instance(bpref, count, blockIdx.x);
-  flux_update_body(args[k], blockIdx.x - __ldg(bpref + k));
+  if (args[k].ph.dd_fp32)
+    flux_update32_body(args[k], blockIdx.x - __ldg(bpref + k));
+  else
+    flux_update_body(args[k], blockIdx.x - __ldg(bpref + k));
 }
 __global__ void finalize_batch_kernel(const DDArgs* __restrict__ args, int count) {
   const DDArgs& a = args[blockIdx.x];
@@ -382,7 +688,10 @@ __global__ void run_reset_batch_kernel(const DDArgs* __restrict__ args, int coun
 static inline int nblk(int n) { return (n + kDDThreads - 1) / kDDThreads; }
 
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st) {
-  node_fields_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
+  if (a.ph.dd_fp32)
+    node_fields32_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
+  else
+    node_fields_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
   return cudaGetLastError();
 }
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
@@ -390,7 +699,10 @@ cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st) {
-  flux_update_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+  if (a.ph.dd_fp32)
+    flux_update32_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+  else
+    flux_update_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st) {

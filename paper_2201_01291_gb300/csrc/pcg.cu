@@ -38,6 +38,7 @@ constexpr int kResTPB = 512;  // block size of the register-resident kernels (on
 
 template <int TPB>
 __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   const int lane = threadIdx.x & 31;
   constexpr int wpb = TPB / 32;
@@ -95,6 +96,10 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
           if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
           rr_true = r2[0];
           if (rr_true <= thresh) break;
+          if (!isfinite(rr_true)) {  // non-finite data: stop at once
+            status = AVIP_ENAN;
+            break;
+          }
           if (it >= a.max_iter || (it > 0 && restarts >= kMaxRestarts)) {
             status = AVIP_ENOTCONV;
             break;
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
         double bs[2];
         if (!grid_allsum<1, 2>(rn, bs, fs, smem, [rr_now, thresh](const double* t, double* e) {
               e[0] = t[0] / rr_now;
-              e[1] = t[0] <= thresh ? 1.0 : 0.0;
+              e[1] = (t[0] <= thresh || !isfinite(t[0])) ? 1.0 : 0.0;
             }))
           goto timeout;
         beta = bs[0];
@@ -173,6 +178,7 @@ timeout:
 // block per SM at most; it needs gridDim.x * warps * MAXS >= slices.
 template <int TPB, int MAXS>
 __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   const int lane = threadIdx.x & 31;
   constexpr int wpb = TPB / 32;
@@ -274,6 +280,10 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
           if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
           rr_true = r2[0];
           if (rr_true <= thresh) break;
+          if (!isfinite(rr_true)) {  // non-finite data: stop at once
+            status = AVIP_ENAN;
+            break;
+          }
           if (it >= a.max_iter || (it > 0 && restarts >= kMaxRestarts)) {
             status = AVIP_ENOTCONV;
             break;
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
         double bs[2];
         if (!grid_allsum<1, 2>(rn, bs, fs, smem, [rr_now, thresh](const double* t, double* e) {
               e[0] = t[0] / rr_now;
-              e[1] = t[0] <= thresh ? 1.0 : 0.0;
+              e[1] = (t[0] <= thresh || !isfinite(t[0])) ? 1.0 : 0.0;
             }))
           goto timeout;
         beta = bs[0];

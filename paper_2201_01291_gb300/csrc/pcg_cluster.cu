@@ -43,6 +43,7 @@ struct ClusterShared {
 // memory (read only at the start and by the true-residual passes).
 // One complete solve of the system described by (a, L) by the calling cluster.
 __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterShared& sh) {
+  if (solve_skipped(a.sc)) return;  // every CTA of the cluster reads the same status
   extern __shared__ __align__(16) double dsm[];
   auto& s_part = sh.part;
   auto& s_thr = sh.thr;
@@ -192,6 +193,10 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
         csum(1, r2, none);
         rr_true = r2[0];
         if (rr_true <= thresh) break;
+        if (!isfinite(rr_true)) {  // non-finite data: stop at once
+          status = AVIP_ENAN;
+          break;
+        }
         if (it >= a.max_iter || (it > 0 && restarts >= 8)) {
           status = AVIP_ENOTCONV;
           break;
@@ -231,7 +236,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
       }
       csum(1, rn, [rr_now, thresh](const double* t, double* e) {
         e[0] = t[0] / rr_now;
-        e[1] = t[0] <= thresh ? 1.0 : 0.0;
+        e[1] = (t[0] <= thresh || !isfinite(t[0])) ? 1.0 : 0.0;
       });
       beta = s_res[4];
       check = s_res[5] != 0.0;
@@ -282,6 +287,7 @@ struct KahanF {
 // Shared memory per CTA: x64[R + H] (FP64), r64[R] (FP64), r32[R + H], e32[R], p32[R], q32[R]
 // (FP32), then vals32[max_elems] (FP32) and cols[max_elems] (int32) when the matrix fits.
 __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, ClusterShared& sh) {
+  if (solve_skipped(a.sc)) return;  // every CTA of the cluster reads the same status
   extern __shared__ __align__(16) double dsm[];
   auto& s_part = sh.part;
   auto& s_thr = sh.thr;
@@ -436,12 +442,17 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
     }
     csum(1, r2, none);
     rr64 = r2[0];
+    if (!isfinite(rr64)) {  // non-finite right-hand side or iterate: stop, never loop on NaN
+      status = AVIP_ENAN;
+      break;
+    }
     if (rr64 <= thresh) break;
     if (it >= a.max_iter) {
       status = AVIP_ENOTCONV;
       break;
     }
     ++outer;
+    const int it_outer = it;
     const double rnorm = sqrt(rr64), rscale = 1.0 / rnorm;
     double g0[1];
     {
@@ -495,6 +506,10 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
       beta = (float)s_res[4];
       rr = rn[0];
       ++it;
+    }
+    if (it == it_outer) {  // the inner solve could not start: no progress is possible
+      status = AVIP_ENOTCONV;
+      break;
     }
     // ---- FP64 correction, pushed to the halos before the next residual
     for (int s = s0 + warp; s < s1; s += nw) {

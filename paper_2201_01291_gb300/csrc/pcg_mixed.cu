@@ -90,6 +90,7 @@ __device__ __forceinline__ double sell_row_dot64(const SellView& A, int slice, i
 
 template <int TPB>
 __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   const int lane = threadIdx.x & 31;
   constexpr int wpb = TPB / 32;
@@ -134,12 +135,17 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
       }
       if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
       rr64 = r2[0];
+      if (!isfinite(rr64)) {  // non-finite right-hand side or iterate: stop, never loop on NaN
+        status = AVIP_ENAN;
+        break;
+      }
       if (rr64 <= thresh || bb[0] == 0.0) break;
       if (it >= a.max_iter) {
         status = AVIP_ENOTCONV;
         break;
       }
       ++outer;
+      const int it_outer = it;
       const double rnorm = sqrt(rr64);
       const double rscale = 1.0 / rnorm;
       // ---- FP32 right-hand side r / ||r||, e = 0
@@ -196,6 +202,10 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
         beta = (float)bs[0];
         rr = rn[0];
         ++it;
+      }
+      if (it == it_outer) {  // the inner solve could not start: no progress is possible
+        status = AVIP_ENOTCONV;
+        break;
       }
       // ---- FP64 correction x += ||r|| e
       for (int s = gwarp; s < nsl; s += nwarps) {

@@ -87,3 +87,12 @@ def test_axisymmetric_validation_on_host(lib):
     o3.geometry = 5
     assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o3)[0] == avip.AVIP_EINVAL
     assert "geometry" in avip.last_error()
+
+
+def test_unknown_flux_scheme_rejected_on_host(lib):
+    from paper_2201_01291_gb300 import avip, workloads as W
+    p = W.config_small(nx=9, ny=9)
+    o = avip.avip_opts_default()
+    assert o.scheme == avip.FLUX_LLW
+    o.scheme = 3
+    assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
