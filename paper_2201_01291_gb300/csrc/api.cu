@@ -15,6 +15,7 @@ namespace avip {
 cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_bicgstab(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
@@ -43,6 +44,9 @@ struct avip_mesh {
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
   double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
+  AmgDev* amg = nullptr;        // AMG hierarchy in device memory (kind 8 only)
+  double* amg_z = nullptr;      // preconditioned residual (level-0 solution of the V-cycle)
+  int32_t amg_levels = 0;
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
   float *gx32 = nullptr, *gy32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *ndat32 = nullptr;  // FP32 DD
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
@@ -160,6 +164,8 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.q32 = h->q32;
   a.inner_rtol = h->opts.inner_rtol;
   a.bcg = h->bcg;
+  a.amg = h->amg;
+  a.z = h->amg_z;
   return a;
 }
 
@@ -202,6 +208,7 @@ int cuda_status(cudaError_t e) {
 cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind == 8) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
@@ -237,6 +244,60 @@ void invalidate_graph(avip_mesh* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
   h->graph_valid = false;
+}
+
+// Device copy of the AMG hierarchy: level 0 reuses the mesh matrix; every other operator in
+// SELL-32; per level x, b, r, d vectors (level 0: b is the CG residual, x the preconditioned
+// residual z).
+bool upload_amg(avip_mesh* h, const AmgHost& H) {
+  AmgDev D;
+  std::memset(&D, 0, sizeof(D));
+  D.nlev = (int32_t)H.lv.size();
+  D.nc = H.nc;
+  auto put = [&](const Csr& M, SellMat& out) {
+    SellHost S;
+    sell_from_csr(M, S);
+    int32_t *slp = nullptr, *slw = nullptr, *rl = nullptr, *col = nullptr;
+    double* val = nullptr;
+    const bool ok = upload(h, slp, S.sl_ptr) && upload(h, slw, S.sl_w) && upload(h, rl, S.rlen) &&
+                    upload(h, col, S.col, 1) && upload(h, val, S.val, 1);
+    out = SellMat{slp, slw, rl, col, val, S.n, S.nslices};
+    return ok;
+  };
+  bool ok = true;
+  for (int32_t l = 0; l < D.nlev && ok; ++l) {
+    const AmgHostLevel& L = H.lv[l];
+    AmgLevelDev& dl = D.L[l];
+    dl.n = L.A.n;
+    dl.lmax = L.lmax;
+    const size_t npad = (size_t)((L.A.n + kSlice - 1) / kSlice) * kSlice;
+    if (l == 0) {
+      dl.A = SellMat{h->sl_ptr, h->sl_w, h->rlen, h->col, h->aval, h->hm.N, h->hm.nslices};
+    } else {
+      ok = ok && put(L.A, dl.A);
+    }
+    if (l + 1 < D.nlev) ok = ok && put(L.P, dl.P) && put(L.R, dl.R);
+    double* dinv = nullptr;
+    ok = ok && upload(h, dinv, L.dinv, npad);
+    dl.dinv = dinv;
+    ok = ok && zalloc(h, dl.r, npad) && zalloc(h, dl.d, npad);
+    if (l == 0) {
+      ok = ok && zalloc(h, dl.x, npad);
+      dl.b = h->r;
+      h->amg_z = dl.x;
+    } else {
+      ok = ok && zalloc(h, dl.x, npad) && zalloc(h, dl.b, npad);
+    }
+  }
+  double* cinv = nullptr;
+  ok = ok && upload(h, cinv, H.cinv, 1);
+  D.cinv = cinv;
+  AmgDev* dd = static_cast<AmgDev*>(dev_alloc(h, sizeof(AmgDev)));
+  ok = ok && dd && cudaMemcpyAsync(dd, &D, sizeof(AmgDev), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+       cudaStreamSynchronize(h->stream) == cudaSuccess;
+  h->amg = dd;
+  h->amg_levels = D.nlev;
+  return ok;
 }
 
 }  // namespace
@@ -301,7 +362,7 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     delete h;
     return AVIP_EINVAL;
   }
-  if (h->opts.pcg_kind == 7 && h->opts.precision != AVIP_PREC_FP64) {
+  if ((h->opts.pcg_kind == 7 || h->opts.pcg_kind == 8) && h->opts.precision != AVIP_PREC_FP64) {
     delete h;
     return AVIP_EINVAL;
   }
@@ -367,6 +428,20 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
       h->clay.push_dst = pdst;
       h->plan = cp;
     }
+  }
+  // large planar FP64 meshes (or kind 8 forced): CG preconditioned by an AMG V-cycle
+  if (!bicg && h->opts.precision == AVIP_PREC_FP64 &&
+      (h->opts.pcg_kind == 8 || (h->opts.pcg_kind == 0 && h->plan.kind != 5))) {
+    AmgHost H;
+    int rc = amg_setup(m, H, g_err, sizeof(g_err));
+    if (rc != AVIP_OK) {
+      dev_free_all(h);
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      delete h;
+      return rc;
+    }
+    ok = ok && upload_amg(h, H);
+    h->plan = amg_plan(m.nslices, h->opts.pcg_threads);
   }
   if (h->opts.precision == AVIP_PREC_MIXED) {
     std::vector<float> a32(m.aval.begin(), m.aval.end());

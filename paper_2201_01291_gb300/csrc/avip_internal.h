@@ -48,6 +48,33 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
                  const int32_t* node_bc, const double* phi_D, int reorder, int geometry, HostMesh& out,
                  char* err, size_t errlen);
 
+// ----------------------------------------------------------------- AMG hierarchy (host)
+constexpr int kAmgMaxLevels = 12;
+struct Csr {  // compressed sparse rows, n x m
+  int32_t n = 0, m = 0;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> v;
+};
+struct AmgHostLevel {
+  Csr A, P, R;                 // level matrix; prolongator from the next level; R = P^T
+  std::vector<double> dinv;    // 1 / diag(A)
+  double lmax = 1.0;           // estimate of the largest eigenvalue of D^-1 A
+};
+struct AmgHost {
+  std::vector<AmgHostLevel> lv;  // lv.back() is the coarsest level
+  int32_t nc = 0;                // coarsest size
+  std::vector<double> cinv;      // dense inverse of the coarsest matrix (row-major)
+};
+// Builds the smoothed-aggregation hierarchy of the scaled Poisson matrix of `m`.
+int amg_setup(const HostMesh& m, AmgHost& out, char* err, size_t errlen);
+// SELL-32 form of a CSR matrix (the conventions of the mesh matrix, rows in order).
+struct SellHost {
+  int32_t n = 0, nslices = 0;
+  std::vector<int32_t> sl_ptr, sl_w, rlen, col;
+  std::vector<double> val;
+};
+void sell_from_csr(const Csr& A, SellHost& out);
+
 // ----------------------------------------------------------------- kernel argument blocks
 struct SellView {  // device pointers of the SELL-32 structure
   const int32_t* sl_ptr;
@@ -61,6 +88,33 @@ struct SellView {  // device pointers of the SELL-32 structure
   const double* sy;
   int32_t N;
   int32_t nslices;
+};
+
+struct SellMat {  // device pointers of a SELL-32 matrix
+  const int32_t* sl_ptr;
+  const int32_t* sl_w;
+  const int32_t* rlen;
+  const int32_t* col;
+  const double* val;
+  int32_t n;
+  int32_t nslices;
+};
+
+struct AmgLevelDev {
+  SellMat A, P, R;     // P: n x n_next (prolongation), R = P^T (restriction); unused on the coarsest
+  const double* dinv;
+  double* x;           // level solution (level 0: the preconditioned residual z)
+  double* b;           // level right-hand side (level 0: the CG residual)
+  double* r;           // scratch: residual
+  double* d;           // scratch: Chebyshev direction
+  double lmax;
+  int32_t n;
+};
+struct AmgDev {
+  int32_t nlev;        // levels including the coarsest
+  int32_t nc;          // coarsest size
+  const double* cinv;  // coarsest dense inverse, nc x nc row-major
+  AmgLevelDev L[kAmgMaxLevels];
 };
 
 struct SpeciesParams {
@@ -151,12 +205,17 @@ struct PcgArgs {
   // BiCGStab (non-symmetric systems): three more vectors s, t and the shadow residual, each
   // Npad long, at bcg + k * Npad (v = A p lives in q_ap)
   double* bcg;
+  // AMG-preconditioned CG (kind 8): the hierarchy (device memory) and the preconditioned
+  // residual z
+  const AmgDev* amg;
+  double* z;
 };
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
-                   // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix)
+                   // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix),
+                   // 8 AMG-preconditioned CG
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
@@ -164,6 +223,7 @@ struct PcgPlan {
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
+PcgPlan amg_plan(int nslices, int requested_tpb);
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

@@ -1,0 +1,364 @@
+// Conjugate gradients preconditioned by one smoothed-aggregation AMG V-cycle (solver kind 8),
+// FP64, one cooperative persistent launch per solve.
+//
+// The system is the symmetrically scaled one of the Jacobi variant, A = D^-1/2 K D^-1/2,
+// x = D^1/2 phi, b' = D^-1/2 b, with the same stopping test (true residual of the free rows,
+// ||b' - A x|| <= rtol ||b'||).  The hierarchy (level matrices, prolongators, restrictions,
+// diagonal inverses, largest-eigenvalue estimates, dense inverse of the coarsest matrix) is
+// built once per mesh on the host (amg_setup.cpp); the preconditioner z = M r is one V-cycle:
+//
+//   down, level l:  x = Chebyshev(degree 2, from x = 0) of A_l x = b_l;
+//                   r = b_l - A_l x;  b_{l+1} = R_l r
+//   coarsest:       x = A_c^-1 b  (dense product)
+//   up, level l:    x += P_l x_{l+1};  x = Chebyshev(degree 2, from x) of A_l x = b_l
+//
+// with the Chebyshev polynomial in D^-1 A on [lmax/30, lmax] (lmax from power iteration).
+// The pre- and post-smoother are the same polynomial and R = P^T, so the V-cycle is a
+// symmetric positive definite operator and plain CG applies.
+//
+// Every product gathers a vector that other blocks wrote in the previous phase, so each phase
+// ends with a grid-wide barrier (a reduction that also carries the dot products CG needs).  No
+// phase writes a vector that it also gathers: the Chebyshev steps gather the direction d and
+// update x, and the first direction of each level is formed where its right-hand side is
+// written (the restriction of the level above, or the CG residual update on the finest).
+// Per CG iteration: 6 barriers per non-coarsest level, 1 for the coarsest, 2 for CG.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "avip_internal.h"
+#include "grid_sync.cuh"
+#include "sell.cuh"
+
+namespace avip {
+
+namespace {
+constexpr int kAmgSizes[] = {512, 768, 1024};  // block sizes; index 0 is the default
+constexpr int kAmgMaxRestarts = 8;
+
+// Degree-2 Chebyshev coefficients on [lmax/30, lmax]: d0 = D^-1 r / theta,
+// d1 = c1 d0 + c2 D^-1 r1.
+struct Cheb {
+  double inv_theta, c1, c2;
+};
+__device__ __forceinline__ Cheb cheb_of(double lmax) {
+  const double lmin = lmax / 30.0;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+  return Cheb{1.0 / theta, rho1 * rho0, 2.0 * rho1 / delta};
+}
+
+__device__ __forceinline__ bool grid_barrier(FlagSync& fs, double* smem) {
+  double d[1] = {0.0};
+  return grid_allsum<1>(d, fs, smem);
+}
+
+// One V-cycle: z = x_0 from b_0 = r.  On entry b_0 and d_0 = D^-1 b_0 / theta_0 are complete
+// (written before the last barrier).  Returns r.z in rz (grid-reduced, also the barrier after
+// which z is complete); false if a wait was abandoned.
+__device__ bool vcycle(const AmgDev* __restrict__ H, FlagSync& fs, double* smem, int gwarp, int nwarps,
+                       int lane, double& rz) {
+  const int nl = H->nlev;
+  for (int l = 0; l + 1 < nl; ++l) {
+    const AmgLevelDev* __restrict__ L = H->L + l;
+    const SellMat A = L->A;
+    const int n = L->n;
+    const double* __restrict__ dinv = L->dinv;
+    const double* __restrict__ b = L->b;
+    double* __restrict__ x = L->x;
+    double* __restrict__ d = L->d;
+    double* __restrict__ r = L->r;
+    {
+      const Cheb ch = cheb_of(L->lmax);
+      // second Chebyshev step from x = d0: r1 = b - A d0, x = d0 + c1 d0 + c2 D^-1 r1
+      for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+        const int i = sl * kSlice + lane;
+        if (i >= n) continue;
+        const double di = d[i];
+        const double r1 = b[i] - sellmat_row_dot(A, sl, lane, i, d);
+        x[i] = di + fma(ch.c1, di, ch.c2 * dinv[i] * r1);
+      }
+    }
+    if (!grid_barrier(fs, smem)) return false;
+    // residual
+    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+      const int i = sl * kSlice + lane;
+      if (i >= n) continue;
+      r[i] = b[i] - sellmat_row_dot(A, sl, lane, i, x);
+    }
+    if (!grid_barrier(fs, smem)) return false;
+    {  // restriction, and the first Chebyshev direction of the next level
+      const AmgLevelDev* __restrict__ C = H->L + l + 1;
+      const SellMat R = L->R;
+      const int nc = C->n;
+      const double c_inv_theta = cheb_of(C->lmax).inv_theta;
+      const double* __restrict__ cdinv = C->dinv;
+      double* __restrict__ cb = C->b;
+      double* __restrict__ cd = C->d;
+      for (int sl = gwarp; sl < R.nslices; sl += nwarps) {
+        const int j = sl * kSlice + lane;
+        if (j >= nc) continue;
+        const double bj = sellmat_row_dot(R, sl, lane, j, r);
+        cb[j] = bj;
+        cd[j] = cdinv[j] * bj * c_inv_theta;
+      }
+    }
+    if (!grid_barrier(fs, smem)) return false;
+  }
+  {  // coarsest level: dense inverse, one warp per row (a one-level hierarchy ends here: r.z)
+    const AmgLevelDev* __restrict__ C = H->L + nl - 1;
+    const int n = H->nc;
+    const double* __restrict__ cinv = H->cinv;
+    const double* __restrict__ cb = C->b;
+    double* __restrict__ cx = C->x;
+    double acc[1] = {0.0};
+    for (int row = gwarp; row < n; row += nwarps) {
+      double s = 0.0;
+      for (int k = lane; k < n; k += 32) s = fma(__ldg(cinv + (size_t)row * n + k), __ldcg(cb + k), s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        cx[row] = s;
+        if (nl == 1) acc[0] = fma(__ldcg(cb + row), s, acc[0]);
+      }
+    }
+    if (!grid_allsum<1>(acc, fs, smem)) return false;
+    if (nl == 1) rz = acc[0];
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    const AmgLevelDev* __restrict__ L = H->L + l;
+    const SellMat A = L->A;
+    const int n = L->n;
+    const double* __restrict__ dinv = L->dinv;
+    const double* __restrict__ b = L->b;
+    double* __restrict__ x = L->x;
+    double* __restrict__ d = L->d;
+    double* __restrict__ r = L->r;
+    {  // prolongation
+      const SellMat P = L->P;
+      const double* __restrict__ cx = H->L[l + 1].x;
+      for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+        const int i = sl * kSlice + lane;
+        if (i >= n) continue;
+        x[i] += sellmat_row_dot(P, sl, lane, i, cx);
+      }
+    }
+    if (!grid_barrier(fs, smem)) return false;
+    const Cheb ch = cheb_of(L->lmax);
+    // first post-smoothing step: r = b - A x, d = D^-1 r / theta (x updated in the next phase)
+    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+      const int i = sl * kSlice + lane;
+      if (i >= n) continue;
+      const double ri = b[i] - sellmat_row_dot(A, sl, lane, i, x);
+      r[i] = ri;
+      d[i] = dinv[i] * ri * ch.inv_theta;
+    }
+    if (!grid_barrier(fs, smem)) return false;
+    // second step: r1 = r - A d, x += d + c1 d + c2 D^-1 r1
+    double acc[1] = {0.0};
+    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+      const int i = sl * kSlice + lane;
+      if (i >= n) continue;
+      const double di = d[i];
+      const double r1 = r[i] - sellmat_row_dot(A, sl, lane, i, d);
+      const double xi = x[i] + di + fma(ch.c1, di, ch.c2 * dinv[i] * r1);
+      x[i] = xi;
+      if (l == 0) acc[0] = fma(b[i], xi, acc[0]);
+    }
+    if (!grid_allsum<1>(acc, fs, smem)) return false;
+    if (l == 0) rz = acc[0];
+  }
+  return true;
+}
+}  // namespace
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
+  __shared__ double smem[2 * 32 * 4];
+  const int lane = threadIdx.x & 31;
+  constexpr int wpb = TPB / 32;
+  const int gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  const int N = a.A.N, nsl = a.A.nslices;
+  const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+  const AmgDev* __restrict__ H = a.amg;
+  const double* __restrict__ dinv0 = H->L[0].dinv;
+  double* __restrict__ d0 = H->L[0].d;
+  double* __restrict__ z = H->L[0].x;
+  const double inv_theta0 = cheb_of(H->L[0].lmax).inv_theta;
+  FlagSync fs{a.flags, a.parts, a.sync, 0u};
+  double one[1];
+
+  // ---- x = D^1/2 phi (warm start) and b'
+  double bb[1] = {0.0};
+  for (int s = gwarp; s < nsl; s += nwarps) {
+    const int i = s * kSlice + lane;
+    if (i >= N) continue;
+    a.x[i] = a.dsq[i] * a.phi[i];
+    double b;
+    if (a.use_density_rhs) {
+      double rho = 0.0;
+      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      a.b[i] = b;
+    } else {
+      b = a.b[i];
+    }
+    if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+  }
+  if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
+  {
+    const double thresh = a.rtol * a.rtol * bb[0];
+    double rz = 0.0, rr_true = 0.0;
+    bool check = true, fresh = true;
+    int it = 0, restarts = 0, status = AVIP_OK;
+    if (bb[0] == 0.0) {
+      for (int s = gwarp; s < nsl; s += nwarps) {
+        const int i = s * kSlice + lane;
+        if (i < N) a.x[i] = a.b[i];  // free b == 0: x = b
+      }
+    } else {
+      while (true) {
+        if (check || it >= a.max_iter) {
+          // ---- true residual r = b' - A x (x complete); first Chebyshev direction of level 0
+          double r2[1] = {0.0};
+          for (int s = gwarp; s < nsl; s += nwarps) {
+            const int i = s * kSlice + lane;
+            if (i >= N) continue;
+            const double r = a.b[i] - sell_row_dot(a.A, s, lane, i, a.x);
+            a.r[i] = r;
+            d0[i] = dinv0[i] * r * inv_theta0;
+            r2[0] = fma(r, r, r2[0]);
+          }
+          if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
+          rr_true = r2[0];
+          if (rr_true <= thresh) break;
+          if (!isfinite(rr_true)) {  // non-finite data: stop at once
+            status = AVIP_ENAN;
+            break;
+          }
+          if (it >= a.max_iter || (it > 0 && restarts >= kAmgMaxRestarts)) {
+            status = AVIP_ENOTCONV;
+            break;
+          }
+          if (it > 0) ++restarts;
+          fresh = true;
+          check = false;
+        }
+        // ---- z = M r (r and the level-0 direction complete)
+        double rz_new = 0.0;
+        if (!vcycle(H, fs, smem, gwarp, nwarps, lane, rz_new)) goto timeout;
+        if (!(rz_new > 0.0) || !isfinite(rz_new)) {  // the preconditioned residual lost positivity
+          if (it == 0 || restarts >= kAmgMaxRestarts) {
+            status = AVIP_ENOTCONV;
+            break;
+          }
+          ++it;
+          check = true;
+          continue;
+        }
+        const double beta = fresh ? 0.0 : rz_new / rz;
+        rz = rz_new;
+        fresh = false;
+        // ---- phase A: w = A z, q = w + beta q, p = z + beta p, p.q -> alpha
+        double pq[1] = {0.0};
+        for (int s = gwarp; s < nsl; s += nwarps) {
+          const int i = s * kSlice + lane;
+          if (i >= N) continue;
+          const double zi = __ldcg(z + i);  // with one level, z rows come from other warps
+          const double w = sell_row_dot(a.A, s, lane, i, z);
+          const double qn = beta == 0.0 ? w : fma(beta, a.q_ap[i], w);
+          const double pn = beta == 0.0 ? zi : fma(beta, a.p[i], zi);
+          a.q_ap[i] = qn;
+          a.p[i] = pn;
+          pq[0] = fma(pn, qn, pq[0]);
+        }
+        const double rz_now = rz;
+        if (!grid_allsum<1, 1>(pq, one, fs, smem, [rz_now](const double* t, double* e) { e[0] = rz_now / t[0]; }))
+          goto timeout;
+        const double alpha = one[0];
+        // ---- phase B: x += alpha p, r -= alpha q, r.r; first direction of level 0
+        double rn[1] = {0.0};
+        for (int s = gwarp; s < nsl; s += nwarps) {
+          const int i = s * kSlice + lane;
+          if (i >= N) continue;
+          a.x[i] = fma(alpha, a.p[i], a.x[i]);
+          const double r = fma(-alpha, a.q_ap[i], a.r[i]);
+          a.r[i] = r;
+          d0[i] = dinv0[i] * r * inv_theta0;
+          rn[0] = fma(r, r, rn[0]);
+        }
+        double stop[1];
+        if (!grid_allsum<1, 1>(rn, stop, fs, smem, [thresh](const double* t, double* e) {
+              e[0] = (t[0] <= thresh || !isfinite(t[0])) ? 1.0 : 0.0;
+            }))
+          goto timeout;
+        check = stop[0] != 0.0;
+        ++it;
+      }
+    }
+    // ---- phi = D^-1/2 x
+    for (int s = gwarp; s < nsl; s += nwarps) {
+      const int i = s * kSlice + lane;
+      if (i < N) a.phi[i] = a.dsqinv[i] * a.x[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.sc->pcg_iters = it;
+      a.sc->pcg_status = status;
+      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+      a.sc->pcg_bnorm = sqrt(bb[0]);
+      if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
+    }
+    return;
+  }
+timeout:
+  if (threadIdx.x == 0) {
+    atomicExch(&a.sync->abort, 1);
+    a.sc->pcg_status = AVIP_ETIMEOUT;
+    atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
+  }
+}
+
+static const void* amg_kernel_ptr(int tpb) {
+  switch (tpb) {
+    case 512: return (const void*)pcg_amg_kernel<512>;
+    case 1024: return (const void*)pcg_amg_kernel<1024>;
+    default: return (const void*)pcg_amg_kernel<768>;
+  }
+}
+
+// Grid: co-resident blocks (one per SM), no more than the finest level needs.
+PcgPlan amg_plan(int nslices, int requested_tpb) {
+  PcgPlan pl;
+  pl.kind = 8;
+  pl.tpb = kAmgSizes[0];
+  for (int t : kAmgSizes)
+    if (t == requested_tpb) pl.tpb = t;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg_kernel_ptr(pl.tpb), pl.tpb, 0);
+  const int wpb = pl.tpb / kSlice;
+  const int want = (nslices + wpb - 1) / wpb;
+  pl.blocks = std::max(1, std::min(std::max(occ, 1) * std::max(sms, 1), want));
+  return pl;
+}
+
+cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.blocks);
+  cfg.blockDim = dim3(pl.tpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* kargs[] = {const_cast<PcgArgs*>(&args)};
+  return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.tpb), kargs);
+}
+
+}  // namespace avip
