@@ -2,8 +2,9 @@
 
 Default workload: the pin-plane streamer, 1 cm x 2 cm, 500 x 1000 jittered nodes (997,002
 triangles), Morton-ordered, 20 kV needle anode, local-field electron mobility mu ~ E^-0.2,
-Townsend ionisation, plain FP64, PCG rtol 1e-12.  One step = Poisson (Jacobi-PCG to rtol,
-warm-started) + E + gradients + time step + fluxes + source + update, all in the CUDA library.
+Townsend ionisation, plain FP64, CG rtol 1e-12.  One step = Poisson (CG preconditioned by an
+AMG V-cycle to rtol, warm-started; `--pcg-kind 2` for Jacobi-PCG) + E + gradients + time step +
+fluxes + source + update, all in the CUDA library.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -162,12 +163,20 @@ def aggregate(elapsed, units_per_rank, world, device="cuda"):
 
 KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (register-resident)",
                 4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)",
-                7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)"}
+                7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)",
+                8: "pcg_amg_kernel (CG + smoothed-aggregation AMG V-cycle)"}
 
-# DRAM bytes per PCG iteration measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of
-# a 300-iteration capture of the pin-plane 500x1000 solve, divided by 300): the working set
-# stays in L2.  Keyed by kernel kind; valid for the kernel revision the capture was taken on.
-NCU_DRAM_BYTES_PER_ITER = {2: (72.372224e6 + 2.023936e6) / 300.0}
+# DRAM bytes per solver iteration measured by ncu on the pin-plane 500 x 1000 workload (the
+# counters of one captured launch divided by its iterations), keyed by solver kind; valid for the
+# kernel revision the capture was taken on and for that workload only.
+NCU_DRAM_BYTES_PER_ITER = {
+    # pcg_fp64_res_kernel: 300-iteration capture, L2-resident working set
+    2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
+                                            "launch's iterations (L2-resident working set)"),
+    # pcg_amg_kernel<512>: one 16-iteration solve
+    8: ((2633.438e6 + 504.461e6) / 16.0, "ncu DRAM read+write of a 16-iteration solve scaled to the launch's "
+                                         "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
+}
 
 
 def pcg_traffic_model(info, iters, solves):
@@ -184,6 +193,8 @@ def pcg_traffic_model(info, iters, solves):
         (8 + 4), reads s, p, v, z, rh, x (48), writes x, r, A r, p, v (40): 24 nnz + 160 N bytes;
         flops 4 nnz + 32 N per iteration."""
     N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
+    if kind == 8:
+        return amg_traffic_model(info["levels"], nnz, N, iters, solves)
     per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
     per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
                  7: 24 * nnz + 170 * N}.get(kind, 0)
@@ -193,6 +204,28 @@ def pcg_traffic_model(info, iters, solves):
     else:
         flops = iters * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
     return bytes_, flops
+
+
+def amg_traffic_model(levels, nnz0, N, iters, solves):
+    """Algorithmic bytes and flops of the AMG-preconditioned CG launch (kind 8).  Per CG
+    iteration and non-coarsest level l (n rows, a = nnz(A_l), p = nnz(P_l), n' coarse rows),
+    counting 12 B per stored entry (column + value), 4 B row length, one 8 B read per gathered
+    and per own vector element: four products with A_l, one with P_l and one with R_l,
+    48 a + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
+    the CG phases add 12 nnz + 116 N.  Flops: 2 per stored entry of every product, 20 per row
+    and level for the smoothing and update arithmetic, 12 N for CG."""
+    per_it = 12 * nnz0 + 116 * N
+    fl_it = 2 * nnz0 + 12 * N
+    for l, (n, a, p) in enumerate(levels):
+        if l + 1 < len(levels):
+            nc = levels[l + 1][0]
+            per_it += 48 * a + 24 * p + 196 * n + 36 * nc
+            fl_it += 2 * (4 * a + 2 * p) + 20 * n
+        else:
+            per_it += 8 * n * n + 16 * n
+            fl_it += 2 * n * n
+    per_solve = 24 * nnz0 + 100 * N
+    return iters * per_it + solves * per_solve, iters * fl_it + solves * (4 * nnz0 + 12 * N)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -280,11 +313,10 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (FMA-chain probe measured 1.197)",
                 "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm, 4)}
     per_launch_iters = iters / args.steps
-    traffic = NCU_DRAM_BYTES_PER_ITER.get(kind)
+    traffic, note = NCU_DRAM_BYTES_PER_ITER.get(kind, (None, None)) if args.workload == "pin_plane" else (None, None)
     roof.update({"kernel": KERNEL_NAMES.get(kind, str(kind)),
                  "traffic": int(traffic * per_launch_iters) if traffic else None,
-                 "traffic_note": ("ncu DRAM read+write of a 300-iteration capture scaled to the launch's "
-                                  "iterations (L2-resident working set)") if traffic else None,
+                 "traffic_note": note,
                  "algorithmic_bytes_per_launch": int(byts / args.steps),
                  "pcg_iters_per_step": per_launch_iters,
                  "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in kernel_ms.items()}})

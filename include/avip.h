@@ -97,7 +97,9 @@ typedef struct avip_opts {
   double inner_rtol;                   /* mixed precision: FP32 inner reduction per refinement */
   int32_t pcg_threads;                 /* streaming PCG block size (256/512/768/1024; 0 = 768) */
   int32_t pcg_kind;                    /* solver kernel: 0 auto, 1 streaming, 2 register-resident,
-                                          5 cluster, 7 BiCGStab (the only one for AXISYMMETRIC) */
+                                          5 cluster, 7 BiCGStab (the only one for AXISYMMETRIC),
+                                          8 CG preconditioned by an AMG V-cycle (auto for planar
+                                          FP64 meshes above 20,000 nodes) */
   void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
   avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
   avip_free_fn free;
@@ -189,9 +191,17 @@ int state_set(avip_mesh_t h, const double* host_state);
 
 /* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
  * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident, 6 cluster mixed,
- * 7 BiCGStab), solver blocks,
+ * 7 BiCGStab, 8 AMG-preconditioned CG), solver blocks,
  * PCG threads per block, device bytes held by the handle}. */
 int mesh_info(avip_mesh_t h, int64_t* info8);
+
+/* Multigrid hierarchy of the AMG-preconditioned solver (kind 8; the paper names no solver, this
+ * reports the set-up built for this project's preconditioner).  Returns the number of levels
+ * (finest first, the last one inverted densely), or 0 when the handle uses another solver; for
+ * the first min(levels, max_levels) levels writes out[3*l] = rows, out[3*l+1] = stored entries
+ * of the level matrix, out[3*l+2] = stored entries of the prolongator from the next level
+ * (0 on the coarsest).  AVIP_EINVAL for a NULL handle or a NULL `out` with max_levels > 0. */
+int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels);
 
 /* ---- batches (many independent instances per step) -------------------------------------
  * A batch advances several mesh handles together: per step, one persistent launch solves the

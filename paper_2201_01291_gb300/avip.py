@@ -62,6 +62,7 @@ _SIGS = {
     "mesh_destroy": (C.c_int, [_H]),
     "mesh_set_stream": (C.c_int, [_H, C.c_void_p]),
     "mesh_info": (C.c_int, [_H, _P(C.c_int64)]),
+    "solver_levels": (C.c_int, [_H, _P(C.c_int64), C.c_int32]),
     "species_set": (C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, _D, C.c_double, C.c_int32, _D]),
     "source_set": (C.c_int, [_H, C.c_int32, _D, _I]),
     "poisson_solve": (C.c_int, [_H, _I, _D]),
@@ -214,6 +215,16 @@ def mesh_info(h):
                 device_bytes=int(info[7]))
 
 
+def solver_levels(h, max_levels=12):
+    """AMG hierarchy of the handle's solver: list of (rows, nnz of A, nnz of P) per level,
+    finest first; empty when the solver is not the AMG-preconditioned CG."""
+    out = np.zeros(3 * max_levels, dtype=np.int64)
+    nl = load().solver_levels(h, out.ctypes.data_as(_P(C.c_int64)), max_levels)
+    if nl < 0:
+        _check(nl, "solver_levels")
+    return [tuple(int(v) for v in out[3 * l:3 * l + 3]) for l in range(min(nl, max_levels))]
+
+
 def state_get(h):
     n = C.c_int64()
     _check(load().state_size(h, C.byref(n)), "state_size")
@@ -318,6 +329,7 @@ class Mesh:
         if src.model != 0:
             _check(source_set(h, src.model, src.params, src.idx), "source_set")
         self.info = mesh_info(h)
+        self.info["levels"] = solver_levels(h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -47,6 +47,7 @@ struct avip_mesh {
   AmgDev* amg = nullptr;        // AMG hierarchy in device memory (kind 8 only)
   double* amg_z = nullptr;      // preconditioned residual (level-0 solution of the V-cycle)
   int32_t amg_levels = 0;
+  std::vector<int64_t> amg_stats;  // per level: rows, nnz(A), nnz(P)
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
   float *gx32 = nullptr, *gy32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *ndat32 = nullptr;  // FP32 DD
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
@@ -297,6 +298,12 @@ bool upload_amg(avip_mesh* h, const AmgHost& H) {
        cudaStreamSynchronize(h->stream) == cudaSuccess;
   h->amg = dd;
   h->amg_levels = D.nlev;
+  h->amg_stats.clear();
+  for (const AmgHostLevel& L : H.lv) {
+    h->amg_stats.push_back(L.A.n);
+    h->amg_stats.push_back(L.A.rp.empty() ? 0 : L.A.rp[L.A.n]);
+    h->amg_stats.push_back(L.P.rp.empty() ? 0 : L.P.rp[L.P.n]);
+  }
   return ok;
 }
 
@@ -530,6 +537,14 @@ int mesh_info(avip_mesh_t h, int64_t* info) {
   info[6] = h->plan.tpb;
   info[7] = (int64_t)h->bytes;
   return AVIP_OK;
+}
+
+int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
+  if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
+  const int32_t nl = h->plan.kind == 8 ? h->amg_levels : 0;
+  for (int32_t l = 0; l < nl && l < max_levels; ++l)
+    for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
+  return nl;
 }
 
 int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model, const double* mob_params, double D,
