@@ -164,7 +164,8 @@ def aggregate(elapsed, units_per_rank, world, device="cuda"):
 KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (register-resident)",
                 4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)",
                 7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)",
-                8: "pcg_amg_kernel (CG + smoothed-aggregation AMG V-cycle)"}
+                8: "pcg_amg_kernel (CG + smoothed-aggregation AMG V-cycle)",
+                9: "bicgstab_amg_kernel (BiCGStab + AMG V-cycle, axisymmetric)"}
 
 # DRAM bytes per solver iteration measured by ncu on the pin-plane 500 x 1000 workload (the
 # counters of one captured launch divided by its iterations), keyed by solver kind; valid for the
@@ -193,8 +194,8 @@ def pcg_traffic_model(info, iters, solves):
         (8 + 4), reads s, p, v, z, rh, x (48), writes x, r, A r, p, v (40): 24 nnz + 160 N bytes;
         flops 4 nnz + 32 N per iteration."""
     N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
-    if kind == 8:
-        return amg_traffic_model(info["levels"], nnz, N, iters, solves)
+    if kind in (8, 9):
+        return amg_traffic_model(info["levels"], nnz, N, iters, solves, kind)
     per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
     per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
                  7: 24 * nnz + 170 * N}.get(kind, 0)
@@ -206,24 +207,29 @@ def pcg_traffic_model(info, iters, solves):
     return bytes_, flops
 
 
-def amg_traffic_model(levels, nnz0, N, iters, solves):
+def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8):
     """Algorithmic bytes and flops of the AMG-preconditioned CG launch (kind 8).  Per CG
     iteration and non-coarsest level l (n rows, a = nnz(A_l), p = nnz(P_l), n' coarse rows),
     counting 12 B per stored entry (column + value), 4 B row length, one 8 B read per gathered
     and per own vector element: four products with A_l, one with P_l and one with R_l,
     48 a + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
     the CG phases add 12 nnz + 116 N.  Flops: 2 per stored entry of every product, 20 per row
-    and level for the smoothing and update arithmetic, 12 N for CG."""
-    per_it = 12 * nnz0 + 116 * N
-    fl_it = 2 * nnz0 + 12 * N
+    and level for the smoothing and update arithmetic, 12 N for CG.  BiCGStab (kind 9) applies
+    two V-cycles per iteration and its phases add 24 nnz + 216 N bytes and 4 nnz + 32 N flops."""
+    cycles = 2 if kind == 9 else 1
+    per_it = (24 * nnz0 + 216 * N) if kind == 9 else (12 * nnz0 + 116 * N)
+    fl_it = (4 * nnz0 + 32 * N) if kind == 9 else (2 * nnz0 + 12 * N)
+    vb, vf = 0, 0
     for l, (n, a, p) in enumerate(levels):
         if l + 1 < len(levels):
             nc = levels[l + 1][0]
-            per_it += 48 * a + 24 * p + 196 * n + 36 * nc
-            fl_it += 2 * (4 * a + 2 * p) + 20 * n
+            vb += 48 * a + 24 * p + 196 * n + 36 * nc
+            vf += 2 * (4 * a + 2 * p) + 20 * n
         else:
-            per_it += 8 * n * n + 16 * n
-            fl_it += 2 * n * n
+            vb += 8 * n * n + 16 * n
+            vf += 2 * n * n
+    per_it += cycles * vb
+    fl_it += cycles * vf
     per_solve = 24 * nnz0 + 100 * N
     return iters * per_it + solves * per_solve, iters * fl_it + solves * (4 * nnz0 + 12 * N)
 

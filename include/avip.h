@@ -99,7 +99,9 @@ typedef struct avip_opts {
   int32_t pcg_kind;                    /* solver kernel: 0 auto, 1 streaming, 2 register-resident,
                                           5 cluster, 7 BiCGStab (the only one for AXISYMMETRIC),
                                           8 CG preconditioned by an AMG V-cycle (auto for planar
-                                          FP64 meshes above 20,000 nodes) */
+                                          FP64 meshes above 20,000 nodes), 9 BiCGStab
+                                          preconditioned by it (auto for AXISYMMETRIC meshes
+                                          above 20,000 nodes) */
   void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
   avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
   avip_free_fn free;
@@ -137,7 +139,7 @@ int avip_opts_default(avip_opts* o);
  * axisymmetric sections), renumbers, and uploads everything.  Errors: AVIP_EINVAL for
  * out-of-range indices, zero-area cells, a mesh with no Dirichlet node, a negative radius or
  * a non-positive Poisson diagonal (AXISYMMETRIC), AXISYMMETRIC with AVIP_PREC_MIXED or with
- * a pcg_kind other than 0 or 7; AVIP_ENOMEM. */
+ * a pcg_kind other than 0, 7 or 9; AVIP_ENOMEM. */
 int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
                 const int32_t* node_bc, const double* phi_D, const avip_opts* opts,
                 avip_mesh_t* out);
@@ -191,11 +193,11 @@ int state_set(avip_mesh_t h, const double* host_state);
 
 /* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
  * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident, 6 cluster mixed,
- * 7 BiCGStab, 8 AMG-preconditioned CG), solver blocks,
+ * 7 BiCGStab, 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab), solver blocks,
  * PCG threads per block, device bytes held by the handle}. */
 int mesh_info(avip_mesh_t h, int64_t* info8);
 
-/* Multigrid hierarchy of the AMG-preconditioned solver (kind 8; the paper names no solver, this
+/* Multigrid hierarchy of the AMG-preconditioned solvers (kinds 8, 9; the paper names no solver, this
  * reports the set-up built for this project's preconditioner).  Returns the number of levels
  * (finest first, the last one inverted densely), or 0 when the handle uses another solver; for
  * the first min(levels, max_levels) levels writes out[3*l] = rows, out[3*l+1] = stored entries

@@ -22,7 +22,10 @@
 //     lambda_max from 30 power iterations (times 1.05);
 //   * restriction R = P^T and Galerkin coarse matrix A_c = R A P (rounding symmetrised);
 //   * levels until at most kCoarseMax unknowns remain, where the coarse matrix is inverted
-//     densely (Cholesky) and applied as a dense product.
+//     densely (Cholesky; Gauss-Jordan with partial pivoting for the non-symmetric matrix of
+//     the axisymmetric configuration) and applied as a dense product.
+// The same construction serves the axisymmetric matrix (mildly non-symmetric; it also maps the
+// constant potential to zero), preconditioning BiCGStab there (solver kind 9).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -210,6 +213,40 @@ bool dense_spd_inverse(std::vector<double>& a, int n) {
   return true;
 }
 
+// dense inverse of a general matrix (row-major n x n) by Gauss-Jordan elimination with
+// partial pivoting; false if singular
+bool dense_inverse(std::vector<double>& a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(a[(size_t)i * n + c]) > std::fabs(a[(size_t)piv * n + c])) piv = i;
+    if (!(std::fabs(a[(size_t)piv * n + c]) > 0)) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)c * n + k], a[(size_t)piv * n + k]);
+        std::swap(inv[(size_t)c * n + k], inv[(size_t)piv * n + k]);
+      }
+    const double dinv = 1.0 / a[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      a[(size_t)c * n + k] *= dinv;
+      inv[(size_t)c * n + k] *= dinv;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = a[(size_t)i * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)i * n + k] -= f * a[(size_t)c * n + k];
+        inv[(size_t)i * n + k] -= f * inv[(size_t)c * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
 }  // namespace
 
 void sell_from_csr(const Csr& A, SellHost& S) {
@@ -244,6 +281,8 @@ void sell_from_csr(const Csr& A, SellHost& S) {
 }
 
 int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
+  // the axisymmetric matrix is not symmetric: no symmetrisation, LU instead of Cholesky
+  const bool symmetric = m.geometry != AVIP_GEOM_AXISYMMETRIC;
   auto fail = [&](const char* msg) {
     if (err && errlen) std::snprintf(err, errlen, "%s", msg);
     return AVIP_EINVAL;
@@ -279,7 +318,8 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
       std::vector<double> dense((size_t)A.n * A.n, 0.0);
       for (int32_t i = 0; i < A.n; ++i)
         for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) dense[(size_t)i * A.n + A.ci[e]] += A.v[e];
-      if (!dense_spd_inverse(dense, A.n)) return fail("AMG set-up: coarse matrix not positive definite");
+      if (symmetric ? !dense_spd_inverse(dense, A.n) : !dense_inverse(dense, A.n))
+        return fail("AMG set-up: coarse matrix is singular");
       H.nc = A.n;
       H.cinv.swap(dense);
       L.A = std::move(A);
@@ -338,7 +378,7 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
     }
     Csr R = transpose(P);
     Csr Ac = spgemm(R, spgemm(A, P));
-    {  // symmetrise the rounding of the Galerkin product (its pattern is symmetric)
+    if (symmetric) {  // symmetrise the rounding of the Galerkin product (its pattern is symmetric)
       const Csr AcT = transpose(Ac);
       for (int32_t i = 0; i < Ac.n; ++i)
         for (int32_t e = Ac.rp[i], f = AcT.rp[i]; e < Ac.rp[i + 1]; ++e, ++f) Ac.v[e] = 0.5 * (Ac.v[e] + AcT.v[f]);

@@ -209,7 +209,7 @@ int cuda_status(cudaError_t e) {
 cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 8) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind == 8 || h->plan.kind == 9) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
@@ -364,12 +364,14 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   }
   // the axisymmetric matrix is not symmetric: only BiCGStab (kind 7, FP64) applies
   const bool axi = h->opts.geometry == AVIP_GEOM_AXISYMMETRIC;
-  if (axi && (h->opts.precision != AVIP_PREC_FP64 || (h->opts.pcg_kind != 0 && h->opts.pcg_kind != 7))) {
-    std::snprintf(g_err, sizeof(g_err), "axisymmetric meshes need precision FP64 and pcg_kind 0 or 7 (BiCGStab)");
+  if (axi && (h->opts.precision != AVIP_PREC_FP64 ||
+              (h->opts.pcg_kind != 0 && h->opts.pcg_kind != 7 && h->opts.pcg_kind != 9))) {
+    std::snprintf(g_err, sizeof(g_err),
+                  "axisymmetric meshes need precision FP64 and pcg_kind 0, 7 or 9 (BiCGStab, Jacobi or AMG)");
     delete h;
     return AVIP_EINVAL;
   }
-  if ((h->opts.pcg_kind == 7 || h->opts.pcg_kind == 8) && h->opts.precision != AVIP_PREC_FP64) {
+  if (h->opts.pcg_kind >= 7 && h->opts.precision != AVIP_PREC_FP64) {
     delete h;
     return AVIP_EINVAL;
   }
@@ -418,10 +420,12 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   // persistent PCG grid (co-resident blocks): register-resident kernel when the mesh fits
   h->plan = h->opts.precision == AVIP_PREC_MIXED ? pcg_mixed_plan(m.nslices, h->opts.pcg_threads)
                                                  : pcg_plan(m.nslices, h->opts.pcg_kind, h->opts.pcg_threads);
-  const bool bicg = axi || h->opts.pcg_kind == 7;
+  const bool bicg = axi || h->opts.pcg_kind == 7 || h->opts.pcg_kind == 9;
+  // BiCGStab preconditioned by the AMG V-cycle: forced, or automatic above the cluster size
+  const bool bicg_amg = bicg && (h->opts.pcg_kind == 9 || (h->opts.pcg_kind == 0 && m.N > kClusterAutoRows));
   if (bicg) {
     h->plan = bicgstab_plan(m.nslices, h->opts.pcg_threads);
-    ok = ok && zalloc(h, h->bcg, 3 * Np);
+    ok = ok && zalloc(h, h->bcg, (bicg_amg ? 5 : 3) * Np);
   } else if (h->opts.pcg_kind == 0 || h->opts.pcg_kind == 5 || h->opts.pcg_kind == 6) {
     // small meshes: one thread-block cluster with everything in shared memory
     const int mixed = h->opts.precision == AVIP_PREC_MIXED ? 1 : 0;
@@ -436,9 +440,10 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
       h->plan = cp;
     }
   }
-  // large planar FP64 meshes (or kind 8 forced): CG preconditioned by an AMG V-cycle
-  if (!bicg && h->opts.precision == AVIP_PREC_FP64 &&
-      (h->opts.pcg_kind == 8 || (h->opts.pcg_kind == 0 && h->plan.kind != 5))) {
+  // large FP64 meshes (or kinds 8/9 forced): CG (planar) or BiCGStab (axisymmetric)
+  // preconditioned by an AMG V-cycle
+  if (bicg_amg || (!bicg && h->opts.precision == AVIP_PREC_FP64 &&
+                   (h->opts.pcg_kind == 8 || (h->opts.pcg_kind == 0 && h->plan.kind != 5)))) {
     AmgHost H;
     int rc = amg_setup(m, H, g_err, sizeof(g_err));
     if (rc != AVIP_OK) {
@@ -448,7 +453,7 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
       return rc;
     }
     ok = ok && upload_amg(h, H);
-    h->plan = amg_plan(m.nslices, h->opts.pcg_threads);
+    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, bicg ? 9 : 8);
   }
   if (h->opts.precision == AVIP_PREC_MIXED) {
     std::vector<float> a32(m.aval.begin(), m.aval.end());
@@ -541,7 +546,7 @@ int mesh_info(avip_mesh_t h, int64_t* info) {
 
 int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
   if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
-  const int32_t nl = h->plan.kind == 8 ? h->amg_levels : 0;
+  const int32_t nl = (h->plan.kind == 8 || h->plan.kind == 9) ? h->amg_levels : 0;
   for (int32_t l = 0; l < nl && l < max_levels; ++l)
     for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
   return nl;
@@ -953,7 +958,7 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
       delete b;
       return h ? AVIP_ESTATE : AVIP_EINVAL;
     }
-    if (h->plan.kind == 7) {  // the batched solver is conjugate gradients (symmetric matrices)
+    if (h->plan.kind == 7 || h->plan.kind == 9) {  // the batched solver is CG (symmetric matrices)
       std::snprintf(g_err, sizeof(g_err), "batches take planar meshes solved by CG only");
       delete b;
       return AVIP_EINVAL;

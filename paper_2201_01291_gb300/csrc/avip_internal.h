@@ -215,7 +215,7 @@ struct PcgArgs {
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
                    // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix),
-                   // 8 AMG-preconditioned CG
+                   // 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
@@ -223,7 +223,7 @@ struct PcgPlan {
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
-PcgPlan amg_plan(int nslices, int requested_tpb);
+PcgPlan amg_plan(int nslices, int requested_tpb, int kind);  // kind 8 (CG) or 9 (BiCGStab)
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

@@ -54,19 +54,20 @@ __device__ __forceinline__ bool grid_barrier(FlagSync& fs, double* smem) {
   return grid_allsum<1>(d, fs, smem);
 }
 
-// One V-cycle: z = x_0 from b_0 = r.  On entry b_0 and d_0 = D^-1 b_0 / theta_0 are complete
-// (written before the last barrier).  Returns r.z in rz (grid-reduced, also the barrier after
-// which z is complete); false if a wait was abandoned.
-__device__ bool vcycle(const AmgDev* __restrict__ H, FlagSync& fs, double* smem, int gwarp, int nwarps,
-                       int lane, double& rz) {
+// One V-cycle: x0 = M b0 (level 0 takes b0 and x0 instead of the hierarchy's own vectors).
+// On entry b0 and d_0 = D^-1 b0 / theta_0 are complete (written before the last barrier).
+// Returns b0.x0 in rz (grid-reduced, also the barrier after which x0 is complete); false if a
+// wait was abandoned.
+__device__ bool vcycle(const AmgDev* __restrict__ H, const double* __restrict__ b0, double* __restrict__ x0,
+                       FlagSync& fs, double* smem, int gwarp, int nwarps, int lane, double& rz) {
   const int nl = H->nlev;
   for (int l = 0; l + 1 < nl; ++l) {
     const AmgLevelDev* __restrict__ L = H->L + l;
     const SellMat A = L->A;
     const int n = L->n;
     const double* __restrict__ dinv = L->dinv;
-    const double* __restrict__ b = L->b;
-    double* __restrict__ x = L->x;
+    const double* __restrict__ b = l == 0 ? b0 : L->b;
+    double* __restrict__ x = l == 0 ? x0 : L->x;
     double* __restrict__ d = L->d;
     double* __restrict__ r = L->r;
     {
@@ -110,8 +111,8 @@ __device__ bool vcycle(const AmgDev* __restrict__ H, FlagSync& fs, double* smem,
     const AmgLevelDev* __restrict__ C = H->L + nl - 1;
     const int n = H->nc;
     const double* __restrict__ cinv = H->cinv;
-    const double* __restrict__ cb = C->b;
-    double* __restrict__ cx = C->x;
+    const double* __restrict__ cb = nl == 1 ? b0 : C->b;
+    double* __restrict__ cx = nl == 1 ? x0 : C->x;
     double acc[1] = {0.0};
     for (int row = gwarp; row < n; row += nwarps) {
       double s = 0.0;
@@ -131,8 +132,8 @@ __device__ bool vcycle(const AmgDev* __restrict__ H, FlagSync& fs, double* smem,
     const SellMat A = L->A;
     const int n = L->n;
     const double* __restrict__ dinv = L->dinv;
-    const double* __restrict__ b = L->b;
-    double* __restrict__ x = L->x;
+    const double* __restrict__ b = l == 0 ? b0 : L->b;
+    double* __restrict__ x = l == 0 ? x0 : L->x;
     double* __restrict__ d = L->d;
     double* __restrict__ r = L->r;
     {  // prolongation
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
         }
         // ---- z = M r (r and the level-0 direction complete)
         double rz_new = 0.0;
-        if (!vcycle(H, fs, smem, gwarp, nwarps, lane, rz_new)) goto timeout;
+        if (!vcycle(H, a.r, z, fs, smem, gwarp, nwarps, lane, rz_new)) goto timeout;
         if (!(rz_new > 0.0) || !isfinite(rz_new)) {  // the preconditioned residual lost positivity
           if (it == 0 || restarts >= kAmgMaxRestarts) {
             status = AVIP_ENOTCONV;
@@ -321,25 +322,237 @@ timeout:
   }
 }
 
-static const void* amg_kernel_ptr(int tpb) {
+// BiCGStab right-preconditioned by the same V-cycle, for the non-symmetric axisymmetric
+// matrix (solver kind 9): with p^ = M p and s^ = M s,
+//   P1  v = A p^, rh.v -> alpha;  P2  s = r - alpha v (barrier);  P3  t = A s^, t.s, t.t, rh.s,
+//   rh.t -> omega, rho', beta;  P4  x += alpha p^ + omega s^, r = s - omega t,
+//   p = r + beta (p - omega v), r.r -> stop test
+// (van der Vorst's iteration with M^-1 applied on the right, so x is updated directly and the
+// stopping test stays on the true scaled residual of the free rows).  Two V-cycles per
+// iteration; breakdowns and a true residual still too large restart from the true residual.
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
+  __shared__ double smem[2 * 32 * 4];
+  const int lane = threadIdx.x & 31;
+  constexpr int wpb = TPB / 32;
+  const int gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  const int N = a.A.N, nsl = a.A.nslices;
+  const size_t Np = (size_t)a.Npad;
+  const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * Np;
+  const AmgDev* __restrict__ H = a.amg;
+  const double* __restrict__ dinv0 = H->L[0].dinv;
+  double* __restrict__ d0 = H->L[0].d;
+  const double inv_theta0 = cheb_of(H->L[0].lmax).inv_theta;
+  double* __restrict__ x = a.x;
+  double* __restrict__ r = a.r;
+  double* __restrict__ p = a.p;
+  double* __restrict__ v = a.q_ap;
+  double* __restrict__ sv = a.bcg;
+  double* __restrict__ tv = a.bcg + Np;
+  double* __restrict__ rh = a.bcg + 2 * Np;
+  double* __restrict__ ph = a.bcg + 3 * Np;
+  double* __restrict__ sh = a.bcg + 4 * Np;
+  FlagSync fs{a.flags, a.parts, a.sync, 0u};
+  double dummy = 0.0;
+
+  double bb[1] = {0.0};
+  for (int sl = gwarp; sl < nsl; sl += nwarps) {
+    const int i = sl * kSlice + lane;
+    if (i >= N) continue;
+    x[i] = a.dsq[i] * a.phi[i];
+    double b;
+    if (a.use_density_rhs) {
+      double rho = 0.0;
+      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * Np + i], rho);
+      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      a.b[i] = b;
+    } else {
+      b = a.b[i];
+    }
+    if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+  }
+  if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
+  {
+    const double thresh = a.rtol * a.rtol * bb[0];
+    double rr_true = 0.0, rho = 0.0;
+    bool restart = true;
+    int it = 0, restarts = 0, status = AVIP_OK;
+    if (bb[0] == 0.0) {
+      for (int sl = gwarp; sl < nsl; sl += nwarps) {
+        const int i = sl * kSlice + lane;
+        if (i < N) x[i] = a.b[i];  // free b == 0: x = b
+      }
+    } else {
+      while (true) {
+        if (restart) {
+          // ---- true residual; rh = p = r; first V-cycle direction of p
+          double r2[1] = {0.0};
+          for (int sl = gwarp; sl < nsl; sl += nwarps) {
+            const int i = sl * kSlice + lane;
+            if (i >= N) continue;
+            const double ri = a.b[i] - sell_row_dot(a.A, sl, lane, i, x);
+            r[i] = ri;
+            rh[i] = ri;
+            p[i] = ri;
+            d0[i] = dinv0[i] * ri * inv_theta0;
+            r2[0] = fma(ri, ri, r2[0]);
+          }
+          if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
+          rr_true = r2[0];
+          if (rr_true <= thresh) break;
+          if (!isfinite(rr_true)) {
+            status = AVIP_ENAN;
+            break;
+          }
+          if (it >= a.max_iter || (it > 0 && restarts >= kAmgMaxRestarts)) {
+            status = AVIP_ENOTCONV;
+            break;
+          }
+          if (it > 0) ++restarts;
+          rho = rr_true;
+          restart = false;
+        }
+        // ---- p^ = M p, then P1: v = A p^
+        if (!vcycle(H, p, ph, fs, smem, gwarp, nwarps, lane, dummy)) goto timeout;
+        double rv[1] = {0.0};
+        for (int sl = gwarp; sl < nsl; sl += nwarps) {
+          const int i = sl * kSlice + lane;
+          if (i >= N) continue;
+          const double w = sell_row_dot(a.A, sl, lane, i, ph);
+          v[i] = w;
+          rv[0] = fma(rh[i], w, rv[0]);
+        }
+        double al[1];
+        const double rho_now = rho;
+        if (!grid_allsum<1, 1>(rv, al, fs, smem, [rho_now](const double* t, double* e) {
+              e[0] = t[0] != 0.0 ? rho_now / t[0] : 0.0;
+            }))
+          goto timeout;
+        if (rv[0] == 0.0 || !isfinite(rv[0])) {  // breakdown
+          if (it == 0) {
+            status = AVIP_ENOTCONV;
+            break;
+          }
+          restart = true;
+          continue;
+        }
+        const double alpha = al[0];
+        // ---- P2: s = r - alpha v; first V-cycle direction of s
+        double ss[1] = {0.0};
+        for (int sl = gwarp; sl < nsl; sl += nwarps) {
+          const int i = sl * kSlice + lane;
+          if (i >= N) continue;
+          const double si = fma(-alpha, v[i], r[i]);
+          sv[i] = si;
+          d0[i] = dinv0[i] * si * inv_theta0;
+          ss[0] = fma(si, si, ss[0]);
+        }
+        if (!grid_allsum<1>(ss, fs, smem)) goto timeout;
+        if (ss[0] <= thresh) {  // s small enough: x += alpha p^, confirm on the true residual
+          for (int sl = gwarp; sl < nsl; sl += nwarps) {
+            const int i = sl * kSlice + lane;
+            if (i < N) x[i] = fma(alpha, __ldcg(ph + i), x[i]);
+          }
+          ++it;
+          restart = true;
+          double z0[1] = {0.0};
+          if (!grid_allsum<1>(z0, fs, smem)) goto timeout;
+          continue;
+        }
+        // ---- s^ = M s, then P3: t = A s^
+        if (!vcycle(H, sv, sh, fs, smem, gwarp, nwarps, lane, dummy)) goto timeout;
+        double d4[4] = {0.0, 0.0, 0.0, 0.0};  // t.s, t.t, rh.s, rh.t
+        for (int sl = gwarp; sl < nsl; sl += nwarps) {
+          const int i = sl * kSlice + lane;
+          if (i >= N) continue;
+          const double ti = sell_row_dot(a.A, sl, lane, i, sh);
+          const double si = sv[i], rhi = rh[i];
+          tv[i] = ti;
+          d4[0] = fma(ti, si, d4[0]);
+          d4[1] = fma(ti, ti, d4[1]);
+          d4[2] = fma(rhi, si, d4[2]);
+          d4[3] = fma(rhi, ti, d4[3]);
+        }
+        double e3[3];
+        if (!grid_allsum<4, 3>(d4, e3, fs, smem, [rho_now, alpha](const double* t, double* e) {
+              const double om = t[1] > 0.0 ? t[0] / t[1] : 0.0;
+              const double rn = t[2] - om * t[3];
+              e[0] = om;
+              e[1] = rn;
+              e[2] = (om != 0.0 && rn != 0.0) ? (rn / rho_now) * (alpha / om) : 0.0;
+            }))
+          goto timeout;
+        const double omega = e3[0], rho_new = e3[1], beta = e3[2];
+        // ---- P4: x, r, p; first V-cycle direction of the new p
+        double rn2[1] = {0.0};
+        for (int sl = gwarp; sl < nsl; sl += nwarps) {
+          const int i = sl * kSlice + lane;
+          if (i >= N) continue;
+          const double si = sv[i], ti = tv[i], pi = p[i];
+          x[i] = fma(omega, __ldcg(sh + i), fma(alpha, __ldcg(ph + i), x[i]));
+          const double ri = fma(-omega, ti, si);
+          r[i] = ri;
+          const double pn = fma(beta, fma(-omega, v[i], pi), ri);
+          p[i] = pn;
+          d0[i] = dinv0[i] * pn * inv_theta0;
+          rn2[0] = fma(ri, ri, rn2[0]);
+        }
+        if (!grid_allsum<1>(rn2, fs, smem)) goto timeout;
+        ++it;
+        rho = rho_new;
+        if (rn2[0] <= thresh || !isfinite(rn2[0]) || omega == 0.0 || rho_new == 0.0 || it >= a.max_iter)
+          restart = true;
+      }
+    }
+    for (int sl = gwarp; sl < nsl; sl += nwarps) {
+      const int i = sl * kSlice + lane;
+      if (i < N) a.phi[i] = a.dsqinv[i] * x[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.sc->pcg_iters = it;
+      a.sc->pcg_status = status;
+      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+      a.sc->pcg_bnorm = sqrt(bb[0]);
+      if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
+    }
+    return;
+  }
+timeout:
+  if (threadIdx.x == 0) {
+    atomicExch(&a.sync->abort, 1);
+    a.sc->pcg_status = AVIP_ETIMEOUT;
+    atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
+  }
+}
+
+static const void* amg_kernel_ptr(int kind, int tpb) {
+  if (kind == 9) {
+    switch (tpb) {
+      case 768: return (const void*)bicgstab_amg_kernel<768>;
+      case 1024: return (const void*)bicgstab_amg_kernel<1024>;
+      default: return (const void*)bicgstab_amg_kernel<512>;
+    }
+  }
   switch (tpb) {
-    case 512: return (const void*)pcg_amg_kernel<512>;
+    case 768: return (const void*)pcg_amg_kernel<768>;
     case 1024: return (const void*)pcg_amg_kernel<1024>;
-    default: return (const void*)pcg_amg_kernel<768>;
+    default: return (const void*)pcg_amg_kernel<512>;
   }
 }
 
 // Grid: co-resident blocks (one per SM), no more than the finest level needs.
-PcgPlan amg_plan(int nslices, int requested_tpb) {
+PcgPlan amg_plan(int nslices, int requested_tpb, int kind) {
   PcgPlan pl;
-  pl.kind = 8;
+  pl.kind = kind;
   pl.tpb = kAmgSizes[0];
   for (int t : kAmgSizes)
     if (t == requested_tpb) pl.tpb = t;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg_kernel_ptr(pl.tpb), pl.tpb, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg_kernel_ptr(kind, pl.tpb), pl.tpb, 0);
   const int wpb = pl.tpb / kSlice;
   const int want = (nslices + wpb - 1) / wpb;
   pl.blocks = std::max(1, std::min(std::max(occ, 1) * std::max(sms, 1), want));
@@ -358,7 +571,7 @@ cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* kargs[] = {const_cast<PcgArgs*>(&args)};
-  return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.tpb), kargs);
+  return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.kind, pl.tpb), kargs);
 }
 
 }  // namespace avip
