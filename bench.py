@@ -165,7 +165,8 @@ KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (regis
                 4: "pcg_mixed_kernel (FP32 inner + FP64 refinement)", 5: "pcg_cluster_kernel (cluster-resident)",
                 7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)",
                 8: "pcg_amg_kernel (CG + smoothed-aggregation AMG V-cycle)",
-                9: "bicgstab_amg_kernel (BiCGStab + AMG V-cycle, axisymmetric)"}
+                9: "bicgstab_amg_kernel (BiCGStab + AMG V-cycle, axisymmetric)",
+                10: "pcg_amg_mixed_kernel (FP32 CG + FP32 AMG V-cycle, FP64 refinement)"}
 
 # DRAM bytes per solver iteration measured by ncu on the pin-plane 500 x 1000 workload (the
 # counters of one captured launch divided by its iterations), keyed by solver kind; valid for the
@@ -194,7 +195,7 @@ def pcg_traffic_model(info, iters, solves):
         (8 + 4), reads s, p, v, z, rh, x (48), writes x, r, A r, p, v (40): 24 nnz + 160 N bytes;
         flops 4 nnz + 32 N per iteration."""
     N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
-    if kind in (8, 9):
+    if kind in (8, 9, 10):
         return amg_traffic_model(info["levels"], nnz, N, iters, solves, kind)
     per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
     per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
@@ -215,19 +216,24 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8):
     48 a + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
     the CG phases add 12 nnz + 116 N.  Flops: 2 per stored entry of every product, 20 per row
     and level for the smoothing and update arithmetic, 12 N for CG.  BiCGStab (kind 9) applies
-    two V-cycles per iteration and its phases add 24 nnz + 216 N bytes and 4 nnz + 32 N flops."""
+    two V-cycles per iteration and its phases add 24 nnz + 216 N bytes and 4 nnz + 32 N flops.
+    The mixed-precision form (kind 10) moves FP32 values: 8 B per stored entry, 4 B per vector
+    element (the handful of FP64 outer residuals per solve are counted with the solve)."""
     cycles = 2 if kind == 9 else 1
+    ent, vec = (8.0 / 12.0, 0.5) if kind == 10 else (1.0, 1.0)
     per_it = (24 * nnz0 + 216 * N) if kind == 9 else (12 * nnz0 + 116 * N)
     fl_it = (4 * nnz0 + 32 * N) if kind == 9 else (2 * nnz0 + 12 * N)
     vb, vf = 0, 0
     for l, (n, a, p) in enumerate(levels):
         if l + 1 < len(levels):
             nc = levels[l + 1][0]
-            vb += 48 * a + 24 * p + 196 * n + 36 * nc
+            vb += ent * (48 * a + 24 * p) + vec * (196 * n + 36 * nc)
             vf += 2 * (4 * a + 2 * p) + 20 * n
         else:
-            vb += 8 * n * n + 16 * n
+            vb += vec * (8 * n * n + 16 * n)
             vf += 2 * n * n
+    if kind == 10:
+        per_it = ent * 12 * nnz0 + vec * 116 * N
     per_it += cycles * vb
     fl_it += cycles * vf
     per_solve = 24 * nnz0 + 100 * N
@@ -309,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     gbs = byts / pcg_s / 1e9
     tfl = flops / pcg_s / 1e12
     kind = info["pcg_kind"]
-    if kind == 4:
+    if kind in (4, 10):
         # FP32 inner solve: bandwidth/latency bound, compare with HBM
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}

@@ -44,7 +44,9 @@ struct avip_mesh {
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
   double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
-  AmgDev* amg = nullptr;        // AMG hierarchy in device memory (kind 8 only)
+  AmgDev* amg = nullptr;        // AMG hierarchy in device memory (kinds 8, 9)
+  AmgDevT<float>* amg32 = nullptr;  // FP32 copy for the mixed-precision solve (kind 10)
+  float* z32 = nullptr;
   double* amg_z = nullptr;      // preconditioned residual (level-0 solution of the V-cycle)
   int32_t amg_levels = 0;
   std::vector<int64_t> amg_stats;  // per level: rows, nnz(A), nnz(P)
@@ -167,6 +169,8 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.bcg = h->bcg;
   a.amg = h->amg;
   a.z = h->amg_z;
+  a.amg32 = h->amg32;
+  a.z32 = h->z32;
   return a;
 }
 
@@ -209,7 +213,7 @@ int cuda_status(cudaError_t e) {
 cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 8 || h->plan.kind == 9) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind >= 8 && h->plan.kind <= 10) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
@@ -247,56 +251,55 @@ void invalidate_graph(avip_mesh* h) {
   h->graph_valid = false;
 }
 
-// Device copy of the AMG hierarchy: level 0 reuses the mesh matrix; every other operator in
-// SELL-32; per level x, b, r, d vectors (level 0: b is the CG residual, x the preconditioned
-// residual z).
-bool upload_amg(avip_mesh* h, const AmgHost& H) {
-  AmgDev D;
+// Device copy of the AMG hierarchy with values of type T (double, or float for the inner
+// solve of the mixed-precision path): level 0 reuses the mesh matrix structure with the values
+// `aval0`; every other operator in SELL-32; per level x, b, r, d vectors (level 0: only r and d,
+// the V-cycle takes its finest right-hand side and solution as arguments).
+template <typename T>
+bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& out) {
+  AmgDevT<T> D;
   std::memset(&D, 0, sizeof(D));
   D.nlev = (int32_t)H.lv.size();
   D.nc = H.nc;
-  auto put = [&](const Csr& M, SellMat& out) {
+  auto put = [&](const Csr& M, SellMatT<T>& dst) {
     SellHost S;
     sell_from_csr(M, S);
     int32_t *slp = nullptr, *slw = nullptr, *rl = nullptr, *col = nullptr;
-    double* val = nullptr;
+    T* val = nullptr;
+    std::vector<T> v(S.val.begin(), S.val.end());
     const bool ok = upload(h, slp, S.sl_ptr) && upload(h, slw, S.sl_w) && upload(h, rl, S.rlen) &&
-                    upload(h, col, S.col, 1) && upload(h, val, S.val, 1);
-    out = SellMat{slp, slw, rl, col, val, S.n, S.nslices};
+                    upload(h, col, S.col, 1) && upload(h, val, v, 1);
+    dst = SellMatT<T>{slp, slw, rl, col, val, S.n, S.nslices};
     return ok;
   };
   bool ok = true;
   for (int32_t l = 0; l < D.nlev && ok; ++l) {
     const AmgHostLevel& L = H.lv[l];
-    AmgLevelDev& dl = D.L[l];
+    AmgLevelT<T>& dl = D.L[l];
     dl.n = L.A.n;
     dl.lmax = L.lmax;
     const size_t npad = (size_t)((L.A.n + kSlice - 1) / kSlice) * kSlice;
     if (l == 0) {
-      dl.A = SellMat{h->sl_ptr, h->sl_w, h->rlen, h->col, h->aval, h->hm.N, h->hm.nslices};
+      dl.A = SellMatT<T>{h->sl_ptr, h->sl_w, h->rlen, h->col, aval0, h->hm.N, h->hm.nslices};
     } else {
       ok = ok && put(L.A, dl.A);
     }
     if (l + 1 < D.nlev) ok = ok && put(L.P, dl.P) && put(L.R, dl.R);
-    double* dinv = nullptr;
-    ok = ok && upload(h, dinv, L.dinv, npad);
+    T* dinv = nullptr;
+    std::vector<T> dv(L.dinv.begin(), L.dinv.end());
+    ok = ok && upload(h, dinv, dv, npad);
     dl.dinv = dinv;
     ok = ok && zalloc(h, dl.r, npad) && zalloc(h, dl.d, npad);
-    if (l == 0) {
-      ok = ok && zalloc(h, dl.x, npad);
-      dl.b = h->r;
-      h->amg_z = dl.x;
-    } else {
-      ok = ok && zalloc(h, dl.x, npad) && zalloc(h, dl.b, npad);
-    }
+    if (l > 0) ok = ok && zalloc(h, dl.x, npad) && zalloc(h, dl.b, npad);
   }
-  double* cinv = nullptr;
-  ok = ok && upload(h, cinv, H.cinv, 1);
+  T* cinv = nullptr;
+  std::vector<T> cv(H.cinv.begin(), H.cinv.end());
+  ok = ok && upload(h, cinv, cv, 1);
   D.cinv = cinv;
-  AmgDev* dd = static_cast<AmgDev*>(dev_alloc(h, sizeof(AmgDev)));
-  ok = ok && dd && cudaMemcpyAsync(dd, &D, sizeof(AmgDev), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+  auto* dd = static_cast<AmgDevT<T>*>(dev_alloc(h, sizeof(D)));
+  ok = ok && dd && cudaMemcpyAsync(dd, &D, sizeof(D), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
        cudaStreamSynchronize(h->stream) == cudaSuccess;
-  h->amg = dd;
+  out = dd;
   h->amg_levels = D.nlev;
   h->amg_stats.clear();
   for (const AmgHostLevel& L : H.lv) {
@@ -371,7 +374,8 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     delete h;
     return AVIP_EINVAL;
   }
-  if (h->opts.pcg_kind >= 7 && h->opts.precision != AVIP_PREC_FP64) {
+  if ((h->opts.pcg_kind >= 7 && h->opts.pcg_kind <= 9 && h->opts.precision != AVIP_PREC_FP64) ||
+      (h->opts.pcg_kind == 10 && h->opts.precision != AVIP_PREC_MIXED)) {
     delete h;
     return AVIP_EINVAL;
   }
@@ -452,12 +456,12 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
       delete h;
       return rc;
     }
-    ok = ok && upload_amg(h, H);
+    ok = ok && upload_amg_t<double>(h, H, h->aval, h->amg) && zalloc(h, h->amg_z, Np);
     h->plan = amg_plan(m.nslices, h->opts.pcg_threads, bicg ? 9 : 8);
   }
   if (h->opts.precision == AVIP_PREC_MIXED) {
     std::vector<float> a32(m.aval.begin(), m.aval.end());
-    ok = upload(h, h->aval32, a32) && zalloc(h, h->e32, Np) && zalloc(h, h->r32, Np) && zalloc(h, h->p32, Np) &&
+    ok = ok && upload(h, h->aval32, a32) && zalloc(h, h->e32, Np) && zalloc(h, h->r32, Np) && zalloc(h, h->p32, Np) &&
          zalloc(h, h->q32, Np);
     // FP32 drift-diffusion stage: gradient weights and edge normals rounded once
     std::vector<float> f(m.gx.begin(), m.gx.end());
@@ -468,6 +472,21 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     ok = ok && upload(h, h->sx32, f);
     f.assign(m.sy.begin(), m.sy.end());
     ok = ok && upload(h, h->sy32, f) && zalloc(h, h->ndat32, 4 * AVIP_MAX_SPECIES * Np);
+  }
+  // large mixed-precision meshes (or kind 10 forced): FP32 inner CG preconditioned by an FP32
+  // AMG V-cycle, FP64 iterative refinement of the residual
+  if (h->opts.precision == AVIP_PREC_MIXED && !bicg &&
+      (h->opts.pcg_kind == 10 || (h->opts.pcg_kind == 0 && h->plan.kind != 6))) {
+    AmgHost H;
+    int rc = amg_setup(m, H, g_err, sizeof(g_err));
+    if (rc != AVIP_OK) {
+      dev_free_all(h);
+      if (h->own_stream) cudaStreamDestroy(h->stream);
+      delete h;
+      return rc;
+    }
+    ok = ok && upload_amg_t<float>(h, H, h->aval32, h->amg32) && zalloc(h, h->z32, Np);
+    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, 10);
   }
   h->nparts = flux_blocks(m.N);
   h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
@@ -546,7 +565,7 @@ int mesh_info(avip_mesh_t h, int64_t* info) {
 
 int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
   if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
-  const int32_t nl = (h->plan.kind == 8 || h->plan.kind == 9) ? h->amg_levels : 0;
+  const int32_t nl = (h->plan.kind >= 8 && h->plan.kind <= 10) ? h->amg_levels : 0;
   for (int32_t l = 0; l < nl && l < max_levels; ++l)
     for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
   return nl;

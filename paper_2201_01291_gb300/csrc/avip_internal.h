@@ -90,32 +90,38 @@ struct SellView {  // device pointers of the SELL-32 structure
   int32_t nslices;
 };
 
-struct SellMat {  // device pointers of a SELL-32 matrix
+template <typename T>
+struct SellMatT {  // device pointers of a SELL-32 matrix with values of type T
   const int32_t* sl_ptr;
   const int32_t* sl_w;
   const int32_t* rlen;
   const int32_t* col;
-  const double* val;
+  const T* val;
   int32_t n;
   int32_t nslices;
 };
+using SellMat = SellMatT<double>;
 
-struct AmgLevelDev {
-  SellMat A, P, R;     // P: n x n_next (prolongation), R = P^T (restriction); unused on the coarsest
-  const double* dinv;
-  double* x;           // level solution (level 0: the preconditioned residual z)
-  double* b;           // level right-hand side (level 0: the CG residual)
-  double* r;           // scratch: residual
-  double* d;           // scratch: Chebyshev direction
+template <typename T>
+struct AmgLevelT {
+  SellMatT<T> A, P, R;  // P: n x n_next (prolongation), R = P^T (restriction); unused on the coarsest
+  const T* dinv;
+  T* x;                 // level solution (the finest level's is passed to the V-cycle instead)
+  T* b;                 // level right-hand side (likewise)
+  T* r;                 // scratch: residual
+  T* d;                 // scratch: Chebyshev direction
   double lmax;
   int32_t n;
 };
-struct AmgDev {
-  int32_t nlev;        // levels including the coarsest
-  int32_t nc;          // coarsest size
-  const double* cinv;  // coarsest dense inverse, nc x nc row-major
-  AmgLevelDev L[kAmgMaxLevels];
+template <typename T>
+struct AmgDevT {
+  int32_t nlev;         // levels including the coarsest
+  int32_t nc;           // coarsest size
+  const T* cinv;        // coarsest dense inverse, nc x nc row-major
+  AmgLevelT<T> L[kAmgMaxLevels];
 };
+using AmgLevelDev = AmgLevelT<double>;
+using AmgDev = AmgDevT<double>;
 
 struct SpeciesParams {
   double q;           // charge number (-1, +1)
@@ -209,13 +215,18 @@ struct PcgArgs {
   // residual z
   const AmgDev* amg;
   double* z;
+  // mixed precision with the AMG preconditioner (kind 10): FP32 copy of the hierarchy and the
+  // FP32 inner-solve vectors e32, r32, p32, q32 (above) plus z32
+  const AmgDevT<float>* amg32;
+  float* z32;
 };
 
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
                    // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix),
-                   // 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab
+                   // 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab, 10 mixed precision
+                   // with the AMG preconditioner (FP32 inner CG + V-cycle, FP64 refinement)
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;

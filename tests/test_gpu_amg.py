@@ -114,3 +114,35 @@ def test_amg_large_mesh_poisson(avip):
     assert rr <= 1e-13 and 0 < it < 200
     assert normwise(m.phi(), phi_ref) <= 1e-10
     m.close()
+
+
+def test_mixed_amg_poisson_and_auto_choice(avip):
+    """Mixed precision with the AMG preconditioner (kind 10): FP32 inner CG and V-cycle, FP64
+    refinement to rtol 1e-12, against the oracle's direct solve; automatic above the cluster
+    size."""
+    p = W.plates_problem(255, 201, 1e-2, 0.8e-2, 2e4, seed=12, field_dependent=True, source=W.SRC_TOWNSEND)
+    o = O.Oracle(p)
+    phi_ref = o.poisson(o.initial_state())
+    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-12)
+    assert m.info["pcg_kind"] == 10
+    it, rr = m.poisson_solve()
+    assert rr <= 1e-12
+    assert normwise(m.phi(), phi_ref) <= 1e-10
+    m.close()
+
+
+def test_mixed_amg_steps_within_1e6(avip):
+    """FP32 gradients, fluxes and inner solve: 50 steps of the reduced pin-plane case within
+    1e-6 of the FP64 oracle."""
+    p = W.plates_problem(41, 81, 1e-2, 2e-2, 2e4, seed=2, field_dependent=True, source=W.SRC_TOWNSEND,
+                         needle_len=2e-3)
+    o = O.Oracle(p)
+    n_ref, phi_ref, _ = o.run(50)
+    m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-10, pcg_kind=10)
+    assert m.info["pcg_kind"] == 10
+    st = m.run(50)
+    assert st["status"] == 0
+    errs = [normwise(m.density(s), n_ref[s]) for s in range(2)] + [normwise(m.phi(), phi_ref)]
+    print("mixed AMG 50-step norm-wise errors (n_e, n_+, phi):", errs)
+    assert max(errs) <= 1e-6
+    m.close()
