@@ -196,18 +196,25 @@ bool dense_spd_inverse(std::vector<double>& a, int n) {
       a[(size_t)i * n + j] = t / ljj;
     }
   }
-  std::vector<double> inv((size_t)n * n), y(n);
+  // U = L^T stored by rows, so that both triangular solves walk memory contiguously
+  std::vector<double> U((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k <= i; ++k) U[(size_t)k * n + i] = a[(size_t)i * n + k];
+  std::vector<double> inv((size_t)n * n), y(n), x(n);
   for (int c = 0; c < n; ++c) {  // column c of the inverse: L y = e_c, L^T x = y
     for (int i = 0; i < n; ++i) {
       double t = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= a[(size_t)i * n + k] * y[k];
-      y[i] = t / a[(size_t)i * n + i];
+      const double* li = &a[(size_t)i * n];
+      for (int k = 0; k < i; ++k) t -= li[k] * y[k];
+      y[i] = t / li[i];
     }
     for (int i = n - 1; i >= 0; --i) {
       double t = y[i];
-      for (int k = i + 1; k < n; ++k) t -= a[(size_t)k * n + i] * inv[(size_t)k * n + c];
-      inv[(size_t)i * n + c] = t / a[(size_t)i * n + i];
+      const double* ui = &U[(size_t)i * n];
+      for (int k = i + 1; k < n; ++k) t -= ui[k] * x[k];
+      x[i] = t / ui[i];
     }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = x[i];
   }
   a.swap(inv);
   return true;
