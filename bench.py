@@ -368,7 +368,10 @@ def run_batch(args, rank, world, local_rank):
     t0 = time.perf_counter()
     probs = W.random_instances(args.instances, seed=4 + 1000 * rank)
     prec = avip.PREC_MIXED if args.precision == "mixed" else avip.PREC_FP64
-    meshes = [avip.Mesh(p, rtol=args.rtol, precision=prec) for p in probs]
+    # instances above 2,000 nodes solve with the cluster form of the AMG-preconditioned CG (kind 8,
+    # or kind 10 in mixed precision); the smaller ones with the shared-memory Jacobi-PCG
+    meshes = [avip.Mesh(p, rtol=args.rtol, precision=prec,
+                        pcg_kind=(8 if prec == avip.PREC_FP64 else 10) if p.n_nodes > 2000 else 0) for p in probs]
     b = avip.Batch(meshes, cluster_size=0)
     setup = time.perf_counter() - t0
     T = sum(p.n_tris for p in probs)

@@ -21,7 +21,9 @@
 //   * smoothed prolongator P = (I - omega D^-1 A) T, omega = 4 / (3 lambda_max(D^-1 A)),
 //     lambda_max from 30 power iterations (times 1.05);
 //   * restriction R = P^T and Galerkin coarse matrix A_c = R A P (rounding symmetrised);
-//   * levels until at most kCoarseMax unknowns remain, where the coarse matrix is inverted
+//   * levels until at most N/64 unknowns remain (clamped to [256, 1500]: a larger dense coarse
+//     level saves barriers per V-cycle on big meshes, a smaller one keeps the O(n^3) set-up of
+//     small meshes cheap), where the coarse matrix is inverted
 //     densely (Cholesky; Gauss-Jordan with partial pivoting for the non-symmetric matrix of
 //     the axisymmetric configuration) and applied as a dense product.
 // The same construction serves the axisymmetric matrix (mildly non-symmetric; it also maps the
@@ -38,7 +40,7 @@ namespace avip {
 namespace {
 
 constexpr double kTheta = 0.08;
-constexpr int kCoarseMax = 1500;
+constexpr int kCoarseMin = 256, kCoarseMax = 1500;
 
 // y = A x (CSR)
 void csr_mv(const Csr& A, const std::vector<double>& x, std::vector<double>& y) {
@@ -290,6 +292,7 @@ void sell_from_csr(const Csr& A, SellHost& S) {
 int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
   // the axisymmetric matrix is not symmetric: no symmetrisation, LU instead of Cholesky
   const bool symmetric = m.geometry != AVIP_GEOM_AXISYMMETRIC;
+  const int32_t coarse_max = std::min(kCoarseMax, std::max(kCoarseMin, m.N / 64));
   auto fail = [&](const char* msg) {
     if (err && errlen) std::snprintf(err, errlen, "%s", msg);
     return AVIP_EINVAL;
@@ -321,7 +324,7 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
       L.dinv[i] = 1.0 / d;
     }
     L.lmax = lambda_max(A, L.dinv);
-    if (A.n <= kCoarseMax || H.lv.size() + 1 >= (size_t)kAmgMaxLevels) {
+    if (A.n <= coarse_max || H.lv.size() + 1 >= (size_t)kAmgMaxLevels) {
       std::vector<double> dense((size_t)A.n * A.n, 0.0);
       for (int32_t i = 0; i < A.n; ++i)
         for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) dense[(size_t)i * A.n + A.ci[e]] += A.v[e];

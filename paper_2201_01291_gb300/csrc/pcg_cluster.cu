@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "avip_internal.h"
+#include "amg_vcycle.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -550,13 +551,40 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, 
   cluster_solve(a, L, sh);
 }
 
+// AMG-preconditioned CG of one instance on one cluster: the rows of every level are shared by
+// the cluster's warps, barriers are cluster barriers and sums go through distributed shared
+// memory (the same V-cycle and CG as the whole-GPU kernel, solver kind 8).
+__device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) {
+  if (solve_skipped(a.sc)) return;  // every CTA of the cluster reads the same status
+  cg::cluster_group cl = cg::this_cluster();
+  ClusterOps ops{cl, part, wsum, 0u};
+  const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
+  amg_cg_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb, (int)(threadIdx.x & 31),
+               rank == 0 && threadIdx.x == 0);
+  cl.sync();  // the next instance reuses the sum buffers
+}
+
+// The same for a mixed-precision instance with an FP32 hierarchy (solver kind 10).
+__device__ void cluster_amg_mixed_solve(const PcgArgs& a, double* part, double* wsum) {
+  if (solve_skipped(a.sc)) return;
+  cg::cluster_group cl = cg::this_cluster();
+  ClusterOps ops{cl, part, wsum, 0u};
+  const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
+  amg_mixed_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb,
+                  (int)(threadIdx.x & 31), rank == 0 && threadIdx.x == 0);
+  cl.sync();
+}
+
 // Batched, persistent: every resident cluster solves instances order[c], order[c + nclusters],
-// ... (the order is sorted by decreasing size, so the largest solves start first).
+// ... (the order is sorted by decreasing size, so the largest solves start first).  Instances
+// that carry an AMG hierarchy (solver kinds 8 and 10) are solved with it, the others with the
+// shared-memory Jacobi-PCG (FP64 or mixed).
 __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const PcgArgs* __restrict__ args,
                                                                             const ClusterLayout* __restrict__ lays,
                                                                             const int32_t* __restrict__ order,
                                                                             int count) {
   __shared__ ClusterShared sh;
+  __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4];
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -564,7 +592,11 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
     const int k = order[j];
     const PcgArgs a = args[k];
     const ClusterLayout L = lays[k];
-    if (L.mixed)
+    if (a.amg)
+      cluster_amg_solve(a, s_amg_part, s_amg_wsum);
+    else if (a.amg32)
+      cluster_amg_mixed_solve(a, s_amg_part, s_amg_wsum);
+    else if (L.mixed)
       cluster_solve_mixed(a, L, sh);
     else
       cluster_solve(a, L, sh);

@@ -80,3 +80,53 @@ def test_mixed_batch_equals_alone_and_oracle(avip):
         assert normwise(meshes[k].phi(), phi_ref) <= 1e-6
         alone.close()
     b.close()
+
+
+def test_batch_with_amg_instances(avip):
+    """Instances above the cluster size carry an AMG hierarchy and are solved inside the batch
+    by the cluster form of the AMG-preconditioned CG; small ones by the shared-memory Jacobi
+    solver.  Every instance matches the oracle; against the same instance alone (whole-GPU AMG
+    kernel, whose dot products are summed in another order) within 1e-10."""
+    ps = [W.plates_problem(181, 151, 1e-2, 0.8e-2, 2e4, seed=51, field_dependent=True, source=W.SRC_TOWNSEND),
+          W.plates_problem(35, 29, 1e-2, 0.8e-2, 1.5e4, seed=52, field_dependent=True, source=W.SRC_TOWNSEND),
+          W.plates_problem(151, 201, 1e-2, 1.3e-2, 2.2e4, seed=53, field_dependent=True,
+                           source=W.SRC_TOWNSEND_ATTACH, n_species=3)]
+    nsteps = 5
+    meshes = [avip.Mesh(p, rtol=1e-13) for p in ps]
+    assert [m.info["pcg_kind"] for m in meshes] == [8, 5, 8]
+    b = avip.Batch(meshes, cluster_size=16)
+    b.run(nsteps)
+    for k, p in enumerate(ps):
+        alone = avip.Mesh(p, rtol=1e-13)
+        alone.run(nsteps)
+        o = O.Oracle(p)
+        n_ref, phi_ref, _ = o.run(nsteps)
+        for s in range(len(p.species)):
+            assert normwise(meshes[k].density(s), n_ref[s]) <= 1e-10, (k, s)
+            assert normwise(meshes[k].density(s), alone.density(s)) <= 1e-10, (k, s)
+        assert normwise(meshes[k].phi(), phi_ref) <= 1e-10
+        alone.close()
+    b.close()
+
+
+def test_mixed_batch_with_amg_instances(avip):
+    """Mixed-precision instances with an FP32 AMG hierarchy (kind 10) inside a batch: within
+    1e-6 of the FP64 oracle, and close to the same instance solved alone by the whole-GPU
+    mixed AMG kernel."""
+    ps = [W.plates_problem(121, 101, 1e-2, 0.8e-2, 2e4, seed=61, field_dependent=True, source=W.SRC_TOWNSEND),
+          W.plates_problem(61, 41, 1e-2, 0.8e-2, 1.5e4, seed=62, field_dependent=True, source=W.SRC_TOWNSEND)]
+    nsteps = 5
+    meshes = [avip.Mesh(p, rtol=1e-11, precision=avip.PREC_MIXED, pcg_kind=10) for p in ps]
+    b = avip.Batch(meshes, cluster_size=16)
+    b.run(nsteps)
+    for k, p in enumerate(ps):
+        alone = avip.Mesh(p, rtol=1e-11, precision=avip.PREC_MIXED, pcg_kind=10)
+        alone.run(nsteps)
+        o = O.Oracle(p)
+        n_ref, phi_ref, _ = o.run(nsteps)
+        for s in range(len(p.species)):
+            assert normwise(meshes[k].density(s), n_ref[s]) <= 1e-6, (k, s)
+            assert normwise(meshes[k].density(s), alone.density(s)) <= 1e-8, (k, s)
+        assert normwise(meshes[k].phi(), phi_ref) <= 1e-6
+        alone.close()
+    b.close()
