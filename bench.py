@@ -166,7 +166,8 @@ KERNEL_NAMES = {1: "pcg_fp64_kernel (streaming)", 2: "pcg_fp64_res_kernel (regis
                 7: "bicgstab_fp64_kernel (non-symmetric, axisymmetric)",
                 8: "pcg_amg_kernel (CG + smoothed-aggregation AMG V-cycle)",
                 9: "bicgstab_amg_kernel (BiCGStab + AMG V-cycle, axisymmetric)",
-                10: "pcg_amg_mixed_kernel (FP32 CG + FP32 AMG V-cycle, FP64 refinement)"}
+                10: "pcg_amg_mixed_kernel (FP32 CG + FP32 AMG V-cycle, FP64 refinement)",
+                11: "pcg_amg_cluster_kernel (AMG-preconditioned CG on one cluster)"}
 
 # DRAM bytes per solver iteration measured by ncu on the pin-plane 500 x 1000 workload (the
 # counters of one captured launch divided by its iterations), keyed by solver kind; valid for the
@@ -309,6 +310,9 @@ def run_ours(args, rank, world, local_rank):
         return None
     # ---- roofline of the dominant kernel (PCG)
     peaks = measured_peaks()
+    kernel_name = KERNEL_NAMES.get(info["pcg_kind"], str(info["pcg_kind"]))
+    if info["pcg_kind"] == 11:  # the one-cluster AMG solve moves the bytes of kind 8 or 10
+        info = dict(info, pcg_kind=10 if args.precision == "mixed" else 8)
     byts, flops = pcg_traffic_model(info, iters, args.steps)
     pcg_s = kernel_ms["pcg"] / 1e3
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -326,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
                 "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm, 4)}
     per_launch_iters = iters / args.steps
     traffic, note = NCU_DRAM_BYTES_PER_ITER.get(kind, (None, None)) if args.workload == "pin_plane" else (None, None)
-    roof.update({"kernel": KERNEL_NAMES.get(kind, str(kind)),
+    roof.update({"kernel": kernel_name,
                  "traffic": int(traffic * per_launch_iters) if traffic else None,
                  "traffic_note": note,
                  "algorithmic_bytes_per_launch": int(byts / args.steps),

@@ -101,7 +101,9 @@ typedef struct avip_opts {
                                           8 CG preconditioned by an AMG V-cycle (auto for planar
                                           FP64 meshes above 20,000 nodes), 9 BiCGStab
                                           preconditioned by it (auto for AXISYMMETRIC meshes
-                                          above 20,000 nodes) */
+                                          above 20,000 nodes), 10 the mixed-precision form of
+                                          8, 11 the AMG solve on one thread-block cluster (auto
+                                          for planar meshes of 501 to 20,000 nodes) */
   void* stream;                        /* cudaStream_t for all work; NULL = default stream    */
   avip_alloc_fn alloc;                 /* optional device allocator (both or neither)         */
   avip_free_fn free;
@@ -193,11 +195,12 @@ int state_set(avip_mesh_t h, const double* host_state);
 
 /* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
  * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident, 6 cluster mixed,
- * 7 BiCGStab, 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab), solver blocks,
+ * 7 BiCGStab, 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab, 10 mixed AMG, 11 AMG on one
+ * cluster), solver blocks,
  * PCG threads per block, device bytes held by the handle}. */
 int mesh_info(avip_mesh_t h, int64_t* info8);
 
-/* Multigrid hierarchy of the AMG-preconditioned solvers (kinds 8, 9; the paper names no solver, this
+/* Multigrid hierarchy of the AMG-preconditioned solvers (kinds 8-11; the paper names no solver, this
  * reports the set-up built for this project's preconditioner).  Returns the number of levels
  * (finest first, the last one inverted densely), or 0 when the handle uses another solver; for
  * the first min(levels, max_levels) levels writes out[3*l] = rows, out[3*l+1] = stored entries

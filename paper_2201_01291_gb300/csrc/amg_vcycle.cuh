@@ -14,20 +14,6 @@
 
 namespace avip {
 
-// Degree-2 Chebyshev coefficients on [lmax/30, lmax]: d0 = D^-1 r / theta,
-// d1 = c1 d0 + c2 D^-1 r1.
-struct Cheb {
-  double inv_theta, c1, c2;
-};
-__device__ __forceinline__ Cheb cheb_of(double lmax) {
-  const double lmin = lmax / 30.0;
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-  const double sigma = theta / delta;
-  const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
-  return Cheb{1.0 / theta, rho1 * rho0, 2.0 * rho1 / delta};
-}
-
-
 // Per-thread accumulation of a dot product: FP64 fused multiply-adds, or compensated (Kahan)
 // FP32 sums in the mixed-precision solve.
 template <typename T>
@@ -68,8 +54,7 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
     T* __restrict__ d = L->d;
     T* __restrict__ r = L->r;
     {
-      const Cheb ch = cheb_of(L->lmax);
-      const T c1 = (T)ch.c1, c2 = (T)ch.c2;
+      const T c1 = (T)L->c1, c2 = (T)L->c2;
       // second Chebyshev step from x = d0: r1 = b - A d0, x = d0 + c1 d0 + c2 D^-1 r1
       for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
         const int i = sl * kSlice + lane;
@@ -91,7 +76,7 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
       const AmgLevelT<T>* __restrict__ C = H->L + l + 1;
       const SellMatT<T> R = L->R;
       const int nc = C->n;
-      const T c_inv_theta = (T)cheb_of(C->lmax).inv_theta;
+      const T c_inv_theta = (T)C->inv_theta;
       const T* __restrict__ cdinv = C->dinv;
       T* __restrict__ cb = C->b;
       T* __restrict__ cd = C->d;
@@ -122,9 +107,13 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
         if (nl == 1) acc.add(__ldcg(cb + row), s);
       }
     }
-    double av[1] = {acc.value()};
-    if (!ops.sum(av)) return false;
-    if (nl == 1) rz = av[0];
+    if (nl == 1) {
+      double av[1] = {acc.value()};
+      if (!ops.sum(av)) return false;
+      rz = av[0];
+    } else if (!ops.barrier()) {
+      return false;
+    }
   }
   for (int l = nl - 2; l >= 0; --l) {
     const AmgLevelT<T>* __restrict__ L = H->L + l;
@@ -145,8 +134,7 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
       }
     }
     if (!ops.barrier()) return false;
-    const Cheb ch = cheb_of(L->lmax);
-    const T inv_theta = (T)ch.inv_theta, c1 = (T)ch.c1, c2 = (T)ch.c2;
+    const T inv_theta = (T)L->inv_theta, c1 = (T)L->c1, c2 = (T)L->c2;
     // first post-smoothing step: r = b - A x, d = D^-1 r / theta (x updated in the next phase)
     for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
       const int i = sl * kSlice + lane;
@@ -167,9 +155,13 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
       x[i] = xi;
       if (l == 0) acc.add(b[i], xi);
     }
-    double av[1] = {acc.value()};
-    if (!ops.sum(av)) return false;
-    if (l == 0) rz = av[0];
+    if (l == 0) {
+      double av[1] = {acc.value()};
+      if (!ops.sum(av)) return false;
+      rz = av[0];
+    } else if (!ops.barrier()) {
+      return false;
+    }
   }
   return true;
 }
@@ -187,7 +179,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
   const double* __restrict__ dinv0 = H->L[0].dinv;
   double* __restrict__ d0 = H->L[0].d;
   double* __restrict__ z = a.z;  // preconditioned residual (the V-cycle's finest solution)
-  const double inv_theta0 = cheb_of(H->L[0].lmax).inv_theta;
+  const double inv_theta0 = H->L[0].inv_theta;
 
   // ---- x = D^1/2 phi (warm start) and b'
   double bb[1] = {0.0};
@@ -318,7 +310,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
   const SellMatT<float> A32 = H->L[0].A;
   const float* __restrict__ dinv0 = H->L[0].dinv;
   float* __restrict__ d0 = H->L[0].d;
-  const float inv_theta0 = (float)cheb_of(H->L[0].lmax).inv_theta;
+  const float inv_theta0 = (float)H->L[0].inv_theta;
   float* __restrict__ r32 = a.r32;
   float* __restrict__ e32 = a.e32;
   float* __restrict__ p32 = a.p32;
@@ -472,12 +464,14 @@ struct GridOps {
 
 // Synchronisation of one thread-block cluster: hardware cluster barrier (release / acquire at
 // cluster scope, so global-memory writes of the cluster are visible after it) and sums through
-// distributed shared memory, combined in rank order (deterministic).  `part` (2 x 4 doubles)
-// and `wsum` (32 x 4 doubles) are the calling CTA's shared scratch.
+// distributed shared memory (at most 32 CTAs; deterministic: fixed shuffle tree over the ranks).
+// `part` (2 x 4 doubles), `wsum` (32 x 4 doubles) and `res` (4 doubles) are the calling CTA's
+// shared scratch.
 struct ClusterOps {
   cooperative_groups::cluster_group cl;
-  double* part;
-  double* wsum;
+  double* part;  // [2][4]: this CTA's partials, double-buffered
+  double* wsum;  // [32][4]: warp partials
+  double* res;   // [4]: cluster totals for this CTA's threads
   unsigned seq;
   __device__ bool barrier() {
     cl.sync();
@@ -503,13 +497,21 @@ struct ClusterOps {
       part[buf * 4 + threadIdx.x] = t;
     }
     cl.sync();
-    const int C = (int)cl.num_blocks();
+    // warp 0 gathers the C partials (lane r reads rank r) and reduces them with a fixed
+    // shuffle tree; the totals reach the other warps through shared memory
+    if (warp == 0) {
+      const int C = (int)cl.num_blocks();
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = 0.0;
-      for (int r = 0; r < C; ++r) t += *cl.map_shared_rank(part + buf * 4 + k, r);
-      v[k] = t;
+      for (int k = 0; k < NV; ++k) {
+        double t = lane < C ? *cl.map_shared_rank(part + buf * 4 + k, lane) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) res[k] = t;
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = res[k];
     return true;
   }
 };

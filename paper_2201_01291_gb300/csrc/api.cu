@@ -16,6 +16,7 @@ cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_bicgstab(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_pcg_amg_cluster(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
@@ -71,7 +72,8 @@ struct avip_mesh {
 namespace {
 
 thread_local char g_err[256];
-constexpr int kClusterAutoRows = 20000;  // cluster-resident PCG below this many nodes
+constexpr int kClusterAutoRows = 20000;  // one-cluster solvers up to this many nodes
+constexpr int kClusterAmgMinRows = 500;  // AMG on one cluster above this many nodes (Jacobi below)
 
 void* dev_alloc(avip_mesh* h, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -214,6 +216,7 @@ cudaError_t enqueue_pcg_only(avip_mesh* h) {
   if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind >= 8 && h->plan.kind <= 10) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
+  if (h->plan.kind == 11) return launch_pcg_amg_cluster(pcg_args(h), h->plan, h->stream);
   if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
   return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
 }
@@ -278,6 +281,13 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& o
     AmgLevelT<T>& dl = D.L[l];
     dl.n = L.A.n;
     dl.lmax = L.lmax;
+    {  // degree-2 Chebyshev smoother on [lmax/30, lmax], coefficients of its two-term recurrence
+      const double lmin = L.lmax / 30.0, theta = 0.5 * (L.lmax + lmin), delta = 0.5 * (L.lmax - lmin);
+      const double sigma = theta / delta, rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+      dl.inv_theta = 1.0 / theta;
+      dl.c1 = rho1 * rho0;
+      dl.c2 = 2.0 * rho1 / delta;
+    }
     const size_t npad = (size_t)((L.A.n + kSlice - 1) / kSlice) * kSlice;
     if (l == 0) {
       dl.A = SellMatT<T>{h->sl_ptr, h->sl_w, h->rlen, h->col, aval0, h->hm.N, h->hm.nslices};
@@ -488,6 +498,26 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     ok = ok && upload_amg_t<float>(h, H, h->aval32, h->amg32) && zalloc(h, h->z32, Np);
     h->plan = amg_plan(m.nslices, h->opts.pcg_threads, 10);
   }
+  // mid-size planar meshes (or kind 11 forced): the AMG-preconditioned solve on one cluster
+  if (!bicg && (h->opts.pcg_kind == 11 ||
+                (h->opts.pcg_kind == 0 && m.N > kClusterAmgMinRows && m.N <= kClusterAutoRows))) {
+    const PcgPlan cp = amg_cluster_plan();
+    if (cp.kind == 11) {
+      AmgHost H;
+      int rc = amg_setup(m, H, g_err, sizeof(g_err));
+      if (rc != AVIP_OK) {
+        dev_free_all(h);
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return rc;
+      }
+      if (h->opts.precision == AVIP_PREC_MIXED)
+        ok = ok && upload_amg_t<float>(h, H, h->aval32, h->amg32) && zalloc(h, h->z32, Np);
+      else
+        ok = ok && upload_amg_t<double>(h, H, h->aval, h->amg) && zalloc(h, h->amg_z, Np);
+      h->plan = cp;
+    }
+  }
   h->nparts = flux_blocks(m.N);
   h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
   ok = ok && zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
@@ -565,7 +595,7 @@ int mesh_info(avip_mesh_t h, int64_t* info) {
 
 int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
   if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
-  const int32_t nl = (h->plan.kind >= 8 && h->plan.kind <= 10) ? h->amg_levels : 0;
+  const int32_t nl = (h->plan.kind >= 8 && h->plan.kind <= 11) ? h->amg_levels : 0;
   for (int32_t l = 0; l < nl && l < max_levels; ++l)
     for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
   return nl;

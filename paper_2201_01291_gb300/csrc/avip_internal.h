@@ -111,6 +111,9 @@ struct AmgLevelT {
   T* r;                 // scratch: residual
   T* d;                 // scratch: Chebyshev direction
   double lmax;
+  // degree-2 Chebyshev smoother on [lmax/30, lmax] (set on the host from lmax):
+  // d0 = D^-1 r * inv_theta,  d1 = c1 d0 + c2 D^-1 r1
+  double inv_theta, c1, c2;
   int32_t n;
 };
 template <typename T>
@@ -226,7 +229,8 @@ struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,
                    // 6 cluster-resident mixed precision, 7 BiCGStab (non-symmetric matrix),
                    // 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab, 10 mixed precision
-                   // with the AMG preconditioner (FP32 inner CG + V-cycle, FP64 refinement)
+                   // with the AMG preconditioner (FP32 inner CG + V-cycle, FP64 refinement),
+                   // 11 AMG-preconditioned CG (FP64 or mixed) on one thread-block cluster
   int tpb = 768;
   int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
   int blocks = 1;
@@ -234,7 +238,8 @@ struct PcgPlan {
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
-PcgPlan amg_plan(int nslices, int requested_tpb, int kind);  // kind 8 (CG) or 9 (BiCGStab)
+PcgPlan amg_plan(int nslices, int requested_tpb, int kind);  // kind 8 (CG), 9 (BiCGStab), 10 (mixed)
+PcgPlan amg_cluster_plan();  // kind 11 (one cluster; kind 0 if no cluster size is schedulable)
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   const AmgDev* __restrict__ H = a.amg;
   const double* __restrict__ dinv0 = H->L[0].dinv;
   double* __restrict__ d0 = H->L[0].d;
-  const double inv_theta0 = cheb_of(H->L[0].lmax).inv_theta;
+  const double inv_theta0 = H->L[0].inv_theta;
   double* __restrict__ x = a.x;
   double* __restrict__ r = a.r;
   double* __restrict__ p = a.p;

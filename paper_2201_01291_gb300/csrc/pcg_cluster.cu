@@ -557,18 +557,20 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, 
 __device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) {
   if (solve_skipped(a.sc)) return;  // every CTA of the cluster reads the same status
   cg::cluster_group cl = cg::this_cluster();
-  ClusterOps ops{cl, part, wsum, 0u};
+  ClusterOps ops{cl, part, wsum, wsum + 32 * 4, 0u};
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
   amg_cg_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb, (int)(threadIdx.x & 31),
                rank == 0 && threadIdx.x == 0);
   cl.sync();  // the next instance reuses the sum buffers
 }
 
+// (wsum holds 32 x 4 warp partials followed by the 4 totals.)
+
 // The same for a mixed-precision instance with an FP32 hierarchy (solver kind 10).
 __device__ void cluster_amg_mixed_solve(const PcgArgs& a, double* part, double* wsum) {
   if (solve_skipped(a.sc)) return;
   cg::cluster_group cl = cg::this_cluster();
-  ClusterOps ops{cl, part, wsum, 0u};
+  ClusterOps ops{cl, part, wsum, wsum + 32 * 4, 0u};
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
   amg_mixed_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb,
                   (int)(threadIdx.x & 31), rank == 0 && threadIdx.x == 0);
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
                                                                             const int32_t* __restrict__ order,
                                                                             int count) {
   __shared__ ClusterShared sh;
-  __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4];
+  __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4 + 4];
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -738,6 +740,61 @@ cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const Clu
   cfg.numAttrs = 1;
   if (L.mixed) return cudaLaunchKernelEx(&cfg, pcg_cluster_mixed_kernel, args, L);
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel, args, L);
+}
+
+// Standalone AMG solve on one thread-block cluster (solver kind 11): small and mid-size meshes
+// whose solve is too short to occupy the whole GPU (FP64 hierarchy, or the FP32 one of the
+// mixed-precision path).  Other work, such as other requests of a server, can run beside it.
+__global__ void __launch_bounds__(kClusterTPB, 1) pcg_amg_cluster_kernel(PcgArgs a) {
+  __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4 + 4];
+  if (a.amg)
+    cluster_amg_solve(a, s_amg_part, s_amg_wsum);
+  else
+    cluster_amg_mixed_solve(a, s_amg_part, s_amg_wsum);
+}
+
+// Largest schedulable cluster (16 or 8 CTAs) for the standalone AMG cluster kernel; 0 if none.
+PcgPlan amg_cluster_plan() {
+  PcgPlan pl;
+  pl.kind = 0;
+  cudaFuncSetAttribute(pcg_amg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kClusterTPB);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, pcg_amg_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
+      pl.kind = 11;
+      pl.tpb = kClusterTPB;
+      pl.blocks = c;
+      pl.maxs = 0;
+      return pl;
+    }
+    cudaGetLastError();
+  }
+  return pl;
+}
+
+cudaError_t launch_pcg_amg_cluster(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.blocks);
+  cfg.blockDim = dim3(pl.tpb);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl.blocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pcg_amg_cluster_kernel, args);
 }
 
 // Clusters of size C that can be resident at once with `smem` bytes per CTA.

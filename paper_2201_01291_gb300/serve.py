@@ -30,7 +30,7 @@ from . import avip
 BYTES_PER_NODE = 1400
 BYTES_PER_TRI = 24
 CLUSTER_NODES = 20000  # meshes up to this size use the cluster-resident solver (shared slots)
-CLUSTER_KINDS = (5, 6)  # solver kinds that occupy one thread-block cluster, not the whole GPU
+CLUSTER_KINDS = (5, 6, 11)  # solver kinds that occupy one thread-block cluster, not the whole GPU
 
 
 def estimate_bytes(problem) -> int:

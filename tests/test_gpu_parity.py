@@ -196,15 +196,16 @@ def test_tiny_and_single_slice_meshes(avip):
 MIXED_TOL = 1e-6
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 6, 1])
 def test_mixed_poisson_matches_oracle(avip, kind):
-    """FP32 inner PCG + FP64 refinement reaches the FP64 answer (rtol 1e-12 on the residual),
-    in one cluster (kind 0 picks it for this size) and with the grid-wide kernel (kind 1)."""
+    """FP32 inner solve + FP64 refinement reaches the FP64 answer (rtol 1e-12 on the
+    residual): the one-cluster AMG form (kind 0 picks it for this size), the one-cluster Jacobi
+    form (6) and the grid-wide Jacobi kernel (1, reported as 4)."""
     p = W.config_small(nx=40, ny=33, seed=5)
     o = O.Oracle(p)
     phi_ref = o.poisson(o.initial_state())
     m = avip.Mesh(p, precision=avip.PREC_MIXED, rtol=1e-12, pcg_kind=kind)
-    assert m.info["pcg_kind"] == (6 if kind == 0 else 4)
+    assert m.info["pcg_kind"] == {0: 11, 6: 6, 1: 4}[kind]
     it, rr = m.poisson_solve()
     assert rr <= 1e-12
     assert normwise(m.phi(), phi_ref) <= 1e-10

@@ -86,7 +86,7 @@ def test_sg_batch_equals_alone(avip):
         m.run(15)
         alone.append([m.density(s) for s in range(2)])
         m.close()
-    ms = [avip.Mesh(p, rtol=1e-12) for p in probs]
+    ms = [avip.Mesh(p, rtol=1e-12, pcg_kind=5) for p in probs]
     b = avip.Batch(ms, cluster_size=16)
     b.run(15)
     for k, m in enumerate(ms):
