@@ -167,6 +167,112 @@ def min_edge_length(xy, tris):
     return np.minimum(np.minimum(L[0], L[1]), L[2])
 
 
+# ----------------------------------------------------------------------------- quadrangles
+# The same metrics for a group of polygonal cells (C, nv) of one vertex count, used for the
+# quadrangles of hybrid meshes (section "Nomenclature and notations": n_v vertices per cell,
+# n_v^f = 2 vertices per face, nodal normal S_k = -(n_d/n_v^f) sum of the faces adjacent to k,
+# dual volume V_tau/n_v, dual faces from the edge midpoints to the cell centre).
+def orient_ccw_poly(xy, cells):
+    """Cells with counter-clockwise vertex order (positive shoelace area)."""
+    cells = np.asarray(cells, dtype=np.int64).copy()
+    flip = poly_volumes(xy, cells) < 0
+    cells[flip] = cells[flip, ::-1]
+    return cells
+
+
+def poly_volumes(xy, cells):
+    """Signed shoelace area of each polygon."""
+    nv = cells.shape[1]
+    a = np.zeros(cells.shape[0])
+    for m in range(nv):
+        p, q = xy[cells[:, m]], xy[cells[:, (m + 1) % nv]]
+        a += p[:, 0] * q[:, 1] - q[:, 0] * p[:, 1]
+    return 0.5 * a
+
+
+def poly_face_normals(xy, cells):
+    """Outward length-scaled normals of the faces (m, m+1) of counter-clockwise polygons."""
+    nv = cells.shape[1]
+    Sf = np.empty((cells.shape[0], nv, 2))
+    for m in range(nv):
+        t = xy[cells[:, (m + 1) % nv]] - xy[cells[:, m]]
+        Sf[:, m, 0] = t[:, 1]
+        Sf[:, m, 1] = -t[:, 0]
+    return Sf
+
+
+def poly_nodal_normals(xy, cells):
+    """S_k = -(n_d / n_v^f) (S_f(k) + S_f(k-1)) with n_d = n_v^f = 2 (Eq. node_normal)."""
+    nv = cells.shape[1]
+    Sf = poly_face_normals(xy, cells)
+    S = np.empty_like(Sf)
+    for k in range(nv):
+        S[:, k] = -(Sf[:, k] + Sf[:, (k - 1) % nv])
+    return S
+
+
+def poly_edge_normals(xy, cells):
+    """Length-scaled normal of the dual face from the midpoint of cell edge (m, m+1) to the
+    cell centre (mean of the vertices), oriented from vertex m towards m+1."""
+    nv = cells.shape[1]
+    c = sum(xy[cells[:, m]] for m in range(nv)) / nv
+    out = np.empty((cells.shape[0], nv, 2))
+    for m in range(nv):
+        xi, xj = xy[cells[:, m]], xy[cells[:, (m + 1) % nv]]
+        v = c - 0.5 * (xi + xj)
+        n = np.stack([v[:, 1], -v[:, 0]], axis=1)
+        sgn = np.sign(np.einsum("ij,ij->i", n, xj - xi))
+        out[:, m] = n * sgn[:, None]
+    return out
+
+
+def poly_min_edge_length(xy, cells):
+    nv = cells.shape[1]
+    L = [np.linalg.norm(xy[cells[:, (m + 1) % nv]] - xy[cells[:, m]], axis=1) for m in range(nv)]
+    return np.min(np.stack(L), axis=0)
+
+
+def poly_poisson_matrix(cells, S, V_tau, n_nodes):
+    """K_ik = sum_tau S_i.S_k / (n_d^2 V_tau) over the cells of one group (Eq. coeff_matriceA)."""
+    nv = cells.shape[1]
+    rows, cols, vals = [], [], []
+    for a in range(nv):
+        for b in range(nv):
+            rows.append(cells[:, a])
+            cols.append(cells[:, b])
+            vals.append(np.einsum("ij,ij->i", S[:, a], S[:, b]) / (4.0 * V_tau))
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n_nodes, n_nodes)).tocsr()
+
+
+def hybrid_edges_and_boundary(xy, groups):
+    """Edge list (i < j) with S_ij summed over every cell of every group, and the boundary
+    nodal normals from the faces that belong to one cell only (a face shared by a triangle
+    and a quadrangle is interior)."""
+    I, J, Sv, F = [], [], [], []
+    for cells, Sc, Sf in groups:
+        nv = cells.shape[1]
+        for m in range(nv):
+            I.append(cells[:, m])
+            J.append(cells[:, (m + 1) % nv])
+            Sv.append(Sc[:, m])
+            F.append(Sf[:, m])
+    I, J, Sv, F = np.concatenate(I), np.concatenate(J), np.concatenate(Sv), np.concatenate(F)
+    n1 = int(xy.shape[0]) + 1
+    lo, hi = np.minimum(I, J), np.maximum(I, J)
+    Sv = np.where((I > J)[:, None], -Sv, Sv)
+    key = lo.astype(np.int64) * n1 + hi
+    uniq, inv, counts = np.unique(key, return_inverse=True, return_counts=True)
+    S = np.zeros((uniq.size, 2))
+    np.add.at(S, inv, Sv)
+    edges = np.stack([uniq // n1, uniq % n1], axis=1).astype(np.int64)
+    bnd = counts[inv] == 1
+    Sb = np.zeros((xy.shape[0], 2))
+    np.add.at(Sb, I[bnd], 0.5 * F[bnd])
+    np.add.at(Sb, J[bnd], 0.5 * F[bnd])
+    return edges, S, Sb
+
+
 # ----------------------------------------------------------------------------- axisymmetry
 # Axisymmetric (x, r) configuration: the second coordinate is the radius r >= 0 and every
 # volume or face integral carries the weight r (per radian; the common factor 2 pi cancels).
@@ -392,17 +498,39 @@ class Oracle:
         self.p = problem
         xy = np.asarray(problem.xy, dtype=np.float64)
         self.xy = xy
-        self.tris = orient_ccw(xy, problem.tris)
+        tris = np.asarray(problem.tris, dtype=np.int64).reshape(-1, 3)
+        self.tris = orient_ccw(xy, tris) if tris.size else tris
+        quads = getattr(problem, "quads", None)
+        self.quads = (orient_ccw_poly(xy, np.asarray(quads, dtype=np.int64).reshape(-1, 4))
+                      if quads is not None and len(quads) else np.zeros((0, 4), dtype=np.int64))
         self.N = xy.shape[0]
         self.V_tau = cell_volumes(xy, self.tris)
         if np.any(self.V_tau <= 0):
             raise ValueError("degenerate triangle")
+        self.V_q = poly_volumes(xy, self.quads)
+        if np.any(self.V_q <= 0):
+            raise ValueError("degenerate quadrangle")
+        self.S_q = poly_nodal_normals(xy, self.quads)
+        self.hybrid = self.quads.shape[0] > 0
         self.S = nodal_normals(xy, self.tris)
         # planar dual areas: the weights of the (two-dimensional) nodal gradient
         self.A_node = nodal_volumes(self.tris, self.V_tau, self.N)
         self.dx_tau = min_edge_length(xy, self.tris)
         self.axisymmetric = bool(getattr(problem, "axisymmetric", False))
-        if self.axisymmetric:
+        if self.hybrid:
+            if self.axisymmetric:
+                raise ValueError("quadrangles are supported in the planar configuration only")
+            for k in range(4):
+                np.add.at(self.A_node, self.quads[:, k], self.V_q / 4.0)
+            self.dx_q = poly_min_edge_length(xy, self.quads)
+            self.V_node = self.A_node
+            groups = [(self.quads, poly_edge_normals(xy, self.quads), poly_face_normals(xy, self.quads))]
+            if self.tris.size:
+                groups.insert(0, (self.tris, cell_edge_normals(xy, self.tris), face_normals(xy, self.tris)))
+            self.edges, self.S_edge, self.S_b = hybrid_edges_and_boundary(xy, groups)
+            self.K = (poisson_matrix(self.tris, self.S, self.V_tau, self.N)
+                      + poly_poisson_matrix(self.quads, self.S_q, self.V_q, self.N)).tocsr()
+        elif self.axisymmetric:
             if np.any(xy[:, 1] < 0):
                 raise ValueError("axisymmetric meshes need r = y >= 0")
             self.V_node = axi_nodal_volumes(xy, self.tris, self.V_tau)
@@ -428,16 +556,33 @@ class Oracle:
     def poisson(self, n):
         return self.solver.solve(poisson_rhs(self.charge_density(n), self.V_node))
 
+    def nodal_gradient(self, u):
+        """Centred nodal gradient over all cells (triangles and quadrangles): the cell
+        gradients weighted by each cell's V_tau / n_v share of the dual area."""
+        if not self.hybrid:
+            return nodal_gradient(u, self.tris, self.S, self.V_tau, self.A_node)
+        g = np.zeros((self.N, 2))
+        for cells, S, V in ((self.tris, self.S, self.V_tau), (self.quads, self.S_q, self.V_q)):
+            nv = cells.shape[1]
+            if not cells.size:
+                continue
+            gc = np.zeros((cells.shape[0], 2))
+            for k in range(nv):
+                gc += u[cells[:, k]][:, None] * S[:, k]
+            gc = -gc / (2.0 * V)[:, None]
+            for k in range(nv):
+                np.add.at(g, cells[:, k], gc * (V / nv)[:, None])
+        return g / self.A_node[:, None]
+
     # -- one explicit step -----------------------------------------------------------
     def fields(self, n):
         """phi, E = -grad phi, |E|, nodal velocities and density gradients."""
         phi = self.poisson(n)
-        E = -nodal_gradient(phi, self.tris, self.S, self.V_tau, self.A_node)
+        E = -self.nodal_gradient(phi)
         Emag = np.sqrt(E[:, 0] ** 2 + E[:, 1] ** 2)
         mu = [mobility(sp_, Emag) for sp_ in self.p.species]
         vel = [np.sign(sp_.charge) * mu[s][:, None] * E for s, sp_ in enumerate(self.p.species)]
-        grad = [nodal_gradient(n[s], self.tris, self.S, self.V_tau, self.A_node)
-                for s in range(len(self.p.species))]
+        grad = [self.nodal_gradient(n[s]) for s in range(len(self.p.species))]
         return phi, E, Emag, mu, vel, grad
 
     def sources(self, n, Emag, mu):
@@ -462,24 +607,30 @@ class Oracle:
         """Minimum over cells and species of the convective, diffusive and dielectric time
         steps, and the chemical limit over nodes (section "Time step computation")."""
         o = self.p.opts
-        t = self.tris
         dts = [np.inf]
-        for s, sp_ in enumerate(self.p.species):
-            Vc = (vel[s][t[:, 0]] + vel[s][t[:, 1]] + vel[s][t[:, 2]]) / 3.0
-            Vm = np.sqrt(Vc[:, 0] ** 2 + Vc[:, 1] ** 2)
-            ok = Vm > 0
+        groups = [(self.tris, self.dx_tau)]
+        if self.hybrid:
+            groups.append((self.quads, self.dx_q))
+        for t, dx in groups:
+            if not t.size:
+                continue
+            nv = t.shape[1]
+            for s, sp_ in enumerate(self.p.species):
+                Vc = sum(vel[s][t[:, k]] for k in range(nv)) / nv
+                Vm = np.sqrt(Vc[:, 0] ** 2 + Vc[:, 1] ** 2)
+                ok = Vm > 0
+                if np.any(ok):
+                    dts.append(np.min(o.cfl * dx[ok] / Vm[ok]))
+                if sp_.D > 0:
+                    dts.append(np.min(o.fourier * dx ** 2 / sp_.D))
+            sigma = np.zeros(t.shape[0])
+            for s, sp_ in enumerate(self.p.species):
+                nm = n[s] * mu[s]
+                cell = sum(nm[t[:, k]] for k in range(nv)) / nv
+                sigma += np.abs(sp_.charge * E_CHARGE * cell)
+            ok = sigma > 0
             if np.any(ok):
-                dts.append(np.min(o.cfl * self.dx_tau[ok] / Vm[ok]))
-            if sp_.D > 0:
-                dts.append(np.min(o.fourier * self.dx_tau ** 2 / sp_.D))
-        sigma = np.zeros(t.shape[0])
-        for s, sp_ in enumerate(self.p.species):
-            nm = n[s] * mu[s]
-            cell = (nm[t[:, 0]] + nm[t[:, 1]] + nm[t[:, 2]]) / 3.0
-            sigma += np.abs(sp_.charge * E_CHARGE * cell)
-        ok = sigma > 0
-        if np.any(ok):
-            dts.append(np.min(o.a_diel * EPS0 / sigma[ok]))
+                dts.append(np.min(o.a_diel * EPS0 / sigma[ok]))
         if self.p.source.model != 0:
             e = self.p.source.idx[0]
             Se = S_src[e]

@@ -87,6 +87,7 @@ class Problem:
     seed: int
     meta: dict
     axisymmetric: bool = False   # True: y is the radius r >= 0, x the axis
+    quads: Optional[np.ndarray] = None  # (Q, 4) int32 quadrangles of a hybrid mesh
 
     @property
     def n_nodes(self) -> int:
@@ -95,6 +96,10 @@ class Problem:
     @property
     def n_tris(self) -> int:
         return int(self.tris.shape[0])
+
+    @property
+    def n_cells(self) -> int:
+        return self.n_tris + (0 if self.quads is None else int(self.quads.shape[0]))
 
 
 def jittered_rectangle(nx: int, ny: int, Lx: float, Ly: float, jitter: float, seed: int,
@@ -286,3 +291,21 @@ def config_axisym_streamer(nx: int = 701, nr: int = 701, seed: int = 2201) -> Pr
     triangles, the size class of the pin-plane workload."""
     return axisym_problem(nx, nr, 1.25e-2, 1.25e-2, 18750.0, seed, n_peak=5e18, n_back=1e13, sigma=4e-4,
                           field_dependent=True, source=SRC_TOWNSEND, x0=1e-2, name="axisym_streamer")
+
+
+def hybrid_plates_problem(nx: int, ny: int, Lx: float, Ly: float, voltage: float, seed: int,
+                          quad_fraction: float = 1.0, **kw) -> Problem:
+    """The parallel-plate problem of plates_problem on a quadrangle or hybrid mesh: the same
+    jittered node grid, each grid cell kept as a quadrangle with probability quad_fraction
+    (seeded), otherwise split into two triangles along its lower-left/upper-right diagonal."""
+    p = plates_problem(nx, ny, Lx, Ly, voltage, seed, **kw)
+    qi, qj = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1))
+    a = (qi + nx * qj).reshape(-1)
+    b, c, d = a + 1, a + 1 + nx, a + nx
+    rng = np.random.Generator(np.random.PCG64(seed + 7777))
+    keep = rng.uniform(size=a.size) < quad_fraction
+    quads = np.stack([a, b, c, d], axis=1)[keep].astype(np.int32)
+    t1 = np.stack([a, b, c], axis=1)[~keep]
+    t2 = np.stack([a, c, d], axis=1)[~keep]
+    tris = np.concatenate([t1, t2]).astype(np.int32).reshape(-1, 3)
+    return dataclasses.replace(p, tris=tris, quads=quads, name=f"hybrid_{nx}x{ny}_q{quad_fraction:g}")
