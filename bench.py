@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "plates65", "axisym", "batch256", "served", "sweep"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "pin_plane_hybrid", "plates65", "axisym", "batch256", "served",
+                                                            "sweep"])
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
     ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
@@ -75,6 +76,11 @@ def _make_problem(name):
         p = W.config_pin_plane()
         desc = ("pin-plane streamer 1cm x 2cm, 500x1000 jittered nodes (997,002 tris), Morton order, "
                 "20 kV needle, mu_e ~ E^-0.2, Townsend alpha (air-like, 1 atm), e + positive ions, FP64")
+    elif name == "pin_plane_hybrid":
+        p = W.config_pin_plane_hybrid()
+        desc = (f"pin-plane streamer 1cm x 2cm on a hybrid mesh, 500x1000 jittered nodes, {p.quads.shape[0]:,} "
+                f"quadrangles + {p.n_tris:,} triangles (each grid cell a quadrangle with probability 0.5), "
+                "Morton order, 20 kV needle, mu_e ~ E^-0.2, Townsend alpha, e + positive ions, FP64")
     elif name == "axisym":
         p = W.config_axisym_streamer()
         desc = ("axisymmetric (x, r) streamer gap 1.25cm x 1.25cm, 701x701 jittered nodes (980,000 tris), "
@@ -252,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
         build.build()
     avip.load()
     problem, desc = make_problem(args.workload, args.scheme)
-    T = problem.n_tris
+    T = problem.n_cells
     stream = torch.cuda.Stream()
     kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
     allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
@@ -341,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": desc, "n_nodes": info["n_nodes"], "n_tris": T, "nnz": info["nnz"],
+        "config": {"workload": desc, "n_nodes": info["n_nodes"], "n_cells": T, "nnz": info["nnz"],
                    "rtol": args.rtol, "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write inside the timed region)",
                    "seed": problem.seed},
@@ -528,7 +534,7 @@ def cpu_baseline(problem, steps):
         n, _ = o.step(n)
     wall = time.perf_counter() - t1
     cpu = time.process_time() - c1
-    return {"value": problem.n_tris * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)),
+    return {"value": problem.n_cells * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)),
             "kind": "oracle",
             "sample": f"{steps} explicit steps of the same workload after a {setup:.1f} s one-off "
                       f"setup (metrics + sparse LU factorisation, excluded); numpy/scipy, "
@@ -552,12 +558,12 @@ def run_reference(args, rank, world):
         n, _ = o.step(n)
     wall = time.perf_counter() - t1
     cpu = time.process_time() - c1
-    value = problem.n_tris * args.steps / wall
+    value = problem.n_cells * args.steps / wall
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": desc, "n_tris": problem.n_tris, "precision": "fp64",
+            "config": {"workload": desc, "n_cells": problem.n_cells, "precision": "fp64",
                        "parallelism": "cpu oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
                              "sample": f"each step one explicit oracle step of the workload "

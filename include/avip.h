@@ -146,6 +146,23 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
                 const int32_t* node_bc, const double* phi_D, const avip_opts* opts,
                 avip_mesh_t* out);
 
+/* Build a mesh handle on a hybrid mesh of triangles and quadrangles (planar geometry only).
+ *   tris[3*n_tris]   triangles as for mesh_create (n_tris may be 0, tris then may be NULL);
+ *   quads[4*n_quads] quadrangles, 4 node indices in boundary order, either orientation (made
+ *                    counter-clockwise), non-self-intersecting (n_quads may be 0).
+ * The other arguments are those of mesh_create.  The metrics are the n_v-vertex forms of the
+ * section "Nomenclature and notations": cell volume by the shoelace formula, nodal normal
+ * S_k = -(n_d/n_v^f) times the sum of the two faces adjacent to k (Eq. node_normal), dual volume
+ * V_tau/n_v, dual faces from the side midpoints to the cell centre (vertex mean), boundary
+ * normals from the sides that belong to one cell; Poisson matrix of Eq. coeff_matriceA over all
+ * n_v^2 vertex pairs.  The time-step limits of the section "Time step computation" take the
+ * cell average of n_v vertices and the shortest side.  Errors: those of mesh_create, plus
+ * AVIP_EINVAL for a quadrangle index out of range, a zero-area quadrangle, n_tris + n_quads < 1,
+ * or quadrangles with opts->geometry AXISYMMETRIC.  info[1] of mesh_info counts all cells. */
+int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                       const int32_t* quads, int32_t n_quads, const int32_t* node_bc, const double* phi_D,
+                       const avip_opts* opts, avip_mesh_t* out);
+
 /* Release every device and host resource of the handle.  NULL is accepted. */
 int mesh_destroy(avip_mesh_t h);
 
@@ -193,7 +210,7 @@ int state_size(avip_mesh_t h, int64_t* n_doubles);
 int state_get(avip_mesh_t h, double* host_state);
 int state_set(avip_mesh_t h, const double* host_state);
 
-/* info[8] = {n_nodes, n_tris, n_edges, nnz of the Poisson matrix, PCG kernel kind
+/* info[8] = {n_nodes, n_cells (triangles + quadrangles), n_edges, nnz of the Poisson matrix, PCG kernel kind
  * (1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident, 6 cluster mixed,
  * 7 BiCGStab, 8 AMG-preconditioned CG, 9 AMG-preconditioned BiCGStab, 10 mixed AMG, 11 AMG on one
  * cluster), solver blocks,

@@ -59,6 +59,7 @@ _H = C.c_void_p
 _SIGS = {
     "avip_opts_default": (C.c_int, [_P(AvipOpts)]),
     "mesh_create": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, _D, _P(AvipOpts), _P(_H)]),
+    "mesh_create_hybrid": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, C.c_int32, _I, _D, _P(AvipOpts), _P(_H)]),
     "mesh_destroy": (C.c_int, [_H]),
     "mesh_set_stream": (C.c_int, [_H, C.c_void_p]),
     "mesh_info": (C.c_int, [_H, _P(C.c_int64)]),
@@ -147,6 +148,19 @@ def mesh_create(xy, tris, node_bc, phi_D, opts: AvipOpts):
     return rc, h
 
 
+def mesh_create_hybrid(xy, tris, quads, node_bc, phi_D, opts: AvipOpts):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    tris = np.ascontiguousarray(tris if tris is not None else np.zeros(0), dtype=np.int32).reshape(-1)
+    quads = np.ascontiguousarray(quads if quads is not None else np.zeros(0), dtype=np.int32).reshape(-1)
+    node_bc = np.ascontiguousarray(node_bc, dtype=np.int32)
+    phi_D = np.ascontiguousarray(phi_D, dtype=np.float64)
+    h = _H()
+    rc = load().mesh_create_hybrid(_dptr(xy), xy.size // 2, _iptr(tris) if tris.size else None, tris.size // 3,
+                                   _iptr(quads) if quads.size else None, quads.size // 4, _iptr(node_bc),
+                                   _dptr(phi_D), C.byref(opts), C.byref(h))
+    return rc, h
+
+
 def mesh_destroy(h):
     return load().mesh_destroy(h)
 
@@ -210,7 +224,7 @@ PCG_KINDS = {1: "streaming", 2: "register-resident", 4: "mixed", 5: "cluster-res
 def mesh_info(h):
     info = np.zeros(8, dtype=np.int64)
     _check(load().mesh_info(h, info.ctypes.data_as(_P(C.c_int64))), "mesh_info")
-    return dict(n_nodes=int(info[0]), n_tris=int(info[1]), n_edges=int(info[2]), nnz=int(info[3]),
+    return dict(n_nodes=int(info[0]), n_tris=int(info[1]), n_cells=int(info[1]), n_edges=int(info[2]), nnz=int(info[3]),
                 pcg_kind=int(info[4]), pcg_blocks=int(info[5]), pcg_threads=int(info[6]),
                 device_bytes=int(info[7]))
 
@@ -319,8 +333,13 @@ class Mesh:
             o.stream = C.c_void_p(stream)
         self.problem = problem
         self.N = problem.n_nodes
-        rc, h = mesh_create(problem.xy, problem.tris, problem.node_bc, problem.phi_D, o)
-        _check(rc, "mesh_create")
+        quads = getattr(problem, "quads", None)
+        if quads is not None and len(quads):
+            rc, h = mesh_create_hybrid(problem.xy, problem.tris, quads, problem.node_bc, problem.phi_D, o)
+            _check(rc, "mesh_create_hybrid")
+        else:
+            rc, h = mesh_create(problem.xy, problem.tris, problem.node_bc, problem.phi_D, o)
+            _check(rc, "mesh_create")
         self.h = h
         for s, sp in enumerate(problem.species):
             _check(species_set(h, s, sp.charge, sp.mob_model, sp.mob_params, sp.D, sp.bnd_mode, sp.n0),

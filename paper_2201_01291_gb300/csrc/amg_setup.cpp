@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdio>
 #include <numeric>
+#include <utility>
 
 #include "avip_internal.h"
 
@@ -298,18 +299,23 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
     return AVIP_EINVAL;
   };
   H.lv.clear();
-  // finest level: the scaled matrix, read back from its SELL form (explicit zeros dropped)
+  // finest level: the scaled matrix, read back from its SELL form (explicit zeros dropped;
+  // diagonal first, then the other columns ascending)
   Csr A;
   A.n = A.m = m.N;
   A.rp.assign(m.N + 1, 0);
+  std::vector<std::pair<int32_t, double>> row;
   for (int32_t i = 0; i < m.N; ++i) {
     const int32_t s = i / kSlice, l = i % kSlice;
+    row.clear();
     for (int32_t k = 0; k < m.rlen[i]; ++k) {
       const int64_t e = (int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l;
-      if (k == 0 || m.aval[e] != 0.0) {
-        A.ci.push_back(m.col[e]);
-        A.v.push_back(m.aval[e]);
-      }
+      if (k == 0 || m.aval[e] != 0.0) row.emplace_back(m.col[e], m.aval[e]);
+    }
+    std::sort(row.begin() + 1, row.end());
+    for (const auto& cv : row) {
+      A.ci.push_back(cv.first);
+      A.v.push_back(cv.second);
     }
     A.rp[i + 1] = (int32_t)A.ci.size();
   }

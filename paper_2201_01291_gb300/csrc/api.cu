@@ -36,7 +36,7 @@ struct avip_mesh {
   std::vector<void*> allocs;
   size_t bytes = 0;  // device bytes held
   // device arrays
-  int32_t *sl_ptr = nullptr, *sl_w = nullptr, *rlen = nullptr, *col = nullptr, *tri = nullptr;
+  int32_t *sl_ptr = nullptr, *sl_w = nullptr, *rlen = nullptr, *col = nullptr, *cell = nullptr, *flen = nullptr;
   double *aval = nullptr, *gx = nullptr, *gy = nullptr, *sx = nullptr, *sy = nullptr;
   double *x = nullptr, *y = nullptr, *vol = nullptr, *dsq = nullptr, *dsqinv = nullptr, *lift = nullptr,
          *rhs_scale = nullptr;
@@ -191,9 +191,11 @@ DDArgs dd_args(const avip_mesh* h) {
   a.src = h->src;
   a.Ex = h->Ex;
   a.Ey = h->Ey;
-  a.tri = h->tri;
+  a.cell = h->cell;
   a.dxmin = h->dxmin;
+  a.flen = h->flen;
   a.T = h->hm.T;
+  a.nvmax = h->hm.nvmax;
   a.Npad = h->Npad;
   a.partials = h->qpart;
   a.sc = h->sc;
@@ -360,6 +362,12 @@ const char* avip_last_error(void) { return g_err; }
 
 int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
                 const int32_t* node_bc, const double* phi_D, const avip_opts* opts, avip_mesh_t* out) {
+  return mesh_create_hybrid(xy, n_nodes, tris, n_tris, nullptr, 0, node_bc, phi_D, opts, out);
+}
+
+int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
+                       const int32_t* quads, int32_t n_quads, const int32_t* node_bc, const double* phi_D,
+                       const avip_opts* opts, avip_mesh_t* out) {
   if (!out) return AVIP_EINVAL;
   *out = nullptr;
   avip_mesh* h = new (std::nothrow) avip_mesh();
@@ -390,8 +398,8 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
     return AVIP_EINVAL;
   }
   // host-side validation and metrics first: bad meshes are rejected without touching the GPU
-  int st = prepare_mesh(xy, n_nodes, tris, n_tris, node_bc, phi_D, h->opts.reorder, h->opts.geometry, h->hm, g_err,
-                        sizeof(g_err));
+  int st = prepare_mesh(xy, n_nodes, tris, n_tris, quads, n_quads, node_bc, phi_D, h->opts.reorder,
+                        h->opts.geometry, h->hm, g_err, sizeof(g_err));
   if (st != AVIP_OK) {
     delete h;
     return st;
@@ -413,7 +421,7 @@ int mesh_create(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t 
   bool ok = upload(h, h->sl_ptr, m.sl_ptr) && upload(h, h->sl_w, m.sl_w) && upload(h, h->rlen, m.rlen) &&
             upload(h, h->col, m.col) && upload(h, h->aval, m.aval) && upload(h, h->gx, m.gx) &&
             upload(h, h->gy, m.gy) && upload(h, h->sx, m.sx) && upload(h, h->sy, m.sy) &&
-            upload(h, h->tri, m.tri) && upload(h, h->dxmin, m.dxmin) && upload(h, h->x, m.x, Np) &&
+            upload(h, h->cell, m.cell) && upload(h, h->flen, m.flen) && upload(h, h->dxmin, m.dxmin) && upload(h, h->x, m.x, Np) &&
             upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dsq, m.dsq, Np) && upload(h, h->dsqinv, m.dsqinv, Np) &&
             upload(h, h->lift, m.lift, Np) && upload(h, h->rhs_scale, m.rhs_scale, Np);
   // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere

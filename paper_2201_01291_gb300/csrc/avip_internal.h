@@ -4,8 +4,10 @@
 //   * rows are grouped in slices of 32 consecutive nodes; slice s owns the element range
 //     [sl_ptr[s], sl_ptr[s] + 32 * sl_w[s]) with element (lane, k) at sl_ptr[s] + 32 k + lane,
 //     so a warp reading slot k of its 32 rows issues one fully coalesced load;
-//   * slot 0 of every row is the diagonal (column = row); slots 1..rlen-1 are the neighbours
-//     in ascending column order; slots >= rlen are padding and never read;
+//   * slot 0 of every row is the diagonal (column = row); slots 1..flen-1 are the neighbours
+//     across a mesh edge (a cell side), ascending; slots flen..rlen-1 the other vertices of the
+//     row's quadrangles (coupled by the Poisson matrix and the gradient, no flux), ascending;
+//     slots >= rlen are padding and never read (flen == rlen on triangle meshes);
 //   * per element: col (int32), aval (Poisson matrix after Dirichlet elimination), gx/gy
 //     (nodal-gradient weights G_ik), sx/sy (edge normal S_ij oriented row -> col; in slot 0
 //     the boundary nodal normal S_i^b).
@@ -22,7 +24,9 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr int kSlice = 32;
 
 struct HostMesh {
-  int32_t N = 0, T = 0, E = 0;        // nodes, triangles, undirected edges
+  int32_t N = 0, T = 0, E = 0;        // nodes, cells (triangles + quadrangles), undirected edges
+  int32_t Q = 0;                      // quadrangles among the T cells
+  int32_t nvmax = 3;                  // 3 (triangles only) or 4
   int32_t nslices = 0;
   int64_t nnz = 0;                    // structural nonzeros (diag + 2 E)
   int64_t nelem = 0;                  // SELL elements incl. padding
@@ -31,9 +35,11 @@ struct HostMesh {
   int32_t geometry = 0;               // AVIP_GEOM_*
   std::vector<double> x, y, vol;      // new order; vol = dual volume (per radian when axisymmetric)
   std::vector<int32_t> bc;            // new order
-  std::vector<int32_t> tri;           // 3*T, new indices, counter-clockwise (SoA: a[T], b[T], c[T])
-  std::vector<double> dxmin;          // T, shortest edge
+  std::vector<int32_t> cell;          // nvmax*T, new indices, counter-clockwise (SoA: v0[T], v1[T], ...;
+                                      // v3 = -1 for the triangles of a hybrid mesh)
+  std::vector<double> dxmin;          // T, shortest side
   std::vector<int32_t> rlen;          // N (padded to nslices*32 with 0)
+  std::vector<int32_t> flen;          // N (padded likewise): 1 + number of edge neighbours
   std::vector<int32_t> sl_ptr, sl_w;  // nslices
   std::vector<int32_t> col;           // nelem
   std::vector<double> aval, gx, gy, sx, sy;  // nelem (aval: D^-1/2 K D^-1/2)
@@ -44,9 +50,10 @@ struct HostMesh {
 
 // Builds every metric and sparse structure; returns AVIP_OK or AVIP_EINVAL.
 // geometry: AVIP_GEOM_PLANAR or AVIP_GEOM_AXISYMMETRIC (second coordinate = radius >= 0).
-int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris,
-                 const int32_t* node_bc, const double* phi_D, int reorder, int geometry, HostMesh& out,
-                 char* err, size_t errlen);
+// quads (4 node indices per cell, may be NULL with n_quads = 0): planar geometry only.
+int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris, const int32_t* quads,
+                 int32_t n_quads, const int32_t* node_bc, const double* phi_D, int reorder, int geometry,
+                 HostMesh& out, char* err, size_t errlen);
 
 // ----------------------------------------------------------------- AMG hierarchy (host)
 constexpr int kAmgMaxLevels = 12;
@@ -281,9 +288,11 @@ struct DDArgs {
   double* src;            // per species per node: source rate
   double* Ex;
   double* Ey;
-  const int32_t* tri;     // SoA a[T], b[T], c[T]
+  const int32_t* cell;    // SoA v0[T], v1[T], v2[T] (, v3[T] when nvmax == 4; -1 for triangles)
   const double* dxmin;
+  const int32_t* flen;    // per row: slots 1..flen-1 carry the mesh edges
   int32_t T;
+  int32_t nvmax;
   int32_t Npad;
   double* partials;       // per-block charge partials
   DevScalars* sc;

@@ -148,7 +148,10 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
   const int c = bid * blockDim.x + threadIdx.x;
   double cand = INFINITY;
   if (c < a.T) {
-    const int n0 = a.tri[c], n1 = a.tri[a.T + c], n2 = a.tri[2 * a.T + c];
+    const int n0 = a.cell[c], n1 = a.cell[a.T + c], n2 = a.cell[2 * a.T + c];
+    const int n3 = a.nvmax == 4 ? a.cell[3 * a.T + c] : -1;  // -1: triangle
+    const bool quad = n3 >= 0;
+    const double nvd = quad ? 4.0 : 3.0;
     const double dx = a.dxmin[c];
     const int ns = a.ph.ns;
     double sigma = 0.0;
@@ -159,18 +162,30 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
         double vx, vy;
         if (a.ph.dd_fp32) {  // FP32 velocities, FP64 candidate and reduction
           const float* d = a.ndat32 + (size_t)s * a.Npad * 4;
-          vx = ((double)d[4 * n0 + 2] + (double)d[4 * n1 + 2] + (double)d[4 * n2 + 2]) / 3.0;
-          vy = ((double)d[4 * n0 + 3] + (double)d[4 * n1 + 3] + (double)d[4 * n2 + 3]) / 3.0;
+          vx = (double)d[4 * n0 + 2] + (double)d[4 * n1 + 2] + (double)d[4 * n2 + 2];
+          vy = (double)d[4 * n0 + 3] + (double)d[4 * n1 + 3] + (double)d[4 * n2 + 3];
+          if (quad) {
+            vx += (double)d[4 * n3 + 2];
+            vy += (double)d[4 * n3 + 3];
+          }
         } else {
           const double* d = a.ndat + (size_t)s * a.Npad * 4;
-          vx = (d[4 * n0 + 2] + d[4 * n1 + 2] + d[4 * n2 + 2]) / 3.0;
-          vy = (d[4 * n0 + 3] + d[4 * n1 + 3] + d[4 * n2 + 3]) / 3.0;
+          vx = d[4 * n0 + 2] + d[4 * n1 + 2] + d[4 * n2 + 2];
+          vy = d[4 * n0 + 3] + d[4 * n1 + 3] + d[4 * n2 + 3];
+          if (quad) {
+            vx += d[4 * n3 + 2];
+            vy += d[4 * n3 + 3];
+          }
         }
+        vx /= nvd;
+        vy /= nvd;
         const double vm = sqrt(vx * vx + vy * vy);
         if (vm > 0.0) cand = fmin(cand, a.ph.cfl * dx / vm);
         if (sp.D > 0.0) cand = fmin(cand, a.ph.fourier * (dx * dx) / sp.D);
         const double* nm = a.nm + (size_t)s * a.Npad;
-        const double cell = (nm[n0] + nm[n1] + nm[n2]) / 3.0;
+        double cell = nm[n0] + nm[n1] + nm[n2];
+        if (quad) cell += nm[n3];
+        cell /= nvd;
         sigma += fabs(sp.q * kECharge * cell);
       }
     }
@@ -266,7 +281,7 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
     double* nn = a.nbuf + (size_t)(par ^ 1) * AVIP_MAX_SPECIES * a.Npad;
     const int slice = i / kSlice, lane = i % kSlice;
     const int base = __ldg(a.A.sl_ptr + slice) + lane;
-    const int rl = __ldg(a.A.rlen + i);
+    const int rl = __ldg(a.flen + i);  // edge slots only
     const double xi = a.x[i], yi = a.y[i];
     double R[AVIP_MAX_SPECIES];
     EdgeEnd me[AVIP_MAX_SPECIES];
@@ -558,7 +573,7 @@ __device__ __forceinline__ void flux_update32_body(const DDArgs& a, int bid) {
     const float4* nd = reinterpret_cast<const float4*>(a.ndat32);
     const int slice = i / kSlice, lane = i % kSlice;
     const int base = __ldg(a.A.sl_ptr + slice) + lane;
-    const int rl = __ldg(a.A.rlen + i);
+    const int rl = __ldg(a.flen + i);  // edge slots only
     const double xi = a.x[i], yi = a.y[i];
     float R[AVIP_MAX_SPECIES];
     EdgeEnd32 me[AVIP_MAX_SPECIES];

@@ -232,6 +232,15 @@ def config_pin_plane(nx: int = 500, ny: int = 1000) -> Problem:
                           source=SRC_TOWNSEND, name=f"pin_plane_{nx}x{ny}", needle_len=2e-3)
 
 
+def config_pin_plane_hybrid(nx: int = 500, ny: int = 1000, quad_fraction: float = 0.5) -> Problem:
+    """The pin-plane streamer of config_pin_plane on a hybrid mesh: the same jittered nodes,
+    each grid cell kept as a quadrangle with probability quad_fraction, otherwise split into
+    two triangles (about 249,500 quadrangles and 499,000 triangles at the default size)."""
+    p = hybrid_plates_problem(nx, ny, 1e-2, 2e-2, 2e4, seed=2, quad_fraction=quad_fraction, field_dependent=True,
+                              source=SRC_TOWNSEND, needle_len=2e-3)
+    return dataclasses.replace(p, name=f"pin_plane_hybrid_{nx}x{ny}_q{quad_fraction:g}")
+
+
 def random_instances(count: int, seed: int, t_min: float = 2e3, t_max: float = 2e5):
     """Many uneven discharge instances: triangle counts log-uniform in [t_min, t_max], aspect
     ratio uniform in [1,4], voltage uniform in [5,25] kV, 2 or 3 charged species (the third a

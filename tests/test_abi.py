@@ -96,3 +96,27 @@ def test_unknown_flux_scheme_rejected_on_host(lib):
     assert o.scheme == avip.FLUX_LLW
     o.scheme = 3
     assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+
+
+def test_hybrid_mesh_validation_on_host(lib):
+    """mesh_create_hybrid rejects quadrangle indices out of range, zero-area quadrangles, an
+    empty cell list and quadrangles in the axisymmetric geometry, in host code."""
+    import numpy as np
+    from paper_2201_01291_gb300 import avip, workloads as W
+    p = W.hybrid_plates_problem(9, 7, 1e-2, 0.8e-2, 5e3, seed=3, quad_fraction=0.5)
+    o = avip.avip_opts_default()
+    bad = p.quads.copy()
+    bad[2, 3] = p.n_nodes
+    assert avip.mesh_create_hybrid(p.xy, p.tris, bad, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "quadrangle index" in avip.last_error()
+    deg = p.quads.copy()
+    deg[0] = [deg[0, 0], deg[0, 1], deg[0, 1], deg[0, 0]]
+    assert avip.mesh_create_hybrid(p.xy, p.tris, deg, p.node_bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "quadrangle" in avip.last_error()
+    empty = np.zeros((0, 3), np.int32)
+    assert avip.mesh_create_hybrid(p.xy, empty, np.zeros((0, 4), np.int32), p.node_bc, p.phi_D,
+                                   o)[0] == avip.AVIP_EINVAL
+    oa = avip.avip_opts_default()
+    oa.geometry = avip.GEOM_AXISYMMETRIC
+    assert avip.mesh_create_hybrid(p.xy, p.tris, p.quads, p.node_bc, p.phi_D, oa)[0] == avip.AVIP_EINVAL
+    assert "planar" in avip.last_error()
