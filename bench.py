@@ -38,8 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "pin_plane_hybrid", "plates65", "axisym", "batch256", "served",
-                                                            "sweep"])
+    ap.add_argument("--workload", default="pin_plane", choices=["pin_plane", "pin_plane_hybrid", "hyperbole_ml", "plates65", "axisym",
+                                                            "batch256", "served", "sweep"])
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
     ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
@@ -81,6 +81,11 @@ def _make_problem(name):
         desc = (f"pin-plane streamer 1cm x 2cm on a hybrid mesh, 500x1000 jittered nodes, {p.quads.shape[0]:,} "
                 f"quadrangles + {p.n_tris:,} triangles (each grid cell a quadrangle with probability 0.5), "
                 "Morton order, 20 kV needle, mu_e ~ E^-0.2, Townsend alpha, e + positive ions, FP64")
+    elif name == "hyperbole_ml":
+        p = W.config_hyperbole_ml()
+        desc = ("three-species air chemistry (ionisation, attachment, e-p and n-p recombination, immobile "
+                "ions) at 1000 K, 5mm x 5mm gap, 800x800 jittered nodes (1,278,402 tris), 1 mm needle anode "
+                "ramped 0 -> 5 kV in 2 ns, 1e15 m^-3 background, Morton order, FP64")
     elif name == "axisym":
         p = W.config_axisym_streamer()
         desc = ("axisymmetric (x, r) streamer gap 1.25cm x 1.25cm, 701x701 jittered nodes (980,000 tris), "

@@ -51,6 +51,12 @@ extern "C" {
 #define AVIP_SRC_NONE 0
 #define AVIP_SRC_TOWNSEND 1          /* alpha(|E|) = A exp(-B/|E|); S = alpha mu_e |E| n_e  */
 #define AVIP_SRC_TOWNSEND_ATTACH 2   /* plus attachment nu_a n_e moved from e to the anion  */
+#define AVIP_SRC_MORROW_LOWKE 3      /* three-species air chemistry of the section "Hyperbole
+                                        electrodes": with w = mu_e |E|, alpha = A exp(-B/|E|),
+                                        eta = A_eta exp(-B_eta/|E|) and recombination rate beta_r,
+                                        S_e = (alpha - eta) w n_e - beta_r n_e n_p,
+                                        S_p = alpha w n_e - beta_r n_e n_p - beta_r n_n n_p,
+                                        S_n = eta w n_e - beta_r n_n n_p                        */
 #define AVIP_BND_NEUMANN 0 /* boundary node flux F = F_C ("Neumann")                        */
 #define AVIP_BND_OUTFLOW 1 /* boundary node flux F = F_C + F_D ("supersonic")              */
 #define AVIP_LIM_SWEBY 0   /* Psi(r) = max(0, min(beta r, 1), min(r, beta))                 */
@@ -110,6 +116,10 @@ typedef struct avip_opts {
   void* alloc_ctx;
   int32_t geometry;                    /* AVIP_GEOM_* (default PLANAR)                          */
   int32_t scheme;                      /* AVIP_FLUX_* edge flux (default LLW)                   */
+  double v_rise;                       /* > 0: every Dirichlet value rises linearly from 0 at
+                                          t = 0 to its phi_D at t = v_rise and stays there (the
+                                          anode ramp of the section "Hyperbole electrodes"; a
+                                          grounded electrode, phi_D = 0, stays at 0); 0 = constant */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */
@@ -176,8 +186,12 @@ int mesh_set_stream(avip_mesh_t h, void* stream);
 int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model,
                 const double* mob_params, double D, int32_t bnd_mode, const double* n0);
 
-/* Source model (section "Bagheri benchmark"): params = {A, B, nu_att}; idx = {electron,
- * positive ion, negative ion (-1 if none)} species indices. */
+/* Source model (section "Bagheri benchmark"): params = {A, B, nu_att} for TOWNSEND and
+ * TOWNSEND_ATTACH; {A, B, A_eta, B_eta, beta_r} for MORROW_LOWKE (section "Hyperbole
+ * electrodes"; all >= 0, SI units: 1/m, V/m, 1/m, V/m, m^3/s).  idx = {electron, positive ion,
+ * negative ion (-1 if none; required, and the three distinct, for TOWNSEND_ATTACH and
+ * MORROW_LOWKE)} species indices.  AVIP_EINVAL for an unknown model, a negative or non-finite
+ * parameter or an index out of range. */
 int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t* idx);
 
 /* Solve the Poisson problem for the current densities (warm start from the last phi).

@@ -399,11 +399,14 @@ class DirichletSolver:
         self.lu = spla.splu(self.K_FF) if self.free.size else None
         self.n = K.shape[0]
 
-    def solve(self, b):
+    def solve(self, b, gain=1.0):
+        """gain scales every Dirichlet value (the voltage ramp of the section "Hyperbole
+        electrodes"; 1 for constant electrode potentials)."""
         phi = np.zeros(self.n)
-        phi[self.dir] = self.phi_D[self.dir]
+        phi_D = self.phi_D[self.dir] * gain
+        phi[self.dir] = phi_D
         if self.free.size:
-            rhs = b[self.free] - self.K_FD @ self.phi_D[self.dir]
+            rhs = b[self.free] - self.K_FD @ phi_D
             phi[self.free] = self.lu.solve(rhs)
         return phi
 
@@ -553,8 +556,16 @@ class Oracle:
             rho += E_CHARGE * sp_.charge * n[s]
         return rho
 
-    def poisson(self, n):
-        return self.solver.solve(poisson_rhs(self.charge_density(n), self.V_node))
+    def dirichlet_gain(self, t):
+        """Factor of the electrode potentials at time t: a linear rise from 0 at t = 0 to the
+        full value at t = v_rise (Fig. pin-pin_anode_time), then constant; 1 without a ramp."""
+        v_rise = getattr(self.p.opts, "v_rise", 0.0)
+        if not v_rise > 0:
+            return 1.0
+        return 1.0 if t >= v_rise else t / v_rise
+
+    def poisson(self, n, t=0.0):
+        return self.solver.solve(poisson_rhs(self.charge_density(n), self.V_node), self.dirichlet_gain(t))
 
     def nodal_gradient(self, u):
         """Centred nodal gradient over all cells (triangles and quadrangles): the cell
@@ -575,9 +586,9 @@ class Oracle:
         return g / self.A_node[:, None]
 
     # -- one explicit step -----------------------------------------------------------
-    def fields(self, n):
-        """phi, E = -grad phi, |E|, nodal velocities and density gradients."""
-        phi = self.poisson(n)
+    def fields(self, n, t=0.0):
+        """phi, E = -grad phi, |E|, nodal velocities and density gradients at time t."""
+        phi = self.poisson(n, t)
         E = -self.nodal_gradient(phi)
         Emag = np.sqrt(E[:, 0] ** 2 + E[:, 1] ** 2)
         mu = [mobility(sp_, Emag) for sp_ in self.p.species]
@@ -592,7 +603,8 @@ class Oracle:
         if src.model == 0:
             return out
         e, pos, neg = src.idx
-        A, B, nu_att = src.params
+        A, B = src.params[0], src.params[1]
+        nu_att = src.params[2] if src.model == 2 else 0.0
         alpha = townsend_alpha(A, B, Emag)
         ion = alpha * mu[e] * Emag * n[e]
         out[e] = out[e] + ion
@@ -601,6 +613,16 @@ class Oracle:
             att = nu_att * n[e]
             out[e] = out[e] - att
             out[neg] = out[neg] + att
+        elif src.model == 3:
+            # three-species air chemistry (section "Hyperbole electrodes"): attachment
+            # eta |W_e| n_e to the negative ion, electron-ion and ion-ion recombination
+            A_eta, B_eta, beta_r = src.params[2], src.params[3], src.params[4]
+            att = townsend_alpha(A_eta, B_eta, Emag) * mu[e] * Emag * n[e]
+            rec_ep = beta_r * n[e] * n[pos]
+            rec_np = beta_r * n[neg] * n[pos]
+            out[e] = out[e] - att - rec_ep
+            out[pos] = out[pos] - rec_ep - rec_np
+            out[neg] = out[neg] + att - rec_np
         return out
 
     def time_step(self, n, mu, vel, S_src):
@@ -682,10 +704,10 @@ class Oracle:
         fb = np.einsum("ij,ij->i", Fb, self.S_b)
         return R - fb, fb
 
-    def step(self, n, dt_fixed=None):
-        """One explicit step from densities n (list of (N,) arrays).  Returns the new
-        densities and a dict of diagnostics (phi, E, dt, charge, boundary ledger)."""
-        phi, E, Emag, mu, vel, grad = self.fields(n)
+    def step(self, n, dt_fixed=None, t=0.0):
+        """One explicit step from densities n (list of (N,) arrays) at time t.  Returns the
+        new densities and a dict of diagnostics (phi, E, dt, charge, boundary ledger)."""
+        phi, E, Emag, mu, vel, grad = self.fields(n, t)
         S_src = self.sources(n, Emag, mu)
         if dt_fixed is not None and dt_fixed > 0:
             dt = float(dt_fixed)
@@ -717,8 +739,10 @@ class Oracle:
         n = self.initial_state() if n is None else [x.copy() for x in n]
         dts = []
         phi = None
+        t = 0.0
         for _ in range(nsteps):
-            n, info = self.step(n)
+            n, info = self.step(n, t=t)
             dts.append(info["dt"])
+            t = t + info["dt"]
             phi = info["phi"]
         return n, phi, dts

@@ -33,7 +33,8 @@ class AvipOpts(C.Structure):
                 ("max_iter", C.c_int32), ("reorder", C.c_int32), ("dt_fixed", C.c_double),
                 ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32),
+                ("v_rise", C.c_double)]
 
 
 class AvipStats(C.Structure):
@@ -173,7 +174,8 @@ def species_set(h, s, charge, mob_model, mob_params, D, bnd_mode, n0):
 
 
 def source_set(h, model, params, idx):
-    p = np.ascontiguousarray(params, dtype=np.float64)
+    p = np.zeros(max(5, len(params)))       # 3 parameters, or 5 for SRC_MORROW_LOWKE
+    p[:len(params)] = params
     i = np.ascontiguousarray(idx, dtype=np.int32)
     return load().source_set(h, model, _dptr(p), _iptr(i))
 
@@ -325,6 +327,7 @@ class Mesh:
         o.pcg_kind = pcg_kind
         o.geometry = GEOM_AXISYMMETRIC if getattr(problem, "axisymmetric", False) else GEOM_PLANAR
         o.scheme = getattr(po, "scheme", FLUX_LLW)
+        o.v_rise = getattr(po, "v_rise", 0.0)
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()

@@ -182,6 +182,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
   const double inv_theta0 = H->L[0].inv_theta;
 
   // ---- x = D^1/2 phi (warm start) and b'
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
@@ -191,12 +192,13 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else a.x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
   if (!ops.sum(bb)) return false;
   {
@@ -317,6 +319,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
   float* __restrict__ q32 = a.q32;
   float* __restrict__ z32 = a.z32;
 
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
@@ -326,12 +329,13 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else a.x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
   if (!ops.sum(bb)) return false;
   {

@@ -160,6 +160,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.sync = h->sync;
   a.sc = h->sc;
   a.rtol = h->opts.rtol;
+  a.v_rise = h->opts.v_rise;
   a.max_iter = h->opts.max_iter;
   a.use_density_rhs = 1;
   a.aval32 = h->aval32;
@@ -377,6 +378,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   else
     avip_opts_default(&h->opts);
   if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
+      !(h->opts.v_rise >= 0) || !std::isfinite(h->opts.v_rise) ||
       (h->opts.scheme != AVIP_FLUX_LLW && h->opts.scheme != AVIP_FLUX_SG) ||
       (h->opts.precision != AVIP_PREC_FP64 && h->opts.precision != AVIP_PREC_MIXED) ||
       (h->opts.precision == AVIP_PREC_MIXED && !(h->opts.inner_rtol > 0 && h->opts.inner_rtol < 1))) {
@@ -427,7 +429,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere
   std::vector<double> phi0(Np, 0.0);
   for (int32_t i = 0; i < m.N; ++i)
-    if (m.bc[i] == 1) phi0[i] = m.lift[i];
+    if (m.bc[i] == 1) phi0[i] = h->opts.v_rise > 0 ? 0.0 : m.lift[i];  // a ramp starts at 0 V
   ok = ok && upload(h, h->phi, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
        zalloc(h, h->p, Np) && zalloc(h, h->q, Np) && zalloc(h, h->nbuf, 2 * AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->ndat, 4 * AVIP_MAX_SPECIES * Np) && zalloc(h, h->nm, AVIP_MAX_SPECIES * Np) &&
@@ -649,15 +651,20 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
     invalidate_graph(h);
     return AVIP_OK;
   }
-  if (!params || !idx || (model != AVIP_SRC_TOWNSEND && model != AVIP_SRC_TOWNSEND_ATTACH)) return AVIP_EINVAL;
+  if (!params || !idx ||
+      (model != AVIP_SRC_TOWNSEND && model != AVIP_SRC_TOWNSEND_ATTACH && model != AVIP_SRC_MORROW_LOWKE))
+    return AVIP_EINVAL;
   if (idx[0] < 0 || idx[0] >= AVIP_MAX_SPECIES || idx[1] < 0 || idx[1] >= AVIP_MAX_SPECIES) return AVIP_EINVAL;
-  if (model == AVIP_SRC_TOWNSEND_ATTACH && (idx[2] < 0 || idx[2] >= AVIP_MAX_SPECIES)) return AVIP_EINVAL;
-  if (!(params[0] >= 0) || !(params[1] >= 0) || !(params[2] >= 0)) return AVIP_EINVAL;
+  const bool three = model != AVIP_SRC_TOWNSEND;
+  if (three && (idx[2] < 0 || idx[2] >= AVIP_MAX_SPECIES || idx[2] == idx[0] || idx[2] == idx[1]))
+    return AVIP_EINVAL;
+  if (idx[0] == idx[1]) return AVIP_EINVAL;
+  const int np = model == AVIP_SRC_MORROW_LOWKE ? 5 : 3;
+  for (int k = 0; k < np; ++k)
+    if (!(params[k] >= 0) || !std::isfinite(params[k])) return AVIP_EINVAL;
   h->ph.src_model = model;
-  for (int k = 0; k < 3; ++k) {
-    h->ph.src_params[k] = params[k];
-    h->ph.src_idx[k] = idx[k];
-  }
+  for (int k = 0; k < 5; ++k) h->ph.src_params[k] = k < np ? params[k] : 0.0;
+  for (int k = 0; k < 3; ++k) h->ph.src_idx[k] = three || k < 2 ? idx[k] : -1;
   invalidate_graph(h);
   return AVIP_OK;
 }

@@ -148,7 +148,7 @@ struct Physics {
   int32_t limiter;
   int32_t scheme;     // AVIP_FLUX_*
   int32_t dd_fp32;    // 1: gradients, velocities, sources and fluxes in FP32 (mixed precision)
-  double src_params[3];
+  double src_params[5];   // {A, B, nu_att} or {A, B, A_eta, B_eta, beta_r} (AVIP_SRC_MORROW_LOWKE)
   double beta, cfl, fourier, a_diel, a_chem;
   double dt_fixed;
   SpeciesParams sp[AVIP_MAX_SPECIES];
@@ -209,6 +209,7 @@ struct PcgArgs {
   GridSync* sync;
   DevScalars* sc;
   double rtol;
+  double v_rise;          // > 0: the Dirichlet lift is scaled by min(t / v_rise, 1) (voltage ramp)
   int32_t max_iter;
   int32_t use_density_rhs;  // 1: b from densities; 0: b already in `b`
   // mixed precision: FP32 copy of the scaled matrix and FP32 inner-CG vectors
@@ -266,6 +267,14 @@ struct ClusterHost {
 PcgPlan pcg_cluster_plan(const HostMesh& m, int max_rows, ClusterLayout* out, ClusterHost* hd, int mixed = 0);
 
 #ifdef __CUDACC__
+// Factor of the Dirichlet values at the simulated time of the solve: min(t / v_rise, 1) during
+// a voltage ramp, exactly 1 otherwise (so the lift is used unchanged).
+__device__ __forceinline__ double dirichlet_gain(const PcgArgs& a) {
+  if (!(a.v_rise > 0.0)) return 1.0;
+  const double t = *((volatile const double*)&a.sc->t);
+  return t >= a.v_rise ? 1.0 : t / a.v_rise;
+}
+
 // A solve is skipped when an earlier stage of the run left non-finite data (AVIP_ENAN) or a
 // device wait gave up (AVIP_ETIMEOUT): every block (or CTA of a cluster) reads the same value
 // at entry, so all leave together.

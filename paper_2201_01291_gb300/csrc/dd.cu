@@ -125,6 +125,24 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
           if (s == ie) src[s] -= att;
           if (s == ineg) src[s] += att;
         }
+      } else if (a.ph.src_model == AVIP_SRC_MORROW_LOWKE) {
+        // attachment eta(|E|) w n_e, recombination beta_r n_e n_p and beta_r n_n n_p
+        double npos = 0.0, nneg = 0.0;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ip) npos = n[(size_t)s * a.Npad + i];
+          if (s == ineg) nneg = n[(size_t)s * a.Npad + i];
+        }
+        const double eta = Emag > 0.0 ? a.ph.src_params[2] * exp(-a.ph.src_params[3] / Emag) : 0.0;
+        const double att = eta * mue * Emag * ne;
+        const double rep = a.ph.src_params[4] * ne * npos;
+        const double rnp = a.ph.src_params[4] * nneg * npos;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ie) src[s] = src[s] - att - rep;
+          if (s == ip) src[s] = src[s] - rep - rnp;
+          if (s == ineg) src[s] = src[s] + att - rnp;
+        }
       }
       double se = 0.0;
 #pragma unroll
@@ -499,6 +517,25 @@ __device__ __forceinline__ void node_fields32_body(const DDArgs& a, int with_dt,
         for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
           if (s == ie) src[s] -= att;
           if (s == ineg) src[s] += att;
+        }
+      } else if (a.ph.src_model == AVIP_SRC_MORROW_LOWKE) {
+        float npos = 0.0f, nneg = 0.0f;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ip) npos = (float)n[(size_t)s * a.Npad + i];
+          if (s == ineg) nneg = (float)n[(size_t)s * a.Npad + i];
+        }
+        const float eta =
+            Emag > 0.0f ? (float)a.ph.src_params[2] * expf(-(float)a.ph.src_params[3] / Emag) : 0.0f;
+        const float att = eta * mue * Emag * ne;
+        const float br = (float)a.ph.src_params[4];
+        const float rep = br * ne * npos;
+        const float rnp = br * nneg * npos;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s == ie) src[s] = src[s] - att - rep;
+          if (s == ip) src[s] = src[s] - rep - rnp;
+          if (s == ineg) src[s] = src[s] + att - rnp;
         }
       }
       float se = 0.0f;

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
   double one[1];
 
   // ---- x = D^1/2 phi (warm start) and b'
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
@@ -59,12 +60,13 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else a.x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
   // x must be complete before the residual gathers it: this reduction is also the barrier
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
   };
 
   // ---- x = D^1/2 phi (warm start) and b'
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
 #pragma unroll
   for (int j = 0; j < MAXS; ++j) {
@@ -244,12 +247,16 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else {  // a Dirichlet unit row takes its (possibly ramped) value exactly
+      x[j] = b;
+      a.x[i] = b;
+    }
   }
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
   {

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   GridOps ops{fs, smem};
   double dummy = 0.0;
 
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int sl = gwarp; sl < nsl; sl += nwarps) {
     const int i = sl * kSlice + lane;
@@ -100,12 +101,13 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * Np + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
   {

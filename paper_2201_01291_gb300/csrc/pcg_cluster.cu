@@ -145,6 +145,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
       vals[e - e0] = __ldg(a.A.aval + e);
     }
   }
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int li = threadIdx.x; li < R; li += blockDim.x) {
     const int i = s0 * kSlice + li;
@@ -154,11 +155,12 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
       if (a.use_density_rhs) {
         double rho = 0.0;
         for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-        b = fma(a.rhs_scale[i], rho, a.lift[i]);
+        b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       } else {
         b = a.b[i];
       }
       if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+      else x = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
       push(xs, i, x);
       a.b[i] = b;
     }
@@ -399,6 +401,7 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
       vals[e - e0] = __ldg(a.aval32 + e);
     }
   }
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int li = threadIdx.x; li < R; li += blockDim.x) {
     const int i = s0 * kSlice + li;
@@ -409,12 +412,13 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
       if (a.use_density_rhs) {
         double rho = 0.0;
         for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-        b = fma(a.rhs_scale[i], rho, a.lift[i]);
+        b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       } else {
         b = a.b[i];
       }
       a.b[i] = b;
       if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+      else x = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
       push64(x64, i, x);
     }
     x64[li] = x;

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
   double one[1];
 
   // ---- x = D^1/2 phi (warm start) and b'
+  const double gain = dirichlet_gain(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
@@ -111,12 +112,13 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
     if (a.use_density_rhs) {
       double rho = 0.0;
       for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
-      b = fma(a.rhs_scale[i], rho, a.lift[i]);
+      b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
       b = a.b[i];
     }
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
+    else a.x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
   if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
   {

@@ -30,6 +30,7 @@ MOB_POWER = 1   # mu = mu0 * (max(|E|, E_floor) / E_ref) ** expo
 SRC_NONE = 0
 SRC_TOWNSEND = 1            # alpha(|E|) = A exp(-B/|E|);  S = alpha mu_e |E| n_e to e and +
 SRC_TOWNSEND_ATTACH = 2     # as above, plus attachment nu_a n_e moved from e to -
+SRC_MORROW_LOWKE = 3        # alpha, eta(|E|) attachment, e-p and n-p recombination (params A, B, A_eta, B_eta, beta_r)
 
 # Transport boundary closure modes (section "Boundary conditions in AVIP").
 BND_NEUMANN = 0             # F = F_C (zero normal gradient implied)
@@ -56,7 +57,7 @@ class Species:
 @dataclasses.dataclass
 class Source:
     model: int = SRC_NONE
-    params: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])  # [A, B, nu_att]
+    params: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])  # [A, B, nu_att] or ML's 5
     idx: List[int] = dataclasses.field(default_factory=lambda: [0, 1, -1])  # [electron, positive, negative]
 
 
@@ -72,6 +73,7 @@ class Opts:
     max_iter: int = 20000
     dt_fixed: float = 0.0       # > 0 replaces the automatic time step
     scheme: int = FLUX_LLW      # edge flux scheme
+    v_rise: float = 0.0         # > 0: electrode potentials rise linearly over this time (s)
 
 
 @dataclasses.dataclass
@@ -239,6 +241,56 @@ def config_pin_plane_hybrid(nx: int = 500, ny: int = 1000, quad_fraction: float 
     p = hybrid_plates_problem(nx, ny, 1e-2, 2e-2, 2e4, seed=2, quad_fraction=quad_fraction, field_dependent=True,
                               source=SRC_TOWNSEND, needle_len=2e-3)
     return dataclasses.replace(p, name=f"pin_plane_hybrid_{nx}x{ny}_q{quad_fraction:g}")
+
+
+def morrow_lowke_air(T_gas: float = 1000.0, p_atm: float = 1.0):
+    """Analytic closure fits for the three-species air chemistry at gas temperature T_gas
+    (project choices standing in for the tabulated coefficients, which are not available): the
+    reduced-field similarity of the Townsend fit with the density-equivalent pressure
+    p = 760 p_atm (300 / T_gas) Torr; attachment eta = 1.3 p /(m Torr) exp(-B_eta/|E|) with
+    B_eta = 20 p V/(m Torr) (about 10 /cm at breakdown at 1 atm, 300 K); recombination
+    beta_r = 2e-13 m^3/s; electron mobility mu_e = (T_gas/300) 0.04 (max(|E|, 1e3)/E_ref)^-0.2
+    with E_ref = 1e6 (300 / T_gas) V/m.  Returns (source params, electron mobility params)."""
+    p_torr = 760.0 * p_atm * 300.0 / T_gas
+    A, B = townsend_air(p_torr)
+    A_eta, B_eta = 1.3 * p_torr, 20.0 * p_torr
+    beta_r = 2e-13
+    s = T_gas / 300.0
+    mob = [0.04 * s / p_atm, 1e6 / s * p_atm, -0.2, 1e3]
+    return [A, B, A_eta, B_eta, beta_r], mob
+
+
+def morrow_lowke_problem(nx: int, ny: int, Lx: float, Ly: float, v_max: float, seed: int,
+                         needle_len: float = 0.0, T_gas: float = 1000.0, v_rise: float = 2e-9,
+                         n_back: float = 1e15, quad_fraction: float = 0.0, **kw) -> Problem:
+    """Three-species (e, p, n) air chemistry of the section "Hyperbole electrodes" on the
+    pin-plane geometry: immobile ions (the ion equations carry no transport term), a uniform
+    neutral background of electrons and positive ions, and the anode potential rising linearly
+    from 0 to v_max over v_rise (Fig. pin-pin_anode_time).  quad_fraction > 0 builds a hybrid
+    mesh."""
+    if quad_fraction > 0:
+        p = hybrid_plates_problem(nx, ny, Lx, Ly, v_max, seed, quad_fraction=quad_fraction, n_peak=0.0,
+                                  n_back=n_back, needle_len=needle_len, **kw)
+    else:
+        p = plates_problem(nx, ny, Lx, Ly, v_max, seed, n_peak=0.0, n_back=n_back, needle_len=needle_len, **kw)
+    params, mob = morrow_lowke_air(T_gas)
+    N = p.n_nodes
+    sp = [
+        Species("e", -1, MOB_POWER, mob, 0.1 * T_gas / 300.0, BND_OUTFLOW, np.full(N, n_back)),
+        Species("p", +1, MOB_CONST, [0.0], 0.0, BND_NEUMANN, np.full(N, n_back)),
+        Species("n", -1, MOB_CONST, [0.0], 0.0, BND_NEUMANN, np.zeros(N)),
+    ]
+    opts = dataclasses.replace(p.opts, v_rise=v_rise)
+    return dataclasses.replace(p, species=sp, source=Source(SRC_MORROW_LOWKE, params, [0, 1, 2]), opts=opts,
+                               name=f"morrow_lowke_{nx}x{ny}")
+
+
+def config_hyperbole_ml(nx: int = 800, ny: int = 800) -> Problem:
+    """Stand-in for the hyperbolic-electrode case: a 5 mm x 5 mm gap, 1 mm needle anode at the
+    top centre rising to 5 kV in 2 ns, grounded plane, 1000 K air (three-species chemistry),
+    1e15 m^-3 background; 800 x 800 jittered nodes (640,000 nodes, 1.28 M triangles, the size of
+    the paper's 6.3e5-node, 1.3e6-cell mesh)."""
+    return morrow_lowke_problem(nx, ny, 5e-3, 5e-3, 5e3, seed=1745, needle_len=1e-3)
 
 
 def random_instances(count: int, seed: int, t_min: float = 2e3, t_max: float = 2e5):
