@@ -83,6 +83,8 @@ extern "C" {
 #define AVIP_FIELD_EY 2
 #define AVIP_FIELD_DENSITY 3  /* species index in `s`                                       */
 #define AVIP_FIELD_VOLUME 4   /* median-dual nodal volume V_i (per radian if axisymmetric)  */
+#define AVIP_FIELD_PHOTO 5    /* photoionisation source S_ph of the last step (photo_set)   */
+#define AVIP_MAX_PHOTO_TERMS 3
 
 typedef void* (*avip_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*avip_free_fn)(void* ptr, void* ctx);
@@ -194,6 +196,26 @@ int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model,
  * parameter or an index out of range. */
 int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t* idx);
 
+/* Photoionisation source (section "Case 3" of the streamer benchmark: the three-term
+ * exponential fit of the radiative transfer by Helmholtz equations).  Each step, after the
+ * ionisation rate I_ion = alpha |W_e| n_e is known, n_terms equations
+ *     -lap S_j + kappa_j^2 S_j = a_j c I_ion,   S_j = 0 on the Dirichlet nodes,
+ *     zero normal derivative on the other boundaries,
+ * are solved (vertex-centred: (K + kappa_j^2 V) S_j = a_j c V I_ion with the Poisson matrix K and
+ * the dual volumes V) by the handle's own solver kind with the term's own diagonal scaling and,
+ * for the AMG kinds, its own hierarchy (built here, once), warm-started from the previous
+ * step; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
+ * source_set) before the time step and the update, and enters the chemical time-step limit.
+ *   a[n_terms]     A_j p_O2^2 (1/m^2)  — with A_j, lambda_j the coefficients of the fit;
+ *   kappa[n_terms] lambda_j p_O2 (1/m), > 0;
+ *   c              I = c I_ion: quenching and photo-efficiency factor
+ *                  (p_q/(p + p_q)) xi nu_u/nu_i (dimensionless), >= 0.
+ * Requires the FP64 solvers (AVIP_EINVAL with AVIP_PREC_MIXED); may be called once per handle
+ * (AVIP_ESTATE after that); n_terms = 0 is a no-op; at most AVIP_MAX_PHOTO_TERMS terms.  A
+ * handle with photoionisation cannot join a batch.  The solves' iteration counts are not part
+ * of avip_stats (those count the Poisson solves); a solve that fails sets the run status. */
+int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kappa, double c);
+
 /* Solve the Poisson problem for the current densities (warm start from the last phi).
  * iters_out / relres_out (may be NULL) receive the PCG iteration count and the final true
  * relative residual.  AVIP_ENOTCONV if max_iter was reached. */
@@ -209,9 +231,10 @@ int run_steps(avip_mesh_t h, int32_t nsteps, avip_stats* stats);
 
 /* Measurement variant of run_steps: the same kernels launched one by one (no graph) with CUDA
  * events recorded on the handle's stream around each of them.  kernel_ms[AVIP_TIMED_KERNELS]
- * receives the summed device time of {PCG solve, nodal fields, cell time step, fluxes +
- * update, finalize} over the call; `stats` (may be NULL) as for run_steps. */
-#define AVIP_TIMED_KERNELS 5
+ * receives the summed device time of {Poisson solve, nodal fields, cell time step, fluxes +
+ * update, finalize, photoionisation solves + source update} over the call; `stats` (may be
+ * NULL) as for run_steps. */
+#define AVIP_TIMED_KERNELS 6
 int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats* stats);
 
 /* Copy a nodal field to host memory, caller numbering: AVIP_FIELD_* (s = species index for

@@ -547,6 +547,15 @@ class Oracle:
             self.K = poisson_matrix(self.tris, self.S, self.V_tau, self.N)
         self.node_bc = np.asarray(problem.node_bc)
         self.solver = DirichletSolver(self.K, self.node_bc, problem.phi_D)
+        # photoionisation: one Helmholtz operator K + kappa_j^2 V per term, zero on the
+        # Dirichlet nodes (the electrodes), zero normal derivative elsewhere
+        self.photo = getattr(problem, "photo", None)
+        self.photo_solvers = []
+        if self.photo is not None:
+            for kap in self.photo.kappa:
+                H = (self.K + sp.diags(kap * kap * self.V_node)).tocsr()
+                self.photo_solvers.append(DirichletSolver(H, self.node_bc, np.zeros(self.N)))
+        self.last_photo = np.zeros(self.N)
         self.is_bnd = np.any(self.S_b != 0.0, axis=1)
 
     # -- Poisson sub-step -------------------------------------------------------------
@@ -596,6 +605,14 @@ class Oracle:
         grad = [self.nodal_gradient(n[s]) for s in range(len(self.p.species))]
         return phi, E, Emag, mu, vel, grad
 
+    def photo_source(self, I):
+        """S_ph = sum_j S_j with -lap S_j + kappa_j^2 S_j = a_j I (three-term Helmholtz fit of
+        the photoionisation in the streamer benchmark's third case); I is the photon
+        production rate c alpha |W_e| n_e.  Integrated over the dual cells:
+        (K + kappa_j^2 V) S_j = a_j V I.  Returns S_ph and the terms."""
+        terms = [solver.solve(a_j * self.V_node * I) for a_j, solver in zip(self.photo.a, self.photo_solvers)]
+        return sum(terms), terms
+
     def sources(self, n, Emag, mu):
         """Per-species source rates S_s,i (m^-3 s^-1) and the net electron rate."""
         src = self.p.source
@@ -623,6 +640,11 @@ class Oracle:
             out[e] = out[e] - att - rec_ep
             out[pos] = out[pos] - rec_ep - rec_np
             out[neg] = out[neg] + att - rec_np
+        if self.photo is not None:
+            S_ph, _ = self.photo_source(self.photo.c * ion)
+            self.last_photo = S_ph
+            out[e] = out[e] + S_ph
+            out[pos] = out[pos] + S_ph
         return out
 
     def time_step(self, n, mu, vel, S_src):

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libavip.so")
 
 AVIP_OK, AVIP_EINVAL, AVIP_ENOMEM, AVIP_ENOTCONV, AVIP_ENAN, AVIP_ECUDA, AVIP_ETIMEOUT, AVIP_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
-FIELD_PHI, FIELD_EX, FIELD_EY, FIELD_DENSITY, FIELD_VOLUME = 0, 1, 2, 3, 4
+FIELD_PHI, FIELD_EX, FIELD_EY, FIELD_DENSITY, FIELD_VOLUME, FIELD_PHOTO = 0, 1, 2, 3, 4, 5
 PREC_FP64, PREC_MIXED = 0, 1
 GEOM_PLANAR, GEOM_AXISYMMETRIC = 0, 1
 FLUX_LLW, FLUX_SG = 0, 1
@@ -67,6 +67,7 @@ _SIGS = {
     "solver_levels": (C.c_int, [_H, _P(C.c_int64), C.c_int32]),
     "species_set": (C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, _D, C.c_double, C.c_int32, _D]),
     "source_set": (C.c_int, [_H, C.c_int32, _D, _I]),
+    "photo_set": (C.c_int, [_H, C.c_int32, _D, _D, C.c_double]),
     "poisson_solve": (C.c_int, [_H, _I, _D]),
     "dd_step": (C.c_int, [_H, C.c_double, _D]),
     "run_steps": (C.c_int, [_H, C.c_int32, _P(AvipStats)]),
@@ -180,6 +181,12 @@ def source_set(h, model, params, idx):
     return load().source_set(h, model, _dptr(p), _iptr(i))
 
 
+def photo_set(h, a, kappa, c):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    return load().photo_set(h, int(a.size), _dptr(a), _dptr(kappa), float(c))
+
+
 def poisson_solve(h):
     it = C.c_int32()
     rr = C.c_double()
@@ -199,7 +206,7 @@ def run_steps(h, nsteps):
     return rc, st.as_dict()
 
 
-TIMED_KERNELS = ("pcg", "node_fields", "dt_cells", "flux_update", "finalize")
+TIMED_KERNELS = ("pcg", "node_fields", "dt_cells", "flux_update", "finalize", "photo")
 
 
 def run_steps_timed(h, nsteps):
@@ -350,6 +357,9 @@ class Mesh:
         src = problem.source
         if src.model != 0:
             _check(source_set(h, src.model, src.params, src.idx), "source_set")
+        ph = getattr(problem, "photo", None)
+        if ph is not None:
+            _check(photo_set(h, ph.a, ph.kappa, ph.c), "photo_set")
         self.info = mesh_info(h)
         self.info["levels"] = solver_levels(h)
 
@@ -397,6 +407,10 @@ class Mesh:
 
     def phi(self):
         return self.field(FIELD_PHI)
+
+    def photo(self):
+        """Photoionisation source S_ph of the last step."""
+        return self.field(FIELD_PHOTO)
 
     def state(self):
         rc, st = state_get(self.h)

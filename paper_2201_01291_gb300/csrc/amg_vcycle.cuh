@@ -191,7 +191,10 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
-      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+      if (a.rhs_src)
+        rho = a.rhs_src[i];
+      else
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
       b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
@@ -291,10 +294,10 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
       if (i < N) a.phi[i] = a.dsqinv[i] * a.x[i];
     }
     if (leader) {
-      a.sc->pcg_iters = it;
-      a.sc->pcg_status = status;
-      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
-      a.sc->pcg_bnorm = sqrt(bb[0]);
+      a.res->pcg_iters = it;
+      a.res->pcg_status = status;
+      a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+      a.res->pcg_bnorm = sqrt(bb[0]);
       if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
     }
     return true;
@@ -328,7 +331,10 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
-      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+      if (a.rhs_src)
+        rho = a.rhs_src[i];
+      else
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
       b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
@@ -440,11 +446,11 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
       if (i < N) a.phi[i] = a.dsqinv[i] * (bb[0] == 0.0 ? a.b[i] : a.x[i]);  // free b == 0: x = b
     }
     if (leader) {
-      a.sc->pcg_iters = it;
-      a.sc->pcg_outer = outer;
-      a.sc->pcg_status = status;
-      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
-      a.sc->pcg_bnorm = sqrt(bb[0]);
+      a.res->pcg_iters = it;
+      a.res->pcg_outer = outer;
+      a.res->pcg_status = status;
+      a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
+      a.res->pcg_bnorm = sqrt(bb[0]);
       if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
     }
     return true;

@@ -20,6 +20,7 @@ cudaError_t launch_pcg_amg_cluster(const PcgArgs& args, const PcgPlan& pl, cudaS
 cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st);
+cudaError_t launch_photo_add(const DDArgs& a, int with_dt, cudaStream_t st);
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st);
 cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st);
@@ -58,6 +59,16 @@ struct avip_mesh {
   double* parts = nullptr;
   size_t sync_bytes = 0;
   DevScalars* sc = nullptr;
+  // photoionisation: per Helmholtz term its scaled matrix values, scaling, right-hand-side
+  // factors, AMG hierarchy (AMG solver kinds) and solution; the ionisation rate, the summed
+  // source, a zero lift and the result block of those solves
+  struct PhotoTerm {
+    double *aval = nullptr, *dsq = nullptr, *dsqinv = nullptr, *rhs = nullptr;
+    AmgDev* amg = nullptr;
+  };
+  std::vector<PhotoTerm> photo;
+  double *photo_psi = nullptr, *photo_I = nullptr, *photo_S = nullptr, *photo_zero = nullptr;
+  DevScalars* sc_aux = nullptr;
   int32_t Npad = 0;
   PcgPlan plan;
   ClusterLayout clay{};
@@ -159,6 +170,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.parts = h->parts;
   a.sync = h->sync;
   a.sc = h->sc;
+  a.res = h->sc;
   a.rtol = h->opts.rtol;
   a.v_rise = h->opts.v_rise;
   a.max_iter = h->opts.max_iter;
@@ -192,6 +204,9 @@ DDArgs dd_args(const avip_mesh* h) {
   a.src = h->src;
   a.Ex = h->Ex;
   a.Ey = h->Ey;
+  a.photo_I = h->photo_I;
+  a.photo_psi = h->photo_psi;
+  a.photo_S = h->photo_S;
   a.cell = h->cell;
   a.dxmin = h->dxmin;
   a.flen = h->flen;
@@ -215,14 +230,16 @@ int cuda_status(cudaError_t e) {
   return AVIP_ECUDA;
 }
 
-cudaError_t enqueue_pcg_only(avip_mesh* h) {
-  if (h->plan.kind == 4) return launch_pcg_mixed(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 7) return launch_bicgstab(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind >= 8 && h->plan.kind <= 10) return launch_pcg_amg(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 11) return launch_pcg_amg_cluster(pcg_args(h), h->plan, h->stream);
-  if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(pcg_args(h), h->plan, h->clay, h->stream);
-  return launch_pcg_fp64(pcg_args(h), h->plan, h->stream);
+cudaError_t enqueue_solver(avip_mesh* h, const PcgArgs& a) {
+  if (h->plan.kind == 4) return launch_pcg_mixed(a, h->plan, h->stream);
+  if (h->plan.kind == 7) return launch_bicgstab(a, h->plan, h->stream);
+  if (h->plan.kind >= 8 && h->plan.kind <= 10) return launch_pcg_amg(a, h->plan, h->stream);
+  if (h->plan.kind == 11) return launch_pcg_amg_cluster(a, h->plan, h->stream);
+  if (h->plan.kind == 5 || h->plan.kind == 6) return launch_pcg_cluster(a, h->plan, h->clay, h->stream);
+  return launch_pcg_fp64(a, h->plan, h->stream);
 }
+
+cudaError_t enqueue_pcg_only(avip_mesh* h) { return enqueue_solver(h, pcg_args(h)); }
 
 // Queue one Poisson solve (cooperative PCG launch).
 cudaError_t enqueue_poisson(avip_mesh* h) {
@@ -231,13 +248,45 @@ cudaError_t enqueue_poisson(avip_mesh* h) {
   return enqueue_pcg_only(h);
 }
 
+// Arguments of the solve of photoionisation term j: the same solver and sparsity as the
+// Poisson problem, the term's scaled Helmholtz values, b = rhs_j * (ionisation rate), zero
+// Dirichlet values, results reported to the auxiliary block.
+PcgArgs photo_args(const avip_mesh* h, int j) {
+  PcgArgs a = pcg_args(h);
+  const avip_mesh::PhotoTerm& t = h->photo[j];
+  a.A.aval = t.aval;
+  a.dsq = t.dsq;
+  a.dsqinv = t.dsqinv;
+  a.rhs_scale = t.rhs;
+  a.lift = h->photo_zero;
+  a.rhs_src = h->photo_I;
+  a.phi = h->photo_psi + (size_t)j * h->Npad;
+  a.res = h->sc_aux;
+  a.v_rise = 0.0;
+  a.amg = t.amg;
+  return a;
+}
+
+// The photoionisation solves and the source update that follows them.
+cudaError_t enqueue_photo(avip_mesh* h, const DDArgs& a, bool auto_dt) {
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < h->ph.photo_terms && e == cudaSuccess; ++j) {
+    e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
+    if (e == cudaSuccess) e = enqueue_solver(h, photo_args(h, j));
+  }
+  if (e == cudaSuccess) e = launch_photo_add(a, auto_dt ? 1 : 0, h->stream);
+  return e;
+}
+
 // Queue one explicit step (no host synchronisation).
 cudaError_t enqueue_step(avip_mesh* h) {
   cudaError_t e = enqueue_poisson(h);
   if (e != cudaSuccess) return e;
   DDArgs a = dd_args(h);
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
-  if ((e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream)) != cudaSuccess) return e;
+  const bool photo = h->ph.photo_terms > 0;
+  if ((e = launch_node_fields(a, auto_dt && !photo ? 1 : 0, h->stream)) != cudaSuccess) return e;
+  if (photo && (e = enqueue_photo(h, a, auto_dt)) != cudaSuccess) return e;
   if (auto_dt && (e = launch_dt_cells(a, h->stream)) != cudaSuccess) return e;
   if ((e = launch_flux_update(a, h->stream)) != cudaSuccess) return e;
   return launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
@@ -262,7 +311,7 @@ void invalidate_graph(avip_mesh* h) {
 // `aval0`; every other operator in SELL-32; per level x, b, r, d vectors (level 0: only r and d,
 // the V-cycle takes its finest right-hand side and solution as arguments).
 template <typename T>
-bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& out) {
+bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& out, bool record = true) {
   AmgDevT<T> D;
   std::memset(&D, 0, sizeof(D));
   D.nlev = (int32_t)H.lv.size();
@@ -313,6 +362,7 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& o
   ok = ok && dd && cudaMemcpyAsync(dd, &D, sizeof(D), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
        cudaStreamSynchronize(h->stream) == cudaSuccess;
   out = dd;
+  if (!record) return ok;
   h->amg_levels = D.nlev;
   h->amg_stats.clear();
   for (const AmgHostLevel& L : H.lv) {
@@ -669,6 +719,81 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
   return AVIP_OK;
 }
 
+int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kappa, double c) {
+  if (!h || n_terms < 0 || n_terms > AVIP_MAX_PHOTO_TERMS || (n_terms > 0 && (!a || !kappa)) ||
+      !(c >= 0) || !std::isfinite(c))
+    return AVIP_EINVAL;
+  for (int j = 0; j < n_terms; ++j)
+    if (!(a[j] >= 0) || !std::isfinite(a[j]) || !(kappa[j] > 0) || !std::isfinite(kappa[j])) return AVIP_EINVAL;
+  if (!h->photo.empty()) {
+    std::snprintf(g_err, sizeof(g_err), "photoionisation terms can be set once per handle");
+    return AVIP_ESTATE;
+  }
+  if (n_terms == 0) return AVIP_OK;
+  const int kind = h->plan.kind;
+  if (h->opts.precision != AVIP_PREC_FP64 || kind == 4 || kind == 6 || kind == 10) {
+    std::snprintf(g_err, sizeof(g_err), "photoionisation needs the FP64 solvers");
+    return AVIP_EINVAL;
+  }
+  const HostMesh& m = h->hm;
+  const size_t Np = (size_t)h->Npad;
+  const bool amg = kind == 8 || kind == 9 || kind == 11;
+  bool ok = zalloc(h, h->photo_psi, (size_t)n_terms * Np) && zalloc(h, h->photo_I, Np) &&
+            zalloc(h, h->photo_S, Np) && zalloc(h, h->photo_zero, Np) && zalloc(h, h->sc_aux, 1);
+  for (int j = 0; j < n_terms && ok; ++j) {
+    // (K + kappa_j^2 V) S_j = c a_j V I with S_j = 0 on the Dirichlet nodes: the unscaled
+    // Poisson values are recovered from the scaled ones, the diagonal of the free rows gains
+    // kappa_j^2 V_i, and the result is scaled symmetrically by its own diagonal.
+    const double k2 = kappa[j] * kappa[j];
+    std::vector<double> dh(Np, 1.0), dhinv(Np, 1.0), rhs(Np, 0.0), val(m.aval.size(), 0.0);
+    for (int32_t i = 0; i < m.N; ++i)
+      if (m.bc[i] != 1) {
+        dh[i] = std::sqrt(m.dsq[i] * m.dsq[i] + k2 * m.vol[i]);
+        dhinv[i] = 1.0 / dh[i];
+        rhs[i] = c * a[j] * m.vol[i] * dhinv[i];
+      }
+    for (int32_t sl = 0; sl < m.nslices; ++sl)
+      for (int l = 0; l < kSlice; ++l) {
+        const int32_t i = sl * kSlice + l;
+        if (i >= m.N) continue;
+        for (int32_t k = 0; k < m.rlen[i]; ++k) {
+          const int64_t e = (int64_t)m.sl_ptr[sl] + (int64_t)k * kSlice + l;
+          const int32_t col = m.col[e];
+          if (m.bc[i] == 1) {
+            val[e] = k == 0 ? 1.0 : 0.0;
+          } else if (k == 0) {
+            val[e] = 1.0;
+          } else {
+            const double K = m.aval[e] * m.dsq[i] * m.dsq[col];
+            val[e] = K / (dh[i] * dh[col]);
+          }
+        }
+      }
+    avip_mesh::PhotoTerm t;
+    ok = upload(h, t.aval, val) && upload(h, t.dsq, dh) && upload(h, t.dsqinv, dhinv) && upload(h, t.rhs, rhs);
+    if (ok && amg) {
+      HostMesh hm;
+      hm.N = m.N;
+      hm.nslices = m.nslices;
+      hm.geometry = m.geometry;
+      hm.rlen = m.rlen;
+      hm.sl_ptr = m.sl_ptr;
+      hm.col = m.col;
+      hm.bc = m.bc;
+      hm.aval = std::move(val);
+      hm.dsq.assign(dh.begin(), dh.begin() + m.N);
+      AmgHost H;
+      if (amg_setup(hm, H, g_err, sizeof(g_err)) != AVIP_OK) return AVIP_EINVAL;
+      ok = upload_amg_t<double>(h, H, t.aval, t.amg, false);
+    }
+    h->photo.push_back(t);
+  }
+  if (!ok) return AVIP_ENOMEM;
+  h->ph.photo_terms = n_terms;
+  invalidate_graph(h);
+  return cudaStreamSynchronize(h->stream) == cudaSuccess ? AVIP_OK : AVIP_ECUDA;
+}
+
 int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out) {
   if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
   cudaError_t e = enqueue_poisson(h);
@@ -763,8 +888,9 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
   DevScalars s0;
   int rc = read_scalars(h, s0);
   if (rc) return rc;
-  cudaEvent_t ev[AVIP_TIMED_KERNELS + 1];
+  cudaEvent_t ev[6], evp[2];
   for (auto& e : ev) cudaEventCreate(&e);
+  for (auto& e : evp) cudaEventCreate(&e);
   cudaError_t e = launch_run_reset(h->sc, h->stream);
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
   for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
@@ -773,7 +899,12 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
     if (e == cudaSuccess) e = enqueue_pcg_only(h);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-    if (e == cudaSuccess) e = launch_node_fields(a, auto_dt ? 1 : 0, h->stream);
+    const bool photo = h->ph.photo_terms > 0;
+    if (e == cudaSuccess) e = launch_node_fields(a, auto_dt && !photo ? 1 : 0, h->stream);
+    // the photoionisation solves and source update are timed on their own
+    if (e == cudaSuccess && photo) e = cudaEventRecord(evp[0], h->stream);
+    if (e == cudaSuccess && photo) e = enqueue_photo(h, a, auto_dt);
+    if (e == cudaSuccess && photo) e = cudaEventRecord(evp[1], h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
     if (e == cudaSuccess && auto_dt) e = launch_dt_cells(a, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
@@ -782,13 +913,20 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
     if (e == cudaSuccess) e = launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5], h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
-    for (int k = 0; k < AVIP_TIMED_KERNELS && e == cudaSuccess; ++k) {
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
       float ms = 0.f;
       e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
       kernel_ms[k] += ms;
     }
+    if (e == cudaSuccess && h->ph.photo_terms > 0) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, evp[0], evp[1]);
+      kernel_ms[5] += ms;
+      kernel_ms[1] -= ms;
+    }
   }
   for (auto& x : ev) cudaEventDestroy(x);
+  for (auto& x : evp) cudaEventDestroy(x);
   if (e != cudaSuccess) return cuda_status(e);
   DevScalars sc;
   rc = read_scalars(h, sc);
@@ -824,6 +962,9 @@ int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out) {
     case AVIP_FIELD_EX: return to_host_perm(h, h->Ex, host_out);
     case AVIP_FIELD_EY: return to_host_perm(h, h->Ey, host_out);
     case AVIP_FIELD_VOLUME: return to_host_perm(h, h->vol, host_out);
+    case AVIP_FIELD_PHOTO:
+      if (!h->photo_S) return AVIP_ESTATE;
+      return to_host_perm(h, h->photo_S, host_out);
     case AVIP_FIELD_DENSITY: {
       if (s < 0 || s >= h->ph.ns) return AVIP_EINVAL;
       DevScalars sc;
@@ -1022,8 +1163,8 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
       delete b;
       return h ? AVIP_ESTATE : AVIP_EINVAL;
     }
-    if (h->plan.kind == 7 || h->plan.kind == 9) {  // the batched solver is CG (symmetric matrices)
-      std::snprintf(g_err, sizeof(g_err), "batches take planar meshes solved by CG only");
+    if (h->plan.kind == 7 || h->plan.kind == 9 || h->ph.photo_terms > 0) {  // the batched solver is CG
+      std::snprintf(g_err, sizeof(g_err), "batches take planar meshes solved by CG, without photoionisation");
       delete b;
       return AVIP_EINVAL;
     }

@@ -148,6 +148,7 @@ struct Physics {
   int32_t limiter;
   int32_t scheme;     // AVIP_FLUX_*
   int32_t dd_fp32;    // 1: gradients, velocities, sources and fluxes in FP32 (mixed precision)
+  int32_t photo_terms;  // > 0: photoionisation source from that many Helmholtz solves
   double src_params[5];   // {A, B, nu_att} or {A, B, A_eta, B_eta, beta_r} (AVIP_SRC_MORROW_LOWKE)
   double beta, cfl, fourier, a_diel, a_chem;
   double dt_fixed;
@@ -207,7 +208,10 @@ struct PcgArgs {
   unsigned* flags;        // [0] grid-reduction arrival counter (zeroed before each launch)
   double* parts;          // grid barrier partials, 2 * gridDim.x * 4
   GridSync* sync;
-  DevScalars* sc;
+  DevScalars* sc;          // status, time and density parity of the handle
+  DevScalars* res;         // where the solve reports iterations / residual (sc, or the
+                           // auxiliary block of the photoionisation solves)
+  const double* rhs_src;   // non-null: b = rhs_scale * rhs_src + lift instead of the charge density
   double rtol;
   double v_rise;          // > 0: the Dirichlet lift is scaled by min(t / v_rise, 1) (voltage ramp)
   int32_t max_iter;
@@ -297,6 +301,9 @@ struct DDArgs {
   double* src;            // per species per node: source rate
   double* Ex;
   double* Ey;
+  double* photo_I;        // per node: ionisation rate alpha |W_e| n_e (written when ph.photo_terms > 0)
+  const double* photo_psi;  // ph.photo_terms solutions S_ph,j, each Npad long
+  double* photo_S;        // per node: S_ph = sum_j S_ph,j
   const int32_t* cell;    // SoA v0[T], v1[T], v2[T] (, v3[T] when nvmax == 4; -1 for triangles)
   const double* dxmin;
   const int32_t* flen;    // per row: slots 1..flen-1 carry the mesh edges

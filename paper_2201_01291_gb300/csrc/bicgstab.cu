@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
-      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * Np + i], rho);
+      if (a.rhs_src)
+        rho = a.rhs_src[i];
+      else
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * Np + i], rho);
       b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
@@ -215,10 +218,10 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
       if (i < N) a.phi[i] = a.dsqinv[i] * x[i];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.sc->pcg_iters = it;
-      a.sc->pcg_status = status;
-      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
-      a.sc->pcg_bnorm = sqrt(bb[0]);
+      a.res->pcg_iters = it;
+      a.res->pcg_status = status;
+      a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+      a.res->pcg_bnorm = sqrt(bb[0]);
       if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
     }
     return;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
 timeout:
   if (threadIdx.x == 0) {
     atomicExch(&a.sync->abort, 1);
-    a.sc->pcg_status = AVIP_ETIMEOUT;
+    a.res->pcg_status = AVIP_ETIMEOUT;
     atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
   }
 }

@@ -113,6 +113,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
         if (s == ie) mue = mu[s];
       const double ion = alpha * mue * Emag * ne;
+      if (a.ph.photo_terms > 0) a.photo_I[i] = ion;
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
         if (s == ie) src[s] += ion;
@@ -406,6 +407,27 @@ __device__ __forceinline__ void finalize_body(DevScalars* sc, const double* part
     sc->run_relres_max = fmax(sc->run_relres_max, sc->pcg_relres);
     sc->dt_bits = (unsigned long long)__double_as_longlong(INFINITY);
   }
+}
+
+// Photoionisation (after the Helmholtz solves): S_ph = sum_j S_ph,j added to the electron and
+// positive-ion sources, and the chemical time-step limit with the complete electron source.
+__global__ void __launch_bounds__(kDDThreads) photo_add_kernel(DDArgs a, int with_dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double chem = INFINITY;
+  if (i < a.A.N) {
+    double S = 0.0;
+    for (int j = 0; j < a.ph.photo_terms; ++j) S += a.photo_psi[(size_t)j * a.Npad + i];
+    a.photo_S[i] = S;
+    const int ie = a.ph.src_idx[0], ip = a.ph.src_idx[1];
+    const double se = a.src[(size_t)ie * a.Npad + i] + S;
+    a.src[(size_t)ie * a.Npad + i] = se;
+    a.src[(size_t)ip * a.Npad + i] += S;
+    if (with_dt && se != 0.0) {
+      const double* n = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+      chem = a.ph.a_chem * fabs(n[(size_t)ie * a.Npad + i]) / fabs(se);
+    }
+  }
+  if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
 }
 
 __global__ void finalize_kernel(DevScalars* sc, const double* partials, int nparts) {
@@ -746,6 +768,11 @@ cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st) {
     node_fields_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
   return cudaGetLastError();
 }
+cudaError_t launch_photo_add(const DDArgs& a, int with_dt, cudaStream_t st) {
+  photo_add_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a, with_dt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
   dt_cells_kernel<<<nblk(a.T), kDDThreads, 0, st>>>(a);
   return cudaGetLastError();

@@ -154,7 +154,10 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
       x = a.dsq[i] * a.phi[i];
       if (a.use_density_rhs) {
         double rho = 0.0;
-        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+        if (a.rhs_src)
+          rho = a.rhs_src[i];
+        else
+          for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
         b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       } else {
         b = a.b[i];
@@ -264,10 +267,10 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
     }
   }
   if (rank == 0 && threadIdx.x == 0) {
-    a.sc->pcg_iters = it;
-    a.sc->pcg_status = status;
-    a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
-    a.sc->pcg_bnorm = sqrt(bb[0]);
+    a.res->pcg_iters = it;
+    a.res->pcg_status = status;
+    a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
+    a.res->pcg_bnorm = sqrt(bb[0]);
     if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
   }
   cl.sync();  // no CTA leaves while another may still write into its shared memory
@@ -411,7 +414,10 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
       double b;
       if (a.use_density_rhs) {
         double rho = 0.0;
-        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+        if (a.rhs_src)
+          rho = a.rhs_src[i];
+        else
+          for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
         b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       } else {
         b = a.b[i];
@@ -535,11 +541,11 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
     }
   }
   if (rank == 0 && threadIdx.x == 0) {
-    a.sc->pcg_iters = it;
-    a.sc->pcg_outer = outer;
-    a.sc->pcg_status = status;
-    a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
-    a.sc->pcg_bnorm = sqrt(bb[0]);
+    a.res->pcg_iters = it;
+    a.res->pcg_outer = outer;
+    a.res->pcg_status = status;
+    a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
+    a.res->pcg_bnorm = sqrt(bb[0]);
     if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
   }
   cl.sync();

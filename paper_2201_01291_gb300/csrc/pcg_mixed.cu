@@ -111,7 +111,10 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
-      for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
+      if (a.rhs_src)
+        rho = a.rhs_src[i];
+      else
+        for (int k = 0; k < a.ns; ++k) rho = fma(a.q[k], nb[(size_t)k * a.Npad + i], rho);
       b = fma(a.rhs_scale[i], rho, gain * a.lift[i]);
       a.b[i] = b;
     } else {
@@ -223,11 +226,11 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
       if (i < N) a.phi[i] = a.dsqinv[i] * (bb[0] == 0.0 ? a.b[i] : a.x[i]);  // free b == 0: x = b
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.sc->pcg_iters = it;
-      a.sc->pcg_status = status;
-      a.sc->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
-      a.sc->pcg_bnorm = sqrt(bb[0]);
-      a.sc->pcg_outer = outer;
+      a.res->pcg_iters = it;
+      a.res->pcg_status = status;
+      a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
+      a.res->pcg_bnorm = sqrt(bb[0]);
+      a.res->pcg_outer = outer;
       if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
     }
     return;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
 timeout:
   if (threadIdx.x == 0) {
     atomicExch(&a.sync->abort, 1);
-    a.sc->pcg_status = AVIP_ETIMEOUT;
+    a.res->pcg_status = AVIP_ETIMEOUT;
     atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
   }
 }

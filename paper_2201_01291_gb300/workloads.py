@@ -62,6 +62,15 @@ class Source:
 
 
 @dataclasses.dataclass
+class Photo:
+    """Photoionisation by the three-term Helmholtz fit: per term a_j = A_j p_O2^2 (1/m^2) and
+    kappa_j = lambda_j p_O2 (1/m); c = (p_q/(p + p_q)) xi nu_u/nu_i scales the ionisation rate."""
+    a: List[float]
+    kappa: List[float]
+    c: float
+
+
+@dataclasses.dataclass
 class Opts:
     cfl: float = 0.4
     fourier: float = 0.25
@@ -90,6 +99,7 @@ class Problem:
     meta: dict
     axisymmetric: bool = False   # True: y is the radius r >= 0, x the axis
     quads: Optional[np.ndarray] = None  # (Q, 4) int32 quadrangles of a hybrid mesh
+    photo: Optional[Photo] = None       # photoionisation source
 
     @property
     def n_nodes(self) -> int:
@@ -293,6 +303,26 @@ def config_hyperbole_ml(nx: int = 800, ny: int = 800) -> Problem:
     return morrow_lowke_problem(nx, ny, 5e-3, 5e-3, 5e3, seed=1745, needle_len=1e-3)
 
 
+def photo_air(p_torr: float = 760.0, p_q_torr: float = 30.0, xi_ratio: float = 0.06) -> Photo:
+    """Three-term fit for air: A_j = (1.986e-4, 0.0051, 0.4886) /(cm^2 Torr^2) and lambda_j =
+    (0.0553, 0.146, 0.89) /(cm Torr), p_O2 = 0.2 p, quenching pressure p_q = 30 Torr and
+    xi nu_u/nu_i = 0.06 (inputs of this stand-in: the values commonly quoted for the fit, not
+    checked here against the original tables)."""
+    p_o2 = 0.2 * p_torr
+    A = [1.986e-4, 0.0051, 0.4886]
+    lam = [0.0553, 0.146, 0.89]
+    a = [Aj * p_o2 ** 2 * 1e4 for Aj in A]
+    kappa = [lj * p_o2 * 1e2 for lj in lam]
+    return Photo(a, kappa, p_q_torr / (p_torr + p_q_torr) * xi_ratio)
+
+
+def config_axisym_photo(nx: int = 701, ny: int = 701) -> Problem:
+    """The axisymmetric streamer gap of config_axisym_streamer with a 1e9 m^-3 background and
+    photoionisation (the benchmark's third case: its second case plus photoionisation)."""
+    p = config_axisym_streamer(nx, ny, n_back=1e9)
+    return dataclasses.replace(p, photo=photo_air(), name=f"axisym_photo_{nx}x{ny}")
+
+
 def random_instances(count: int, seed: int, t_min: float = 2e3, t_max: float = 2e5):
     """Many uneven discharge instances: triangle counts log-uniform in [t_min, t_max], aspect
     ratio uniform in [1,4], voltage uniform in [5,25] kV, 2 or 3 charged species (the third a
@@ -343,14 +373,14 @@ def axisym_problem(nx: int, nr: int, Lx: float, Lr: float, voltage: float, seed:
                    dict(nx=nx, nr=nr, Lx=Lx, Lr=Lr, voltage=voltage), axisymmetric=True)
 
 
-def config_axisym_streamer(nx: int = 701, nr: int = 701, seed: int = 2201) -> Problem:
+def config_axisym_streamer(nx: int = 701, nr: int = 701, seed: int = 2201, n_back: float = 1e13) -> Problem:
     """Axisymmetric streamer gap in the geometry of the paper's axisymmetric streamer benchmark
     (section "Bagheri benchmark"): 1.25 cm x 1.25 cm, 1.5 MV/m background field (18.75 kV),
     Gaussian seed of 5e18 m^-3 (sigma 0.4 mm) on the axis at x = 1 cm over a 1e13 m^-3
     background; local-field electron mobility and Townsend ionisation of this library's models
     (the benchmark's tabulated transport data are not used).  701 x 701 nodes: 980,000
     triangles, the size class of the pin-plane workload."""
-    return axisym_problem(nx, nr, 1.25e-2, 1.25e-2, 18750.0, seed, n_peak=5e18, n_back=1e13, sigma=4e-4,
+    return axisym_problem(nx, nr, 1.25e-2, 1.25e-2, 18750.0, seed, n_peak=5e18, n_back=n_back, sigma=4e-4,
                           field_dependent=True, source=SRC_TOWNSEND, x0=1e-2, name="axisym_streamer")
 
 

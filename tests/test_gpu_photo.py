@@ -1,0 +1,102 @@
+"""Parity of the photoionisation source on the GPU (three Helmholtz solves per step by the
+handle's own solver kind) with the FP64 oracle: the source S_ph of one step with every FP64
+solver kind (planar and axisymmetric), steps with photoionisation on both geometries, a large
+axisymmetric mesh on the AMG-preconditioned BiCGStab, and the error paths.  Tolerances: 1e-10
+norm-wise on S_ph, phi and the densities (solves at rtol 1e-13)."""
+import numpy as np
+import pytest
+
+import avip_oracle as O
+from helpers import normwise
+from paper_2201_01291_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def avip():
+    from paper_2201_01291_gb300 import build
+    build.build()
+    from paper_2201_01291_gb300 import avip as A
+    A.load()
+    return A
+
+
+def planar(nx=33, ny=31, **kw):
+    p = W.plates_problem(nx, ny, 1e-2, 1e-2, 2.5e4, seed=9, field_dependent=True, source=W.SRC_TOWNSEND,
+                         n_back=1e9, **kw)
+    return W.dataclasses.replace(p, photo=W.photo_air())
+
+
+def axisym(nx=33, nr=29, **kw):
+    p = W.axisym_problem(nx, nr, 1.25e-2, 1.25e-2, 18750.0, seed=5, n_peak=5e18, n_back=1e9, sigma=4e-4,
+                         field_dependent=True, source=W.SRC_TOWNSEND, x0=1e-2, **kw)
+    return W.dataclasses.replace(p, photo=W.photo_air())
+
+
+@pytest.mark.parametrize("geom,kind", [("planar", 1), ("planar", 2), ("planar", 5), ("planar", 8),
+                                       ("planar", 11), ("axisym", 7), ("axisym", 9)])
+def test_photo_source_one_step(avip, geom, kind):
+    p = planar() if geom == "planar" else axisym()
+    o = O.Oracle(p)
+    n1, info = o.step(o.initial_state())
+    m = avip.Mesh(p, rtol=1e-13, pcg_kind=kind)
+    assert m.info["pcg_kind"] == kind
+    dt = m.step()
+    assert abs(dt - info["dt"]) <= 1e-12 * info["dt"]
+    assert o.last_photo.max() > 0
+    assert normwise(m.photo(), o.last_photo) <= TOL
+    for s in range(2):
+        assert normwise(m.density(s), n1[s]) <= TOL, s
+    m.close()
+
+
+@pytest.mark.parametrize("geom", ["planar", "axisym"])
+def test_photo_steps_parity(avip, geom):
+    p = planar(41, 39) if geom == "planar" else axisym(41, 33)
+    nsteps = 20
+    o = O.Oracle(p)
+    n_ref, phi_ref, dts = o.run(nsteps)
+    m = avip.Mesh(p, rtol=1e-13)
+    st = m.run(nsteps)
+    assert st["steps"] == nsteps and st["status"] == 0
+    assert abs(st["t"] - sum(dts)) <= 1e-12 * sum(dts)
+    for s in range(2):
+        assert normwise(m.density(s), n_ref[s]) <= TOL, s
+    assert normwise(m.phi(), phi_ref) <= TOL
+    assert normwise(m.photo(), o.last_photo) <= TOL
+    m.close()
+
+
+def test_photo_large_axisymmetric_amg(avip):
+    """40,000 nodes: the automatic AMG-preconditioned BiCGStab for the Poisson and the three
+    Helmholtz problems (each with its own hierarchy), 6 steps."""
+    p = axisym(201, 201)
+    o = O.Oracle(p)
+    n_ref, phi_ref, _ = o.run(6)
+    m = avip.Mesh(p, rtol=1e-13)
+    assert m.info["pcg_kind"] == 9
+    st = m.run(6)
+    assert st["status"] == 0
+    for s in range(2):
+        assert normwise(m.density(s), n_ref[s]) <= TOL, s
+    assert normwise(m.photo(), o.last_photo) <= TOL
+    m.close()
+
+
+def test_photo_error_paths(avip):
+    p = planar(21, 19)
+    ph = p.photo
+    q = W.dataclasses.replace(p, photo=None)
+    mixed = avip.Mesh(q, precision=avip.PREC_MIXED)
+    assert avip.photo_set(mixed.h, ph.a, ph.kappa, ph.c) == avip.AVIP_EINVAL
+    mixed.close()
+    m = avip.Mesh(q)
+    assert avip.photo_set(m.h, ph.a, [-1.0, 2.0, 3.0], ph.c) == avip.AVIP_EINVAL
+    assert avip.photo_set(m.h, ph.a, ph.kappa, ph.c) == avip.AVIP_OK
+    assert avip.photo_set(m.h, ph.a, ph.kappa, ph.c) == avip.AVIP_ESTATE
+    with pytest.raises(avip.AvipError):
+        avip.Batch([m])
+    m.close()
