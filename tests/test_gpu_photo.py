@@ -45,7 +45,8 @@ def test_photo_source_one_step(avip, geom, kind):
     m = avip.Mesh(p, rtol=1e-13, pcg_kind=kind)
     assert m.info["pcg_kind"] == kind
     dt = m.step()
-    assert abs(dt - info["dt"]) <= 1e-12 * info["dt"]
+    # the chemical limit divides by S_ph, an iterative solve's output: the solve bar applies
+    assert abs(dt - info["dt"]) <= TOL * info["dt"]
     assert o.last_photo.max() > 0
     assert normwise(m.photo(), o.last_photo) <= TOL
     for s in range(2):
@@ -62,7 +63,7 @@ def test_photo_steps_parity(avip, geom):
     m = avip.Mesh(p, rtol=1e-13)
     st = m.run(nsteps)
     assert st["steps"] == nsteps and st["status"] == 0
-    assert abs(st["t"] - sum(dts)) <= 1e-12 * sum(dts)
+    assert abs(st["t"] - sum(dts)) <= TOL * sum(dts)
     for s in range(2):
         assert normwise(m.density(s), n_ref[s]) <= TOL, s
     assert normwise(m.phi(), phi_ref) <= TOL
