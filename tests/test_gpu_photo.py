@@ -2,7 +2,8 @@
 handle's own solver kind) with the FP64 oracle: the source S_ph of one step with every FP64
 solver kind (planar and axisymmetric), steps with photoionisation on both geometries, a large
 axisymmetric mesh on the AMG-preconditioned BiCGStab, and the error paths.  Tolerances: 1e-10
-norm-wise on S_ph, phi and the densities (solves at rtol 1e-13)."""
+norm-wise on S_ph, phi and the densities (solves at rtol 1e-14, 1e-13 on the large mesh: the
+Helmholtz terms with small kappa are as ill-conditioned as the Poisson problem)."""
 import numpy as np
 import pytest
 
@@ -42,7 +43,7 @@ def test_photo_source_one_step(avip, geom, kind):
     p = planar() if geom == "planar" else axisym()
     o = O.Oracle(p)
     n1, info = o.step(o.initial_state())
-    m = avip.Mesh(p, rtol=1e-13, pcg_kind=kind)
+    m = avip.Mesh(p, rtol=1e-14, pcg_kind=kind)
     assert m.info["pcg_kind"] == kind
     dt = m.step()
     # the chemical limit divides by S_ph, an iterative solve's output: the solve bar applies
@@ -60,7 +61,7 @@ def test_photo_steps_parity(avip, geom):
     nsteps = 20
     o = O.Oracle(p)
     n_ref, phi_ref, dts = o.run(nsteps)
-    m = avip.Mesh(p, rtol=1e-13)
+    m = avip.Mesh(p, rtol=1e-14)
     st = m.run(nsteps)
     assert st["steps"] == nsteps and st["status"] == 0
     assert abs(st["t"] - sum(dts)) <= TOL * sum(dts)
