@@ -9,7 +9,8 @@
 //
 // Construction (smoothed aggregation of Vanek, Mandel and Brezina, written from its published
 // description):
-//   * strength of connection: |a_ij| >= theta sqrt(|a_ii a_jj|), theta = 0.08;
+//   * strength of connection: |a_ij| >= theta sqrt(|a_ii a_jj|), theta = 0.08 (0, i.e. the matrix graph,
+//     when no connection is strong: strongly diagonally dominant Helmholtz operators);
 //   * aggregation in node order (Morton order keeps aggregates compact): a node whose strong
 //     neighbours are all free starts an aggregate with them; remaining nodes join the
 //     aggregate of their strongest aggregated neighbour; what is left forms aggregates with
@@ -134,13 +135,13 @@ double lambda_max(const Csr& A, const std::vector<double>& dinv) {
 }
 
 // aggregate index per row (-1: no coarse unknown); returns the number of aggregates
-int32_t aggregate(const Csr& A, std::vector<int32_t>& agg) {
+int32_t aggregate(const Csr& A, std::vector<int32_t>& agg, double theta) {
   const int32_t n = A.n;
   std::vector<double> d(n);
   for (int32_t i = 0; i < n; ++i) d[i] = std::fabs(diag_of(A, i));
   auto strong = [&](int32_t i, int32_t e) {
     const int32_t j = A.ci[e];
-    return j != i && std::fabs(A.v[e]) >= kTheta * std::sqrt(d[i] * d[j]);
+    return j != i && A.v[e] != 0.0 && std::fabs(A.v[e]) >= theta * std::sqrt(d[i] * d[j]);
   };
   agg.assign(n, -2);  // -2 free, -1 isolated
   int32_t na = 0;
@@ -343,7 +344,10 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
       break;
     }
     std::vector<int32_t> agg;
-    const int32_t na = aggregate(A, agg);
+    int32_t na = aggregate(A, agg, kTheta);
+    // a strongly diagonally dominant matrix (a Helmholtz operator with a large shift on a
+    // coarse mesh) may have no strong connection at all: aggregate its graph instead
+    if (na <= 0 || na >= A.n) na = aggregate(A, agg, 0.0);
     if (na <= 0 || na >= A.n) return fail("AMG set-up: aggregation made no progress");
     std::vector<double> norm2(na, 0.0);
     for (int32_t i = 0; i < A.n; ++i)
