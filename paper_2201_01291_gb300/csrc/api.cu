@@ -41,7 +41,7 @@ struct avip_mesh {
   double *aval = nullptr, *gx = nullptr, *gy = nullptr, *sx = nullptr, *sy = nullptr;
   double *x = nullptr, *y = nullptr, *vol = nullptr, *dsq = nullptr, *dsqinv = nullptr, *lift = nullptr,
          *rhs_scale = nullptr;
-  double* dxmin = nullptr;
+  double* cw = nullptr;
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
@@ -194,6 +194,11 @@ DDArgs dd_args(const avip_mesh* h) {
   std::memset(&a, 0, sizeof(a));
   a.A = sell_view(h);
   a.ph = h->ph;
+  // Fourier limit: fourier dx^2 / D is smallest at the shortest side and the largest D
+  a.ph.dt_fourier = INFINITY;
+  for (int sp = 0; sp < h->ph.ns; ++sp)
+    if (h->ph.sp[sp].D > 0.0)
+      a.ph.dt_fourier = std::fmin(a.ph.dt_fourier, h->ph.fourier * (h->hm.dxmin_all * h->hm.dxmin_all) / h->ph.sp[sp].D);
   a.x = h->x;
   a.y = h->y;
   a.vol = h->vol;
@@ -208,7 +213,7 @@ DDArgs dd_args(const avip_mesh* h) {
   a.photo_psi = h->photo_psi;
   a.photo_S = h->photo_S;
   a.cell = h->cell;
-  a.dxmin = h->dxmin;
+  a.cw = h->cw;
   a.flen = h->flen;
   a.T = h->hm.T;
   a.nvmax = h->hm.nvmax;
@@ -473,7 +478,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   bool ok = upload(h, h->sl_ptr, m.sl_ptr) && upload(h, h->sl_w, m.sl_w) && upload(h, h->rlen, m.rlen) &&
             upload(h, h->col, m.col) && upload(h, h->aval, m.aval) && upload(h, h->gx, m.gx) &&
             upload(h, h->gy, m.gy) && upload(h, h->sx, m.sx) && upload(h, h->sy, m.sy) &&
-            upload(h, h->cell, m.cell) && upload(h, h->flen, m.flen) && upload(h, h->dxmin, m.dxmin) && upload(h, h->x, m.x, Np) &&
+            upload(h, h->cell, m.cell) && upload(h, h->flen, m.flen) && upload(h, h->cw, m.cw) && upload(h, h->x, m.x, Np) &&
             upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dsq, m.dsq, Np) && upload(h, h->dsqinv, m.dsqinv, Np) &&
             upload(h, h->lift, m.lift, Np) && upload(h, h->rhs_scale, m.rhs_scale, Np);
   // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere

@@ -38,6 +38,8 @@ struct HostMesh {
   std::vector<int32_t> cell;          // nvmax*T, new indices, counter-clockwise (SoA: v0[T], v1[T], ...;
                                       // v3 = -1 for the triangles of a hybrid mesh)
   std::vector<double> dxmin;          // T, shortest side
+  std::vector<double> cw;             // T, 1 / (n_v dxmin): |sum of the n_v nodal V| * cw = |V_cell| / dx
+  double dxmin_all = 0.0;             // shortest side of the mesh
   std::vector<int32_t> rlen;          // N (padded to nslices*32 with 0)
   std::vector<int32_t> flen;          // N (padded likewise): 1 + number of edge neighbours
   std::vector<int32_t> sl_ptr, sl_w;  // nslices
@@ -152,6 +154,7 @@ struct Physics {
   double src_params[5];   // {A, B, nu_att} or {A, B, A_eta, B_eta, beta_r} (AVIP_SRC_MORROW_LOWKE)
   double beta, cfl, fourier, a_diel, a_chem;
   double dt_fixed;
+  double dt_fourier;  // min over cells and species of fourier dx^2 / D (constant per mesh)
   SpeciesParams sp[AVIP_MAX_SPECIES];
 };
 
@@ -305,7 +308,7 @@ struct DDArgs {
   const double* photo_psi;  // ph.photo_terms solutions S_ph,j, each Npad long
   double* photo_S;        // per node: S_ph = sum_j S_ph,j
   const int32_t* cell;    // SoA v0[T], v1[T], v2[T] (, v3[T] when nvmax == 4; -1 for triangles)
-  const double* dxmin;
+  const double* cw;       // per cell 1 / (n_v dx_min)
   const int32_t* flen;    // per row: slots 1..flen-1 carry the mesh edges
   int32_t T;
   int32_t nvmax;

@@ -163,21 +163,25 @@ __global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int w
 }
 
 // ------------------------------------------------------------------------ time step
-__device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
-  const int c = bid * blockDim.x + threadIdx.x;
-  double cand = INFINITY;
-  if (c < a.T) {
+// Convective and dielectric limits over cells (section "Time step computation"), with the cell
+// velocity and conductivity the means of the n_v nodal values.  Each thread carries the largest
+// |V_cell| / dx (the sum of the nodal velocities times the per-cell weight 1/(n_v dx)) and the
+// largest conductivity over its cells and species, and divides once at the end:
+// min_c cfl dx / |V| = cfl / max_c |V| / dx, likewise for the dielectric limit.  The Fourier
+// limit, fourier dx^2 / D over cells and species, depends on the mesh only (ph.dt_fourier).
+__device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid, int nblocks) {
+  double vmax = 0.0, smax = 0.0;
+  const int ns = a.ph.ns;
+  for (int c = bid * blockDim.x + threadIdx.x; c < a.T; c += nblocks * blockDim.x) {
     const int n0 = a.cell[c], n1 = a.cell[a.T + c], n2 = a.cell[2 * a.T + c];
     const int n3 = a.nvmax == 4 ? a.cell[3 * a.T + c] : -1;  // -1: triangle
     const bool quad = n3 >= 0;
-    const double nvd = quad ? 4.0 : 3.0;
-    const double dx = a.dxmin[c];
-    const int ns = a.ph.ns;
+    const double w = a.cw[c];
+    const double inv_nv = quad ? 0.25 : (1.0 / 3.0);
     double sigma = 0.0;
 #pragma unroll
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
       if (s < ns) {
-        const SpeciesParams& sp = a.ph.sp[s];
         double vx, vy;
         if (a.ph.dd_fp32) {  // FP32 velocities, FP64 candidate and reduction
           const float* d = a.ndat32 + (size_t)s * a.Npad * 4;
@@ -196,24 +200,22 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid) {
             vy += d[4 * n3 + 3];
           }
         }
-        vx /= nvd;
-        vy /= nvd;
-        const double vm = sqrt(vx * vx + vy * vy);
-        if (vm > 0.0) cand = fmin(cand, a.ph.cfl * dx / vm);
-        if (sp.D > 0.0) cand = fmin(cand, a.ph.fourier * (dx * dx) / sp.D);
+        vmax = fmax(vmax, sqrt(vx * vx + vy * vy) * w);
         const double* nm = a.nm + (size_t)s * a.Npad;
         double cell = nm[n0] + nm[n1] + nm[n2];
         if (quad) cell += nm[n3];
-        cell /= nvd;
-        sigma += fabs(sp.q * kECharge * cell);
+        sigma += fabs(a.ph.sp[s].q * kECharge * cell);
       }
     }
-    if (sigma > 0.0) cand = fmin(cand, a.ph.a_diel * kEps0 / sigma);
+    smax = fmax(smax, sigma * inv_nv);
   }
+  double cand = a.ph.dt_fourier;
+  if (vmax > 0.0) cand = fmin(cand, a.ph.cfl / vmax);
+  if (smax > 0.0) cand = fmin(cand, a.ph.a_diel * kEps0 / smax);
   block_min_to_global(cand, &a.sc->dt_bits);
 }
 
-__global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) { dt_cells_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kDDThreads) dt_cells_kernel(DDArgs a) { dt_cells_body(a, blockIdx.x, gridDim.x); }
 
 // ------------------------------------------------------------------------ fluxes + update
 struct EdgeEnd {
@@ -731,7 +733,7 @@ __global__ void __launch_bounds__(kDDThreads) dt_cells_batch_kernel(const DDArgs
   const int k = batch_instance(bpref, count, blockIdx.x);
   const DDArgs& a = args[k];
   if (a.ph.dt_fixed > 0.0) return;
-  dt_cells_body(a, blockIdx.x - __ldg(bpref + k));
+  dt_cells_body(a, blockIdx.x - __ldg(bpref + k), __ldg(bpref + k + 1) - __ldg(bpref + k));
 }
 __global__ void __launch_bounds__(kDDThreads, 2) flux_update_batch_kernel(const DDArgs* __restrict__ args,
                                                                         const int32_t* __restrict__ bpref, int count) {
@@ -774,7 +776,9 @@ cudaError_t launch_photo_add(const DDArgs& a, int with_dt, cudaStream_t st) {
 }
 
 cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
-  dt_cells_kernel<<<nblk(a.T), kDDThreads, 0, st>>>(a);
+  // a few cells per thread: 8 resident blocks on each of the 152 SMs
+  const int blocks = nblk(a.T) < 152 * 8 ? nblk(a.T) : 152 * 8;
+  dt_cells_kernel<<<blocks, kDDThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st) {

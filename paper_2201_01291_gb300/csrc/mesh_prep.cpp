@@ -226,6 +226,12 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
     }
     m.dxmin[c] = l;
   }
+  m.cw.resize(T);
+  m.dxmin_all = INFINITY;
+  for (int32_t c = 0; c < T; ++c) {
+    m.cw[c] = 1.0 / ((double)nv[c] * m.dxmin[c]);
+    m.dxmin_all = std::min(m.dxmin_all, m.dxmin[c]);
+  }
   m.cell.assign((size_t)m.nvmax * T, -1);
   for (int32_t c = 0; c < T; ++c)
     for (int k = 0; k < nv[c]; ++k) m.cell[(size_t)k * T + c] = tv[4 * (size_t)c + k];
