@@ -106,3 +106,21 @@ def test_photo_error_paths(avip):
     with pytest.raises(avip.AvipError):
         avip.Batch([m])
     m.close()
+
+
+def test_photo_on_hybrid_mesh_with_chemistry_and_ramp(avip):
+    """Photoionisation with the three-species chemistry and the voltage ramp on a hybrid
+    triangle/quadrangle mesh (the second case of smoke())."""
+    q = W.morrow_lowke_problem(23, 21, 5e-3, 5e-3, 5e3, seed=3, needle_len=1e-3, quad_fraction=0.5, v_rise=2e-10)
+    q.species[0].n0[:] = W.gaussian(q.xy, 2.5e-3, 3.5e-3, 3e-4, 1e19, 1e15)
+    q.species[1].n0[:] = q.species[0].n0
+    q = W.dataclasses.replace(q, photo=W.photo_air(p_torr=760.0 * 300.0 / 1000.0))
+    o = O.Oracle(q)
+    n_ref, phi_ref, _ = o.run(12)
+    m = avip.Mesh(q, rtol=1e-14)
+    st = m.run(12)
+    assert st["status"] == 0
+    for s in range(3):
+        assert normwise(m.density(s), n_ref[s]) <= TOL, s
+    assert normwise(m.photo(), o.last_photo) <= TOL
+    m.close()
