@@ -462,10 +462,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
 struct GridOps {
   FlagSync& fs;
   double* smem;
-  __device__ bool barrier() {
-    double d[1] = {0.0};
-    return grid_allsum<1>(d, fs, smem);
-  }
+  __device__ bool barrier() { return grid_barrier(fs); }
   template <int NV>
   __device__ bool sum(double (&v)[NV]) {
     return grid_allsum<NV>(v, fs, smem);

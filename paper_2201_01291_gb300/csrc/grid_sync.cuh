@@ -217,4 +217,38 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], FlagSync& fs, doubl
   return grid_allsum<NV, 0>(v, dummy, fs, smem, NoEpilogue());
 }
 
+// Grid barrier without a sum: the block's writes are ordered before one release increment of
+// the same monotone arrival counter by thread 0, which then waits (acquire, bounded) for
+// seq * gridDim.x arrivals.  It shares the counter and the sequence number with grid_allsum,
+// whose partials it does not touch; a reduction k and the next one of the same buffer parity,
+// k + 2, are then separated by this barrier k + 1, which no block passes before every block has
+// finished reading reduction k.  Returns false if the wait was abandoned.
+__device__ __forceinline__ bool grid_barrier(FlagSync& fs) {
+  const unsigned seq = ++fs.seq;
+  AllsumScratch& scr = allsum_scratch();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const int nb = gridDim.x;
+    if (nb > 1) {
+      red_add_release_u32(fs.flags, 1u);
+      const unsigned target = seq * (unsigned)nb;
+      const unsigned long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(fs.flags) < target) {
+        if ((++spins & 63u) == 0) {
+          if (*((volatile int*)&fs.gs->abort) || global_timer_ns() - t0 > kSpinLimitNs) {
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    if (!ok) atomicExch(&fs.gs->abort, 1);
+    scr.ok = ok;
+  }
+  __syncthreads();
+  return scr.ok != 0;
+}
+
 }  // namespace avip
