@@ -193,7 +193,7 @@ NCU_DRAM_BYTES_PER_ITER = {
     2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
                                             "launch's iterations (L2-resident working set)"),
     # pcg_amg_kernel<512>: one 16-iteration solve
-    8: ((2633.231e6 + 509.570e6) / 16.0, "ncu DRAM read+write of a 16-iteration solve scaled to the launch's "
+    8: ((2631.223e6 + 501.175e6) / 16.0, "ncu DRAM read+write of a 16-iteration solve scaled to the launch's "
                                          "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
 }
 
