@@ -241,8 +241,12 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
  * densities).  out[n_nodes] doubles. */
 int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out);
 
-/* Checkpoint / resume.  state layout: [n_species * n_nodes densities][n_nodes phi][t],
- * caller numbering; size = (n_species + 1) * n_nodes + 1 doubles. */
+/* Checkpoint / resume.  state layout, caller numbering: [n_species * n_nodes densities]
+ * [n_nodes phi][t][n_nodes phi_{n-1}][n_nodes phi_{n-2}][h], where phi_{n-1}, phi_{n-2} and
+ * h (0, 1 or 2 of them valid) are the history of the Poisson solver's initial-guess predictor
+ * (quadratic extrapolation of the last potentials), so that a resumed run repeats the
+ * uninterrupted one bit for bit; size = (n_species + 3) * n_nodes + 2 doubles.  state_set
+ * returns AVIP_EINVAL for h outside {0, 1, 2}, AVIP_ENAN for a non-finite entry. */
 int state_size(avip_mesh_t h, int64_t* n_doubles);
 int state_get(avip_mesh_t h, double* host_state);
 int state_set(avip_mesh_t h, const double* host_state);

@@ -183,11 +183,12 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
     if (i >= N) continue;
-    a.x[i] = a.dsq[i] * a.phi[i];
+    a.x[i] = a.dsq[i] * predict_phi(a, i, hist);
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
@@ -295,6 +296,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
     }
     if (leader) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);
@@ -323,11 +325,12 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
   float* __restrict__ z32 = a.z32;
 
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
     if (i >= N) continue;
-    a.x[i] = a.dsq[i] * a.phi[i];
+    a.x[i] = a.dsq[i] * predict_phi(a, i, hist);
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
@@ -447,6 +450,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
     }
     if (leader) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_outer = outer;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;

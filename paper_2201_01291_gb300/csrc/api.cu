@@ -42,6 +42,7 @@ struct avip_mesh {
   double *x = nullptr, *y = nullptr, *vol = nullptr, *dsq = nullptr, *dsqinv = nullptr, *lift = nullptr,
          *rhs_scale = nullptr;
   double* cw = nullptr;
+  double *phi1 = nullptr, *phi2 = nullptr;  // the two previous potentials (predictor)
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
@@ -161,6 +162,8 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.ns = h->ph.ns;
   for (int s = 0; s < AVIP_MAX_SPECIES; ++s) a.q[s] = h->ph.sp[s].q;
   a.phi = h->phi;
+  a.phi1 = h->phi1;
+  a.phi2 = h->phi2;
   a.x = h->xs;
   a.b = h->b;
   a.r = h->r;
@@ -266,6 +269,7 @@ PcgArgs photo_args(const avip_mesh* h, int j) {
   a.lift = h->photo_zero;
   a.rhs_src = h->photo_I;
   a.phi = h->photo_psi + (size_t)j * h->Npad;
+  a.phi1 = a.phi2 = nullptr;  // plain warm start
   a.res = h->sc_aux;
   a.v_rise = 0.0;
   a.amg = t.amg;
@@ -485,7 +489,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   std::vector<double> phi0(Np, 0.0);
   for (int32_t i = 0; i < m.N; ++i)
     if (m.bc[i] == 1) phi0[i] = h->opts.v_rise > 0 ? 0.0 : m.lift[i];  // a ramp starts at 0 V
-  ok = ok && upload(h, h->phi, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
+  ok = ok && upload(h, h->phi, phi0) && upload(h, h->phi1, phi0) && upload(h, h->phi2, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
        zalloc(h, h->p, Np) && zalloc(h, h->q, Np) && zalloc(h, h->nbuf, 2 * AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->ndat, 4 * AVIP_MAX_SPECIES * Np) && zalloc(h, h->nm, AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->src, AVIP_MAX_SPECIES * Np) && zalloc(h, h->Ex, Np) && zalloc(h, h->Ey, Np);
@@ -983,7 +987,7 @@ int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out) {
 
 int state_size(avip_mesh_t h, int64_t* n) {
   if (!h || !n) return AVIP_EINVAL;
-  *n = (int64_t)(h->ph.ns + 1) * h->hm.N + 1;
+  *n = (int64_t)(h->ph.ns + 3) * h->hm.N + 2;
   return AVIP_OK;
 }
 
@@ -1000,6 +1004,11 @@ int state_get(avip_mesh_t h, double* out) {
   rc = read_scalars(h, sc);
   if (rc) return rc;
   out[(size_t)(h->ph.ns + 1) * N] = sc.t;
+  // the predictor's history: phi_{n-1}, phi_{n-2} and how many of them are valid
+  double* hist = out + (size_t)(h->ph.ns + 1) * N + 1;
+  if ((rc = to_host_perm(h, h->phi1, hist)) != AVIP_OK) return rc;
+  if ((rc = to_host_perm(h, h->phi2, hist + N)) != AVIP_OK) return rc;
+  hist[2 * (size_t)N] = (double)sc.phi_hist;
   return AVIP_OK;
 }
 
@@ -1023,7 +1032,22 @@ int state_set(avip_mesh_t h, const double* in) {
   }
   if (e != cudaSuccess) return cuda_status(e);
   const double t = in[(size_t)(h->ph.ns + 1) * N];
-  e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  const double* hist = in + (size_t)(h->ph.ns + 1) * N + 1;
+  const double hn = hist[2 * (size_t)N];
+  if (!(hn == 0.0 || hn == 1.0 || hn == 2.0)) return AVIP_EINVAL;
+  const int32_t hv = (int32_t)hn;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int32_t i = 0; i < N; ++i) {
+      tmp[i] = hist[(size_t)k * N + h->hm.perm[i]];
+      if (!std::isfinite(tmp[i])) return AVIP_ENAN;
+    }
+    e = cudaMemcpyAsync(k == 0 ? h->phi1 : h->phi2, tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h->sc->phi_hist, &hv, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return cuda_status(e);
 }

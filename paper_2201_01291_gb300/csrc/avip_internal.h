@@ -185,6 +185,7 @@ struct DevScalars {
   int32_t run_iters_total;
   int32_t run_iters_max;
   int32_t pcg_outer;            // refinement steps of the last mixed-precision solve
+  int32_t phi_hist;             // earlier potentials kept for the predictor (0, 1 or 2)
   double run_dt_min, run_dt_max, run_relres_max;
 };
 
@@ -215,6 +216,8 @@ struct PcgArgs {
   DevScalars* res;         // where the solve reports iterations / residual (sc, or the
                            // auxiliary block of the photoionisation solves)
   const double* rhs_src;   // non-null: b = rhs_scale * rhs_src + lift instead of the charge density
+  double* phi1;            // non-null: the two previous solutions phi_{n-1}, phi_{n-2} (predictor)
+  double* phi2;
   double rtol;
   double v_rise;          // > 0: the Dirichlet lift is scaled by min(t / v_rise, 1) (voltage ramp)
   int32_t max_iter;
@@ -280,6 +283,27 @@ __device__ __forceinline__ double dirichlet_gain(const PcgArgs& a) {
   if (!(a.v_rise > 0.0)) return 1.0;
   const double t = *((volatile const double*)&a.sc->t);
   return t >= a.v_rise ? 1.0 : t / a.v_rise;
+}
+
+// Number of earlier solutions available to the predictor (read by every block at entry, before
+// the solve's first barrier; the solve's leader advances it at the end).
+__device__ __forceinline__ int history_length(const PcgArgs& a) {
+  return a.phi1 ? *((volatile const int*)&a.sc->phi_hist) : 0;
+}
+
+// Initial guess of row i from the last solutions: the quadratic extrapolation
+// 3 phi_n - 3 phi_{n-1} + phi_{n-2} once two earlier solutions exist, the linear one with one,
+// phi_n otherwise; the row's history is shifted at the same time (each row is owned by one
+// thread of the solve).
+__device__ __forceinline__ double predict_phi(const PcgArgs& a, int i, int hist) {
+  const double p0 = a.phi[i];
+  if (!a.phi1) return p0;
+  const double p1 = a.phi1[i], p2 = a.phi2[i];
+  a.phi2[i] = p1;
+  a.phi1[i] = p0;
+  if (hist >= 2) return fma(3.0, p0 - p1, p2);
+  if (hist == 1) return fma(2.0, p0, -p1);
+  return p0;
 }
 
 // A solve is skipped when an earlier stage of the run left non-finite data (AVIP_ENAN) or a

@@ -63,11 +63,12 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int sl = gwarp; sl < nsl; sl += nwarps) {
     const int i = sl * kSlice + lane;
     if (i >= N) continue;
-    x[i] = a.dsq[i] * a.phi[i];
+    x[i] = a.dsq[i] * predict_phi(a, i, hist);
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
@@ -219,6 +220,7 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);

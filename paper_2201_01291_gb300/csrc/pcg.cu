@@ -51,11 +51,12 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int s = gwarp; s < nsl; s += nwarps) {
     const int i = s * kSlice + lane;
     if (i >= N) continue;
-    a.x[i] = a.dsq[i] * a.phi[i];
+    a.x[i] = a.dsq[i] * predict_phi(a, i, hist);
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);
@@ -239,12 +241,13 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
 #pragma unroll
   for (int j = 0; j < MAXS; ++j) {
     const int i = (gwarp * MAXS + j) * kSlice + lane;
     if (rl[j] == 0) continue;
-    x[j] = a.dsq[i] * a.phi[i];
+    x[j] = a.dsq[i] * predict_phi(a, i, hist);
     a.x[i] = x[j];
     double b;
     if (a.use_density_rhs) {
@@ -369,6 +372,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);

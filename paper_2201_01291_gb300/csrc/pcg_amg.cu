@@ -92,11 +92,12 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   double dummy = 0.0;
 
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int sl = gwarp; sl < nsl; sl += nwarps) {
     const int i = sl * kSlice + lane;
     if (i >= N) continue;
-    x[i] = a.dsq[i] * a.phi[i];
+    x[i] = a.dsq[i] * predict_phi(a, i, hist);
     double b;
     if (a.use_density_rhs) {
       double rho = 0.0;
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.res->pcg_iters = it;
+      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);

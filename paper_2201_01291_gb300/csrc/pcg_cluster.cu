@@ -146,12 +146,13 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
     }
   }
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int li = threadIdx.x; li < R; li += blockDim.x) {
     const int i = s0 * kSlice + li;
     double x = 0.0, b = 0.0;
     if (i < N) {
-      x = a.dsq[i] * a.phi[i];
+      x = a.dsq[i] * predict_phi(a, i, hist);
       if (a.use_density_rhs) {
         double rho = 0.0;
         if (a.rhs_src)
@@ -268,6 +269,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
   }
   if (rank == 0 && threadIdx.x == 0) {
     a.res->pcg_iters = it;
+    if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
     a.res->pcg_status = status;
     a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
     a.res->pcg_bnorm = sqrt(bb[0]);
@@ -405,12 +407,13 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
     }
   }
   const double gain = dirichlet_gain(a);
+  const int hist = history_length(a);
   double bb[1] = {0.0};
   for (int li = threadIdx.x; li < R; li += blockDim.x) {
     const int i = s0 * kSlice + li;
     double x = 0.0;
     if (i < N) {
-      x = a.dsq[i] * a.phi[i];
+      x = a.dsq[i] * predict_phi(a, i, hist);
       double b;
       if (a.use_density_rhs) {
         double rho = 0.0;
@@ -542,6 +545,7 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
   }
   if (rank == 0 && threadIdx.x == 0) {
     a.res->pcg_iters = it;
+    if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
     a.res->pcg_outer = outer;
     a.res->pcg_status = status;
     a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
