@@ -203,8 +203,8 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
  *     zero normal derivative on the other boundaries,
  * are solved (vertex-centred: (K + kappa_j^2 V) S_j = a_j c V I_ion with the Poisson matrix K and
  * the dual volumes V) by the handle's own solver kind with the term's own diagonal scaling and,
- * for the AMG kinds, its own hierarchy (built here, once), warm-started from the previous
- * step; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
+ * for the AMG kinds, its own hierarchy (built here, once), started from the quadratic
+ * extrapolation of its last three solutions; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
  * source_set) before the time step and the update, and enters the chemical time-step limit.
  *   a[n_terms]     A_j p_O2^2 (1/m^2)  — with A_j, lambda_j the coefficients of the fit;
  *   kappa[n_terms] lambda_j p_O2 (1/m), > 0;
@@ -245,7 +245,9 @@ int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out);
  * [n_nodes phi][t][n_nodes phi_{n-1}][n_nodes phi_{n-2}][h], where phi_{n-1}, phi_{n-2} and
  * h (0, 1 or 2 of them valid) are the history of the Poisson solver's initial-guess predictor
  * (quadratic extrapolation of the last potentials), so that a resumed run repeats the
- * uninterrupted one bit for bit; size = (n_species + 3) * n_nodes + 2 doubles.  state_set
+ * uninterrupted one bit for bit (with photoionisation the Helmholtz solutions and their
+ * histories are not part of the state: a resumed run then agrees within the solve
+ * tolerance); size = (n_species + 3) * n_nodes + 2 doubles.  state_set
  * returns AVIP_EINVAL for h outside {0, 1, 2}, AVIP_ENAN for a non-finite entry. */
 int state_size(avip_mesh_t h, int64_t* n_doubles);
 int state_get(avip_mesh_t h, double* host_state);

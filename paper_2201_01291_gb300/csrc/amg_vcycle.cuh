@@ -296,7 +296,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
     }
     if (leader) {
       a.res->pcg_iters = it;
-      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
+      if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);
@@ -450,7 +450,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
     }
     if (leader) {
       a.res->pcg_iters = it;
-      if (a.phi1) a.sc->phi_hist = a.sc->phi_hist < 2 ? a.sc->phi_hist + 1 : 2;
+      if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
       a.res->pcg_outer = outer;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;

@@ -69,6 +69,7 @@ struct avip_mesh {
   };
   std::vector<PhotoTerm> photo;
   double *photo_psi = nullptr, *photo_I = nullptr, *photo_S = nullptr, *photo_zero = nullptr;
+  int32_t* photo_hist = nullptr;  // per term: earlier solutions kept for the predictor
   DevScalars* sc_aux = nullptr;
   int32_t Npad = 0;
   PcgPlan plan;
@@ -164,6 +165,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.phi = h->phi;
   a.phi1 = h->phi1;
   a.phi2 = h->phi2;
+  a.hist = &h->sc->phi_hist;
   a.x = h->xs;
   a.b = h->b;
   a.r = h->r;
@@ -269,7 +271,9 @@ PcgArgs photo_args(const avip_mesh* h, int j) {
   a.lift = h->photo_zero;
   a.rhs_src = h->photo_I;
   a.phi = h->photo_psi + (size_t)j * h->Npad;
-  a.phi1 = a.phi2 = nullptr;  // plain warm start
+  a.phi1 = h->photo_psi + (size_t)(h->ph.photo_terms + 2 * j) * h->Npad;  // own history
+  a.phi2 = a.phi1 + h->Npad;
+  a.hist = h->photo_hist + j;
   a.res = h->sc_aux;
   a.v_rise = 0.0;
   a.amg = t.amg;
@@ -747,7 +751,9 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
   const HostMesh& m = h->hm;
   const size_t Np = (size_t)h->Npad;
   const bool amg = kind == 8 || kind == 9 || kind == 11;
-  bool ok = zalloc(h, h->photo_psi, (size_t)n_terms * Np) && zalloc(h, h->photo_I, Np) &&
+  // solutions of the terms, then two history vectors per term
+  bool ok = zalloc(h, h->photo_psi, (size_t)3 * n_terms * Np) && zalloc(h, h->photo_hist, n_terms) &&
+            zalloc(h, h->photo_I, Np) &&
             zalloc(h, h->photo_S, Np) && zalloc(h, h->photo_zero, Np) && zalloc(h, h->sc_aux, 1);
   for (int j = 0; j < n_terms && ok; ++j) {
     // (K + kappa_j^2 V) S_j = c a_j V I with S_j = 0 on the Dirichlet nodes: the unscaled

@@ -218,6 +218,7 @@ struct PcgArgs {
   const double* rhs_src;   // non-null: b = rhs_scale * rhs_src + lift instead of the charge density
   double* phi1;            // non-null: the two previous solutions phi_{n-1}, phi_{n-2} (predictor)
   double* phi2;
+  int32_t* hist;           // how many of them are valid (0, 1, 2); advanced by the solve
   double rtol;
   double v_rise;          // > 0: the Dirichlet lift is scaled by min(t / v_rise, 1) (voltage ramp)
   int32_t max_iter;
@@ -288,7 +289,7 @@ __device__ __forceinline__ double dirichlet_gain(const PcgArgs& a) {
 // Number of earlier solutions available to the predictor (read by every block at entry, before
 // the solve's first barrier; the solve's leader advances it at the end).
 __device__ __forceinline__ int history_length(const PcgArgs& a) {
-  return a.phi1 ? *((volatile const int*)&a.sc->phi_hist) : 0;
+  return a.phi1 ? *((volatile const int*)a.hist) : 0;
 }
 
 // Initial guess of row i from the last solutions: the quadratic extrapolation
