@@ -301,7 +301,9 @@ def run_ours(args, rank, world, local_rank):
             for key in kernel_ms:
                 kernel_ms[key] += ms[key]
             iters += st["pcg_iters_total"]
-            launches += 5 + (len(problem.photo.a) + 1 if problem.photo is not None else 0)
+            # pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation
+            launches += 5 + (1 if args.precision == "fp64" else 0) + \
+                (len(problem.photo.a) + 1 if problem.photo is not None else 0)
         ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:

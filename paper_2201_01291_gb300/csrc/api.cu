@@ -42,6 +42,8 @@ struct avip_mesh {
   double *x = nullptr, *y = nullptr, *vol = nullptr, *dsq = nullptr, *dsqinv = nullptr, *lift = nullptr,
          *rhs_scale = nullptr;
   double* cw = nullptr;
+  int32_t *e_lo = nullptr, *e_hi = nullptr, *slot_eid = nullptr;  // edge list (flux once per edge)
+  double *e_sx = nullptr, *e_sy = nullptr, *eflux = nullptr;
   double *phi1 = nullptr, *phi2 = nullptr;  // the two previous potentials (predictor)
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
@@ -219,6 +221,13 @@ DDArgs dd_args(const avip_mesh* h) {
   a.photo_S = h->photo_S;
   a.cell = h->cell;
   a.cw = h->cw;
+  a.e_lo = h->e_lo;
+  a.e_hi = h->e_hi;
+  a.e_sx = h->e_sx;
+  a.e_sy = h->e_sy;
+  a.slot_eid = h->slot_eid;
+  a.eflux = h->eflux;
+  a.E = (int32_t)h->hm.e_lo.size();
   a.flen = h->flen;
   a.T = h->hm.T;
   a.nvmax = h->hm.nvmax;
@@ -486,7 +495,9 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   bool ok = upload(h, h->sl_ptr, m.sl_ptr) && upload(h, h->sl_w, m.sl_w) && upload(h, h->rlen, m.rlen) &&
             upload(h, h->col, m.col) && upload(h, h->aval, m.aval) && upload(h, h->gx, m.gx) &&
             upload(h, h->gy, m.gy) && upload(h, h->sx, m.sx) && upload(h, h->sy, m.sy) &&
-            upload(h, h->cell, m.cell) && upload(h, h->flen, m.flen) && upload(h, h->cw, m.cw) && upload(h, h->x, m.x, Np) &&
+            upload(h, h->cell, m.cell) && upload(h, h->flen, m.flen) && upload(h, h->cw, m.cw) && upload(h, h->e_lo, m.e_lo, 1) && upload(h, h->e_hi, m.e_hi, 1) &&
+            upload(h, h->e_sx, m.e_sx, 1) && upload(h, h->e_sy, m.e_sy, 1) && upload(h, h->slot_eid, m.slot_eid) &&
+            zalloc(h, h->eflux, (size_t)AVIP_MAX_SPECIES * std::max<size_t>(m.e_lo.size(), 1)) && upload(h, h->x, m.x, Np) &&
             upload(h, h->y, m.y, Np) && upload(h, h->vol, m.vol, Np) && upload(h, h->dsq, m.dsq, Np) && upload(h, h->dsqinv, m.dsqinv, Np) &&
             upload(h, h->lift, m.lift, Np) && upload(h, h->rhs_scale, m.rhs_scale, Np);
   // initial potential: Dirichlet values on Dirichlet rows, zero elsewhere
@@ -1219,6 +1230,7 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
   for (int k = 0; k < count; ++k) {
     pa[k] = pcg_args(b->m[k]);
     da[k] = dd_args(b->m[k]);
+    da[k].eflux = nullptr;  // batched flux kernel: each row evaluates its edges
     da[k].partials = b->m[k]->qpart;
     order[k] = k;
     npref[k + 1] = npref[k] + (b->m[k]->hm.N + T - 1) / T;

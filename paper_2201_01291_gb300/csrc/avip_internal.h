@@ -46,6 +46,10 @@ struct HostMesh {
   std::vector<int32_t> col;           // nelem
   std::vector<double> aval, gx, gy, sx, sy;  // nelem (aval: D^-1/2 K D^-1/2)
   std::vector<double> dsq, dsqinv;    // N: sqrt(K_ii) and its inverse (symmetric Jacobi scaling)
+  // edges (lo < hi, ordered by lo then hi) with the normal S oriented lo -> hi, and per SELL
+  // element of an edge slot the edge id, bit 31 set when the row is the edge's hi end
+  std::vector<int32_t> e_lo, e_hi, slot_eid;
+  std::vector<double> e_sx, e_sy;
   std::vector<double> lift;           // N: free rows -sum_{k in D} K_ik phi_D,k ; Dirichlet rows phi_D (scaled by 1/sqrt(K_ii))
   std::vector<double> rhs_scale;      // N: free rows e V_i / eps0 ; Dirichlet rows 0 (scaled by 1/sqrt(K_ii))
 };
@@ -334,6 +338,15 @@ struct DDArgs {
   double* photo_S;        // per node: S_ph = sum_j S_ph,j
   const int32_t* cell;    // SoA v0[T], v1[T], v2[T] (, v3[T] when nvmax == 4; -1 for triangles)
   const double* cw;       // per cell 1 / (n_v dx_min)
+  // edge fluxes computed once per edge (FP64 single-instance path; eflux == nullptr: each
+  // row evaluates the fluxes of its edges itself)
+  const int32_t* e_lo;
+  const int32_t* e_hi;
+  const double* e_sx;
+  const double* e_sy;
+  const int32_t* slot_eid;
+  double* eflux;          // [species][E]: flux from lo to hi
+  int32_t E;
   const int32_t* flen;    // per row: slots 1..flen-1 carry the mesh edges
   int32_t T;
   int32_t nvmax;

@@ -464,6 +464,55 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
       }
     }
   }
+  // ---- edge list for the flux-per-edge kernel: each edge once, from its lo row
+  {
+    std::vector<int32_t> first(N + 1, 0);
+    for (int32_t i = 0; i < N; ++i) {
+      int32_t c = 0;
+      for (int32_t k = 1; k < fl[i]; ++k)
+        if (cols[rowptr[i] + k] > i) ++c;
+      first[i + 1] = first[i] + c;
+    }
+    const int32_t E = first[N];
+    m.e_lo.resize(E);
+    m.e_hi.resize(E);
+    m.e_sx.resize(E);
+    m.e_sy.resize(E);
+    m.slot_eid.assign(off, 0);
+    for (int32_t i = 0; i < N; ++i) {
+      int32_t e = first[i];
+      for (int32_t k = 1; k < fl[i]; ++k) {
+        const int32_t j = cols[rowptr[i] + k];
+        if (j > i) {
+          m.e_lo[e] = i;
+          m.e_hi[e] = j;
+          m.e_sx[e] = Sx[rowptr[i] + k];
+          m.e_sy[e] = Sy[rowptr[i] + k];
+          ++e;
+        }
+      }
+    }
+    // slot -> edge: the lo row's edges are found by position, the hi row's by search in the
+    // lo row's (ascending) edge range
+    for (int32_t i = 0; i < N; ++i) {
+      const int32_t s = i / kSlice, l = i % kSlice;
+      int32_t e = first[i];
+      for (int32_t k = 1; k < fl[i]; ++k) {
+        const int32_t j = cols[rowptr[i] + k];
+        int32_t id;
+        if (j > i) {
+          id = e++;
+        } else {
+          const int32_t* b = m.e_hi.data() + first[j];
+          const int32_t* f = m.e_hi.data() + first[j + 1];
+          const int32_t* p = std::lower_bound(b, f, i);
+          if (p == f || *p != i) return fail("internal: edge list inconsistent");
+          id = (int32_t)(p - m.e_hi.data()) | (int32_t)0x80000000u;
+        }
+        m.slot_eid[(int64_t)m.sl_ptr[s] + (int64_t)k * kSlice + l] = id;
+      }
+    }
+  }
   return AVIP_OK;
 }
 
