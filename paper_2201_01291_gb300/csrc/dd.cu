@@ -315,7 +315,22 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
         me[s] = EdgeEnd{n[(size_t)s * a.Npad + i], g.x, g.y, v.x, v.y, xi, yi};
       }
     }
-    for (int k = 1; k < rl; ++k) {
+    if (a.eflux) {
+      // fluxes already evaluated once per edge (lo -> hi), gathered in the same slot order
+      for (int k = 1; k < rl; ++k) {
+        const int32_t v = __ldg(a.slot_eid + base + k * kSlice);
+        const bool lo_is_me = v >= 0;
+        const int id = v & 0x7fffffff;
+#pragma unroll
+        for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+          if (s < ns) {
+            const double F = a.eflux[(size_t)s * a.E + id];
+            R[s] = lo_is_me ? R[s] - F : R[s] + F;
+          }
+        }
+      }
+    }
+    for (int k = 1; k < (a.eflux ? 0 : rl); ++k) {
       const int e = base + k * kSlice;
       const int j = __ldg(a.A.col + e);
       const double Sx = __ldg(a.A.sx + e), Sy = __ldg(a.A.sy + e);
@@ -380,6 +395,35 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
 }
 
 __global__ void __launch_bounds__(kDDThreads, 2) flux_update_kernel(DDArgs a) { flux_update_body(a, blockIdx.x); }
+
+// One thread per edge (lo, hi): the flux of every species from lo to hi through the edge's dual
+// face, the same function of the same operands as in flux_update_body's per-row evaluation, so
+// both ends receive identical values.
+__global__ void __launch_bounds__(kDDThreads) edge_flux_kernel(DDArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  const int ns = a.ph.ns;
+  const double dt = a.ph.dt_fixed > 0.0 ? a.ph.dt_fixed : __longlong_as_double((long long)a.sc->dt_bits);
+  const double* n = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
+  const int lo = __ldg(a.e_lo + e), hi = __ldg(a.e_hi + e);
+  const double Sx = __ldg(a.e_sx + e), Sy = __ldg(a.e_sy + e);
+  const double xl = a.x[lo], yl = a.y[lo], xh = a.x[hi], yh = a.y[hi];
+  const bool use_sg = a.ph.scheme == AVIP_FLUX_SG;
+  SgGeo geo;
+  if (use_sg) geo = sg_geometry(xh - xl, yh - yl, Sx, Sy);
+#pragma unroll
+  for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
+    if (s < ns) {
+      const double2* dl = reinterpret_cast<const double2*>(a.ndat + ((size_t)s * a.Npad + lo) * 4);
+      const double2* dh = reinterpret_cast<const double2*>(a.ndat + ((size_t)s * a.Npad + hi) * 4);
+      const double2 gl = dl[0], vl = dl[1], gh = dh[0], vh = dh[1];
+      const EdgeEnd L{n[(size_t)s * a.Npad + lo], gl.x, gl.y, vl.x, vl.y, xl, yl};
+      const EdgeEnd H{n[(size_t)s * a.Npad + hi], gh.x, gh.y, vh.x, vh.y, xh, yh};
+      a.eflux[(size_t)s * a.E + e] =
+          edge_flux(L, H, Sx, Sy, a.ph.sp[s].D, dt, a.ph.beta, a.ph.limiter, use_sg ? &geo : nullptr);
+    }
+  }
+}
 
 // Single block: charge in block order, time, parity, statistics; re-arm the dt minimum.
 __device__ __forceinline__ void finalize_body(DevScalars* sc, const double* partials, int nparts) {
@@ -782,10 +826,12 @@ cudaError_t launch_dt_cells(const DDArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st) {
-  if (a.ph.dd_fp32)
+  if (a.ph.dd_fp32) {
     flux_update32_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
-  else
+  } else {
+    if (a.eflux && a.E > 0) edge_flux_kernel<<<nblk(a.E), kDDThreads, 0, st>>>(a);
     flux_update_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st) {
