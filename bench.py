@@ -192,8 +192,8 @@ NCU_DRAM_BYTES_PER_ITER = {
     # pcg_fp64_res_kernel: 300-iteration capture, L2-resident working set
     2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
                                             "launch's iterations (L2-resident working set)"),
-    # pcg_amg_kernel<512>: one 16-iteration solve
-    8: ((2631.223e6 + 501.175e6) / 16.0, "ncu DRAM read+write of a 16-iteration solve scaled to the launch's "
+    # pcg_amg_kernel<512>: one 21-iteration solve
+    8: ((3429.264e6 + 682.181e6) / 21.0, "ncu DRAM read+write of a 21-iteration solve scaled to the launch's "
                                          "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
 }
 
