@@ -145,7 +145,9 @@ int avip_opts_default(avip_opts* o);
 /* Build a mesh handle.
  *   xy[2*n_nodes]   node coordinates, interleaved (x0,y0,x1,y1,...);
  *   tris[3*n_tris]  0-based node indices, either orientation (made counter-clockwise);
- *   node_bc[n_nodes] 0 = free node (interior or zero-normal-field side), 1 = Dirichlet;
+ *   node_bc[n_nodes] 0 = free node (interior or zero-normal-field side), 1 = Dirichlet,
+ *                    2 = node of a Neumann (zero normal field) side: the natural condition,
+ *                    treated as 0;
  *   phi_D[n_nodes]  Dirichlet potential (read where node_bc == 1).
  * Computes the metrics of the section "Nomenclature and notations" (cell volumes, nodal
  * normals, median-dual volumes, edge normals, boundary nodal normals) and the Poisson matrix

@@ -390,8 +390,10 @@ class DirichletSolver:
     a sparse LU factorisation computed once per mesh."""
 
     def __init__(self, K, node_bc, phi_D):
-        self.free = np.flatnonzero(node_bc == 0)
-        self.dir = np.flatnonzero(node_bc != 0)
+        # 1 = Dirichlet; 0 (interior) and 2 (Neumann side: zero normal field, the natural
+        # condition of the vertex-centred scheme) are unknowns
+        self.free = np.flatnonzero(node_bc != 1)
+        self.dir = np.flatnonzero(node_bc == 1)
         self.phi_D = np.asarray(phi_D, dtype=np.float64)
         Kc = K.tocsc()
         self.K_FF = Kc[self.free][:, self.free].tocsc()

@@ -102,7 +102,7 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
     if (quads[k] < 0 || quads[k] >= N) return fail("quadrangle index out of range");
   int ndir = 0;
   for (int32_t i = 0; i < N; ++i) {
-    if (node_bc[i] != 0 && node_bc[i] != 1) return fail("node_bc must be 0 or 1");
+    if (node_bc[i] < 0 || node_bc[i] > 2) return fail("node_bc must be 0, 1 or 2");
     if (!std::isfinite(xy[2 * i]) || !std::isfinite(xy[2 * i + 1])) return fail("non-finite coordinate");
     if (node_bc[i] == 1) {
       ++ndir;
@@ -137,7 +137,7 @@ int prepare_mesh(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t
   for (int32_t i = 0; i < N; ++i) {
     m.x[i] = xy[2 * m.perm[i]];
     m.y[i] = xy[2 * m.perm[i] + 1];
-    m.bc[i] = node_bc[m.perm[i]];
+    m.bc[i] = node_bc[m.perm[i]] == 1 ? 1 : 0;  // 2 (Neumann side) is the natural condition, as 0
   }
 
   // ---- cells: orientation, volume, nodal normals, side normals of the dual faces, shortest side

@@ -120,3 +120,17 @@ def test_hybrid_mesh_validation_on_host(lib):
     oa.geometry = avip.GEOM_AXISYMMETRIC
     assert avip.mesh_create_hybrid(p.xy, p.tris, p.quads, p.node_bc, p.phi_D, oa)[0] == avip.AVIP_EINVAL
     assert "planar" in avip.last_error()
+
+
+def test_node_bc_values_on_host(lib):
+    """node_bc accepts 0, 1 and 2 (a Neumann side's node) and rejects anything else."""
+    import numpy as np
+    from paper_2201_01291_gb300 import avip, workloads as W
+    p = W.config_small(nx=9, ny=9)
+    o = avip.avip_opts_default()
+    bc = p.node_bc.copy()
+    bc[3] = 3
+    assert avip.mesh_create(p.xy, p.tris, bc, p.phi_D, o)[0] == avip.AVIP_EINVAL
+    assert "node_bc" in avip.last_error()
+    bc[3] = -1
+    assert avip.mesh_create(p.xy, p.tris, bc, p.phi_D, o)[0] == avip.AVIP_EINVAL

@@ -278,3 +278,19 @@ def test_every_pcg_kernel_matches_oracle(avip, kind):
     for s in range(2):
         assert normwise(m.density(s), n_ref[s]) <= TOL
     assert normwise(m.phi(), phi_ref) <= TOL
+
+
+def test_neumann_marker_same_as_free(avip):
+    """node_bc = 2 on the side nodes gives bit-identical results to 0 (the natural condition)."""
+    import dataclasses
+    p = W.config_small(nx=21, ny=19, seed=4)
+    bc2 = p.node_bc.copy()
+    ii = np.tile(np.arange(21), 19)
+    bc2[((ii == 0) | (ii == 20)) & (p.node_bc == 0)] = 2
+    a = avip.Mesh(p)
+    b = avip.Mesh(dataclasses.replace(p, node_bc=bc2))
+    a.run(5)
+    b.run(5)
+    np.testing.assert_array_equal(a.state(), b.state())
+    a.close()
+    b.close()

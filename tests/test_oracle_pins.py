@@ -310,3 +310,20 @@ def test_chemical_time_step_closed_form():
         ref = min(0.2 / nu, 0.5 * O.EPS0 / (O.E_CHARGE * abs(nb) * (0.04 + 2e-4)))
         assert info["dt"] > 0
         assert abs(info["dt"] - ref) <= 1e-12 * ref
+
+
+def test_neumann_marker_is_the_natural_condition():
+    """node_bc = 2 on the side nodes (zero normal field) gives the same potential and step as 0."""
+    import dataclasses
+    p = W.plates_problem(17, 15, 1e-2, 1e-2, 2e4, seed=3, field_dependent=True, source=W.SRC_TOWNSEND)
+    ii = np.tile(np.arange(17), 15)
+    bc2 = p.node_bc.copy()
+    side = ((ii == 0) | (ii == 16)) & (p.node_bc == 0)
+    bc2[side] = 2
+    q = dataclasses.replace(p, node_bc=bc2)
+    a, b = O.Oracle(p), O.Oracle(q)
+    na, ia = a.step(a.initial_state())
+    nb, ib = b.step(b.initial_state())
+    np.testing.assert_array_equal(ia["phi"], ib["phi"])
+    for s in range(2):
+        np.testing.assert_array_equal(na[s], nb[s])
