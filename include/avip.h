@@ -177,6 +177,21 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
                        const int32_t* quads, int32_t n_quads, const int32_t* node_bc, const double* phi_D,
                        const avip_opts* opts, avip_mesh_t* out);
 
+/* Host-only inspection of the preparation mesh_create / mesh_create_hybrid performs (no device
+ * is touched): the metrics of the section "Nomenclature and notations" in the caller's
+ * numbering.  Arguments as for mesh_create_hybrid, plus geometry (AVIP_GEOM_*).
+ *   counts[3]  out: number of edges E, stored entries of the Poisson matrix, cells;
+ *   vol        out (may be NULL): [n_nodes] dual volumes (per radian if axisymmetric);
+ *   edges      out (may be NULL): [2 E] node pairs (i, j), i < j, sorted by (i, j);
+ *   S_edge     out (may be NULL): [2 E] edge normal S_ij (x, y), oriented i -> j;
+ *   S_b        out (may be NULL): [2 n_nodes] boundary nodal normals S_i^b (0 inside).
+ * Call once with NULL outputs to learn E.  Errors: those of mesh_create_hybrid's host
+ * validation (AVIP_EINVAL; avip_inspect_error() gives the reason). */
+int mesh_inspect(const double* xy, int32_t n_nodes, const int32_t* tris, int32_t n_tris, const int32_t* quads,
+                 int32_t n_quads, const int32_t* node_bc, const double* phi_D, int32_t geometry, int64_t* counts,
+                 double* vol, int32_t* edges, double* S_edge, double* S_b);
+const char* avip_inspect_error(void);
+
 /* Release every device and host resource of the handle.  NULL is accepted. */
 int mesh_destroy(avip_mesh_t h);
 

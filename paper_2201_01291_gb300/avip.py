@@ -62,6 +62,9 @@ _SIGS = {
     "mesh_create": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, _D, _P(AvipOpts), _P(_H)]),
     "mesh_create_hybrid": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, C.c_int32, _I, _D, _P(AvipOpts), _P(_H)]),
     "mesh_destroy": (C.c_int, [_H]),
+    "mesh_inspect": (C.c_int, [_D, C.c_int32, _I, C.c_int32, _I, C.c_int32, _I, _D, C.c_int32, _P(C.c_int64),
+                               _D, _I, _D, _D]),
+    "avip_inspect_error": (C.c_char_p, []),
     "mesh_set_stream": (C.c_int, [_H, C.c_void_p]),
     "mesh_info": (C.c_int, [_H, _P(C.c_int64)]),
     "solver_levels": (C.c_int, [_H, _P(C.c_int64), C.c_int32]),
@@ -161,6 +164,31 @@ def mesh_create_hybrid(xy, tris, quads, node_bc, phi_D, opts: AvipOpts):
                                    _iptr(quads) if quads.size else None, quads.size // 4, _iptr(node_bc),
                                    _dptr(phi_D), C.byref(opts), C.byref(h))
     return rc, h
+
+
+def mesh_inspect(xy, tris, quads, node_bc, phi_D, geometry=0):
+    """Host-only metrics of the prepared mesh (no device): dict with vol, edges, S_edge, S_b,
+    nnz and n_cells in the caller's numbering."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    tris = np.ascontiguousarray(tris if tris is not None else np.zeros(0), dtype=np.int32).reshape(-1)
+    quads = np.ascontiguousarray(quads if quads is not None else np.zeros(0), dtype=np.int32).reshape(-1)
+    node_bc = np.ascontiguousarray(node_bc, dtype=np.int32)
+    phi_D = np.ascontiguousarray(phi_D, dtype=np.float64)
+    n = xy.size // 2
+    counts = np.zeros(3, dtype=np.int64)
+    args = (_dptr(xy), n, _iptr(tris) if tris.size else None, tris.size // 3, _iptr(quads) if quads.size else None,
+            quads.size // 4, _iptr(node_bc), _dptr(phi_D), int(geometry), counts.ctypes.data_as(_P(C.c_int64)))
+    rc = load().mesh_inspect(*args, None, None, None, None)
+    if rc != AVIP_OK:
+        return rc, None
+    E = int(counts[0])
+    vol = np.zeros(n)
+    edges = np.zeros(2 * max(E, 1), dtype=np.int32)
+    S_edge = np.zeros(2 * max(E, 1))
+    S_b = np.zeros(2 * n)
+    rc = load().mesh_inspect(*args, _dptr(vol), _iptr(edges), _dptr(S_edge), _dptr(S_b))
+    return rc, dict(vol=vol, edges=edges[:2 * E].reshape(-1, 2), S_edge=S_edge[:2 * E].reshape(-1, 2),
+                    S_b=S_b.reshape(-1, 2), nnz=int(counts[1]), n_cells=int(counts[2]))
 
 
 def mesh_destroy(h):
