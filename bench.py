@@ -227,10 +227,10 @@ def pcg_traffic_model(info, iters, solves):
 
 def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8):
     """Algorithmic bytes and flops of the AMG-preconditioned CG launch (kind 8).  Per CG
-    iteration and non-coarsest level l (n rows, a = nnz(A_l), p = nnz(P_l), q = nnz(A_l P_l),
-    n' coarse rows), counting 12 B per stored entry (column + value), 4 B row length, one 8 B
-    read per gathered and per own vector element: three products with A_l, one with A_l P_l,
-    one with P_l and one with R_l, 36 a + 12 q + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
+    iteration and non-coarsest level l (n rows, a = nnz(A_l), p = nnz(P_l), n' coarse rows),
+    counting 12 B per stored entry (column + value), 4 B row length, one 8 B read per gathered
+    and per own vector element: four products with A_l, one with P_l and one with R_l,
+    48 a + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
     the CG phases add 12 nnz + 116 N.  Flops: 2 per stored entry of every product, 20 per row
     and level for the smoothing and update arithmetic, 12 N for CG.  BiCGStab (kind 9) applies
     two V-cycles per iteration and its phases add 24 nnz + 216 N bytes and 4 nnz + 32 N flops.
@@ -241,11 +241,11 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8):
     per_it = (24 * nnz0 + 216 * N) if kind == 9 else (12 * nnz0 + 116 * N)
     fl_it = (4 * nnz0 + 32 * N) if kind == 9 else (2 * nnz0 + 12 * N)
     vb, vf = 0, 0
-    for l, (n, a, p, q) in enumerate(levels):
+    for l, (n, a, p) in enumerate(levels):
         if l + 1 < len(levels):
             nc = levels[l + 1][0]
-            vb += ent * (36 * a + 12 * q + 24 * p) + vec * (196 * n + 36 * nc)
-            vf += 2 * (3 * a + q + 2 * p) + 20 * n
+            vb += ent * (48 * a + 24 * p) + vec * (196 * n + 36 * nc)
+            vf += 2 * (4 * a + 2 * p) + 20 * n
         else:
             vb += vec * (8 * n * n + 16 * n)
             vf += 2 * n * n

@@ -280,10 +280,9 @@ int mesh_info(avip_mesh_t h, int64_t* info8);
 /* Multigrid hierarchy of the AMG-preconditioned solvers (kinds 8-11; the paper names no solver, this
  * reports the set-up built for this project's preconditioner).  Returns the number of levels
  * (finest first, the last one inverted densely), or 0 when the handle uses another solver; for
- * the first min(levels, max_levels) levels writes out[4*l] = rows, out[4*l+1] = stored entries
- * of the level matrix, out[4*l+2] = stored entries of the prolongator from the next level and
- * out[4*l+3] = stored entries of the level matrix times that prolongator (both 0 on the
- * coarsest).  AVIP_EINVAL for a NULL handle or a NULL `out` with max_levels > 0. */
+ * the first min(levels, max_levels) levels writes out[3*l] = rows, out[3*l+1] = stored entries
+ * of the level matrix, out[3*l+2] = stored entries of the prolongator from the next level
+ * (0 on the coarsest).  AVIP_EINVAL for a NULL handle or a NULL `out` with max_levels > 0. */
 int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels);
 
 /* ---- batches (many independent instances per step) -------------------------------------

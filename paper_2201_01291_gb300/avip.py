@@ -267,13 +267,13 @@ def mesh_info(h):
 
 
 def solver_levels(h, max_levels=12):
-    """AMG hierarchy of the handle's solver: list of (rows, nnz of A, nnz of P, nnz of A P)
-    per level, finest first; empty when the solver is not the AMG-preconditioned CG."""
-    out = np.zeros(4 * max_levels, dtype=np.int64)
+    """AMG hierarchy of the handle's solver: list of (rows, nnz of A, nnz of P) per level,
+    finest first; empty when the solver is not the AMG-preconditioned CG."""
+    out = np.zeros(3 * max_levels, dtype=np.int64)
     nl = load().solver_levels(h, out.ctypes.data_as(_P(C.c_int64)), max_levels)
     if nl < 0:
         _check(nl, "solver_levels")
-    return [tuple(int(v) for v in out[4 * l:4 * l + 4]) for l in range(min(nl, max_levels))]
+    return [tuple(int(v) for v in out[3 * l:3 * l + 3]) for l in range(min(nl, max_levels))]
 
 
 def state_get(h):

@@ -397,8 +397,7 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
       }
     }
     Csr R = transpose(P);
-    Csr AP = spgemm(A, P);
-    Csr Ac = spgemm(R, AP);
+    Csr Ac = spgemm(R, spgemm(A, P));
     if (symmetric) {  // symmetrise the rounding of the Galerkin product (its pattern is symmetric)
       const Csr AcT = transpose(Ac);
       for (int32_t i = 0; i < Ac.n; ++i)
@@ -407,7 +406,6 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
     L.A = std::move(A);
     L.P = std::move(P);
     L.R = std::move(R);
-    L.AP = std::move(AP);
     H.lv.push_back(std::move(L));
     A = std::move(Ac);
     B.swap(Bc);

@@ -124,20 +124,24 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b
     T* __restrict__ x = l == 0 ? x0 : L->x;
     T* __restrict__ d = L->d;
     T* __restrict__ r = L->r;
-    const T inv_theta = (T)L->inv_theta, c1 = (T)L->c1, c2 = (T)L->c2;
-    {  // prolongation x += P x_c and, in the same phase, the first post-smoothing step: the new
-       // residual b - A (x + P x_c) is the residual r kept from before the restriction minus
-       // (A P) x_c, so both read only the complete coarse solution; d = D^-1 r / theta
-      const SellMatT<T> P = L->P, AP = L->AP;
+    {  // prolongation
+      const SellMatT<T> P = L->P;
       const T* __restrict__ cx = H->L[l + 1].x;
       for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
         const int i = sl * kSlice + lane;
         if (i >= n) continue;
         x[i] += sellmat_row_dot(P, sl, lane, i, cx);
-        const T ri = r[i] - sellmat_row_dot(AP, sl, lane, i, cx);
-        r[i] = ri;
-        d[i] = dinv[i] * ri * inv_theta;
       }
+    }
+    if (!ops.barrier()) return false;
+    const T inv_theta = (T)L->inv_theta, c1 = (T)L->c1, c2 = (T)L->c2;
+    // first post-smoothing step: r = b - A x, d = D^-1 r / theta (x updated in the next phase)
+    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
+      const int i = sl * kSlice + lane;
+      if (i >= n) continue;
+      const T ri = b[i] - sellmat_row_dot(A, sl, lane, i, (const T*)x);
+      r[i] = ri;
+      d[i] = dinv[i] * ri * inv_theta;
     }
     if (!ops.barrier()) return false;
     // second step: r1 = r - A d, x += d + c1 d + c2 D^-1 r1

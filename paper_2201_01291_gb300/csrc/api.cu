@@ -54,7 +54,7 @@ struct avip_mesh {
   float* z32 = nullptr;
   double* amg_z = nullptr;      // preconditioned residual (level-0 solution of the V-cycle)
   int32_t amg_levels = 0;
-  std::vector<int64_t> amg_stats;  // per level: rows, nnz(A), nnz(P), nnz(A P)
+  std::vector<int64_t> amg_stats;  // per level: rows, nnz(A), nnz(P)
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
   float *gx32 = nullptr, *gy32 = nullptr, *sx32 = nullptr, *sy32 = nullptr, *ndat32 = nullptr;  // FP32 DD
   GridSync* sync = nullptr;     // followed in the same allocation by the barrier flags
@@ -368,7 +368,7 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& o
     } else {
       ok = ok && put(L.A, dl.A);
     }
-    if (l + 1 < D.nlev) ok = ok && put(L.P, dl.P) && put(L.R, dl.R) && put(L.AP, dl.AP);
+    if (l + 1 < D.nlev) ok = ok && put(L.P, dl.P) && put(L.R, dl.R);
     T* dinv = nullptr;
     std::vector<T> dv(L.dinv.begin(), L.dinv.end());
     ok = ok && upload(h, dinv, dv, npad);
@@ -391,7 +391,6 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& o
     h->amg_stats.push_back(L.A.n);
     h->amg_stats.push_back(L.A.rp.empty() ? 0 : L.A.rp[L.A.n]);
     h->amg_stats.push_back(L.P.rp.empty() ? 0 : L.P.rp[L.P.n]);
-    h->amg_stats.push_back(L.AP.rp.empty() ? 0 : L.AP.rp[L.AP.n]);
   }
   return ok;
 }
@@ -682,7 +681,7 @@ int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
   if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
   const int32_t nl = (h->plan.kind >= 8 && h->plan.kind <= 11) ? h->amg_levels : 0;
   for (int32_t l = 0; l < nl && l < max_levels; ++l)
-    for (int k = 0; k < 4; ++k) out[4 * l + k] = h->amg_stats[4 * (size_t)l + k];
+    for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
   return nl;
 }
 

@@ -70,7 +70,6 @@ struct Csr {  // compressed sparse rows, n x m
 };
 struct AmgHostLevel {
   Csr A, P, R;                 // level matrix; prolongator from the next level; R = P^T
-  Csr AP;                      // A P: the residual change of a coarse correction
   std::vector<double> dinv;    // 1 / diag(A)
   double lmax = 1.0;           // estimate of the largest eigenvalue of D^-1 A
 };
@@ -119,7 +118,6 @@ using SellMat = SellMatT<double>;
 template <typename T>
 struct AmgLevelT {
   SellMatT<T> A, P, R;  // P: n x n_next (prolongation), R = P^T (restriction); unused on the coarsest
-  SellMatT<T> AP;       // A P (n x n_next): b - A (x + P x_c) = r - (A P) x_c
   const T* dinv;
   T* x;                 // level solution (the finest level's is passed to the V-cycle instead)
   T* b;                 // level right-hand side (likewise)
