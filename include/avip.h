@@ -233,7 +233,9 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
  * of avip_stats (those count the Poisson solves); a solve that fails sets the run status. */
 int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kappa, double c);
 
-/* Solve the Poisson problem for the current densities (warm start from the last phi).
+/* Solve the Poisson problem for the current densities, starting from the quadratic
+ * extrapolation of the last potentials (the last one alone after mesh_create or a state with
+ * no history).  Every call advances that history.
  * iters_out / relres_out (may be NULL) receive the PCG iteration count and the final true
  * relative residual.  AVIP_ENOTCONV if max_iter was reached. */
 int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out);
