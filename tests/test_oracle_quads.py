@@ -3,7 +3,8 @@
 Green-Gauss gradients exact on linear fields, the Poisson operator annihilating linear fields
 at interior rows and converging at second order on a manufactured solution, the linear
 potential between plates, the one-dimensional limited Lax-Wendroff scheme on an unjittered
-quadrangle strip, a uniform state preserved and the charge ledger.  CPU only."""
+quadrangle strip (and the one-dimensional Scharfetter-Gummel scheme), a uniform state preserved
+and the charge ledger.  CPU only."""
 import numpy as np
 import pytest
 
@@ -143,3 +144,29 @@ def test_hybrid_uniform_state_and_charge_ledger():
         ledger = sum(-info["dt"] * O.E_CHARGE * sp_.charge * (info["outflow"][s] - info["source_total"][s])
                      for s, sp_ in enumerate(p.species))
         assert abs(o.charge(n) - Q0 - ledger) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("c", [3.0, -2.0])
+def test_quad_strip_reduces_to_1d_scharfetter_gummel(c):
+    """On an unjittered quadrangle strip the dual faces are normal to the edges (no normal part
+    of S): with u = u(x) and V = (c, 0) the residual per unit face height is the textbook 1D
+    Scharfetter-Gummel one, F_{i+1/2} = (D/h) (B(-a) u_i - B(a) u_{i+1}), a = h c / D."""
+    nx, ny = 24, 8
+    h = 1.0 / (nx - 1)
+    p = W.hybrid_plates_problem(nx, ny, 1.0, h * (ny - 1), 0.0, seed=1, quad_fraction=1.0, jitter=0.0,
+                                n_peak=0.0, n_back=0.0)
+    p.opts.scheme = W.FLUX_SG
+    o = O.Oracle(p)
+    prof = lambda xx: 1e2 + 0.5 * (1.0 + np.tanh((xx - 0.45) / 0.08)) * 1e6 + 3e5 * np.sin(7 * xx)
+    u = prof(p.xy[:, 0])
+    vel = np.tile([c, 0.0], (p.n_nodes, 1))
+    D = 0.05
+    R, _ = o.residual(u, o.nodal_gradient(u), vel, D, 0, 0.01)
+    U = prof(np.arange(nx) * h)
+    a = h * c / D
+    B = lambda x: x / np.expm1(x)
+    face = lambda i: (D / h) * (B(-a) * U[i] - B(a) * U[i + 1])
+    ii, jj = np.tile(np.arange(nx), ny), np.repeat(np.arange(ny), nx)
+    sel = (ii >= 1) & (ii <= nx - 2) & (jj >= 1) & (jj <= ny - 2)
+    R1 = np.array([-(face(i) - face(i - 1)) for i in ii[sel]])
+    np.testing.assert_allclose(R[sel] / h, R1, rtol=0, atol=1e-11 * np.abs(U).max() * (abs(c) + D / h))
