@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-v"] + ARCH
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall"]
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-pthread"]
 
 
 def _nvcc():
@@ -70,7 +70,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         if rc != 0:
             raise RuntimeError(f"compile failed: {cmd}\n{out}")
     tmp = LIB + ".tmp"
-    rc, cmd, out = _run([nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs])
+    rc, cmd, out = _run([nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs, "-lpthread"])
     if rc != 0:
         raise RuntimeError(f"link failed: {cmd}\n{out}")
     os.replace(tmp, LIB)

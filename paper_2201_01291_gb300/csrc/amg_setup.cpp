@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstdio>
 #include <numeric>
+#include <thread>
 #include <utility>
 
 #include "avip_internal.h"
@@ -186,6 +187,14 @@ int32_t aggregate(const Csr& A, std::vector<int32_t>& agg, double theta) {
   return na;
 }
 
+// Host threads for a dense set-up step of order n: one below 256 rows, else up to 16 (the
+// hardware concurrency when it is known).
+int host_threads(int n) {
+  if (n < 256) return 1;
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(16u, hc == 0 ? 1u : hc));
+}
+
 // dense inverse of an SPD matrix (row-major n x n) through its Cholesky factor
 bool dense_spd_inverse(std::vector<double>& a, int n) {
   for (int j = 0; j < n; ++j) {  // a = L L^T, L in the lower triangle
@@ -204,22 +213,34 @@ bool dense_spd_inverse(std::vector<double>& a, int n) {
   std::vector<double> U((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k <= i; ++k) U[(size_t)k * n + i] = a[(size_t)i * n + k];
-  std::vector<double> inv((size_t)n * n), y(n), x(n);
-  for (int c = 0; c < n; ++c) {  // column c of the inverse: L y = e_c, L^T x = y
-    for (int i = 0; i < n; ++i) {
-      double t = (i == c) ? 1.0 : 0.0;
-      const double* li = &a[(size_t)i * n];
-      for (int k = 0; k < i; ++k) t -= li[k] * y[k];
-      y[i] = t / li[i];
+  std::vector<double> inv((size_t)n * n);
+  // the columns are independent: spread them over the host cores (each column's arithmetic
+  // does not depend on the thread that computes it)
+  auto columns = [&](int first, int stride) {
+    std::vector<double> y(n), x(n);
+    for (int c = first; c < n; c += stride) {  // column c of the inverse: L y = e_c, L^T x = y
+      // y_i = 0 for i < c exactly, so the forward solve starts at row c
+      for (int i = 0; i < c; ++i) y[i] = 0.0;
+      for (int i = c; i < n; ++i) {
+        double t = (i == c) ? 1.0 : 0.0;
+        const double* li = &a[(size_t)i * n];
+        for (int k = c; k < i; ++k) t -= li[k] * y[k];
+        y[i] = t / li[i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        const double* ui = &U[(size_t)i * n];
+        for (int k = i + 1; k < n; ++k) t -= ui[k] * x[k];
+        x[i] = t / ui[i];
+      }
+      for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = x[i];
     }
-    for (int i = n - 1; i >= 0; --i) {
-      double t = y[i];
-      const double* ui = &U[(size_t)i * n];
-      for (int k = i + 1; k < n; ++k) t -= ui[k] * x[k];
-      x[i] = t / ui[i];
-    }
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = x[i];
-  }
+  };
+  const int nt = host_threads(n);
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(columns, t, nt);
+  columns(0, nt);
+  for (auto& th : pool) th.join();
   a.swap(inv);
   return true;
 }
