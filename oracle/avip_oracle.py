@@ -30,7 +30,14 @@ Structure (each function cites the passage it follows):
   * explicit update and the charge sum;
   * axisymmetric (x, r) variant (section "Axisymmetric configuration" and the axisymmetric
     flux form): r-weighted Poisson rows (closed-form dual-contour integral), r-weighted edge
-    and boundary normals, dual volumes of revolution; gradients stay two-dimensional.
+    and boundary normals, dual volumes of revolution; gradients stay two-dimensional;
+  * quadrangle and hybrid meshes (n_v-vertex forms of the metrics, section "Nomenclature and
+    notations"): shoelace volumes, nodal normals from the two adjacent faces, dual faces from
+    the side midpoints to the vertex-mean centre, Poisson coupling of all vertex pairs;
+  * three-species air chemistry (section "Hyperbole electrodes": ionisation, attachment,
+    electron-ion and ion-ion recombination) and the linear electrode-voltage ramp;
+  * photoionisation by the three-term Helmholtz fit (the streamer benchmark's third case):
+    (K + kappa_j^2 V) S_j = a_j V I per term, S_ph = sum_j S_j to electrons and positive ions.
 
 Readings where the paper is silent or garbled (each also listed in the design notes):
   * ratio of gradients: r = (u_U - u_k)/(u_W - u_U) with the virtual upwind node
@@ -38,13 +45,16 @@ Readings where the paper is silent or garbled (each also listed in the design no
   * for V_ij.S_ij < 0 the roles of i and j are mirrored (the 1D form of the limited scheme);
   * u_W == u_U gives Psi = 0;
   * nodal velocity V_s = sign(q_s) mu_s(|E|) E, edge velocity = mean of nodal velocities;
-  * Delta x_tau = shortest edge of the cell; cell values = mean of the three nodal values;
+  * Delta x_tau = shortest side of the cell; cell values = mean of the n_v nodal values;
   * chemical time step A_tau * min over nodes of |n_e|/|S_e| (the printed form is not a
     time; the magnitudes keep it a positive time scale when a density undershoots below 0);
   * Dirichlet rows eliminated symmetrically (same solution as the unit-row form);
   * axisymmetric dual volume: the integral of r over the median-dual cell (the centroid
     radius of the dual cell in the Pappus relation; the node radius would give zero volume to
-    nodes on the axis); the nodal gradient keeps the planar area weights.
+    nodes on the axis); the nodal gradient keeps the planar area weights;
+  * node_bc = 2 (a Neumann side's node) is the natural condition, an unknown like 0;
+  * photoionisation terms vanish on the Dirichlet nodes and have zero normal derivative on
+    the other boundaries; S_ph enters the chemical time-step limit.
 """
 from __future__ import annotations
 
