@@ -174,14 +174,16 @@ def test_plates_linear_potential_exact():
 
 
 # ---------------------------------------------------------------- transport
-def one_d_reduction(c, D, dt, nx=24, ny=8, beta=1.0):
+def one_d_reduction(c, D, dt, nx=24, ny=8, beta=1.0, van_leer=False):
     """Run the 2D residual on an unjittered strip with u = u(x) and V = (c, 0); return the
     2D residual per unit face height and the 1D limited Lax-Wendroff residual written with
-    real upwind nodes and centred nodal gradients."""
+    real upwind nodes and centred nodal gradients.  van_leer: the limiter is Van Leer's
+    (r + |r|)/(1 + |r|) instead of Sweby's (limiter functions of the LLW section)."""
     h = 1.0 / (nx - 1)
     Ly = h * (ny - 1)
     p = W.plates_problem(nx, ny, 1.0, Ly, 0.0, seed=1, jitter=0.0, n_peak=0.0, n_back=0.0)
     p.opts.beta = beta
+    p.opts.limiter = 1 if van_leer else 0
     o = O.Oracle(p)
     x = p.xy[:, 0]
     prof = lambda xx: 1e2 + 0.5 * (1.0 + np.tanh((xx - 0.45) / 0.08)) * 1e6 + 3e5 * np.sin(7 * xx)
@@ -205,7 +207,10 @@ def one_d_reduction(c, D, dt, nx=24, ny=8, beta=1.0):
             psi = 0.0
         else:
             r = (U[up] - U[uu]) / delta
-            psi = max(0.0, min(beta * r, 1.0), min(r, beta))
+            if van_leer:
+                psi = (r + abs(r)) / (1.0 + abs(r))
+            else:
+                psi = max(0.0, min(beta * r, 1.0), min(r, beta))
         gf = 0.5 * (g[i] + g[i + 1])
         fc = (U[up] + (0.5 * delta - 0.5 * dt * gf * c) * psi) * c
         return fc - D * gf
@@ -224,6 +229,64 @@ def test_llw_reduces_to_1d_limited_lax_wendroff(c, beta):
     np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
     R2, R1, scale = one_d_reduction(c, D=0.05, dt=0.01, beta=beta)
     np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("c", [3.0, -2.0])
+def test_llw_van_leer_reduces_to_1d_limited_lax_wendroff(c):
+    """The Van Leer branch of the limiter against the same 1D restatement, on a profile whose
+    upwind ratios span negative values, (0, 1) and values above 1 (both limiters differ there)."""
+    R2, R1, scale = one_d_reduction(c, D=0.0, dt=0.01, van_leer=True)
+    np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
+    R2, R1, scale = one_d_reduction(c, D=0.05, dt=0.01, van_leer=True)
+    np.testing.assert_allclose(R2, R1, atol=1e-12 * scale)
+    # the pin sees the limiter: Sweby min-mod gives a different residual on the same data
+    R2s, _, _ = one_d_reduction(c, D=0.05, dt=0.01)
+    assert np.abs(R2s - R2).max() > 1e-6 * scale
+
+
+@pytest.mark.parametrize("c", [3.0, -2.0])
+@pytest.mark.parametrize("bnd_mode", [0, 1])
+def test_boundary_node_flux_closure_1d(c, bnd_mode):
+    """Node-flux closure of the section "Boundary conditions in AVIP" on the left and right
+    sides of an unjittered strip, with the linear profile u = a + b x and V = (c, 0): the
+    gradient is exact there, the upwind ratio is 1, and the boundary node's residual per unit
+    height is minus the 1D face flux towards its neighbour minus the node flux through the
+    boundary normal (+-1 per unit height): F_b = u V ("Neumann") or u V - D grad u
+    ("supersonic"/outflow)."""
+    nx, ny, D, dt = 12, 8, 0.07, 0.01
+    a, b = 2.0e3, -1.5e3
+    h = 1.0 / (nx - 1)
+    Ly = h * (ny - 1)
+    p = W.plates_problem(nx, ny, 1.0, Ly, 0.0, seed=1, jitter=0.0, n_peak=0.0, n_back=0.0)
+    o = O.Oracle(p)
+    u = a + b * p.xy[:, 0]
+    grad = O.nodal_gradient(u, o.tris, o.S, o.V_tau, o.V_node)
+    np.testing.assert_allclose(grad, np.tile([b, 0.0], (p.n_nodes, 1)), atol=1e-9 * abs(b))
+    vel = np.tile([c, 0.0], (p.n_nodes, 1))
+    R, _ = o.residual(u, grad, vel, D, bnd_mode, dt)
+    lin = lambda xx: a + b * xx
+
+    def face(x_lo):  # 1D flux from the node at x_lo to the node at x_lo + h (unit height)
+        x_up, x_dn = (x_lo, x_lo + h) if c >= 0 else (x_lo + h, x_lo)
+        delta = lin(x_dn) - lin(x_up)
+        x_uu = x_up - (x_dn - x_up)       # the real node behind the upwind one (linear extension)
+        r = (lin(x_up) - lin(x_uu)) / delta
+        psi = max(0.0, min(r, 1.0), min(r, 1.0))
+        fc = (lin(x_up) + (0.5 * delta - 0.5 * dt * b * c) * psi) * c
+        return fc - D * b
+
+    def node_flux(x):
+        f = lin(x) * c
+        return f - D * b if bnd_mode == 1 else f
+
+    ii = np.tile(np.arange(nx), ny)
+    jj = np.repeat(np.arange(ny), nx)
+    mid = (jj >= 2) & (jj <= ny - 3)
+    left, right = mid & (ii == 0), mid & (ii == nx - 1)
+    scale = (abs(a) + abs(b)) * (abs(c) + D)
+    # left side: outward normal (-1, 0); right side: (+1, 0)
+    np.testing.assert_allclose(R[left] / h, -face(0.0) + node_flux(0.0), atol=1e-12 * scale)
+    np.testing.assert_allclose(R[right] / h, face(1.0 - h) - node_flux(1.0), atol=1e-12 * scale)
 
 
 def test_uniform_state_and_exponential_source():
