@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-steps/s (DD+Poisson) plain vs mixed/batched/served; p50/p99 latency"
 UNIT = "cell-steps/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 data-sheet rate, used only if the in-run probe fails
 
 
 def parse():
@@ -100,6 +100,38 @@ def _make_problem(name):
         p = W.config_plates_65()
         desc = "parallel plates 1cm x 1cm, 65x65 jittered nodes (8192 tris), 5 kV, constant mu/D, FP64"
     return p, desc
+
+
+def workload_config(problem, desc, args):
+    """The `config` dict of the JSON line: the workload only, identical in both arms."""
+    return {"workload": desc, "n_nodes": int(problem.n_nodes), "n_cells": int(problem.n_cells),
+            "rtol": args.rtol, "precision": args.precision, "seed": problem.seed}
+
+
+def host_cpu():
+    """CPU model and the number of cores visible to this process."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count()
+    return {"cpu_model": model or "unknown", "nproc": n}
 
 
 def measured_peaks():
@@ -278,6 +310,10 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     with torch.cuda.stream(stream):
         flush.fill_(-1.0)  # the first fill loads torch's fill kernel (~0.25 s): keep it out of the timing
+    # roofline denominators of this device, measured now (before the timed region)
+    rc64, fp64_peak = avip.peak_probe(avip.PROBE_FP64_FMA, stream.cuda_stream)
+    rcbw, copy_gbs = avip.peak_probe(avip.PROBE_HBM_COPY, stream.cuda_stream)
+    torch.cuda.synchronize()
     # warm-up (graph capture happens here too)
     with torch.cuda.stream(stream):
         m.run(args.warmup, allow=allow)
@@ -324,6 +360,15 @@ def run_ours(args, rank, world, local_rank):
     state_bytes = host.size * 8
     info = m.info
     m.close()
+    # a fresh handle for the oracle comparison of the CPU-baseline leg (same steps from t = 0)
+    check = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mc = avip.Mesh(problem, rtol=args.rtol, pcg_kind=args.pcg_kind, precision=prec, **kw)
+        with torch.cuda.stream(stream):
+            mc.run(args.cpu_steps, allow=allow)
+        torch.cuda.synchronize()
+        check = ([mc.density(s) for s in range(len(problem.species))], mc.phi())
+        mc.close()
     if rank != 0:
         return None
     # ---- roofline of the dominant kernel (PCG)
@@ -333,19 +378,30 @@ def run_ours(args, rank, world, local_rank):
         info = dict(info, pcg_kind=10 if args.precision == "mixed" else 8)
     byts, flops = pcg_traffic_model(info, iters, args.steps)
     pcg_s = kernel_ms["pcg"] / 1e3
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    if not hbm:
+        hbm, hbm_src = (copy_gbs, "measured in this run (copy probe)") if rcbw == 0 else (6800.0, "fallback")
+    if rc64 == 0 and fp64_peak > 0:
+        f64, f64_src = fp64_peak, "measured in this run (FP64 FMA-chain probe, peak_probe)"
+    else:
+        f64, f64_src = FP64_NOMINAL_TFLOPS, "nominal (the in-run probe failed)"
     gbs = byts / pcg_s / 1e9
     tfl = flops / pcg_s / 1e12
     kind = info["pcg_kind"]
-    if kind in (4, 10):
-        # FP32 inner solve: bandwidth/latency bound, compare with HBM
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    # the binding roof is the unit the kernel uses the largest fraction of; the FP32 inner
+    # solve of the mixed path is compared with HBM only (its FP32 rate is far from binding)
+    hbm_frac, f64_frac = gbs / hbm, tfl / f64
+    if kind in (4, 10) or hbm_frac >= f64_frac:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": hbm_src}
     else:
-        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(tfl / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (FMA-chain probe measured 1.197)",
-                "hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm, 4)}
+        roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": round(f64, 4), "unit": "TFLOP/s",
+                "frac": round(f64_frac, 4), "peak_source": f64_src}
+    roof.update({"hbm_gbs_algorithmic": round(gbs, 1), "hbm_frac_of_measured": round(hbm_frac, 4),
+                 "fp64_tflops": round(tfl, 4), "fp64_frac_of_measured": round(f64_frac, 4),
+                 "fp64_peak_tflops_measured": round(fp64_peak, 4) if rc64 == 0 else None,
+                 "copy_gbs_measured_in_run": round(copy_gbs, 1) if rcbw == 0 else None})
     per_launch_iters = iters / args.steps
     traffic, note = NCU_DRAM_BYTES_PER_ITER.get(kind, (None, None)) if args.workload == "pin_plane" else (None, None)
     roof.update({"kernel": kernel_name,
@@ -359,10 +415,9 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": desc, "n_nodes": info["n_nodes"], "n_cells": T, "nnz": info["nnz"],
-                   "rtol": args.rtol, "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MiB write inside the timed region)",
-                   "seed": problem.seed},
+        "config": workload_config(problem, desc, args),
+        "parallelism": f"replicas x{world}", "nnz": info["nnz"],
+        "l2": "flushed between timed steps (256 MiB write inside the timed region)",
         "e2e": {"value": world * T * e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes,
                 "how": "per step: state_set from host, run_steps(1), state_get to host"},
@@ -371,8 +426,21 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(problem, args.cpu_steps)
+        out["cpu_baseline"], ref = cpu_baseline(problem, args.cpu_steps)
+        n_gpu, phi_gpu = check
+        err = {"steps": args.cpu_steps, "phi": normwise(phi_gpu, ref[1])}
+        for s_, sp_ in enumerate(problem.species):
+            err["n_" + str(s_)] = normwise(n_gpu[s_], ref[0][s_])
+        err["max"] = max(v for k, v in err.items() if k != "steps")
+        err["metric"] = "norm-wise max_i |x - x_oracle| / max_i |x_oracle|, fresh handle vs the CPU-baseline oracle run"
+        out["oracle_error"] = err
     return out
+
+
+def normwise(x, ref):
+    x, ref = np.asarray(x, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref).max()
+    return float(np.abs(x - ref).max() / scale) if scale > 0 else float(np.abs(x).max())
 
 
 def run_batch(args, rank, world, local_rank):
@@ -533,24 +601,30 @@ def oracle_module():
 
 
 def cpu_baseline(problem, steps):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload.
+    Returns the baseline record and the oracle's densities and potential after `steps` steps
+    from the initial state (the reference of the line's oracle_error)."""
     O = oracle_module()
     t0 = time.perf_counter()
-    c0 = time.process_time()
     o = O.Oracle(problem)
     setup = time.perf_counter() - t0
     n = o.initial_state()
     t1 = time.perf_counter()
     c1 = time.process_time()
+    t = 0.0
+    phi = None
     for _ in range(steps):
-        n, _ = o.step(n)
+        n, info = o.step(n, t=t)
+        t += info["dt"]
+        phi = info["phi"]
     wall = time.perf_counter() - t1
     cpu = time.process_time() - c1
-    return {"value": problem.n_cells * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)),
-            "kind": "oracle",
-            "sample": f"{steps} explicit steps of the same workload after a {setup:.1f} s one-off "
-                      f"setup (metrics + sparse LU factorisation, excluded); numpy/scipy, "
-                      f"{os.cpu_count()} host cores visible"}
+    hc = host_cpu()
+    rec = {"value": problem.n_cells * steps / wall, "unit": UNIT, "cores": max(1, round(cpu / wall)),
+           "kind": "oracle", "cpu_model": hc["cpu_model"], "nproc": hc["nproc"],
+           "sample": f"{steps} explicit steps of the same workload after a {setup:.1f} s one-off "
+                     f"setup (metrics + sparse LU factorisation, excluded); numpy/scipy"}
+    return rec, (n, phi)
 
 
 def run_reference(args, rank, world):
@@ -575,9 +649,9 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": desc, "n_cells": problem.n_cells, "precision": "fp64",
-                       "parallelism": "cpu oracle"},
+            "config": workload_config(problem, desc, args), "parallelism": "cpu oracle (rank 0 only)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+                             **host_cpu(),
                              "sample": f"each step one explicit oracle step of the workload "
                                        f"(setup {setup:.1f} s excluded)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -2,11 +2,14 @@
  * avip.h -- C ABI of the GB300 (sm_103a) library for the Poisson-coupled drift-diffusion
  * step of the AVIP low-temperature plasma method (arXiv 2201.01291).
  *
- * One explicit time step on an unstructured triangle mesh:
+ * One explicit time step on an unstructured triangle, quadrangle or hybrid mesh:
  *   1. potential phi from  -lap(phi) = rho/eps0  with Dirichlet / zero-normal-field
  *      boundaries (section "Integrating the Poisson equation", Eq. poisson, Eq.
  *      poisson_discretization_cartesian, Eq. coeff_matriceA, "Boundary conditions"),
- *      solved by Jacobi-preconditioned conjugate gradients on the device;
+ *      solved on the device by conjugate gradients preconditioned by a smoothed-aggregation
+ *      AMG V-cycle (planar meshes above 500 nodes; Jacobi-preconditioned CG below, and as an
+ *      option), or by BiCGStab for the non-symmetric axisymmetric matrix (the paper names no
+ *      linear solver);
  *   2. E = -grad(phi) with Green-Gauss cell gradients through nodal normals;
  *   3. edge-based limited Lax-Wendroff + central diffusion fluxes of every charged species
  *      (section "Development of TVD schemes", Eq. vertex_centered_flux) with the node-flux
@@ -122,6 +125,12 @@ typedef struct avip_opts {
                                           t = 0 to its phi_D at t = v_rise and stays there (the
                                           anode ramp of the section "Hyperbole electrodes"; a
                                           grounded electrode, phi_D = 0, stays at 0); 0 = constant */
+  double wait_timeout;                 /* seconds a device-side wait of a cooperative solver
+                                          (a grid-wide barrier) may last before the kernel gives
+                                          up: its blocks leave, the call returns AVIP_ETIMEOUT and
+                                          the handle stays usable.  Default 2; 0 gives up at the
+                                          first wait that is not already satisfied (a test of the
+                                          failure path); at most 60 */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */
@@ -197,6 +206,10 @@ int mesh_destroy(avip_mesh_t h);
 
 /* Queue subsequent work of the handle on `stream` (a cudaStream_t). */
 int mesh_set_stream(avip_mesh_t h, void* stream);
+
+/* Change the handle's wait_timeout (see avip_opts; 0 <= seconds <= 60, else AVIP_EINVAL).
+ * Takes effect from the next call that steps or solves. */
+int mesh_set_wait_timeout(avip_mesh_t h, double seconds);
 
 /* Declare species s (0 <= s < AVIP_MAX_SPECIES; species must be declared 0,1,2,... in order)
  * of the drift-diffusion system (section "Drift-diffusion equations"): charge in units of e
@@ -309,23 +322,40 @@ int batch_destroy(avip_batch_t b);
 
 /* No-allocation Jacobi-preconditioned CG for callers that cannot allocate device memory.
  * The paper has no counterpart: it exists for code that must not call cudaMalloc or any
- * allocating routine (for example while a CUDA stream is being captured, in a real-time loop
- * with a fixed memory budget, or under a framework that owns all device memory), which also
- * rules out mesh_create.  Such a caller places the Dirichlet-eliminated Poisson matrix (or any
+ * allocating routine, for example a real-time loop with a fixed memory budget that forbids
+ * allocation after start-up (an allocation may block or fail under fragmentation), or a
+ * framework that owns all device memory through its own pool; mesh_create allocates, so such
+ * code cannot use a handle.  It places the Dirichlet-eliminated Poisson matrix (or any
  * symmetric positive definite matrix) in device memory as CSR and solves A x = b:
  *   row_ptr[n+1], col[nnz], val[nnz], b[n]  device pointers, read only;
- *   x[n]  device pointer: initial guess in, solution out;
+ *   x[n]  device pointer: initial guess in, solution out (b = 0 gives x = 0);
  *   stop when ||b - A x||_2 <= rtol ||b||_2 (true residual), at most max_iter iterations;
- *   stream: cudaStream_t the solve is queued on (NULL = default); the call waits for it.
+ *   stream: cudaStream_t the solve is queued on (NULL = default).
+ * The call is synchronous: it copies the status back and waits for `stream`, so it blocks the
+ * host thread until the solve ends.  iters_out / relres_out (may be NULL) receive the
+ * iteration count and ||b - A x|| / ||b|| of the returned x.
  * Work vectors live in one fixed array compiled into the library (AVIP_STATIC_PCG_MAX_ROWS
  * rows, about 10.5 MB, present on every GPU that loads the library until exit).  The first
- * call on a device looks up that array's device address; make it before any stream capture.
- * Calls that overlap on the GPU share the array and race: order them on one stream.
+ * call made on a device looks up that array's device address (no allocation); after
+ * cudaDeviceReset of that device the entry point must not be called on it again.  Calls that
+ * overlap on the GPU share the array and race: order them on one stream.
  * Returns AVIP_EINVAL for n > AVIP_STATIC_PCG_MAX_ROWS or bad arguments, AVIP_ENOTCONV when
  * max_iter was reached (x holds the last iterate).  Allocates nothing. */
 #define AVIP_STATIC_PCG_MAX_ROWS 262144
 int pcg_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* col, const double* val, const double* b,
                    double* x, double rtol, int32_t max_iter, void* stream, int32_t* iters_out, double* relres_out);
+
+/* Roofline denominators measured on the current device (the paper has no counterpart: a
+ * measurement aid).  which = AVIP_PROBE_FP64_FMA: FP64 fused multiply-add rate in TFLOP/s (8
+ * independent FMA chains per thread, every SM full, 2 flops per FMA); AVIP_PROBE_HBM_COPY:
+ * device-memory copy bandwidth in GB/s (1 GiB copied between two buffers larger than L2, read
+ * plus write bytes).  Best of 5 launches timed with CUDA events on `stream` (NULL = default)
+ * after one untimed launch; the call waits for them and writes the figure to *value_out.  It
+ * allocates and frees its own device buffers (2 GiB for the copy).  AVIP_EINVAL for an unknown
+ * `which` or a NULL value_out, AVIP_ENOMEM, AVIP_ECUDA. */
+#define AVIP_PROBE_FP64_FMA 0
+#define AVIP_PROBE_HBM_COPY 1
+int peak_probe(int32_t which, void* stream, double* value_out);
 
 /* Human-readable text of a status code (static storage). */
 const char* avip_status_str(int status);

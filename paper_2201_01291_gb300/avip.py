@@ -34,7 +34,7 @@ class AvipOpts(C.Structure):
                 ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32),
-                ("v_rise", C.c_double)]
+                ("v_rise", C.c_double), ("wait_timeout", C.c_double)]
 
 
 class AvipStats(C.Structure):
@@ -66,6 +66,7 @@ _SIGS = {
                                _D, _I, _D, _D]),
     "avip_inspect_error": (C.c_char_p, []),
     "mesh_set_stream": (C.c_int, [_H, C.c_void_p]),
+    "mesh_set_wait_timeout": (C.c_int, [_H, C.c_double]),
     "mesh_info": (C.c_int, [_H, _P(C.c_int64)]),
     "solver_levels": (C.c_int, [_H, _P(C.c_int64), C.c_int32]),
     "species_set": (C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, _D, C.c_double, C.c_int32, _D]),
@@ -85,6 +86,7 @@ _SIGS = {
     "batch_destroy": (C.c_int, [_H]),
     "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_int32, C.c_void_p, _I, _D]),
+    "peak_probe": (C.c_int, [C.c_int32, C.c_void_p, _D]),
     "avip_status_str": (C.c_char_p, [C.c_int]),
     "avip_last_error": (C.c_char_p, []),
 }
@@ -248,6 +250,10 @@ def mesh_set_stream(h, stream):
     return load().mesh_set_stream(h, C.c_void_p(stream))
 
 
+def mesh_set_wait_timeout(h, seconds):
+    return load().mesh_set_wait_timeout(h, float(seconds))
+
+
 def field_get(h, which, s, n_nodes):
     out = np.empty(n_nodes)
     rc = load().field_get(h, which, s, _dptr(out))
@@ -300,6 +306,16 @@ def pcg_csr_static(n, row_ptr, col, val, b, x, rtol, max_iter, stream=0):
     return rc, it.value, rr.value
 
 
+PROBE_FP64_FMA, PROBE_HBM_COPY = 0, 1
+
+
+def peak_probe(which, stream=0):
+    """Measured FP64 FMA rate (TFLOP/s) or copy bandwidth (GB/s) of the current device."""
+    v = C.c_double()
+    rc = load().peak_probe(int(which), C.c_void_p(stream), C.byref(v))
+    return rc, v.value
+
+
 def batch_create(handles, cluster_size=0):
     arr = (_H * len(handles))(*[h.value if isinstance(h, _H) else h for h in handles])
     b = _H()
@@ -348,7 +364,8 @@ class Mesh:
     """Owns one handle built from a synthetic workload (see workloads.Problem)."""
 
     def __init__(self, problem, precision=PREC_FP64, rtol=None, max_iter=None, dt_fixed=None,
-                 reorder=1, use_torch_allocator=False, stream=None, pcg_threads=0, pcg_kind=0):
+                 reorder=1, use_torch_allocator=False, stream=None, pcg_threads=0, pcg_kind=0,
+                 wait_timeout=None):
         o = avip_opts_default()
         po = problem.opts
         o.cfl, o.fourier, o.a_diel, o.a_chem = po.cfl, po.fourier, po.a_diel, po.a_chem
@@ -363,6 +380,8 @@ class Mesh:
         o.geometry = GEOM_AXISYMMETRIC if getattr(problem, "axisymmetric", False) else GEOM_PLANAR
         o.scheme = getattr(po, "scheme", FLUX_LLW)
         o.v_rise = getattr(po, "v_rise", 0.0)
+        if wait_timeout is not None:
+            o.wait_timeout = wait_timeout
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()
@@ -424,6 +443,9 @@ class Mesh:
 
     def set_stream(self, stream):
         _check(mesh_set_stream(self.h, stream), "mesh_set_stream")
+
+    def set_wait_timeout(self, seconds):
+        _check(mesh_set_wait_timeout(self.h, seconds), "mesh_set_wait_timeout")
 
     def field(self, which, s=0):
         rc, out = field_get(self.h, which, s, self.N)

@@ -70,7 +70,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         if rc != 0:
             raise RuntimeError(f"compile failed: {cmd}\n{out}")
     tmp = LIB + ".tmp"
-    rc, cmd, out = _run([nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs, "-lpthread"])
+    rc, cmd, out = _run([nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs, "-lpthread", "-ldl"])
     if rc != 0:
         raise RuntimeError(f"link failed: {cmd}\n{out}")
     os.replace(tmp, LIB)

@@ -9,9 +9,20 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "avip_internal.h"
 
 namespace avip {
+// NVTX range around the host code that queues one stage (kernel) or one step, so that a
+// timeline tool shows the library's work by name; free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_bicgstab(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
@@ -180,6 +191,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.res = h->sc;
   a.rtol = h->opts.rtol;
   a.v_rise = h->opts.v_rise;
+  a.spin_ns = (unsigned long long)(h->opts.wait_timeout * 1e9);
   a.max_iter = h->opts.max_iter;
   a.use_density_rhs = 1;
   a.aval32 = h->aval32;
@@ -302,15 +314,32 @@ cudaError_t enqueue_photo(avip_mesh* h, const DDArgs& a, bool auto_dt) {
 
 // Queue one explicit step (no host synchronisation).
 cudaError_t enqueue_step(avip_mesh* h) {
-  cudaError_t e = enqueue_poisson(h);
-  if (e != cudaSuccess) return e;
+  NvtxRange step("avip.step");
+  cudaError_t e;
+  {
+    NvtxRange r("avip.poisson_solve");
+    if ((e = enqueue_poisson(h)) != cudaSuccess) return e;
+  }
   DDArgs a = dd_args(h);
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
   const bool photo = h->ph.photo_terms > 0;
-  if ((e = launch_node_fields(a, auto_dt && !photo ? 1 : 0, h->stream)) != cudaSuccess) return e;
-  if (photo && (e = enqueue_photo(h, a, auto_dt)) != cudaSuccess) return e;
-  if (auto_dt && (e = launch_dt_cells(a, h->stream)) != cudaSuccess) return e;
-  if ((e = launch_flux_update(a, h->stream)) != cudaSuccess) return e;
+  {
+    NvtxRange r("avip.node_fields");
+    if ((e = launch_node_fields(a, auto_dt && !photo ? 1 : 0, h->stream)) != cudaSuccess) return e;
+  }
+  if (photo) {
+    NvtxRange r("avip.photoionisation");
+    if ((e = enqueue_photo(h, a, auto_dt)) != cudaSuccess) return e;
+  }
+  if (auto_dt) {
+    NvtxRange r("avip.dt_cells");
+    if ((e = launch_dt_cells(a, h->stream)) != cudaSuccess) return e;
+  }
+  {
+    NvtxRange r("avip.fluxes_update");
+    if ((e = launch_flux_update(a, h->stream)) != cudaSuccess) return e;
+  }
+  NvtxRange r("avip.finalize");
   return launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
 }
 
@@ -414,8 +443,12 @@ int avip_opts_default(avip_opts* o) {
   o->reorder = 1;
   o->dt_fixed = 0.0;
   o->inner_rtol = 1e-4;
+  o->wait_timeout = 2.0;
   return AVIP_OK;
 }
+
+// Accepted range of a device-wait limit (seconds).
+static bool wait_timeout_ok(double s) { return s >= 0.0 && s <= 60.0; }
 
 const char* avip_status_str(int s) {
   switch (s) {
@@ -450,7 +483,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   else
     avip_opts_default(&h->opts);
   if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
-      !(h->opts.v_rise >= 0) || !std::isfinite(h->opts.v_rise) ||
+      !(h->opts.v_rise >= 0) || !std::isfinite(h->opts.v_rise) || !wait_timeout_ok(h->opts.wait_timeout) ||
       (h->opts.scheme != AVIP_FLUX_LLW && h->opts.scheme != AVIP_FLUX_SG) ||
       (h->opts.precision != AVIP_PREC_FP64 && h->opts.precision != AVIP_PREC_MIXED) ||
       (h->opts.precision == AVIP_PREC_MIXED && !(h->opts.inner_rtol > 0 && h->opts.inner_rtol < 1))) {
@@ -664,6 +697,15 @@ int mesh_set_stream(avip_mesh_t h, void* stream) {
   return AVIP_OK;
 }
 
+int mesh_set_wait_timeout(avip_mesh_t h, double seconds) {
+  if (!h || !wait_timeout_ok(seconds)) return AVIP_EINVAL;
+  if (h->opts.wait_timeout != seconds) {
+    h->opts.wait_timeout = seconds;
+    invalidate_graph(h);  // the captured step carries the old limit in its kernel arguments
+  }
+  return AVIP_OK;
+}
+
 int mesh_info(avip_mesh_t h, int64_t* info) {
   if (!h || !info) return AVIP_EINVAL;
   info[0] = h->hm.N;
@@ -822,7 +864,9 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
 
 int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out) {
   if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
-  cudaError_t e = enqueue_poisson(h);
+  // clear the status a failed earlier run left (a solve is skipped while it says ENAN/ETIMEOUT)
+  cudaError_t e = launch_run_reset(h->sc, h->stream);
+  if (e == cudaSuccess) e = enqueue_poisson(h);
   if (e == cudaSuccess) e = launch_node_fields(dd_args(h), 0, h->stream);
   if (e != cudaSuccess) return cuda_status(e);
   DevScalars sc;
@@ -865,7 +909,10 @@ static int run_impl(avip_mesh_t h, int32_t nsteps, double dt, avip_stats* stats,
         e = cudaSuccess;
       }
     }
-    for (int32_t k = 0; k < nsteps && e == cudaSuccess && use_graph; ++k) e = cudaGraphLaunch(h->graph, h->stream);
+    for (int32_t k = 0; k < nsteps && e == cudaSuccess && use_graph; ++k) {
+      NvtxRange r("avip.step_graph");
+      e = cudaGraphLaunch(h->graph, h->stream);
+    }
     if (!use_graph)
       for (int32_t k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(h);
   } else {
@@ -920,6 +967,7 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
   cudaError_t e = launch_run_reset(h->sc, h->stream);
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
   for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    NvtxRange r("avip.step_timed");
     DDArgs a = dd_args(h);
     e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);

@@ -225,6 +225,7 @@ struct PcgArgs {
   int32_t* hist;           // how many of them are valid (0, 1, 2); advanced by the solve
   double rtol;
   double v_rise;          // > 0: the Dirichlet lift is scaled by min(t / v_rise, 1) (voltage ramp)
+  unsigned long long spin_ns;  // bound of every grid-barrier wait (the handle's wait_timeout)
   int32_t max_iter;
   int32_t use_density_rhs;  // 1: b from densities; 0: b already in `b`
   // mixed precision: FP32 copy of the scaled matrix and FP32 inner-CG vectors

@@ -5,8 +5,13 @@
 // totals (deterministic, independent of arrival order).  An optional epilogue derives scalars
 // from the totals (e.g. the CG step alpha = r.r / p.q) once per block.
 //
-// Every wait is bounded: after kSpinLimitNs of polling a block raises `abort`, every waiter
-// leaves, and the kernel reports a timeout instead of hanging.
+// Every wait is bounded: after FlagSync::spin_ns of polling (the handle's wait_timeout) a block
+// raises `abort`, every waiter leaves, and the kernel reports a timeout instead of hanging.
+//
+// The arrival counter is a 32-bit value that only grows (mod 2^32); a block waits for barrier
+// seq until counter - seq * gridDim.x, taken as a signed difference, is no longer negative.  The
+// counter never runs more than gridDim.x arrivals ahead of or behind the barrier a block waits
+// for, so the test stays right when seq * gridDim.x wraps past 2^32 on very long solves.
 #pragma once
 #include <cstdint>
 
@@ -14,7 +19,7 @@
 
 namespace avip {
 
-constexpr unsigned long long kSpinLimitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kSpinLimitNs = 2000000000ull;  // default wait limit: 2 s
 constexpr int kPollUnroll = 8;  // partial loads per lane kept in flight (grids up to 256 blocks)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -74,7 +79,27 @@ struct FlagSync {
   double* parts;  // [2][gridDim.x][4]
   GridSync* gs;   // abort flag
   unsigned seq;   // reductions passed so far (identical in every thread)
+  unsigned long long spin_ns;  // give up a wait after this long (0: at the first unsatisfied poll)
 };
+
+// True while the arrival counter has not reached `target` (wrap-safe, see above).
+__device__ __forceinline__ bool arrivals_behind(const unsigned* counter, unsigned target) {
+  return (int)(ld_acquire_u32(counter) - target) < 0;
+}
+
+// Bounded wait of one thread for `target` arrivals: false if the wait was abandoned (its time
+// limit passed, or another block raised `abort`).  The limit and the abort flag are checked on
+// the first poll and then every 64 polls.
+__device__ __forceinline__ bool wait_arrivals(const FlagSync& fs, unsigned target) {
+  const unsigned long long t0 = global_timer_ns();
+  unsigned spins = 0;
+  while (arrivals_behind(fs.flags, target)) {
+    if ((spins++ & 63u) == 0) {
+      if (*((volatile int*)&fs.gs->abort) || global_timer_ns() - t0 >= fs.spin_ns) return false;
+    }
+  }
+  return true;
+}
 
 // Shared-memory scratch of grid_allsum.  A __shared__ variable declared inside a function
 // template exists once per instantiation, so a kernel that reduces with several (NV, NE)
@@ -147,17 +172,7 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 
         for (int k = 0; k < NV; ++k) __stcg(mine + k, bt[k]);
         red_add_release_u32(fs.flags, 1u);
       }
-      const unsigned target = seq * (unsigned)nb;
-      const unsigned long long t0 = global_timer_ns();
-      unsigned spins = 0;
-      while (ld_acquire_u32(fs.flags) < target) {
-        if ((++spins & 63u) == 0) {
-          if (*((volatile int*)&fs.gs->abort) || global_timer_ns() - t0 > kSpinLimitNs) {
-            ok = 0;
-            break;
-          }
-        }
-      }
+      if (!wait_arrivals(fs, seq * (unsigned)nb)) ok = 0;
       ok = __all_sync(0xffffffffu, ok);
       double acc[NV];
 #pragma unroll
@@ -232,17 +247,7 @@ __device__ __forceinline__ bool grid_barrier(FlagSync& fs) {
     const int nb = gridDim.x;
     if (nb > 1) {
       red_add_release_u32(fs.flags, 1u);
-      const unsigned target = seq * (unsigned)nb;
-      const unsigned long long t0 = global_timer_ns();
-      unsigned spins = 0;
-      while (ld_acquire_u32(fs.flags) < target) {
-        if ((++spins & 63u) == 0) {
-          if (*((volatile int*)&fs.gs->abort) || global_timer_ns() - t0 > kSpinLimitNs) {
-            ok = 0;
-            break;
-          }
-        }
-      }
+      if (!wait_arrivals(fs, seq * (unsigned)nb)) ok = 0;
     }
     if (!ok) atomicExch(&fs.gs->abort, 1);
     scr.ok = ok;

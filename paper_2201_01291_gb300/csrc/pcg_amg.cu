@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   constexpr int wpb = TPB / 32;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
   if (!amg_cg_solve(a, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb, threadIdx.x & 31,
                     blockIdx.x == 0 && threadIdx.x == 0) &&
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   double* __restrict__ rh = a.bcg + 2 * Np;
   double* __restrict__ ph = a.bcg + 3 * Np;
   double* __restrict__ sh = a.bcg + 4 * Np;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
   double dummy = 0.0;
 
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_mixed_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   constexpr int wpb = TPB / 32;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
   if (!amg_mixed_solve(a, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb, threadIdx.x & 31,
                        blockIdx.x == 0 && threadIdx.x == 0) &&

@@ -3,15 +3,27 @@
 // fixed-size scratch array compiled into this library.
 //
 // Who needs it: callers that must not call cudaMalloc or any allocating routine at all, e.g.
-// code that runs while a CUDA stream is being captured into a graph (allocation is not
-// permitted during capture), real-time loops with a fixed memory budget that forbid
-// allocation after start-up, or hosts whose framework has reserved all device memory through
-// its own pool.  Such callers cannot create a mesh handle (mesh_create allocates), but they
-// can solve the same Poisson system from CSR arrays they placed in device memory themselves.
+// real-time loops with a fixed memory budget that forbid allocation after start-up (an
+// allocation can block on the driver or fail under fragmentation at the worst moment), or
+// hosts whose framework has reserved all device memory through its own pool, so that a
+// cudaMalloc from a library would fail or steal from it.  Such callers cannot create a mesh
+// handle (mesh_create allocates), but they can solve the same Poisson system from CSR arrays
+// they placed in device memory themselves.
+//
+// The call is synchronous: it queues the solve on the caller's stream, copies the status back
+// to the host and waits for that stream, so it blocks the calling host thread until the solve
+// has finished.
 //
 // The scratch array lives in every GPU that loads the library until the process exits
-// (kStaticMaxRows rows, about 10.5 MB).  All calls share it: calls that overlap on the GPU
-// (different streams or host threads without ordering) race and corrupt each other.
+// (kStaticMaxRows rows, about 10.5 MB).  All calls share it and it keeps the last call's
+// contents: every call clears the barrier words it needs and overwrites the work vectors
+// before reading them.  Calls that overlap on the GPU (different streams or host threads
+// without ordering) race and corrupt each other.
+//
+// Its device address is looked up once per device, by the first call made with that device
+// current (cudaGetSymbolAddress, which allocates nothing).  cudaDeviceReset destroys the
+// context that address belongs to: a process that resets a device must not call this entry
+// point on that device again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,7 +80,7 @@ __global__ void __launch_bounds__(kStaticTPB) pcg_csr_static_kernel(StaticPcgArg
   double* z = r + kStaticMaxRows;
   double* p = z + kStaticMaxRows;
   double* q = p + kStaticMaxRows;
-  FlagSync fs{flags, parts, gs, 0u};
+  FlagSync fs{flags, parts, gs, 0u, kSpinLimitNs};
   const int n = a.n;
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,6 +108,15 @@ __global__ void __launch_bounds__(kStaticTPB) pcg_csr_static_kernel(StaticPcgArg
     red[2] = fma(bi, bi, red[2]);
   }
   if (!grid_allsum<3>(red, fs, smem)) goto timeout;
+  if (red[2] == 0.0) {  // b = 0: the solution is x = 0, whatever the initial guess
+    for (int i = t0; i < n; i += stride) a.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.status_out[0] = AVIP_OK;
+      a.status_out[1] = 0;
+      a.relres_out[0] = 0.0;  // b - A 0 = 0 exactly
+    }
+    return;
+  }
   {
     double rz = red[0], rr = red[1];
     const double bb = red[2];
@@ -119,7 +140,7 @@ __global__ void __launch_bounds__(kStaticTPB) pcg_csr_static_kernel(StaticPcgArg
         }
         if (!grid_allsum<2>(tr, fs, smem)) goto timeout;
         rr_true = tr[1];
-        if (rr_true <= thresh || bb == 0.0) break;
+        if (rr_true <= thresh) break;
         if (it >= a.max_iter || restarts >= 8) {
           status = AVIP_ENOTCONV;
           break;
@@ -163,7 +184,7 @@ __global__ void __launch_bounds__(kStaticTPB) pcg_csr_static_kernel(StaticPcgArg
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.status_out[0] = status;
       a.status_out[1] = it;
-      a.relres_out[0] = bb > 0.0 ? sqrt(rr_true / bb) : 0.0;
+      a.relres_out[0] = sqrt(rr_true / bb);  // true residual of the x returned
     }
     return;
   }

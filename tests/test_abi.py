@@ -64,6 +64,14 @@ def test_mesh_validation_on_host(lib):
     o2 = avip.avip_opts_default()
     o2.rtol = -1.0
     assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o2)[0] == avip.AVIP_EINVAL
+    # the device-wait limit: default 2 s, 0 allowed (fail at the first wait), negative, NaN or
+    # above 60 s rejected before any CUDA call
+    assert avip.avip_opts_default().wait_timeout == 2.0
+    for bad_limit in (-1.0, float("nan"), 61.0):
+        o3 = avip.avip_opts_default()
+        o3.wait_timeout = bad_limit
+        assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o3)[0] == avip.AVIP_EINVAL
+    assert avip.mesh_set_wait_timeout(None, 1.0) == avip.AVIP_EINVAL
 
 
 def test_axisymmetric_validation_on_host(lib):

@@ -24,6 +24,9 @@ def test_reference_arm_json_contract():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+    # both arms print the same workload-only config, and the baseline names its host CPU
+    assert set(line["config"]) == {"workload", "n_nodes", "n_cells", "rtol", "precision", "seed"}
+    assert line["cpu_baseline"]["cpu_model"] and line["cpu_baseline"]["nproc"] >= 1
 
 
 def test_traffic_models_match_their_formulas():

@@ -1,0 +1,44 @@
+"""Parity at the full size the benchmark times: the pin-plane streamer, 1 cm x 2 cm, 500 x 1000
+jittered nodes (997,002 triangles), 20 kV needle, local-field mobility and Townsend ionisation,
+FP64, in the benchmark's launch configuration (library defaults: CG preconditioned by the AMG
+V-cycle over the whole GPU, rtol 1e-12, the step graph of run_steps).  The oracle (exact sparse
+LU solve of the Poisson system of Eq. coeff_matriceA, then the step of Eq. vertex_centered_flux)
+finishes the three steps in seconds; phi and both densities must agree norm-wise to 1e-10."""
+import numpy as np
+import pytest
+
+import avip_oracle as O
+from helpers import normwise
+from paper_2201_01291_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 3
+RTOL_BENCH = 1e-12
+
+
+@pytest.fixture(scope="module")
+def avip():
+    from paper_2201_01291_gb300 import build
+    build.build()
+    from paper_2201_01291_gb300 import avip as A
+    A.load()
+    return A
+
+
+def test_pin_plane_500x1000_matches_oracle(avip):
+    p = W.config_pin_plane()
+    assert p.n_nodes == 500_000 and p.n_cells == 997_002
+    o = O.Oracle(p)
+    n_ref, phi_ref, dts = o.run(STEPS)
+    m = avip.Mesh(p, rtol=RTOL_BENCH)
+    assert m.info["pcg_kind"] == 8            # the benchmark's solver
+    st = m.run(STEPS)
+    assert st["status"] == avip.AVIP_OK and st["steps"] == STEPS
+    assert st["relres_max"] <= RTOL_BENCH
+    err = {"phi": normwise(m.phi(), phi_ref)}
+    for s, name in enumerate(("n_e", "n_p")):
+        err[name] = normwise(m.density(s), n_ref[s])
+    assert abs(st["t"] - sum(dts)) <= 1e-12 * sum(dts)
+    m.close()
+    assert max(err.values()) <= 1e-10, err

@@ -55,6 +55,40 @@ def test_static_pcg_matches_poisson_solve_twice():
     m.close()
 
 
+def test_static_pcg_iteration_cap_and_zero_rhs():
+    """The failure path: max_iter reached gives AVIP_ENOTCONV, x holds the last iterate and the
+    reported relative residual is that of x (recomputed here on the host); a zero right-hand
+    side gives x = 0 from any initial guess."""
+    import torch
+    from paper_2201_01291_gb300 import avip, build
+    build.build()
+    avip.load()
+    p = W.config_small(nx=41, ny=37, seed=23, voltage=1e4)
+    o = O.Oracle(p)
+    free, KFF, b = _free_system(o, p, o.initial_state())
+    dev = torch.device("cuda", 0)
+    rp = torch.tensor(KFF.indptr, dtype=torch.int32, device=dev)
+    ci = torch.tensor(KFF.indices, dtype=torch.int32, device=dev)
+    va = torch.tensor(KFF.data, dtype=torch.float64, device=dev)
+    bd = torch.tensor(b, dtype=torch.float64, device=dev)
+    x = torch.zeros(free.size, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    rc, it, rr = avip.pcg_csr_static(free.size, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), bd.data_ptr(),
+                                     x.data_ptr(), 1e-14, 5, st)
+    assert rc == avip.AVIP_ENOTCONV and it == 5
+    xh = x.cpu().numpy()
+    ref = np.linalg.norm(b - KFF @ xh) / np.linalg.norm(b)
+    assert abs(rr - ref) <= 1e-8 * ref and ref > 1e-6
+    # b = 0 from the non-zero iterate left above: x = 0, converged at once
+    bd.zero_()
+    torch.cuda.synchronize()
+    rc, it, rr = avip.pcg_csr_static(free.size, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), bd.data_ptr(),
+                                     x.data_ptr(), 1e-14, 5, st)
+    assert rc == avip.AVIP_OK and it == 0 and rr == 0.0
+    assert torch.count_nonzero(x).item() == 0
+
+
 def test_static_pcg_rejects_oversize():
     from paper_2201_01291_gb300 import avip
     avip.load()
