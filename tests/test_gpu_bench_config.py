@@ -39,6 +39,8 @@ def test_pin_plane_500x1000_matches_oracle(avip):
     err = {"phi": normwise(m.phi(), phi_ref)}
     for s, name in enumerate(("n_e", "n_p")):
         err[name] = normwise(m.density(s), n_ref[s])
-    assert abs(st["t"] - sum(dts)) <= 1e-12 * sum(dts)
+    # the automatic time step divides by the largest drift speed, i.e. by max |E|, which the
+    # solve fixes only to its tolerance: the simulated time is held to the parity bar
+    err["t"] = abs(st["t"] - sum(dts)) / sum(dts)
     m.close()
     assert max(err.values()) <= 1e-10, err
