@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--pcg-kind", type=int, default=0,
                     help="solver kernel: 0 auto, 1 streaming, 2 register-resident, 5 cluster-resident, 7 BiCGStab, "
                          "8 AMG-preconditioned CG")
+    ap.add_argument("--precond-fp64", action="store_true",
+                    help="AMG solvers: apply the V-cycle in FP64 instead of FP32")
     ap.add_argument("--pcg-max-iter", type=int, default=0,
                     help="cap PCG iterations per solve (profiling captures only; not a bench setting)")
     return ap.parse_args()
@@ -224,9 +226,6 @@ NCU_DRAM_BYTES_PER_ITER = {
     # pcg_fp64_res_kernel: 300-iteration capture, L2-resident working set
     2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
                                             "launch's iterations (L2-resident working set)"),
-    # pcg_amg_kernel<512>: one 21-iteration solve
-    8: ((3429.264e6 + 682.181e6) / 21.0, "ncu DRAM read+write of a 21-iteration solve scaled to the launch's "
-                                         "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
 }
 
 
@@ -245,7 +244,7 @@ def pcg_traffic_model(info, iters, solves):
         flops 4 nnz + 32 N per iteration."""
     N, nnz, kind = info["n_nodes"], info["nnz"], info["pcg_kind"]
     if kind in (8, 9, 10):
-        return amg_traffic_model(info["levels"], nnz, N, iters, solves, kind)
+        return amg_traffic_model(info["levels"], nnz, N, iters, solves, kind, sv=info.get("precond_bytes", 4))
     per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
     per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
                  7: 24 * nnz + 170 * N}.get(kind, 0)
@@ -257,34 +256,44 @@ def pcg_traffic_model(info, iters, solves):
     return bytes_, flops
 
 
-def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8):
-    """Algorithmic bytes and flops of the AMG-preconditioned CG launch (kind 8).  Per CG
-    iteration and non-coarsest level l (n rows, a = nnz(A_l), p = nnz(P_l), n' coarse rows),
-    counting 12 B per stored entry (column + value), 4 B row length, one 8 B read per gathered
-    and per own vector element: four products with A_l, one with P_l and one with R_l,
-    48 a + 24 p + 196 n + 36 n' bytes; the coarsest level reads its dense inverse (8 n_c^2);
-    the CG phases add 12 nnz + 116 N.  Flops: 2 per stored entry of every product, 20 per row
-    and level for the smoothing and update arithmetic, 12 N for CG.  BiCGStab (kind 9) applies
-    two V-cycles per iteration and its phases add 24 nnz + 216 N bytes and 4 nnz + 32 N flops.
-    The mixed-precision form (kind 10) moves FP32 values: 8 B per stored entry, 4 B per vector
-    element (the handful of FP64 outer residuals per solve are counted with the solve)."""
-    cycles = 2 if kind == 9 else 1
-    ent, vec = (8.0 / 12.0, 0.5) if kind == 10 else (1.0, 1.0)
-    per_it = (24 * nnz0 + 216 * N) if kind == 9 else (12 * nnz0 + 116 * N)
-    fl_it = (4 * nnz0 + 32 * N) if kind == 9 else (2 * nnz0 + 12 * N)
-    vb, vf = 0, 0
-    for l, (n, a, p) in enumerate(levels):
-        if l + 1 < len(levels):
-            nc = levels[l + 1][0]
-            vb += ent * (48 * a + 24 * p) + vec * (196 * n + 36 * nc)
-            vf += 2 * (4 * a + 2 * p) + 20 * n
+def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
+    """Algorithmic bytes and flops of one step's AMG-preconditioned launch (kinds 8, 9, 10).
+
+    Conventions: every stored entry of an operator is read once (4 B column + sv B value; sv = 4
+    for the FP32 hierarchy, 8 for FP64) and costs 2 flops; a gathered vector is read once per
+    product (as if every reuse hit a cache), an own-row vector element once per access, a
+    written one once, and each row length once (4 B).  With levels[l] = (n, nnz A, nnz P, nnz
+    Rf, nnz U, nnz Pf) and n' the next level's rows, one V-cycle moves, per non-coarsest level:
+      down  (nnz A + nnz Rf)(4 + sv) + sv (n + n + n') + 4 (n + n')   [Q b, Rf b]
+      up    (nnz U + nnz Pf)(4 + sv) + sv (n + n' + n) + 8 n           [U xp + Pf x']
+    and on the coarsest level sv (n_c^2 + 2 n_c) (dense inverse).  In the FP64 CG (kind 8) the
+    finest down phase gathers the FP64 residual and q (16 N instead of sv N) and updates x and
+    r (p, x read, x, r written: 32 N); the finest up phase reads r for r.z (8 N); w = A z reads
+    A (12 nnz), z (sv N), p, q (16 N), writes p, q (16 N), 4 N row lengths.  BiCGStab (kind 9)
+    applies two V-cycles per iteration (FP64 input and output, 8 N each instead of sv N) and its
+    phases add 24 nnz + 216 N bytes.  The mixed-precision solve (kind 10) runs the FP32 V-cycle
+    on FP32 vectors and its inner CG moves 8 B per stored entry of A and 4 B per vector element:
+    8 nnz + 60 N.  Per solve: set-up and the final true residual, 24 nnz + 100 N."""
+    vb, vf = 0.0, 0.0
+    nl = len(levels)
+    for l, (n, a, p, rf, u, pf) in enumerate(levels):
+        if l + 1 < nl:
+            nn = levels[l + 1][0]
+            vb += (a + rf) * (4 + sv) + sv * (2 * n + nn) + 4 * (n + nn)
+            vb += (u + pf) * (4 + sv) + sv * (2 * n + nn) + 8 * n
+            vf += 2 * (a + rf + u + pf) + n
         else:
-            vb += vec * (8 * n * n + 16 * n)
+            vb += sv * (n * n + 2 * n)
             vf += 2 * n * n
-    if kind == 10:
-        per_it = ent * 12 * nnz0 + vec * 116 * N
-    per_it += cycles * vb
-    fl_it += cycles * vf
+    if kind == 9:
+        per_it = 2 * (vb + 2 * (8 - sv) * N) + 24 * nnz0 + 216 * N
+        fl_it = 2 * vf + 4 * nnz0 + 32 * N
+    elif kind == 10:
+        per_it = vb + 8 * nnz0 + 60 * N
+        fl_it = vf + 2 * nnz0 + 12 * N
+    else:
+        per_it = vb + (16 - sv) * N + 32 * N + 8 * N + 12 * nnz0 + (sv + 36) * N
+        fl_it = vf + 2 * nnz0 + 14 * N
     per_solve = 24 * nnz0 + 100 * N
     return iters * per_it + solves * per_solve, iters * fl_it + solves * (4 * nnz0 + 12 * N)
 
@@ -305,6 +314,7 @@ def run_ours(args, rank, world, local_rank):
     kw = {"max_iter": args.pcg_max_iter} if args.pcg_max_iter > 0 else {}
     allow = (avip.AVIP_OK, avip.AVIP_ENOTCONV) if args.pcg_max_iter > 0 else (avip.AVIP_OK,)
     prec = avip.PREC_MIXED if args.precision == "mixed" else avip.PREC_FP64
+    kw["precond_fp64"] = 1 if args.precond_fp64 else 0
     m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads,
                   pcg_kind=args.pcg_kind, precision=prec, **kw)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
@@ -358,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
         host = m.state()
     e2e_t, _ = aggregate(max(time.perf_counter() - t0, 1e-9), 1, world)
     state_bytes = host.size * 8
-    info = m.info
+    info = dict(m.info, precond_bytes=8 if (args.precond_fp64 and args.precision == "fp64") else 4)
     m.close()
     # a fresh handle for the oracle comparison of the CPU-baseline leg (same steps from t = 0)
     check = None
@@ -416,6 +426,9 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": workload_config(problem, desc, args),
+        "preconditioner": ("AMG V-cycle in " + ("FP64" if info["precond_bytes"] == 8 else "FP32") +
+                           "; Krylov iterate, residuals, products with the Poisson matrix and stopping test in FP64")
+        if info["pcg_kind"] in (8, 9, 11) else None,
         "parallelism": f"replicas x{world}", "nnz": info["nnz"],
         "l2": "flushed between timed steps (256 MiB write inside the timed region)",
         "e2e": {"value": world * T * e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,

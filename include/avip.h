@@ -131,6 +131,12 @@ typedef struct avip_opts {
                                           the handle stays usable.  Default 2; 0 gives up at the
                                           first wait that is not already satisfied (a test of the
                                           failure path); at most 60 */
+  int32_t precond_fp64;                /* AMG solvers of the FP64 path: 0 (default) applies the
+                                          V-cycle preconditioner with FP32 values and vectors
+                                          (the Krylov iterate, the products with the Poisson
+                                          matrix, the residuals and the stopping test stay
+                                          FP64, so the solution meets rtol all the same); 1
+                                          applies it in FP64 */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */
@@ -295,9 +301,12 @@ int mesh_info(avip_mesh_t h, int64_t* info8);
 /* Multigrid hierarchy of the AMG-preconditioned solvers (kinds 8-11; the paper names no solver, this
  * reports the set-up built for this project's preconditioner).  Returns the number of levels
  * (finest first, the last one inverted densely), or 0 when the handle uses another solver; for
- * the first min(levels, max_levels) levels writes out[3*l] = rows, out[3*l+1] = stored entries
- * of the level matrix, out[3*l+2] = stored entries of the prolongator from the next level
- * (0 on the coarsest).  AVIP_EINVAL for a NULL handle or a NULL `out` with max_levels > 0. */
+ * the first min(levels, max_levels) levels writes AVIP_LEVEL_STATS values per level at
+ * out[AVIP_LEVEL_STATS * l]: rows, stored entries of the level matrix A, of the prolongator P
+ * from the next level, and of the composite operators the V-cycle applies, Rf = R (I - A Q),
+ * U = 2 I - Q A and Pf = (I - Q A) P (Q: the smoother, with A's sparsity); the last four are 0
+ * on the coarsest level.  AVIP_EINVAL for a NULL handle or a NULL `out` with max_levels > 0. */
+#define AVIP_LEVEL_STATS 6
 int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels);
 
 /* ---- batches (many independent instances per step) -------------------------------------

@@ -34,7 +34,7 @@ class AvipOpts(C.Structure):
                 ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32),
-                ("v_rise", C.c_double), ("wait_timeout", C.c_double)]
+                ("v_rise", C.c_double), ("wait_timeout", C.c_double), ("precond_fp64", C.c_int32)]
 
 
 class AvipStats(C.Structure):
@@ -272,14 +272,17 @@ def mesh_info(h):
                 device_bytes=int(info[7]))
 
 
+LEVEL_STATS = 6
+
+
 def solver_levels(h, max_levels=12):
-    """AMG hierarchy of the handle's solver: list of (rows, nnz of A, nnz of P) per level,
-    finest first; empty when the solver is not the AMG-preconditioned CG."""
-    out = np.zeros(3 * max_levels, dtype=np.int64)
+    """AMG hierarchy of the handle's solver: list of (rows, nnz of A, nnz of P, nnz of Rf,
+    nnz of U, nnz of Pf) per level, finest first; empty when the solver is not AMG."""
+    out = np.zeros(LEVEL_STATS * max_levels, dtype=np.int64)
     nl = load().solver_levels(h, out.ctypes.data_as(_P(C.c_int64)), max_levels)
     if nl < 0:
         _check(nl, "solver_levels")
-    return [tuple(int(v) for v in out[3 * l:3 * l + 3]) for l in range(min(nl, max_levels))]
+    return [tuple(int(v) for v in out[LEVEL_STATS * l:LEVEL_STATS * (l + 1)]) for l in range(min(nl, max_levels))]
 
 
 def state_get(h):
@@ -365,7 +368,7 @@ class Mesh:
 
     def __init__(self, problem, precision=PREC_FP64, rtol=None, max_iter=None, dt_fixed=None,
                  reorder=1, use_torch_allocator=False, stream=None, pcg_threads=0, pcg_kind=0,
-                 wait_timeout=None):
+                 wait_timeout=None, precond_fp64=0):
         o = avip_opts_default()
         po = problem.opts
         o.cfl, o.fourier, o.a_diel, o.a_chem = po.cfl, po.fourier, po.a_diel, po.a_chem
@@ -382,6 +385,7 @@ class Mesh:
         o.v_rise = getattr(po, "v_rise", 0.0)
         if wait_timeout is not None:
             o.wait_timeout = wait_timeout
+        o.precond_fp64 = int(precond_fp64)
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()

@@ -22,6 +22,15 @@
 //   * smoothed prolongator P = (I - omega D^-1 A) T, omega = 4 / (3 lambda_max(D^-1 A)),
 //     lambda_max from 30 power iterations (times 1.05);
 //   * restriction R = P^T and Galerkin coarse matrix A_c = R A P (rounding symmetrised);
+//   * smoother: the degree-2 Chebyshev polynomial in D^-1 A on [lmax/30, lmax], from zero
+//     x = Q b and from a given x  x <- x + Q (b - A x), with the one matrix
+//     Q = a D^-1 + b D^-1 A D^-1 (same sparsity as A);
+//   * composite operators, so that the V-cycle needs two grid-wide phases per level instead of
+//     six: with xp = Q b,
+//         b' = R (b - A xp)                 = Rf b,   Rf = R (I - A Q)
+//         x  = xp + P x' + Q (b - A (xp + P x'))
+//            = (2 I - Q A) xp + (I - Q A) P x' = U xp + Pf x'
+//     (the same V-cycle in exact arithmetic; for a symmetric A, Rf = Pf^T exactly);
 //   * levels until at most N/64 unknowns remain (clamped to [256, 1500]: a larger dense coarse
 //     level saves barriers per V-cycle on big meshes, a smaller one keeps the O(n^3) set-up of
 //     small meshes cheap), where the coarse matrix is inverted
@@ -279,20 +288,99 @@ bool dense_inverse(std::vector<double>& a, int n) {
   return true;
 }
 
+// alpha I + beta M (M square; the diagonal entry is created where M has none)
+Csr identity_plus(double alpha, double beta, const Csr& M) {
+  Csr C;
+  C.n = M.n;
+  C.m = M.m;
+  C.rp.assign(M.n + 1, 0);
+  for (int32_t i = 0; i < M.n; ++i) {
+    bool diag = false;
+    for (int32_t e = M.rp[i]; e < M.rp[i + 1]; ++e) {
+      const int32_t j = M.ci[e];
+      if (!diag && j > i) {  // columns are sorted: insert the missing diagonal in place
+        C.ci.push_back(i);
+        C.v.push_back(alpha);
+        diag = true;
+      }
+      double v = beta * M.v[e];
+      if (j == i) {
+        v += alpha;
+        diag = true;
+      }
+      C.ci.push_back(j);
+      C.v.push_back(v);
+    }
+    if (!diag) {
+      C.ci.push_back(i);
+      C.v.push_back(alpha);
+    }
+    C.rp[i + 1] = (int32_t)C.ci.size();
+  }
+  return C;
+}
+
+// Q = q_diag D^-1 + q_off D^-1 A D^-1, columns sorted like A's (A's rows are sorted)
+Csr smoother_matrix(const Csr& A, const std::vector<double>& dinv, double q_diag, double q_off) {
+  Csr Q = A;
+  for (int32_t i = 0; i < A.n; ++i)
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+      const int32_t j = A.ci[e];
+      Q.v[e] = q_off * dinv[i] * A.v[e] * dinv[j] + (j == i ? q_diag * dinv[i] : 0.0);
+    }
+  return Q;
+}
+
+// Composite operators of level L (Q, Rf, U, Pf; see the header comment)
+void composite_operators(AmgHostLevel& L, bool symmetric) {
+  chebyshev_q(L.lmax, L.q_diag, L.q_off);
+  // the level matrix with sorted rows (the finest level keeps its diagonal first)
+  Csr A = L.A;
+  for (int32_t i = 0; i < A.n; ++i) {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) row.emplace_back(A.ci[e], A.v[e]);
+    std::sort(row.begin(), row.end());
+    for (size_t k = 0; k < row.size(); ++k) {
+      A.ci[A.rp[i] + k] = row[k].first;
+      A.v[A.rp[i] + k] = row[k].second;
+    }
+  }
+  L.Q = smoother_matrix(A, L.dinv, L.q_diag, L.q_off);
+  const Csr QA = spgemm(L.Q, A);
+  L.U = identity_plus(2.0, -1.0, QA);
+  L.Pf = spgemm(identity_plus(1.0, -1.0, QA), L.P);
+  if (symmetric) {
+    L.Rf = transpose(L.Pf);  // R (I - A Q) = ((I - Q A) P)^T when A and Q are symmetric
+  } else {
+    L.Rf = spgemm(L.R, identity_plus(1.0, -1.0, spgemm(A, L.Q)));
+  }
+}
+
 }  // namespace
 
-void sell_from_csr(const Csr& A, SellHost& S) {
+void chebyshev_q(double lmax, double& q_diag, double& q_off) {
+  // two-term recurrence of the degree-2 Chebyshev smoother on [lmax/30, lmax]:
+  // d0 = D^-1 r / theta, x = d0 + c1 d0 + c2 D^-1 (r - A d0)
+  const double lmin = lmax / 30.0, theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta, rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+  const double inv_theta = 1.0 / theta, c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
+  q_diag = (1.0 + c1) * inv_theta + c2;
+  q_off = -c2 * inv_theta;
+}
+
+void sell_from_csr(const Csr& A, SellHost& S, int lpr) {
+  const int rps = kSlice / lpr;  // rows per slice
   S.n = A.n;
-  S.nslices = (A.n + kSlice - 1) / kSlice;
-  const int32_t npad = S.nslices * kSlice;
-  S.rlen.assign(npad, 0);
+  S.lpr = lpr;
+  S.nslices = (A.n + rps - 1) / rps;
+  S.rlen.assign((size_t)S.nslices * rps, 0);
   for (int32_t i = 0; i < A.n; ++i) S.rlen[i] = A.rp[i + 1] - A.rp[i];
   S.sl_ptr.assign(S.nslices + 1, 0);
   S.sl_w.assign(S.nslices, 0);
   int64_t off = 0;
   for (int32_t s = 0; s < S.nslices; ++s) {
     int32_t w = 0;
-    for (int l = 0; l < kSlice; ++l) w = std::max(w, S.rlen[s * kSlice + l]);
+    for (int r = 0; r < rps; ++r) w = std::max(w, (S.rlen[(size_t)s * rps + r] + lpr - 1) / lpr);
     S.sl_w[s] = w;
     S.sl_ptr[s] = (int32_t)off;
     off += (int64_t)w * kSlice;
@@ -301,15 +389,22 @@ void sell_from_csr(const Csr& A, SellHost& S) {
   S.col.assign(off, 0);
   S.val.assign(off, 0.0);
   for (int32_t s = 0; s < S.nslices; ++s)
-    for (int l = 0; l < kSlice; ++l) {
-      const int32_t i = s * kSlice + l;
+    for (int r = 0; r < rps; ++r) {
+      const int32_t i = s * rps + r;
       if (i >= A.n) continue;
-      for (int32_t k = 0; k < S.rlen[i]; ++k) {  // padding slots keep column 0 and are never read
-        const int64_t e = (int64_t)S.sl_ptr[s] + (int64_t)k * kSlice + l;
+      for (int32_t k = 0; k < S.rlen[i]; ++k) {  // padding slots keep column 0 and value 0
+        const int64_t e = (int64_t)S.sl_ptr[s] + (int64_t)(k / lpr) * kSlice + r * lpr + (k % lpr);
         S.col[e] = A.ci[A.rp[i] + k];
         S.val[e] = A.v[A.rp[i] + k];
       }
     }
+}
+
+int lanes_per_row(const Csr& A) {
+  const double avg = A.n > 0 ? (double)A.rp[A.n] / A.n : 0.0;
+  int lpr = 1;
+  while (lpr < kSlice && avg > 8.0 * lpr) lpr *= 2;
+  return lpr;
 }
 
 int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
@@ -419,6 +514,7 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
     }
     Csr R = transpose(P);
     Csr Ac = spgemm(R, spgemm(A, P));
+    // (the composite operators of this level are formed below, once P and R are final)
     if (symmetric) {  // symmetrise the rounding of the Galerkin product (its pattern is symmetric)
       const Csr AcT = transpose(Ac);
       for (int32_t i = 0; i < Ac.n; ++i)
@@ -427,6 +523,7 @@ int amg_setup(const HostMesh& m, AmgHost& H, char* err, size_t errlen) {
     L.A = std::move(A);
     L.P = std::move(P);
     L.R = std::move(R);
+    composite_operators(L, symmetric);
     H.lv.push_back(std::move(L));
     A = std::move(Ac);
     B.swap(Bc);

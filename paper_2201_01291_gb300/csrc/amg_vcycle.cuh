@@ -1,5 +1,13 @@
 // Smoothed-aggregation AMG V-cycle shared by the whole-GPU cooperative solvers (grid-wide
-// barriers) and the batched solver (one thread-block cluster per instance, cluster barriers).
+// barriers) and the cluster solvers (one thread-block cluster per instance, cluster barriers).
+//
+// Each non-coarsest level takes two phases, through the composite operators built on the host
+// (amg_setup.cpp): down, xp = Q b and b' = Rf b (the pre-smoothing, the residual and its
+// restriction); up, x = U xp + Pf x' (the coarse correction and the post-smoothing).  It is the
+// V-cycle of a degree-2 Chebyshev smoother (the same polynomial before and after), R = P^T and
+// a dense coarsest solve, written with fewer grid-wide phases: every phase gathers only vectors
+// completed by an earlier one.  The values are FP32 by default (the preconditioner only shapes
+// the search directions; the iterate, the residuals and the stopping test stay FP64) or FP64.
 //
 // `Ops` supplies the synchronisation of the participating threads: barrier() completes every
 // vector written before it, sum(v) returns the sum of v over all participants (and is a
@@ -36,150 +44,171 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// One V-cycle: x0 = M b0 (level 0 takes b0 and x0 instead of the hierarchy's own vectors).
-// On entry b0 and d_0 = D^-1 b0 / theta_0 are complete (written before the last barrier).
-// Returns b0.x0 in rz (grid-reduced, also the barrier after which x0 is complete); false if a
-// wait was abandoned.  T = double, or float for the inner solve of the mixed-precision path.
-template <typename T, class Ops>
-__device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const T* __restrict__ b0, T* __restrict__ x0, Ops& ops,
-                       int gwarp, int nwarps, int lane, double& rz) {
-  const int nl = H->nlev;
-  for (int l = 0; l + 1 < nl; ++l) {
-    const AmgLevelT<T>* __restrict__ L = H->L + l;
-    const SellMatT<T> A = L->A;
-    const int n = L->n;
-    const T* __restrict__ dinv = L->dinv;
-    const T* __restrict__ b = l == 0 ? b0 : L->b;
-    T* __restrict__ x = l == 0 ? x0 : L->x;
-    T* __restrict__ d = L->d;
-    T* __restrict__ r = L->r;
-    {
-      const T c1 = (T)L->c1, c2 = (T)L->c2;
-      // second Chebyshev step from x = d0: r1 = b - A d0, x = d0 + c1 d0 + c2 D^-1 r1
-      for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
-        const int i = sl * kSlice + lane;
-        if (i >= n) continue;
-        const T di = d[i];
-        const T r1 = b[i] - sellmat_row_dot(A, sl, lane, i, (const T*)d);
-        x[i] = di + fma_t(c1, di, c2 * dinv[i] * r1);
-      }
-    }
-    if (!ops.barrier()) return false;
-    // residual
-    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
-      const int i = sl * kSlice + lane;
-      if (i >= n) continue;
-      r[i] = b[i] - sellmat_row_dot(A, sl, lane, i, (const T*)x);
-    }
-    if (!ops.barrier()) return false;
-    {  // restriction, and the first Chebyshev direction of the next level
-      const AmgLevelT<T>* __restrict__ C = H->L + l + 1;
-      const SellMatT<T> R = L->R;
-      const int nc = C->n;
-      const T c_inv_theta = (T)C->inv_theta;
-      const T* __restrict__ cdinv = C->dinv;
-      T* __restrict__ cb = C->b;
-      T* __restrict__ cd = C->d;
-      for (int sl = gwarp; sl < R.nslices; sl += nwarps) {
-        const int j = sl * kSlice + lane;
-        if (j >= nc) continue;
-        const T bj = sellmat_row_dot(R, sl, lane, j, (const T*)r);
-        cb[j] = bj;
-        cd[j] = cdinv[j] * bj * c_inv_theta;
-      }
-    }
-    if (!ops.barrier()) return false;
+// Steps per batch of the streamed products: 16 with FP32 values, 8 with FP64.
+template <typename T>
+struct StreamDepth {
+  static constexpr int value = sizeof(T) == 4 ? 16 : 8;
+};
+
+// The warps of a phase that works on two operators over different rows are split in
+// proportion to the operators' stored entries: warps [0, k) take the first, [k, nwarps) the
+// second.  k = nwarps when the second is empty, 0 when the first is.
+__device__ __forceinline__ int split_warps(int nwarps, int64_t e1, int64_t e2) {
+  if (e2 <= 0) return nwarps;
+  if (e1 <= 0) return 0;
+  const int k = (int)((double)nwarps * (double)e1 / (double)(e1 + e2) + 0.5);
+  return min(max(k, 1), nwarps - 1);
+}
+
+// Down phase of level l: xp = Q b on the rows of level l and b' = Rf b on the rows of level
+// l + 1, b given by `src` (complete on entry).  `hook` (see spmv_stream's begin / emit) takes
+// part in every row of level l: hook.begin(i) fetches the row's own operands ahead, hook.end(i,
+// pre) runs before xp_i is stored (the CG update folded into the finest level's phase).  The
+// warps are split between Q and Rf in proportion to their steps; each warp streams a contiguous
+// share of its operator's slices; a single warp does both.
+template <typename T, class Src, class Hook>
+__device__ __forceinline__ void amg_down(const AmgDevT<T>* __restrict__ H, int l, Src src, Hook hook, int gwarp,
+                                         int nwarps, int lane) {
+  constexpr int U = StreamDepth<T>::value;
+  const AmgLevelT<T>& L = H->L[l];
+  T* __restrict__ bn = H->L[l + 1].b;
+  T* __restrict__ xp = L.xp;
+  const bool one = nwarps == 1;
+  const int k = one ? 1 : split_warps(nwarps, L.steps_q, L.steps_rf);
+  int sa, sb;
+  if (one || gwarp < k) {
+    warp_slices(L.Q.nslices, one ? 0 : gwarp, one ? 1 : k, sa, sb);
+    spmv_stream<T, U>(L.Q, sa, sb, lane, src, [&](int i) { return hook.begin(i); },
+                      [&](int i, T v, const decltype(hook.begin(0))& pre) {
+                        hook.end(i, pre);
+                        xp[i] = v;
+                      });
   }
-  {  // coarsest level: dense inverse, one warp per row (a one-level hierarchy ends here: b0.x0)
-    const AmgLevelT<T>* __restrict__ C = H->L + nl - 1;
-    const int n = H->nc;
-    const T* __restrict__ cinv = H->cinv;
-    const T* __restrict__ cb = nl == 1 ? b0 : C->b;
-    T* __restrict__ cx = nl == 1 ? x0 : C->x;
-    DotAcc<T> acc;
-    for (int row = gwarp; row < n; row += nwarps) {
-      T s = T(0);
-      for (int k = lane; k < n; k += 32) s = fma_t(__ldg(cinv + (size_t)row * n + k), __ldcg(cb + k), s);
+  if (one || gwarp >= k) {
+    warp_slices(L.Rf.nslices, one ? 0 : gwarp - k, one ? 1 : nwarps - k, sa, sb);
+    spmv_stream<T, U>(L.Rf, sa, sb, lane, src, NoBegin(), [&](int j, T v, NoPre) { bn[j] = v; });
+  }
+}
+
+// Up phase of level l: x = U xp + Pf x' = [U | Pf] [xp; x'] on the rows of level l (x' = the
+// next level's solution, complete on entry), each row handed to out.end(i, value, pre) with the
+// operands out.begin(i) fetched ahead.
+template <typename T, class Out>
+__device__ __forceinline__ void amg_up(const AmgDevT<T>* __restrict__ H, int l, Out out, int gwarp, int nwarps,
+                                       int lane) {
+  constexpr int U = StreamDepth<T>::value;
+  const AmgLevelT<T>& L = H->L[l];
+  const T* __restrict__ xp = L.xp;
+  const T* __restrict__ xn = H->L[l + 1].x;
+  const int n = L.n;
+  int sa, sb;
+  warp_slices(L.UP.nslices, gwarp, nwarps, sa, sb);
+  spmv_stream<T, U>(L.UP, sa, sb, lane, [xp, xn, n](int c) { return __ldca(c < n ? xp + c : xn + (c - n)); },
+                    [&](int i) { return out.begin(i); },
+                    [&](int i, T v, const decltype(out.begin(0))& pre) { out.end(i, v, pre); });
+}
+
+// Row hooks and outputs without prefetched operands.
+struct NoHook {
+  __device__ NoPre begin(int) const { return NoPre(); }
+  __device__ void end(int, NoPre) const {}
+};
+template <typename T>
+struct StoreOut {  // x_i = value
+  T* x;
+  __device__ NoPre begin(int) const { return NoPre(); }
+  __device__ void end(int i, T v, NoPre) const { x[i] = v; }
+};
+
+// Coarsest level: x = A_c^-1 b as a dense product, one warp per row; b given by `src`
+// (complete on entry), each row handed to out(row, value) by lane 0.
+template <typename T, class Src, class Out>
+__device__ __forceinline__ void amg_coarse(const AmgDevT<T>* __restrict__ H, Src src, Out out, int gwarp,
+                                           int nwarps, int lane) {
+  const int n = H->nc;
+  const T* __restrict__ cinv = H->cinv;
+  for (int row = gwarp; row < n; row += nwarps) {
+    T s = T(0);
+    for (int k = lane; k < n; k += 32) s = fma_t(__ldg(cinv + (size_t)row * n + k), src(k), s);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) {
-        cx[row] = s;
-        if (nl == 1) acc.add(__ldcg(cb + row), s);
-      }
-    }
-    if (nl == 1) {
-      double av[1] = {acc.value()};
-      if (!ops.sum(av)) return false;
-      rz = av[0];
-    } else if (!ops.barrier()) {
-      return false;
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out(row, s);
   }
-  for (int l = nl - 2; l >= 0; --l) {
-    const AmgLevelT<T>* __restrict__ L = H->L + l;
-    const SellMatT<T> A = L->A;
-    const int n = L->n;
-    const T* __restrict__ dinv = L->dinv;
-    const T* __restrict__ b = l == 0 ? b0 : L->b;
-    T* __restrict__ x = l == 0 ? x0 : L->x;
-    T* __restrict__ d = L->d;
-    T* __restrict__ r = L->r;
-    {  // prolongation
-      const SellMatT<T> P = L->P;
-      const T* __restrict__ cx = H->L[l + 1].x;
-      for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
-        const int i = sl * kSlice + lane;
-        if (i >= n) continue;
-        x[i] += sellmat_row_dot(P, sl, lane, i, cx);
-      }
-    }
+}
+
+// The V-cycle below the finest level: down phases of levels 1 .. nlev-2, the coarsest solve,
+// up phases of levels nlev-2 .. 1, one barrier after each.  Entered once the finest down phase
+// is complete (nlev >= 2); on return the level-1 solution is complete.
+template <typename T, class Ops>
+__device__ bool amg_inner(const AmgDevT<T>* __restrict__ H, Ops& ops, int gwarp, int nwarps, int lane) {
+  const int nl = H->nlev;
+  for (int l = 1; l + 1 < nl; ++l) {
+    const T* __restrict__ b = H->L[l].b;
+    amg_down(H, l, [b](int c) { return __ldca(b + c); }, NoHook(), gwarp, nwarps, lane);
     if (!ops.barrier()) return false;
-    const T inv_theta = (T)L->inv_theta, c1 = (T)L->c1, c2 = (T)L->c2;
-    // first post-smoothing step: r = b - A x, d = D^-1 r / theta (x updated in the next phase)
-    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
-      const int i = sl * kSlice + lane;
-      if (i >= n) continue;
-      const T ri = b[i] - sellmat_row_dot(A, sl, lane, i, (const T*)x);
-      r[i] = ri;
-      d[i] = dinv[i] * ri * inv_theta;
-    }
+  }
+  {
+    const T* __restrict__ cb = H->L[nl - 1].b;
+    T* __restrict__ cx = H->L[nl - 1].x;
+    amg_coarse(H, [cb](int k) { return __ldca(cb + k); }, [cx](int row, T v) { cx[row] = v; }, gwarp, nwarps, lane);
     if (!ops.barrier()) return false;
-    // second step: r1 = r - A d, x += d + c1 d + c2 D^-1 r1
-    DotAcc<T> acc;
-    for (int sl = gwarp; sl < A.nslices; sl += nwarps) {
-      const int i = sl * kSlice + lane;
-      if (i >= n) continue;
-      const T di = d[i];
-      const T r1 = r[i] - sellmat_row_dot(A, sl, lane, i, (const T*)d);
-      const T xi = x[i] + di + fma_t(c1, di, c2 * dinv[i] * r1);
-      x[i] = xi;
-      if (l == 0) acc.add(b[i], xi);
-    }
-    if (l == 0) {
-      double av[1] = {acc.value()};
-      if (!ops.sum(av)) return false;
-      rz = av[0];
-    } else if (!ops.barrier()) {
-      return false;
-    }
+  }
+  for (int l = nl - 2; l >= 1; --l) {
+    amg_up(H, l, StoreOut<T>{H->L[l].x}, gwarp, nwarps, lane);
+    if (!ops.barrier()) return false;
   }
   return true;
 }
 
-// CG preconditioned by the V-cycle on the scaled system (the whole solve of kinds 8 and the
-// batched AMG solve): warm start, b', true-residual checks and restarts, phi = D^-1/2 x.
-// `leader` is the one thread that writes the solve statistics.  Returns false if a wait was
-// abandoned (grid barriers only).
-template <class Ops>
-__device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, int lane, bool leader) {
+// One V-cycle z = M b0, b0 complete on entry (TB: its type; TZ: the type z is stored in).  With
+// want_dot the last barrier is a grid sum that returns dot = b0.z; otherwise a plain barrier.
+// Returns false if a wait was abandoned.
+template <typename T, typename TB, typename TZ, class Ops>
+__device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const TB* __restrict__ b0, TZ* __restrict__ z, Ops& ops,
+                       int gwarp, int nwarps, int lane, bool want_dot, double& dot) {
+  auto src = [b0](int c) { return (T)__ldca(b0 + c); };
+  DotAcc<double> acc;
+  struct Out {  // z_i = value, b0_i z_i into the dot product
+    const TB* b0;
+    TZ* z;
+    DotAcc<double>* acc;
+    __device__ double begin(int i) const { return (double)__ldca(b0 + i); }
+    __device__ void end(int i, T v, double bi) const {
+      z[i] = (TZ)v;
+      acc->add(bi, (double)v);
+    }
+  } out{b0, z, &acc};
+  if (H->nlev == 1) {
+    amg_coarse(H, src, [&](int row, T v) { out.end(row, v, out.begin(row)); }, gwarp, nwarps, lane);
+  } else {
+    amg_down(H, 0, src, NoHook(), gwarp, nwarps, lane);
+    if (!ops.barrier()) return false;
+    if (!amg_inner(H, ops, gwarp, nwarps, lane)) return false;
+    amg_up(H, 0, out, gwarp, nwarps, lane);
+  }
+  if (want_dot) {
+    double v[1] = {acc.value()};
+    if (!ops.sum(v)) return false;
+    dot = v[0];
+    return true;
+  }
+  return ops.barrier();
+}
+
+// CG preconditioned by the V-cycle on the scaled system (kinds 8, 11 and the batched FP64 form):
+// warm start, b', true-residual checks and restarts, phi = D^-1/2 x.  The hierarchy H (values of
+// type T) writes the preconditioned residual z (type T).  The residual update r - alpha q and
+// x += alpha p of iteration k are folded into the finest down phase of iteration k + 1, whose
+// products gather r - alpha q directly (the new residual goes to the other buffer, r2), so an
+// iteration takes 2 nlev grid-wide phases: the finest down phase (sum of r.r: stop test), the
+// levels below, the finest up phase (sum of r.z), and w = A z (sum of p.q).  `leader` is the
+// one thread that writes the solve statistics.  Returns false if a wait was abandoned.
+template <typename T, class Ops>
+__device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H, T* __restrict__ z, Ops& ops,
+                             int gwarp, int nwarps, int lane, bool leader) {
   constexpr int kMaxRestarts = 8;
-  const int N = a.A.N, nsl = a.A.nslices;
+  const int N = a.A.N, nsl = a.A.nslices, nl = H->nlev;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
-  const AmgDev* __restrict__ H = a.amg;
-  const double* __restrict__ dinv0 = H->L[0].dinv;
-  double* __restrict__ d0 = H->L[0].d;
-  double* __restrict__ z = a.z;  // preconditioned residual (the V-cycle's finest solution)
-  const double inv_theta0 = H->L[0].inv_theta;
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);
@@ -207,7 +236,19 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
   if (!ops.sum(bb)) return false;
   {
     const double thresh = a.rtol * a.rtol * bb[0];
-    double rz = 0.0, rr_true = 0.0;
+    // the Poisson matrix as a streamed operator, and this warp's contiguous share of its slices
+    const SellMatT<double> A0{a.A.sl_ptr, a.A.sl_w, a.A.rlen, a.A.col, a.A.aval, N, nsl, 1};
+    int ma, mb;
+    warp_slices(nsl, gwarp, nwarps, ma, mb);
+    double* rc = a.r;   // current residual
+    double* rn = a.r2;  // the other buffer
+    // the vectors the finest down phase gathers, in the hierarchy's type: with T = float, FP32
+    // copies of r (both buffers) and q, written beside them; with T = double, r and q themselves
+    constexpr bool kCopies = sizeof(T) == 4;
+    T* tc = kCopies ? (T*)a.rq32 : (T*)rc;
+    T* tn = kCopies ? (T*)a.rq32 + a.Npad : (T*)rn;
+    T* tq = kCopies ? (T*)a.rq32 + 2 * (size_t)a.Npad : (T*)a.q_ap;
+    double rz = 0.0, rr_true = 0.0, alpha = 0.0;
     bool check = true, fresh = true;
     int it = 0, restarts = 0, status = AVIP_OK;
     if (bb[0] == 0.0) {
@@ -218,15 +259,21 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
     } else {
       while (true) {
         if (check || it >= a.max_iter) {
-          // ---- true residual r = b' - A x (x complete); first Chebyshev direction of level 0
+          // ---- true residual r = b' - A x (x complete)
           double r2[1] = {0.0};
-          for (int s = gwarp; s < nsl; s += nwarps) {
-            const int i = s * kSlice + lane;
-            if (i >= N) continue;
-            const double r = a.b[i] - sell_row_dot(a.A, s, lane, i, a.x);
-            a.r[i] = r;
-            d0[i] = dinv0[i] * r * inv_theta0;
-            r2[0] = fma(r, r, r2[0]);
+          {
+            const double* __restrict__ xv = a.x;
+            const double* __restrict__ bv = a.b;
+            double* __restrict__ rw = rc;
+            T* __restrict__ tw = tc;
+            spmv_stream<double, 8>(
+                A0, ma, mb, lane, [xv](int c) { return __ldca(xv + c); }, [bv](int i) { return bv[i]; },
+                [&](int i, double ax, double bi) {
+                  const double r = bi - ax;
+                  rw[i] = r;
+                  if (kCopies) tw[i] = (T)r;
+                  r2[0] = fma(r, r, r2[0]);
+                });
           }
           if (!ops.sum(r2)) return false;
           rr_true = r2[0];
@@ -243,50 +290,128 @@ __device__ bool amg_cg_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarps, 
           fresh = true;
           check = false;
         }
-        // ---- z = M r (r and the level-0 direction complete)
-        double rz_new = 0.0;
-        if (!vcycle(H, (const double*)a.r, z, ops, gwarp, nwarps, lane, rz_new)) return false;
+        // ---- finest down phase on the residual, updated by the last step unless fresh:
+        //      r' = r - alpha q, x += alpha p (own rows), r'.r'; xp0 = Q r', b1 = Rf r'
+        {
+          const double al = fresh ? 0.0 : alpha;
+          const bool upd = !fresh;
+          const double* __restrict__ rv = rc;
+          const double* __restrict__ qv = a.q_ap;
+          const T* __restrict__ trv = tc;
+          const T* __restrict__ tqv = tq;
+          const T alT = (T)al;
+          // the gathered residual r - alpha q in the hierarchy's type
+          auto res = [trv, tqv, alT, upd](int c) {
+            return upd ? fma_t(-alT, __ldca(tqv + c), __ldca(trv + c)) : __ldca(trv + c);
+          };
+          double rr = 0.0;
+          struct Pre {
+            double r, q, x, p;
+          };
+          struct Hook {  // r' = r - alpha q into the other buffer (and its copy), x += alpha p, r'.r'
+            const double *rv, *qv, *pv;
+            double *xv, *rnv, *rr;
+            T* tnv;
+            double al;
+            bool upd;
+            __device__ Pre begin(int i) const {
+              if (!upd) return Pre{0.0, 0.0, 0.0, 0.0};
+              return Pre{__ldca(rv + i), __ldca(qv + i), xv[i], pv[i]};
+            }
+            __device__ void end(int i, const Pre& p) const {
+              if (!upd) return;
+              const double v = fma(-al, p.q, p.r);
+              rnv[i] = v;
+              if (kCopies) tnv[i] = (T)v;
+              xv[i] = fma(al, p.p, p.x);
+              *rr = fma(v, v, *rr);
+            }
+          } hook{rv, qv, a.p, a.x, rn, &rr, tn, al, upd};
+          if (nl == 1) {
+            for (int s = gwarp; s < nsl; s += nwarps) {
+              const int i = s * kSlice + lane;
+              if (i < N) hook.end(i, hook.begin(i));
+            }
+          } else {
+            amg_down(H, 0, [res](int c) { return (T)res(c); }, hook, gwarp, nwarps, lane);
+          }
+          if (upd) {
+            double v[1] = {rr};
+            if (!ops.sum(v)) return false;
+            ++it;
+            double* t = rc;
+            rc = rn;
+            rn = t;
+            T* tt = tc;
+            tc = tn;
+            tn = tt;
+            check = v[0] <= thresh || !isfinite(v[0]);
+            if (check) continue;  // confirm on the true residual
+          } else if (!ops.barrier()) {
+            return false;
+          }
+        }
+        // ---- the levels below, then the finest up phase: z = U0 xp0 + Pf0 x1, r.z
+        double rzv[1];
+        {
+          DotAcc<double> acc;
+          const double* __restrict__ rv = rc;
+          struct Out {  // z_i = value, r_i z_i into r.z
+            const double* rv;
+            T* z;
+            DotAcc<double>* acc;
+            __device__ double begin(int i) const { return __ldca(rv + i); }
+            __device__ void end(int i, T v, double ri) const {
+              z[i] = v;
+              acc->add(ri, (double)v);
+            }
+          } out{rv, z, &acc};
+          if (nl == 1) {
+            amg_coarse(H, [rv](int k) { return (T)__ldca(rv + k); },
+                       [&](int row, T v) { out.end(row, v, out.begin(row)); }, gwarp, nwarps, lane);
+          } else {
+            if (!amg_inner(H, ops, gwarp, nwarps, lane)) return false;
+            amg_up(H, 0, out, gwarp, nwarps, lane);
+          }
+          rzv[0] = acc.value();
+          if (!ops.sum(rzv)) return false;
+        }
+        const double rz_new = rzv[0];
         if (!(rz_new > 0.0) || !isfinite(rz_new)) {  // the preconditioned residual lost positivity
           if (it == 0 || restarts >= kMaxRestarts) {
             status = AVIP_ENOTCONV;
             break;
           }
-          ++it;
           check = true;
           continue;
         }
         const double beta = fresh ? 0.0 : rz_new / rz;
         rz = rz_new;
         fresh = false;
-        // ---- phase A: w = A z, q = w + beta q, p = z + beta p, p.q -> alpha
+        // ---- w = A z, q = w + beta q, p = z + beta p, p.q -> alpha
         double pq[1] = {0.0};
-        for (int s = gwarp; s < nsl; s += nwarps) {
-          const int i = s * kSlice + lane;
-          if (i >= N) continue;
-          const double zi = __ldcg(z + i);  // with one level, z rows come from other warps
-          const double w = sell_row_dot(a.A, s, lane, i, z);
-          const double qn = beta == 0.0 ? w : fma(beta, a.q_ap[i], w);
-          const double pn = beta == 0.0 ? zi : fma(beta, a.p[i], zi);
-          a.q_ap[i] = qn;
-          a.p[i] = pn;
-          pq[0] = fma(pn, qn, pq[0]);
+        {
+          const T* __restrict__ zc = z;
+          double* __restrict__ qv = a.q_ap;
+          double* __restrict__ pv = a.p;
+          T* __restrict__ tqw = tq;
+          struct PreA {
+            double z, q, p;
+          };
+          spmv_stream<double, 8>(
+              A0, ma, mb, lane, [zc](int c) { return (double)__ldca(zc + c); },
+              [=](int i) { return PreA{(double)__ldca(zc + i), qv[i], pv[i]}; },
+              [&](int i, double w, const PreA& o) {
+                const double qn = beta == 0.0 ? w : fma(beta, o.q, w);
+                const double pn = beta == 0.0 ? o.z : fma(beta, o.p, o.z);
+                qv[i] = qn;
+                if (kCopies) tqw[i] = (T)qn;
+                pv[i] = pn;
+                pq[0] = fma(pn, qn, pq[0]);
+              });
         }
         if (!ops.sum(pq)) return false;
-        const double alpha = rz / pq[0];
-        // ---- phase B: x += alpha p, r -= alpha q, r.r; first direction of level 0
-        double rn[1] = {0.0};
-        for (int s = gwarp; s < nsl; s += nwarps) {
-          const int i = s * kSlice + lane;
-          if (i >= N) continue;
-          a.x[i] = fma(alpha, a.p[i], a.x[i]);
-          const double r = fma(-alpha, a.q_ap[i], a.r[i]);
-          a.r[i] = r;
-          d0[i] = dinv0[i] * r * inv_theta0;
-          rn[0] = fma(r, r, rn[0]);
-        }
-        if (!ops.sum(rn)) return false;
-        check = rn[0] <= thresh || !isfinite(rn[0]);
-        ++it;
+        alpha = rz / pq[0];
       }
     }
     // ---- phi = D^-1/2 x
@@ -314,10 +439,9 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
   const int N = a.A.N, nsl = a.A.nslices;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
   const AmgDevT<float>* __restrict__ H = a.amg32;
-  const SellMatT<float> A32 = H->L[0].A;
-  const float* __restrict__ dinv0 = H->L[0].dinv;
-  float* __restrict__ d0 = H->L[0].d;
-  const float inv_theta0 = (float)H->L[0].inv_theta;
+  const SellMatT<float> A32{a.A.sl_ptr, a.A.sl_w, a.A.rlen, a.A.col, a.aval32, N, nsl, 1};
+  int ma, mb;
+  warp_slices(nsl, gwarp, nwarps, ma, mb);
   float* __restrict__ r32 = a.r32;
   float* __restrict__ e32 = a.e32;
   float* __restrict__ p32 = a.p32;
@@ -375,7 +499,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
       ++outer;
       const int it_outer = it;
       const double rnorm = sqrt(rr64), rscale = 1.0 / rnorm;
-      // ---- FP32 right-hand side r / ||r||, e = 0, first V-cycle direction
+      // ---- FP32 right-hand side r / ||r||, e = 0
       double g0[1];
       {
         DotAcc<float> k;
@@ -385,7 +509,6 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
           const float r = (float)(a.r[i] * rscale);
           r32[i] = r;
           e32[i] = 0.f;
-          d0[i] = dinv0[i] * r * inv_theta0;
           k.add(r, r);
         }
         g0[0] = k.value();
@@ -396,23 +519,25 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
       bool fresh = true;
       while (rr > inner_thresh && it < a.max_iter) {
         double rz_new = 0.0;
-        if (!vcycle(H, (const float*)r32, z32, ops, gwarp, nwarps, lane, rz_new)) return false;
+        if (!vcycle(H, (const float*)r32, z32, ops, gwarp, nwarps, lane, true, rz_new)) return false;
         if (!(rz_new > 0.0) || !isfinite(rz_new)) break;  // refine with what the inner solve has
         const float beta = fresh ? 0.f : (float)(rz_new / rz);
         rz = rz_new;
         fresh = false;
         DotAcc<float> kpq;
-        for (int s = gwarp; s < nsl; s += nwarps) {
-          const int i = s * kSlice + lane;
-          if (i >= N) continue;
-          const float zi = __ldcg(z32 + i);
-          const float w = sellmat_row_dot(A32, s, lane, i, (const float*)z32);
-          const float qn = beta == 0.f ? w : fmaf(beta, q32[i], w);  // (restart: old p, q unused)
-          const float pn = beta == 0.f ? zi : fmaf(beta, p32[i], zi);
-          q32[i] = qn;
-          p32[i] = pn;
-          kpq.add(pn, qn);
-        }
+        struct PreA {
+          float z, q, p;
+        };
+        spmv_stream<float, 16>(
+            A32, ma, mb, lane, [z32](int c) { return __ldca(z32 + c); },
+            [=](int i) { return PreA{__ldca(z32 + i), q32[i], p32[i]}; },
+            [&](int i, float w, const PreA& o) {
+              const float qn = beta == 0.f ? w : fmaf(beta, o.q, w);  // (restart: old p, q unused)
+              const float pn = beta == 0.f ? o.z : fmaf(beta, o.p, o.z);
+              q32[i] = qn;
+              p32[i] = pn;
+              kpq.add(pn, qn);
+            });
         double pq[1] = {kpq.value()};
         if (!ops.sum(pq)) return false;
         const float alpha = (float)(rz / pq[0]);
@@ -423,7 +548,6 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
           e32[i] = fmaf(alpha, p32[i], e32[i]);
           const float r = fmaf(-alpha, q32[i], r32[i]);
           r32[i] = r;
-          d0[i] = dinv0[i] * r * inv_theta0;
           krr.add(r, r);
         }
         double rn[1] = {krr.value()};

@@ -60,10 +60,12 @@ struct avip_mesh {
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
   double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
-  AmgDev* amg = nullptr;        // AMG hierarchy in device memory (kinds 8, 9)
-  AmgDevT<float>* amg32 = nullptr;  // FP32 copy for the mixed-precision solve (kind 10)
-  float* z32 = nullptr;
-  double* amg_z = nullptr;      // preconditioned residual (level-0 solution of the V-cycle)
+  AmgDev* amg = nullptr;            // AMG hierarchy with FP64 values (opts.precond_fp64)
+  AmgDevT<float>* amg32 = nullptr;  // AMG hierarchy with FP32 values (default; kind 10 always)
+  float* z32 = nullptr;             // preconditioned residual of the FP32 hierarchy
+  double* amg_z = nullptr;          // preconditioned residual of the FP64 hierarchy
+  double* r2 = nullptr;             // second buffer of the AMG-CG residual
+  float* rq32 = nullptr;            // FP32 copies of both residual buffers and of q (FP32 hierarchy)
   int32_t amg_levels = 0;
   std::vector<int64_t> amg_stats;  // per level: rows, nnz(A), nnz(P)
   float *aval32 = nullptr, *e32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // mixed precision
@@ -79,6 +81,7 @@ struct avip_mesh {
   struct PhotoTerm {
     double *aval = nullptr, *dsq = nullptr, *dsqinv = nullptr, *rhs = nullptr;
     AmgDev* amg = nullptr;
+    AmgDevT<float>* amg32 = nullptr;
   };
   std::vector<PhotoTerm> photo;
   double *photo_psi = nullptr, *photo_I = nullptr, *photo_S = nullptr, *photo_zero = nullptr;
@@ -205,6 +208,9 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.z = h->amg_z;
   a.amg32 = h->amg32;
   a.z32 = h->z32;
+  a.r2 = h->r2;
+  a.rq32 = h->rq32;
+  a.amg_mixed = h->opts.precision == AVIP_PREC_MIXED ? 1 : 0;
   return a;
 }
 
@@ -298,6 +304,7 @@ PcgArgs photo_args(const avip_mesh* h, int j) {
   a.res = h->sc_aux;
   a.v_rise = 0.0;
   a.amg = t.amg;
+  a.amg32 = t.amg32;
   return a;
 }
 
@@ -357,52 +364,56 @@ void invalidate_graph(avip_mesh* h) {
   h->graph_valid = false;
 }
 
-// Device copy of the AMG hierarchy with values of type T (double, or float for the inner
-// solve of the mixed-precision path): level 0 reuses the mesh matrix structure with the values
-// `aval0`; every other operator in SELL-32; per level x, b, r, d vectors (level 0: only r and d,
-// the V-cycle takes its finest right-hand side and solution as arguments).
+// Device copy of the AMG hierarchy with values of type T (float by default, or double): per
+// non-coarsest level the composite operators Q, Rf, U, Pf in SELL-32 and the vectors xp (and,
+// below the finest level, x and b); the coarsest level's x, b and its dense inverse.
 template <typename T>
-bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& out, bool record = true) {
+bool upload_amg_t(avip_mesh* h, const AmgHost& H, AmgDevT<T>*& out, bool record = true) {
   AmgDevT<T> D;
   std::memset(&D, 0, sizeof(D));
   D.nlev = (int32_t)H.lv.size();
   D.nc = H.nc;
-  auto put = [&](const Csr& M, SellMatT<T>& dst) {
+  auto put = [&](const Csr& M, SellMatT<T>& dst, int64_t& steps) {
     SellHost S;
-    sell_from_csr(M, S);
+    sell_from_csr(M, S, lanes_per_row(M));
     int32_t *slp = nullptr, *slw = nullptr, *rl = nullptr, *col = nullptr;
     T* val = nullptr;
     std::vector<T> v(S.val.begin(), S.val.end());
     const bool ok = upload(h, slp, S.sl_ptr) && upload(h, slw, S.sl_w) && upload(h, rl, S.rlen) &&
                     upload(h, col, S.col, 1) && upload(h, val, v, 1);
-    dst = SellMatT<T>{slp, slw, rl, col, val, S.n, S.nslices};
+    dst = SellMatT<T>{slp, slw, rl, col, val, S.n, S.nslices, S.lpr};
+    steps = S.sl_ptr.back() / kSlice;
     return ok;
+  };
+  // [U | Pf]: Pf's columns shifted past U's n columns
+  auto concat = [](const Csr& Uo, const Csr& Pfo) {
+    Csr C;
+    C.n = Uo.n;
+    C.m = Uo.m + Pfo.m;
+    C.rp.assign(C.n + 1, 0);
+    for (int32_t i = 0; i < C.n; ++i) {
+      for (int32_t e = Uo.rp[i]; e < Uo.rp[i + 1]; ++e) {
+        C.ci.push_back(Uo.ci[e]);
+        C.v.push_back(Uo.v[e]);
+      }
+      for (int32_t e = Pfo.rp[i]; e < Pfo.rp[i + 1]; ++e) {
+        C.ci.push_back(Uo.m + Pfo.ci[e]);
+        C.v.push_back(Pfo.v[e]);
+      }
+      C.rp[i + 1] = (int32_t)C.ci.size();
+    }
+    return C;
   };
   bool ok = true;
   for (int32_t l = 0; l < D.nlev && ok; ++l) {
     const AmgHostLevel& L = H.lv[l];
     AmgLevelT<T>& dl = D.L[l];
     dl.n = L.A.n;
-    dl.lmax = L.lmax;
-    {  // degree-2 Chebyshev smoother on [lmax/30, lmax], coefficients of its two-term recurrence
-      const double lmin = L.lmax / 30.0, theta = 0.5 * (L.lmax + lmin), delta = 0.5 * (L.lmax - lmin);
-      const double sigma = theta / delta, rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
-      dl.inv_theta = 1.0 / theta;
-      dl.c1 = rho1 * rho0;
-      dl.c2 = 2.0 * rho1 / delta;
-    }
     const size_t npad = (size_t)((L.A.n + kSlice - 1) / kSlice) * kSlice;
-    if (l == 0) {
-      dl.A = SellMatT<T>{h->sl_ptr, h->sl_w, h->rlen, h->col, aval0, h->hm.N, h->hm.nslices};
-    } else {
-      ok = ok && put(L.A, dl.A);
-    }
-    if (l + 1 < D.nlev) ok = ok && put(L.P, dl.P) && put(L.R, dl.R);
-    T* dinv = nullptr;
-    std::vector<T> dv(L.dinv.begin(), L.dinv.end());
-    ok = ok && upload(h, dinv, dv, npad);
-    dl.dinv = dinv;
-    ok = ok && zalloc(h, dl.r, npad) && zalloc(h, dl.d, npad);
+    int64_t up_steps = 0;
+    if (l + 1 < D.nlev)
+      ok = ok && put(L.Q, dl.Q, dl.steps_q) && put(L.Rf, dl.Rf, dl.steps_rf) &&
+           put(concat(L.U, L.Pf), dl.UP, up_steps) && zalloc(h, dl.xp, npad);
     if (l > 0) ok = ok && zalloc(h, dl.x, npad) && zalloc(h, dl.b, npad);
   }
   T* cinv = nullptr;
@@ -417,11 +428,19 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, const T* aval0, AmgDevT<T>*& o
   h->amg_levels = D.nlev;
   h->amg_stats.clear();
   for (const AmgHostLevel& L : H.lv) {
-    h->amg_stats.push_back(L.A.n);
-    h->amg_stats.push_back(L.A.rp.empty() ? 0 : L.A.rp[L.A.n]);
-    h->amg_stats.push_back(L.P.rp.empty() ? 0 : L.P.rp[L.P.n]);
+    auto nz = [](const Csr& M) -> int64_t { return M.rp.empty() ? 0 : M.rp[M.n]; };
+    for (int64_t v : {(int64_t)L.A.n, nz(L.A), nz(L.P), nz(L.Rf), nz(L.U), nz(L.Pf)}) h->amg_stats.push_back(v);
   }
   return ok;
+}
+
+// Upload the hierarchy in the handle's preconditioner precision (FP64 values when asked for and
+// the solve is not the mixed-precision one) with its preconditioned-residual vector.
+bool upload_amg(avip_mesh* h, const AmgHost& H, size_t Np) {
+  const bool fp64 = h->opts.precond_fp64 && h->opts.precision == AVIP_PREC_FP64;
+  if (fp64) return upload_amg_t<double>(h, H, h->amg) && zalloc(h, h->amg_z, Np) && zalloc(h, h->r2, Np);
+  return upload_amg_t<float>(h, H, h->amg32) && zalloc(h, h->z32, Np) && zalloc(h, h->r2, Np) &&
+         zalloc(h, h->rq32, 3 * Np);
 }
 
 }  // namespace
@@ -583,8 +602,8 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
       delete h;
       return rc;
     }
-    ok = ok && upload_amg_t<double>(h, H, h->aval, h->amg) && zalloc(h, h->amg_z, Np);
-    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, bicg ? 9 : 8);
+    ok = ok && upload_amg(h, H, Np);
+    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, bicg ? 9 : 8, h->amg ? 1 : 0);
   }
   if (h->opts.precision == AVIP_PREC_MIXED) {
     std::vector<float> a32(m.aval.begin(), m.aval.end());
@@ -612,8 +631,8 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
       delete h;
       return rc;
     }
-    ok = ok && upload_amg_t<float>(h, H, h->aval32, h->amg32) && zalloc(h, h->z32, Np);
-    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, 10);
+    ok = ok && upload_amg(h, H, Np);
+    h->plan = amg_plan(m.nslices, h->opts.pcg_threads, 10, 0);
   }
   // mid-size planar meshes (or kind 11 forced): the AMG-preconditioned solve on one cluster
   if (!bicg && (h->opts.pcg_kind == 11 ||
@@ -628,10 +647,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
         delete h;
         return rc;
       }
-      if (h->opts.precision == AVIP_PREC_MIXED)
-        ok = ok && upload_amg_t<float>(h, H, h->aval32, h->amg32) && zalloc(h, h->z32, Np);
-      else
-        ok = ok && upload_amg_t<double>(h, H, h->aval, h->amg) && zalloc(h, h->amg_z, Np);
+      ok = ok && upload_amg(h, H, Np);
       h->plan = cp;
     }
   }
@@ -723,7 +739,8 @@ int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels) {
   if (!h || (max_levels > 0 && !out) || max_levels < 0) return AVIP_EINVAL;
   const int32_t nl = (h->plan.kind >= 8 && h->plan.kind <= 11) ? h->amg_levels : 0;
   for (int32_t l = 0; l < nl && l < max_levels; ++l)
-    for (int k = 0; k < 3; ++k) out[3 * l + k] = h->amg_stats[3 * (size_t)l + k];
+    for (int k = 0; k < AVIP_LEVEL_STATS; ++k)
+      out[AVIP_LEVEL_STATS * l + k] = h->amg_stats[AVIP_LEVEL_STATS * (size_t)l + k];
   return nl;
 }
 
@@ -852,7 +869,10 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
       hm.dsq.assign(dh.begin(), dh.begin() + m.N);
       AmgHost H;
       if (amg_setup(hm, H, g_err, sizeof(g_err)) != AVIP_OK) return AVIP_EINVAL;
-      ok = upload_amg_t<double>(h, H, t.aval, t.amg, false);
+      if (h->amg)
+        ok = upload_amg_t<double>(h, H, t.amg, false);
+      else
+        ok = upload_amg_t<float>(h, H, t.amg32, false);
     }
     h->photo.push_back(t);
   }

@@ -72,21 +72,41 @@ struct AmgHostLevel {
   Csr A, P, R;                 // level matrix; prolongator from the next level; R = P^T
   std::vector<double> dinv;    // 1 / diag(A)
   double lmax = 1.0;           // estimate of the largest eigenvalue of D^-1 A
+  // degree-2 Chebyshev smoother on [lmax/30, lmax] as one matrix: x = Q b from x = 0, and
+  // x <- x + Q (b - A x) from a given x, with Q = a D^-1 + b D^-1 A D^-1 (chebyshev_q)
+  double q_diag = 0.0, q_off = 0.0;
+  // composite operators of the two-phase V-cycle (non-coarsest levels only):
+  //   Q  (n x n)      pre-smoothing from zero
+  //   Rf (n' x n)     = R (I - A Q): restriction of the pre-smoothed residual
+  //   U  (n x n)      = 2 I - Q A:  the pre-smoothed iterate through the post-smoother
+  //   Pf (n x n')     = (I - Q A) P: the coarse correction through the post-smoother
+  Csr Q, Rf, U, Pf;
 };
 struct AmgHost {
   std::vector<AmgHostLevel> lv;  // lv.back() is the coarsest level
   int32_t nc = 0;                // coarsest size
   std::vector<double> cinv;      // dense inverse of the coarsest matrix (row-major)
 };
-// Builds the smoothed-aggregation hierarchy of the scaled Poisson matrix of `m`.
+// Builds the smoothed-aggregation hierarchy of the scaled Poisson matrix of `m`, with the
+// composite operators of every non-coarsest level.
 int amg_setup(const HostMesh& m, AmgHost& out, char* err, size_t errlen);
-// SELL-32 form of a CSR matrix (the conventions of the mesh matrix, rows in order).
+// Coefficients (a, b) of Q = a D^-1 + b D^-1 A D^-1, the degree-2 Chebyshev smoother on
+// [lmax/30, lmax] written as one matrix.
+void chebyshev_q(double lmax, double& q_diag, double& q_off);
+// SELL-32 form of a CSR matrix with `lpr` lanes per row (1, 2, 4, 8, 16 or 32): a slice holds
+// 32 / lpr consecutive rows; step k of a slice is 32 contiguous elements, entries k*lpr ..
+// k*lpr + lpr - 1 of each of its rows (row r of the slice at r*lpr + e % lpr); a slice has as
+// many steps as its longest row needs; padding holds column 0 and value 0.  With lpr = 1 this is
+// the layout of the mesh matrix.
 struct SellHost {
-  int32_t n = 0, nslices = 0;
+  int32_t n = 0, nslices = 0, lpr = 1;
   std::vector<int32_t> sl_ptr, sl_w, rlen, col;
   std::vector<double> val;
 };
-void sell_from_csr(const Csr& A, SellHost& out);
+void sell_from_csr(const Csr& A, SellHost& out, int lpr = 1);
+// Lanes per row for a streamed operator: the smallest power of two (at most 32) that leaves
+// at most 8 stored entries per lane on an average row.
+int lanes_per_row(const Csr& A);
 
 // ----------------------------------------------------------------- kernel argument blocks
 struct SellView {  // device pointers of the SELL-32 structure
@@ -105,28 +125,29 @@ struct SellView {  // device pointers of the SELL-32 structure
 
 template <typename T>
 struct SellMatT {  // device pointers of a SELL-32 matrix with values of type T
-  const int32_t* sl_ptr;
-  const int32_t* sl_w;
+  const int32_t* sl_ptr;  // nslices + 1 element offsets
+  const int32_t* sl_w;    // steps per slice
   const int32_t* rlen;
   const int32_t* col;
   const T* val;
   int32_t n;
   int32_t nslices;
+  int32_t lpr;            // lanes per row (SellHost)
 };
 using SellMat = SellMatT<double>;
 
+// One level of the two-phase V-cycle on the device (values of type T: float by default, double
+// on request).  Down phase: xp = Q b (n rows) and b' = Rf b (n' rows of the next level); up
+// phase: x = [U | Pf] [xp; x'] (n rows; UP holds U's columns as they are and Pf's shifted by n).
+// Level 0 takes its right-hand side and writes its solution through the solver's own vectors;
+// x and b are used from level 1 on.
 template <typename T>
 struct AmgLevelT {
-  SellMatT<T> A, P, R;  // P: n x n_next (prolongation), R = P^T (restriction); unused on the coarsest
-  const T* dinv;
-  T* x;                 // level solution (the finest level's is passed to the V-cycle instead)
-  T* b;                 // level right-hand side (likewise)
-  T* r;                 // scratch: residual
-  T* d;                 // scratch: Chebyshev direction
-  double lmax;
-  // degree-2 Chebyshev smoother on [lmax/30, lmax] (set on the host from lmax):
-  // d0 = D^-1 r * inv_theta,  d1 = c1 d0 + c2 D^-1 r1
-  double inv_theta, c1, c2;
+  SellMatT<T> Q, Rf, UP;  // empty on the coarsest level
+  int64_t steps_q, steps_rf;  // 32-wide steps of Q and Rf (the split of the down phase's warps)
+  T* xp;                // pre-smoothed iterate Q b
+  T* x;                 // level solution
+  T* b;                 // level right-hand side
   int32_t n;
 };
 template <typename T>
@@ -238,14 +259,18 @@ struct PcgArgs {
   // BiCGStab (non-symmetric systems): three more vectors s, t and the shadow residual, each
   // Npad long, at bcg + k * Npad (v = A p lives in q_ap)
   double* bcg;
-  // AMG-preconditioned CG (kind 8): the hierarchy (device memory) and the preconditioned
-  // residual z
+  // AMG-preconditioned solvers (kinds 8-11): the hierarchy in device memory, FP32 (amg32,
+  // default) or FP64 (amg); the preconditioned residual z (of the hierarchy's type: z32 or z);
+  // r2: the second buffer of the CG residual (the update r - alpha q is written to the other
+  // buffer while neighbours still gather the old one)
   const AmgDev* amg;
   double* z;
-  // mixed precision with the AMG preconditioner (kind 10): FP32 copy of the hierarchy and the
-  // FP32 inner-solve vectors e32, r32, p32, q32 (above) plus z32
   const AmgDevT<float>* amg32;
   float* z32;
+  double* r2;
+  float* rq32;            // FP32 hierarchy: FP32 copies of the two residual buffers and of q
+                          // (3 x Npad), the vectors the finest down phase gathers
+  int32_t amg_mixed;      // 1: FP32 inner CG + FP64 refinement (kind 10); 0: FP64 CG
 };
 
 // Kernel and grid of a PCG launch.
@@ -256,13 +281,14 @@ struct PcgPlan {
                    // with the AMG preconditioner (FP32 inner CG + V-cycle, FP64 refinement),
                    // 11 AMG-preconditioned CG (FP64 or mixed) on one thread-block cluster
   int tpb = 768;
-  int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster)
+  int maxs = 0;    // slices per warp (register-resident); dynamic shared memory bytes (cluster);
+                   // 1 for an FP64 AMG hierarchy (kinds 8, 9, 11), 0 for the FP32 one
   int blocks = 1;
 };
 PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
-PcgPlan amg_plan(int nslices, int requested_tpb, int kind);  // kind 8 (CG), 9 (BiCGStab), 10 (mixed)
+PcgPlan amg_plan(int nslices, int requested_tpb, int kind, int fp64);  // kind 8 (CG), 9 (BiCGStab), 10 (mixed)
 PcgPlan amg_cluster_plan();  // kind 11 (one cluster; kind 0 if no cluster size is schedulable)
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.

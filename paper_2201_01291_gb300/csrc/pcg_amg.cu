@@ -1,27 +1,27 @@
 // Conjugate gradients preconditioned by one smoothed-aggregation AMG V-cycle (solver kind 8),
-// FP64, one cooperative persistent launch per solve.
+// BiCGStab preconditioned by it (kind 9, the non-symmetric axisymmetric matrix) and the
+// mixed-precision form (kind 10): one cooperative persistent launch per solve.
 //
 // The system is the symmetrically scaled one of the Jacobi variant, A = D^-1/2 K D^-1/2,
 // x = D^1/2 phi, b' = D^-1/2 b, with the same stopping test (true residual of the free rows,
-// ||b' - A x|| <= rtol ||b'||).  The hierarchy (level matrices, prolongators, restrictions,
-// diagonal inverses, largest-eigenvalue estimates, dense inverse of the coarsest matrix) is
-// built once per mesh on the host (amg_setup.cpp); the preconditioner z = M r is one V-cycle:
+// ||b' - A x|| <= rtol ||b'||).  The hierarchy (composite level operators, dense inverse of the
+// coarsest matrix) is built once per mesh on the host (amg_setup.cpp); the preconditioner
+// z = M r is one V-cycle of two grid-wide phases per level (amg_vcycle.cuh):
 //
-//   down, level l:  x = Chebyshev(degree 2, from x = 0) of A_l x = b_l;
-//                   r = b_l - A_l x;  b_{l+1} = R_l r
+//   down, level l:  xp = Q b  (degree-2 Chebyshev pre-smoothing from zero),
+//                   b' = Rf b = R (b - A xp)
 //   coarsest:       x = A_c^-1 b  (dense product)
-//   up, level l:    x += P_l x_{l+1};  x = Chebyshev(degree 2, from x) of A_l x = b_l
+//   up, level l:    x = U xp + Pf x' = xp + P x' + Q (b - A (xp + P x'))  (post-smoothing)
 //
 // with the Chebyshev polynomial in D^-1 A on [lmax/30, lmax] (lmax from power iteration).
 // The pre- and post-smoother are the same polynomial and R = P^T, so the V-cycle is a
-// symmetric positive definite operator and plain CG applies.
+// symmetric positive definite operator and plain CG applies.  Its values are FP32 by default
+// (T = float) or FP64; the Krylov vectors, the products with A and the stopping test are FP64.
 //
-// Every product gathers a vector that other blocks wrote in the previous phase, so each phase
-// ends with a grid-wide barrier (a reduction that also carries the dot products CG needs).  No
-// phase writes a vector that it also gathers: the Chebyshev steps gather the direction d and
-// update x, and the first direction of each level is formed where its right-hand side is
-// written (the restriction of the level above, or the CG residual update on the finest).
-// Per CG iteration: 6 barriers per non-coarsest level, 1 for the coarsest, 2 for CG.
+// Every phase gathers only vectors that other blocks completed in an earlier phase, so each
+// ends with a grid-wide barrier (a reduction where CG needs a dot product).  Per CG iteration:
+// 2 barriers per non-coarsest level, 1 for the coarsest, 1 for w = A z; the residual update of
+// the iteration is folded into the finest down phase of the next (amg_cg_solve).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,15 +39,29 @@ constexpr int kAmgMaxRestarts = 8;
 
 }  // namespace
 
-template <int TPB>
+// The hierarchy and the preconditioned residual of value type T.
+template <typename T>
+__device__ __forceinline__ const AmgDevT<T>* amg_of(const PcgArgs& a);
+template <>
+__device__ __forceinline__ const AmgDevT<float>* amg_of<float>(const PcgArgs& a) { return a.amg32; }
+template <>
+__device__ __forceinline__ const AmgDevT<double>* amg_of<double>(const PcgArgs& a) { return a.amg; }
+template <typename T>
+__device__ __forceinline__ T* z_of(const PcgArgs& a);
+template <>
+__device__ __forceinline__ float* z_of<float>(const PcgArgs& a) { return a.z32; }
+template <>
+__device__ __forceinline__ double* z_of<double>(const PcgArgs& a) { return a.z; }
+
+template <int TPB, typename T>
 __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   constexpr int wpb = TPB / 32;
   FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
-  if (!amg_cg_solve(a, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb, threadIdx.x & 31,
-                    blockIdx.x == 0 && threadIdx.x == 0) &&
+  if (!amg_cg_solve<T>(a, amg_of<T>(a), z_of<T>(a), ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb,
+                       threadIdx.x & 31, blockIdx.x == 0 && threadIdx.x == 0) &&
       threadIdx.x == 0) {
     atomicExch(&a.sync->abort, 1);
     a.res->pcg_status = AVIP_ETIMEOUT;
@@ -63,7 +77,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
 // (van der Vorst's iteration with M^-1 applied on the right, so x is updated directly and the
 // stopping test stays on the true scaled residual of the free rows).  Two V-cycles per
 // iteration; breakdowns and a true residual still too large restart from the true residual.
-template <int TPB>
+template <int TPB, typename T>
 __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
@@ -74,10 +88,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   const int N = a.A.N, nsl = a.A.nslices;
   const size_t Np = (size_t)a.Npad;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * Np;
-  const AmgDev* __restrict__ H = a.amg;
-  const double* __restrict__ dinv0 = H->L[0].dinv;
-  double* __restrict__ d0 = H->L[0].d;
-  const double inv_theta0 = H->L[0].inv_theta;
+  const AmgDevT<T>* __restrict__ H = amg_of<T>(a);
   double* __restrict__ x = a.x;
   double* __restrict__ r = a.r;
   double* __restrict__ p = a.p;
@@ -136,7 +147,6 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
             r[i] = ri;
             rh[i] = ri;
             p[i] = ri;
-            d0[i] = dinv0[i] * ri * inv_theta0;
             r2[0] = fma(ri, ri, r2[0]);
           }
           if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           restart = false;
         }
         // ---- p^ = M p, then P1: v = A p^
-        if (!vcycle(H, (const double*)p, ph, ops, gwarp, nwarps, lane, dummy)) goto timeout;
+        if (!vcycle(H, (const double*)p, ph, ops, gwarp, nwarps, lane, false, dummy)) goto timeout;
         double rv[1] = {0.0};
         for (int sl = gwarp; sl < nsl; sl += nwarps) {
           const int i = sl * kSlice + lane;
@@ -186,7 +196,6 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           if (i >= N) continue;
           const double si = fma(-alpha, v[i], r[i]);
           sv[i] = si;
-          d0[i] = dinv0[i] * si * inv_theta0;
           ss[0] = fma(si, si, ss[0]);
         }
         if (!grid_allsum<1>(ss, fs, smem)) goto timeout;
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           continue;
         }
         // ---- s^ = M s, then P3: t = A s^
-        if (!vcycle(H, (const double*)sv, sh, ops, gwarp, nwarps, lane, dummy)) goto timeout;
+        if (!vcycle(H, (const double*)sv, sh, ops, gwarp, nwarps, lane, false, dummy)) goto timeout;
         double d4[4] = {0.0, 0.0, 0.0, 0.0};  // t.s, t.t, rh.s, rh.t
         for (int sl = gwarp; sl < nsl; sl += nwarps) {
           const int i = sl * kSlice + lane;
@@ -236,7 +245,6 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           r[i] = ri;
           const double pn = fma(beta, fma(-omega, v[i], pi), ri);
           p[i] = pn;
-          d0[i] = dinv0[i] * pn * inv_theta0;
           rn2[0] = fma(ri, ri, rn2[0]);
         }
         if (!grid_allsum<1>(rn2, fs, smem)) goto timeout;
@@ -289,7 +297,25 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_mixed_kernel(PcgArgs a) {
   }
 }
 
-static const void* amg_kernel_ptr(int kind, int tpb) {
+template <typename T>
+static const void* amg_kernel_ptr_t(int kind, int tpb) {
+  if (kind == 9) {
+    switch (tpb) {
+      case 768: return (const void*)bicgstab_amg_kernel<768, T>;
+      case 1024: return (const void*)bicgstab_amg_kernel<1024, T>;
+      default: return (const void*)bicgstab_amg_kernel<512, T>;
+    }
+  }
+  switch (tpb) {
+    case 768: return (const void*)pcg_amg_kernel<768, T>;
+    case 1024: return (const void*)pcg_amg_kernel<1024, T>;
+    default: return (const void*)pcg_amg_kernel<512, T>;
+  }
+}
+
+// Kernel of solver kind 8 (CG), 9 (BiCGStab) or 10 (mixed precision) with an FP32 (fp64 = 0)
+// or FP64 hierarchy; kind 10 always takes the FP32 one.
+static const void* amg_kernel_ptr(int kind, int tpb, int fp64) {
   if (kind == 10) {
     switch (tpb) {
       case 768: return (const void*)pcg_amg_mixed_kernel<768>;
@@ -297,31 +323,21 @@ static const void* amg_kernel_ptr(int kind, int tpb) {
       default: return (const void*)pcg_amg_mixed_kernel<512>;
     }
   }
-  if (kind == 9) {
-    switch (tpb) {
-      case 768: return (const void*)bicgstab_amg_kernel<768>;
-      case 1024: return (const void*)bicgstab_amg_kernel<1024>;
-      default: return (const void*)bicgstab_amg_kernel<512>;
-    }
-  }
-  switch (tpb) {
-    case 768: return (const void*)pcg_amg_kernel<768>;
-    case 1024: return (const void*)pcg_amg_kernel<1024>;
-    default: return (const void*)pcg_amg_kernel<512>;
-  }
+  return fp64 ? amg_kernel_ptr_t<double>(kind, tpb) : amg_kernel_ptr_t<float>(kind, tpb);
 }
 
 // Grid: co-resident blocks (one per SM), no more than the finest level needs.
-PcgPlan amg_plan(int nslices, int requested_tpb, int kind) {
+PcgPlan amg_plan(int nslices, int requested_tpb, int kind, int fp64) {
   PcgPlan pl;
   pl.kind = kind;
+  pl.maxs = fp64;  // FP64 hierarchy (1) or FP32 (0)
   pl.tpb = kAmgSizes[0];
   for (int t : kAmgSizes)
     if (t == requested_tpb) pl.tpb = t;
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg_kernel_ptr(kind, pl.tpb), pl.tpb, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg_kernel_ptr(kind, pl.tpb, fp64), pl.tpb, 0);
   const int wpb = pl.tpb / kSlice;
   const int want = (nslices + wpb - 1) / wpb;
   pl.blocks = std::max(1, std::min(std::max(occ, 1) * std::max(sms, 1), want));
@@ -340,7 +356,7 @@ cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* kargs[] = {const_cast<PcgArgs*>(&args)};
-  return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.kind, pl.tpb), kargs);
+  return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.kind, pl.tpb, pl.maxs), kargs);
 }
 
 }  // namespace avip

@@ -573,8 +573,11 @@ __device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) 
   cg::cluster_group cl = cg::this_cluster();
   ClusterOps ops{cl, part, wsum, wsum + 32 * 4, 0u};
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
-  amg_cg_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb, (int)(threadIdx.x & 31),
-               rank == 0 && threadIdx.x == 0);
+  const int gw = rank * wpb + (int)(threadIdx.x >> 5), nw = (int)cl.num_blocks() * wpb, lane = (int)(threadIdx.x & 31);
+  if (a.amg32)  // FP32 hierarchy (default), else FP64
+    amg_cg_solve<float>(a, a.amg32, a.z32, ops, gw, nw, lane, rank == 0 && threadIdx.x == 0);
+  else
+    amg_cg_solve<double>(a, a.amg, a.z, ops, gw, nw, lane, rank == 0 && threadIdx.x == 0);
   cl.sync();  // the next instance reuses the sum buffers
 }
 
@@ -593,8 +596,8 @@ __device__ void cluster_amg_mixed_solve(const PcgArgs& a, double* part, double* 
 
 // Batched, persistent: every resident cluster solves instances order[c], order[c + nclusters],
 // ... (the order is sorted by decreasing size, so the largest solves start first).  Instances
-// that carry an AMG hierarchy (solver kinds 8 and 10) are solved with it, the others with the
-// shared-memory Jacobi-PCG (FP64 or mixed).
+// that carry an AMG hierarchy (solver kinds 8 and 10) are solved with it (FP64 CG, or the
+// mixed-precision solve), the others with the shared-memory Jacobi-PCG (FP64 or mixed).
 __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const PcgArgs* __restrict__ args,
                                                                             const ClusterLayout* __restrict__ lays,
                                                                             const int32_t* __restrict__ order,
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_batch_kernel(const
     const int k = order[j];
     const PcgArgs a = args[k];
     const ClusterLayout L = lays[k];
-    if (a.amg)
+    if ((a.amg || a.amg32) && !a.amg_mixed)
       cluster_amg_solve(a, s_amg_part, s_amg_wsum);
     else if (a.amg32)
       cluster_amg_mixed_solve(a, s_amg_part, s_amg_wsum);
@@ -757,14 +760,14 @@ cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const Clu
 }
 
 // Standalone AMG solve on one thread-block cluster (solver kind 11): small and mid-size meshes
-// whose solve is too short to occupy the whole GPU (FP64 hierarchy, or the FP32 one of the
-// mixed-precision path).  Other work, such as other requests of a server, can run beside it.
+// whose solve is too short to occupy the whole GPU (FP64 CG with an FP32 or FP64 hierarchy, or
+// the mixed-precision solve).  Other work, such as other requests of a server, can run beside it.
 __global__ void __launch_bounds__(kClusterTPB, 1) pcg_amg_cluster_kernel(PcgArgs a) {
   __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4 + 4];
-  if (a.amg)
-    cluster_amg_solve(a, s_amg_part, s_amg_wsum);
-  else
+  if (a.amg_mixed)
     cluster_amg_mixed_solve(a, s_amg_part, s_amg_wsum);
+  else
+    cluster_amg_solve(a, s_amg_part, s_amg_wsum);
 }
 
 // Largest schedulable cluster (16 or 8 CTAs) for the standalone AMG cluster kernel; 0 if none.

@@ -35,11 +35,13 @@ def test_traffic_models_match_their_formulas():
     b, f = bench.pcg_traffic_model(info, it, solves)
     assert b == it * (12 * nnz + 24 * N) + solves * (24 * nnz + 80 * N)
     assert f == it * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
-    # two smoothed levels and a dense coarsest level of 20 rows
-    levels = [(N, nnz, 3000), (150, 1200, 400), (20, 300, 0)]
-    b8, f8 = bench.amg_traffic_model(levels, nnz, N, it, solves, kind=8)
-    vb = (48 * nnz + 24 * 3000) + (196 * N + 36 * 150) + (48 * 1200 + 24 * 400) + (196 * 150 + 36 * 20) \
-        + (8 * 20 * 20 + 16 * 20)
-    assert b8 == it * (12 * nnz + 116 * N + vb) + solves * (24 * nnz + 100 * N)
-    vf = 2 * (4 * nnz + 2 * 3000) + 20 * N + 2 * (4 * 1200 + 2 * 400) + 20 * 150 + 2 * 20 * 20
-    assert f8 == it * (2 * nnz + 12 * N + vf) + solves * (4 * nnz + 12 * N)
+    # two smoothed levels and a dense coarsest level of 20 rows: (n, A, P, Rf, U, Pf)
+    levels = [(N, nnz, 3000, 9000, 19000, 9500), (150, 1200, 400, 1300, 3000, 1400), (20, 300, 0, 0, 0, 0)]
+    b8, f8 = bench.amg_traffic_model(levels, nnz, N, it, solves, kind=8, sv=4)
+    vb = ((nnz + 9000) * 8 + 4 * (2 * N + 150) + 4 * (N + 150)) + ((19000 + 9500) * 8 + 4 * (2 * N + 150) + 8 * N) \
+        + ((1200 + 1300) * 8 + 4 * (2 * 150 + 20) + 4 * (150 + 20)) + ((3000 + 1400) * 8 + 4 * (2 * 150 + 20) + 8 * 150) \
+        + 4 * (20 * 20 + 2 * 20)
+    per_it = vb + 12 * N + 32 * N + 8 * N + 12 * nnz + 40 * N
+    assert b8 == it * per_it + solves * (24 * nnz + 100 * N)
+    vf = 2 * (nnz + 9000 + 19000 + 9500) + N + 2 * (1200 + 1300 + 3000 + 1400) + 150 + 2 * 20 * 20
+    assert f8 == it * (vf + 2 * nnz + 14 * N) + solves * (4 * nnz + 12 * N)
