@@ -4,8 +4,8 @@
 // Each non-coarsest level takes two phases, through the composite operators built on the host
 // (amg_setup.cpp): down, xp = Q b and b' = Rf b (the pre-smoothing, the residual and its
 // restriction); up, x = U xp + Pf x' (the coarse correction and the post-smoothing).  It is the
-// V-cycle of a degree-2 Chebyshev smoother (the same polynomial before and after), R = P^T and
-// a dense coarsest solve, written with fewer grid-wide phases: every phase gathers only vectors
+// V-cycle of a damped Jacobi smoother (the same step before and after), R = P^T and a dense
+// coarsest solve, written with fewer grid-wide phases: every phase gathers only vectors
 // completed by an earlier one.  The values are FP32 by default (the preconditioner only shapes
 // the search directions; the iterate, the residuals and the stopping test stay FP64) or FP64.
 //
@@ -47,47 +47,51 @@ struct DotAcc<float> {
 // Steps per batch of the streamed products: 16 with FP32 values, 8 with FP64.
 template <typename T>
 struct StreamDepth {
-  static constexpr int value = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int value = 8;
 };
 
-// The warps of a phase that works on two operators over different rows are split in
-// proportion to the operators' stored entries: warps [0, k) take the first, [k, nwarps) the
-// second.  k = nwarps when the second is empty, 0 when the first is.
-__device__ __forceinline__ int split_warps(int nwarps, int64_t e1, int64_t e2) {
-  if (e2 <= 0) return nwarps;
-  if (e1 <= 0) return 0;
-  const int k = (int)((double)nwarps * (double)e1 / (double)(e1 + e2) + 0.5);
-  return min(max(k, 1), nwarps - 1);
-}
-
-// Down phase of level l: xp = Q b on the rows of level l and b' = Rf b on the rows of level
-// l + 1, b given by `src` (complete on entry).  `hook` (see spmv_stream's begin / emit) takes
-// part in every row of level l: hook.begin(i) fetches the row's own operands ahead, hook.end(i,
-// pre) runs before xp_i is stored (the CG update folded into the finest level's phase).  The
-// warps are split between Q and Rf in proportion to their steps; each warp streams a contiguous
-// share of its operator's slices; a single warp does both.
+// Down phase of level l: xp = Q b on the rows of level l (Q = omega D^-1 is diagonal: an
+// elementwise pass) and b' = Rf b on the rows of level l + 1 (a streamed product), b given by
+// `src` (complete on entry).  `hook` takes part in every row i of level l: hook.begin(i) loads
+// the row's own operands, hook.end(i, pre) runs with them (the CG update folded into the
+// finest level's phase).  The elementwise pass takes kRowBatch rows per thread at a time, their
+// loads all issued before their use; then every warp streams a contiguous share of Rf.
 template <typename T, class Src, class Hook>
 __device__ __forceinline__ void amg_down(const AmgDevT<T>* __restrict__ H, int l, Src src, Hook hook, int gwarp,
                                          int nwarps, int lane) {
   constexpr int U = StreamDepth<T>::value;
+  constexpr int kRowBatch = 4;
   const AmgLevelT<T>& L = H->L[l];
   T* __restrict__ bn = H->L[l + 1].b;
   T* __restrict__ xp = L.xp;
-  const bool one = nwarps == 1;
-  const int k = one ? 1 : split_warps(nwarps, L.steps_q, L.steps_rf);
+  const T* __restrict__ qd = L.qd;
+  const int n = L.n;
+  const int stride = nwarps * kSlice;
+  using Pre = decltype(hook.begin(0));
+  for (int i0 = gwarp * kSlice + lane; i0 < n; i0 += kRowBatch * stride) {
+    Pre pre[kRowBatch];
+    T bi[kRowBatch], qi[kRowBatch];
+#pragma unroll
+    for (int k = 0; k < kRowBatch; ++k) {
+      const int i = i0 + k * stride;
+      if (i < n) {
+        pre[k] = hook.begin(i);
+        bi[k] = src(i);
+        qi[k] = __ldg(qd + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRowBatch; ++k) {
+      const int i = i0 + k * stride;
+      if (i < n) {
+        hook.end(i, pre[k]);
+        xp[i] = qi[k] * bi[k];
+      }
+    }
+  }
   int sa, sb;
-  if (one || gwarp < k) {
-    warp_slices(L.Q.nslices, one ? 0 : gwarp, one ? 1 : k, sa, sb);
-    spmv_stream<T, U>(L.Q, sa, sb, lane, src, [&](int i) { return hook.begin(i); },
-                      [&](int i, T v, const decltype(hook.begin(0))& pre) {
-                        hook.end(i, pre);
-                        xp[i] = v;
-                      });
-  }
-  if (one || gwarp >= k) {
-    warp_slices(L.Rf.nslices, one ? 0 : gwarp - k, one ? 1 : nwarps - k, sa, sb);
-    spmv_stream<T, U>(L.Rf, sa, sb, lane, src, NoBegin(), [&](int j, T v, NoPre) { bn[j] = v; });
-  }
+  warp_slices(L.Rf.nslices, gwarp, nwarps, sa, sb);
+  spmv_stream<T, U>(L.Rf, sa, sb, lane, src, NoBegin(), [&](int j, T v, NoPre) { bn[j] = v; });
 }
 
 // Up phase of level l: x = U xp + Pf x' = [U | Pf] [xp; x'] on the rows of level l (x' = the
@@ -125,11 +129,23 @@ struct StoreOut {  // x_i = value
 template <typename T, class Src, class Out>
 __device__ __forceinline__ void amg_coarse(const AmgDevT<T>* __restrict__ H, Src src, Out out, int gwarp,
                                            int nwarps, int lane) {
+  constexpr int K = 8;  // independent loads per lane in flight
   const int n = H->nc;
   const T* __restrict__ cinv = H->cinv;
   for (int row = gwarp; row < n; row += nwarps) {
+    const T* __restrict__ crow = cinv + (size_t)row * n;
     T s = T(0);
-    for (int k = lane; k < n; k += 32) s = fma_t(__ldg(cinv + (size_t)row * n + k), src(k), s);
+    for (int k0 = lane; k0 < n; k0 += 32 * K) {
+      T c[K], b[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const int k = k0 + 32 * u;
+        c[u] = k < n ? __ldg(crow + k) : T(0);
+        b[u] = k < n ? src(k) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < K; ++u) s = fma_t(c[u], b[u], s);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out(row, s);
@@ -197,14 +213,14 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const TB* __restrict__ 
 
 // CG preconditioned by the V-cycle on the scaled system (kinds 8, 11 and the batched FP64 form):
 // warm start, b', true-residual checks and restarts, phi = D^-1/2 x.  The hierarchy H (values of
-// type T) writes the preconditioned residual z (type T).  The residual update r - alpha q and
+// type T) writes the preconditioned residual z in FP64 (only w = A z gathers it).  The residual update r - alpha q and
 // x += alpha p of iteration k are folded into the finest down phase of iteration k + 1, whose
 // products gather r - alpha q directly (the new residual goes to the other buffer, r2), so an
 // iteration takes 2 nlev grid-wide phases: the finest down phase (sum of r.r: stop test), the
 // levels below, the finest up phase (sum of r.z), and w = A z (sum of p.q).  `leader` is the
 // one thread that writes the solve statistics.  Returns false if a wait was abandoned.
 template <typename T, class Ops>
-__device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H, T* __restrict__ z, Ops& ops,
+__device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H, double* __restrict__ z, Ops& ops,
                              int gwarp, int nwarps, int lane, bool leader) {
   constexpr int kMaxRestarts = 8;
   const int N = a.A.N, nsl = a.A.nslices, nl = H->nlev;
@@ -356,14 +372,15 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
         {
           DotAcc<double> acc;
           const double* __restrict__ rv = rc;
-          struct Out {  // z_i = value, r_i z_i into r.z
+          struct Out {  // z_i = value (widened once here: w = A z gathers it in FP64), r_i z_i into r.z
             const double* rv;
-            T* z;
+            double* z;
             DotAcc<double>* acc;
             __device__ double begin(int i) const { return __ldca(rv + i); }
             __device__ void end(int i, T v, double ri) const {
-              z[i] = v;
-              acc->add(ri, (double)v);
+              const double zi = (double)v;
+              z[i] = zi;
+              acc->add(ri, zi);
             }
           } out{rv, z, &acc};
           if (nl == 1) {
@@ -391,7 +408,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
         // ---- w = A z, q = w + beta q, p = z + beta p, p.q -> alpha
         double pq[1] = {0.0};
         {
-          const T* __restrict__ zc = z;
+          const double* __restrict__ zc = z;
           double* __restrict__ qv = a.q_ap;
           double* __restrict__ pv = a.p;
           T* __restrict__ tqw = tq;
@@ -399,8 +416,8 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
             double z, q, p;
           };
           spmv_stream<double, 8>(
-              A0, ma, mb, lane, [zc](int c) { return (double)__ldca(zc + c); },
-              [=](int i) { return PreA{(double)__ldca(zc + i), qv[i], pv[i]}; },
+              A0, ma, mb, lane, [zc](int c) { return __ldca(zc + c); },
+              [=](int i) { return PreA{__ldca(zc + i), qv[i], pv[i]}; },
               [&](int i, double w, const PreA& o) {
                 const double qn = beta == 0.0 ? w : fma(beta, o.q, w);
                 const double pn = beta == 0.0 ? o.z : fma(beta, o.p, o.z);

@@ -62,8 +62,8 @@ struct avip_mesh {
   double* bcg = nullptr;        // BiCGStab vectors (kind 7 only)
   AmgDev* amg = nullptr;            // AMG hierarchy with FP64 values (opts.precond_fp64)
   AmgDevT<float>* amg32 = nullptr;  // AMG hierarchy with FP32 values (default; kind 10 always)
-  float* z32 = nullptr;             // preconditioned residual of the FP32 hierarchy
-  double* amg_z = nullptr;          // preconditioned residual of the FP64 hierarchy
+  float* z32 = nullptr;             // preconditioned residual of the mixed-precision solve
+  double* amg_z = nullptr;          // preconditioned residual of the FP64 CG (either hierarchy)
   double* r2 = nullptr;             // second buffer of the AMG-CG residual
   float* rq32 = nullptr;            // FP32 copies of both residual buffers and of q (FP32 hierarchy)
   int32_t amg_levels = 0;
@@ -410,10 +410,14 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, AmgDevT<T>*& out, bool record 
     AmgLevelT<T>& dl = D.L[l];
     dl.n = L.A.n;
     const size_t npad = (size_t)((L.A.n + kSlice - 1) / kSlice) * kSlice;
-    int64_t up_steps = 0;
-    if (l + 1 < D.nlev)
-      ok = ok && put(L.Q, dl.Q, dl.steps_q) && put(L.Rf, dl.Rf, dl.steps_rf) &&
-           put(concat(L.U, L.Pf), dl.UP, up_steps) && zalloc(h, dl.xp, npad);
+    int64_t rf_steps = 0, up_steps = 0;
+    if (l + 1 < D.nlev) {
+      T* qd = nullptr;
+      std::vector<T> qv(L.Q.v.begin(), L.Q.v.end());  // Q is diagonal: one entry per row, in order
+      ok = ok && upload(h, qd, qv, npad) && put(L.Rf, dl.Rf, rf_steps) && put(concat(L.U, L.Pf), dl.UP, up_steps) &&
+           zalloc(h, dl.xp, npad);
+      dl.qd = qd;
+    }
     if (l > 0) ok = ok && zalloc(h, dl.x, npad) && zalloc(h, dl.b, npad);
   }
   T* cinv = nullptr;
@@ -439,8 +443,10 @@ bool upload_amg_t(avip_mesh* h, const AmgHost& H, AmgDevT<T>*& out, bool record 
 bool upload_amg(avip_mesh* h, const AmgHost& H, size_t Np) {
   const bool fp64 = h->opts.precond_fp64 && h->opts.precision == AVIP_PREC_FP64;
   if (fp64) return upload_amg_t<double>(h, H, h->amg) && zalloc(h, h->amg_z, Np) && zalloc(h, h->r2, Np);
-  return upload_amg_t<float>(h, H, h->amg32) && zalloc(h, h->z32, Np) && zalloc(h, h->r2, Np) &&
-         zalloc(h, h->rq32, 3 * Np);
+  // (the FP64 CG writes its preconditioned residual in FP64 whatever the hierarchy's type; the
+  // mixed-precision solve keeps its own FP32 one)
+  return upload_amg_t<float>(h, H, h->amg32) && zalloc(h, h->z32, Np) && zalloc(h, h->amg_z, Np) &&
+         zalloc(h, h->r2, Np) && zalloc(h, h->rq32, 3 * Np);
 }
 
 }  // namespace

@@ -72,11 +72,10 @@ struct AmgHostLevel {
   Csr A, P, R;                 // level matrix; prolongator from the next level; R = P^T
   std::vector<double> dinv;    // 1 / diag(A)
   double lmax = 1.0;           // estimate of the largest eigenvalue of D^-1 A
-  // degree-2 Chebyshev smoother on [lmax/30, lmax] as one matrix: x = Q b from x = 0, and
-  // x <- x + Q (b - A x) from a given x, with Q = a D^-1 + b D^-1 A D^-1 (chebyshev_q)
-  double q_diag = 0.0, q_off = 0.0;
+  // smoother: x = Q b from x = 0 and x <- x + Q (b - A x) from a given x, Q = omega D^-1
+  double omega = 0.0;
   // composite operators of the two-phase V-cycle (non-coarsest levels only):
-  //   Q  (n x n)      pre-smoothing from zero
+  //   Q  (n x n)      pre-smoothing from zero (diagonal)
   //   Rf (n' x n)     = R (I - A Q): restriction of the pre-smoothed residual
   //   U  (n x n)      = 2 I - Q A:  the pre-smoothed iterate through the post-smoother
   //   Pf (n x n')     = (I - Q A) P: the coarse correction through the post-smoother
@@ -90,9 +89,7 @@ struct AmgHost {
 // Builds the smoothed-aggregation hierarchy of the scaled Poisson matrix of `m`, with the
 // composite operators of every non-coarsest level.
 int amg_setup(const HostMesh& m, AmgHost& out, char* err, size_t errlen);
-// Coefficients (a, b) of Q = a D^-1 + b D^-1 A D^-1, the degree-2 Chebyshev smoother on
-// [lmax/30, lmax] written as one matrix.
-void chebyshev_q(double lmax, double& q_diag, double& q_off);
+
 // SELL-32 form of a CSR matrix with `lpr` lanes per row (1, 2, 4, 8, 16 or 32): a slice holds
 // 32 / lpr consecutive rows; step k of a slice is 32 contiguous elements, entries k*lpr ..
 // k*lpr + lpr - 1 of each of its rows (row r of the slice at r*lpr + e % lpr); a slice has as
@@ -137,14 +134,14 @@ struct SellMatT {  // device pointers of a SELL-32 matrix with values of type T
 using SellMat = SellMatT<double>;
 
 // One level of the two-phase V-cycle on the device (values of type T: float by default, double
-// on request).  Down phase: xp = Q b (n rows) and b' = Rf b (n' rows of the next level); up
+// on request).  Down phase: xp = Q b (n rows; Q diagonal) and b' = Rf b (n' rows of the next level); up
 // phase: x = [U | Pf] [xp; x'] (n rows; UP holds U's columns as they are and Pf's shifted by n).
 // Level 0 takes its right-hand side and writes its solution through the solver's own vectors;
 // x and b are used from level 1 on.
 template <typename T>
 struct AmgLevelT {
-  SellMatT<T> Q, Rf, UP;  // empty on the coarsest level
-  int64_t steps_q, steps_rf;  // 32-wide steps of Q and Rf (the split of the down phase's warps)
+  SellMatT<T> Rf, UP;   // empty on the coarsest level
+  const T* qd;          // the smoother Q = omega D^-1 (its diagonal, n entries)
   T* xp;                // pre-smoothed iterate Q b
   T* x;                 // level solution
   T* b;                 // level right-hand side

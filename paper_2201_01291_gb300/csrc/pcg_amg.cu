@@ -8,14 +8,14 @@
 // coarsest matrix) is built once per mesh on the host (amg_setup.cpp); the preconditioner
 // z = M r is one V-cycle of two grid-wide phases per level (amg_vcycle.cuh):
 //
-//   down, level l:  xp = Q b  (degree-2 Chebyshev pre-smoothing from zero),
+//   down, level l:  xp = Q b  (damped Jacobi pre-smoothing from zero, Q = omega D^-1),
 //                   b' = Rf b = R (b - A xp)
 //   coarsest:       x = A_c^-1 b  (dense product)
 //   up, level l:    x = U xp + Pf x' = xp + P x' + Q (b - A (xp + P x'))  (post-smoothing)
 //
-// with the Chebyshev polynomial in D^-1 A on [lmax/30, lmax] (lmax from power iteration).
-// The pre- and post-smoother are the same polynomial and R = P^T, so the V-cycle is a
-// symmetric positive definite operator and plain CG applies.  Its values are FP32 by default
+// with omega = 1.7 / lambda_max(D^-1 A) (lambda_max from power iteration).  The pre- and
+// post-smoother are the same step and R = P^T, so the V-cycle is a symmetric positive definite
+// operator and plain CG applies.  Its values are FP32 by default
 // (T = float) or FP64; the Krylov vectors, the products with A and the stopping test are FP64.
 //
 // Every phase gathers only vectors that other blocks completed in an earlier phase, so each
@@ -34,7 +34,7 @@
 namespace avip {
 
 namespace {
-constexpr int kAmgSizes[] = {512, 768, 1024};  // block sizes; index 0 is the default
+constexpr int kAmgSizes[] = {768, 512, 1024};  // block sizes; index 0 is the default
 constexpr int kAmgMaxRestarts = 8;
 
 }  // namespace
@@ -46,13 +46,6 @@ template <>
 __device__ __forceinline__ const AmgDevT<float>* amg_of<float>(const PcgArgs& a) { return a.amg32; }
 template <>
 __device__ __forceinline__ const AmgDevT<double>* amg_of<double>(const PcgArgs& a) { return a.amg; }
-template <typename T>
-__device__ __forceinline__ T* z_of(const PcgArgs& a);
-template <>
-__device__ __forceinline__ float* z_of<float>(const PcgArgs& a) { return a.z32; }
-template <>
-__device__ __forceinline__ double* z_of<double>(const PcgArgs& a) { return a.z; }
-
 template <int TPB, typename T>
 __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
@@ -60,7 +53,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
   constexpr int wpb = TPB / 32;
   FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
-  if (!amg_cg_solve<T>(a, amg_of<T>(a), z_of<T>(a), ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb,
+  if (!amg_cg_solve<T>(a, amg_of<T>(a), a.z, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb,
                        threadIdx.x & 31, blockIdx.x == 0 && threadIdx.x == 0) &&
       threadIdx.x == 0) {
     atomicExch(&a.sync->abort, 1);

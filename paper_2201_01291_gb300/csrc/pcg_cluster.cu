@@ -575,7 +575,7 @@ __device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) 
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
   const int gw = rank * wpb + (int)(threadIdx.x >> 5), nw = (int)cl.num_blocks() * wpb, lane = (int)(threadIdx.x & 31);
   if (a.amg32)  // FP32 hierarchy (default), else FP64
-    amg_cg_solve<float>(a, a.amg32, a.z32, ops, gw, nw, lane, rank == 0 && threadIdx.x == 0);
+    amg_cg_solve<float>(a, a.amg32, a.z, ops, gw, nw, lane, rank == 0 && threadIdx.x == 0);
   else
     amg_cg_solve<double>(a, a.amg, a.z, ops, gw, nw, lane, rank == 0 && threadIdx.x == 0);
   cl.sync();  // the next instance reuses the sum buffers
