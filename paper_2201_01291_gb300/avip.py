@@ -87,6 +87,7 @@ _SIGS = {
     "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_int32, C.c_void_p, _I, _D]),
     "peak_probe": (C.c_int, [C.c_int32, C.c_void_p, _D]),
+    "fp64_math_check": (C.c_int, [_D]),
     "avip_status_str": (C.c_char_p, [C.c_int]),
     "avip_last_error": (C.c_char_p, []),
 }
@@ -317,6 +318,14 @@ def peak_probe(which, stream=0):
     v = C.c_double()
     rc = load().peak_probe(int(which), C.c_void_p(stream), C.byref(v))
     return rc, v.value
+
+
+def fp64_math_check():
+    """Largest relative differences (exp, log, pow) of the library's FP64 closures' math from
+    the CUDA math library."""
+    out = np.zeros(3)
+    rc = load().fp64_math_check(_dptr(out))
+    return rc, out
 
 
 def batch_create(handles, cluster_size=0):

@@ -21,13 +21,16 @@
 #include <cfloat>
 
 #include "avip_internal.h"
+#include "fp64_math.cuh"
 
 namespace avip {
 
 constexpr int kDDThreads = 256;
 
+// Local-field mobility and the Townsend exponential with the library's FP64 exp / log
+// (fp64_math.cuh: a few ulp, a fraction of the FP64 instructions of the general routines).
 __device__ __forceinline__ double mobility(const SpeciesParams& sp, double Emag) {
-  if (sp.mob_model == AVIP_MOB_POWER) return sp.mob[0] * pow(fmax(Emag, sp.mob[3]) / sp.mob[1], sp.mob[2]);
+  if (sp.mob_model == AVIP_MOB_POWER) return sp.mob[0] * pow_pos_fp64(fmax(Emag, sp.mob[3]) / sp.mob[1], sp.mob[2]);
   return sp.mob[0];
 }
 
@@ -67,19 +70,43 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
     double gnx[AVIP_MAX_SPECIES], gny[AVIP_MAX_SPECIES];
 #pragma unroll
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s) gnx[s] = gny[s] = 0.0;
-    for (int k = 0; k < rl; ++k) {
-      const int e = base + k * kSlice;
-      const int j = __ldg(a.A.col + e);
-      const double wx = __ldg(a.A.gx + e), wy = __ldg(a.A.gy + e);
-      const double pj = a.phi[j];
-      gpx = fma(wx, pj, gpx);
-      gpy = fma(wy, pj, gpy);
+    // neighbours in groups of kG: the column and weight loads of a group are issued together,
+    // then its potential and density gathers, then the sums (in slot order, as one at a time)
+    constexpr int kG = 8;
+    for (int k0 = 0; k0 < rl; k0 += kG) {
+      int c[kG];
+      double wx[kG], wy[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int e = base + (k0 + u) * kSlice;
+        const bool in = k0 + u < rl;
+        c[u] = in ? __ldg(a.A.col + e) : i;
+        wx[u] = in ? __ldg(a.A.gx + e) : 0.0;
+        wy[u] = in ? __ldg(a.A.gy + e) : 0.0;
+      }
+      double pj[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) pj[u] = a.phi[c[u]];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        if (k0 + u < rl) {
+          gpx = fma(wx[u], pj[u], gpx);
+          gpy = fma(wy[u], pj[u], gpy);
+        }
+      }
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
         if (s < ns) {
-          const double u = n[(size_t)s * a.Npad + j];
-          gnx[s] = fma(wx, u, gnx[s]);
-          gny[s] = fma(wy, u, gny[s]);
+          double uj[kG];
+#pragma unroll
+          for (int u = 0; u < kG; ++u) uj[u] = n[(size_t)s * a.Npad + c[u]];
+#pragma unroll
+          for (int u = 0; u < kG; ++u) {
+            if (k0 + u < rl) {
+              gnx[s] = fma(wx[u], uj[u], gnx[s]);
+              gny[s] = fma(wy[u], uj[u], gny[s]);
+            }
+          }
         }
       }
     }
@@ -107,7 +134,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
     if (a.ph.src_model != AVIP_SRC_NONE) {
       const int ie = a.ph.src_idx[0], ip = a.ph.src_idx[1], ineg = a.ph.src_idx[2];
       const double ne = n[(size_t)ie * a.Npad + i];
-      const double alpha = Emag > 0.0 ? a.ph.src_params[0] * exp(-a.ph.src_params[1] / Emag) : 0.0;
+      const double alpha = Emag > 0.0 ? a.ph.src_params[0] * exp_fp64(-a.ph.src_params[1] / Emag) : 0.0;
       double mue = 0.0;
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
@@ -134,7 +161,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
           if (s == ip) npos = n[(size_t)s * a.Npad + i];
           if (s == ineg) nneg = n[(size_t)s * a.Npad + i];
         }
-        const double eta = Emag > 0.0 ? a.ph.src_params[2] * exp(-a.ph.src_params[3] / Emag) : 0.0;
+        const double eta = Emag > 0.0 ? a.ph.src_params[2] * exp_fp64(-a.ph.src_params[3] / Emag) : 0.0;
         const double att = eta * mue * Emag * ne;
         const double rep = a.ph.src_params[4] * ne * npos;
         const double rnp = a.ph.src_params[4] * nneg * npos;

@@ -11,8 +11,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "avip_internal.h"
+#include "fp64_math.cuh"
 
 namespace avip {
 namespace {
@@ -65,10 +67,56 @@ cudaError_t best_ms(cudaStream_t st, F launch, float& best) {
   return e;
 }
 
+// Largest relative difference between this library's FP64 exp / log / pow (fp64_math.cuh) and
+// the CUDA math library over log-spaced arguments: exp on [-700, 700], log on 1e-300 .. 1e300,
+// pow (exponents -0.2, 0.5, -1.7, 2.3) on bases 1e-6 .. 1e6.
+constexpr int kCheckPoints = 1 << 16;
+__global__ void fp64_math_check_kernel(unsigned long long* worst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kCheckPoints) return;
+  const double t = (double)k / (kCheckPoints - 1);
+  const double xe = -700.0 + 1400.0 * t;
+  const double xl = exp10(-300.0 + 600.0 * t) * (1.0 + 0.3 * sin(37.0 * k));
+  auto rel = [](double a, double b) { return b != 0.0 ? fabs(a - b) / fabs(b) : fabs(a); };
+  double e[3];
+  e[0] = rel(exp_fp64(xe), exp(xe));
+  e[1] = rel(log_fp64(xl), log(xl));
+  e[2] = 0.0;
+  const double ps[4] = {-0.2, 0.5, -1.7, 2.3};
+  for (double pp : ps) {
+    const double xb = exp10(-6.0 + 12.0 * t) * (1.0 + 0.3 * sin(11.0 * k));
+    e[2] = fmax(e[2], rel(pow_pos_fp64(xb, pp), pow(xb, pp)));
+  }
+  for (int j = 0; j < 3; ++j) atomicMax(worst + j, (unsigned long long)__double_as_longlong(e[j]));
+}
+
 }  // namespace
 }  // namespace avip
 
 using namespace avip;
+
+extern "C" int fp64_math_check(double* max_rel_err) {
+  if (!max_rel_err) return AVIP_EINVAL;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    return AVIP_ENOMEM;
+  }
+  unsigned long long h[3] = {0, 0, 0};
+  cudaError_t e = cudaMemset(d, 0, sizeof(h));
+  if (e == cudaSuccess) {
+    fp64_math_check_kernel<<<kCheckPoints / 256, 256>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return AVIP_ECUDA;
+  }
+  for (int j = 0; j < 3; ++j) std::memcpy(max_rel_err + j, h + j, sizeof(double));
+  return AVIP_OK;
+}
 
 extern "C" int peak_probe(int32_t which, void* stream, double* value_out) {
   if (!value_out || (which != AVIP_PROBE_FP64_FMA && which != AVIP_PROBE_HBM_COPY)) return AVIP_EINVAL;
