@@ -317,10 +317,12 @@ int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels);
  * statistics, and gives the same result alone and in the batch (tests check it).
  *   meshes[count]: FP64 handles with every species set; they must outlive the batch and must
  *                  not be stepped on their own while the batch runs;
- *   cluster_size:  8 or 16 CTAs per cluster, or 0 to pick by timing both on the batch (the
- *                  instances' state is saved and restored around the trial).
- * AVIP_EINVAL if an instance does not fit one cluster's shared memory (the cluster kernel holds
- * every vector of its instance there; about 100k nodes at most). */
+ *   cluster_size:  2, 4, 8 or 16 CTAs per cluster, or 0 to pick by timing each on the batch
+ *                  (the instances' state is saved and restored around the trial): fewer, larger
+ *                  clusters solve each instance faster, more, smaller ones run more at once.
+ * AVIP_EINVAL if an instance solved by the shared-memory Jacobi-PCG does not fit one cluster's
+ * shared memory (it holds every vector of its instance there; about 100k nodes at most with 16
+ * CTAs); instances with an AMG hierarchy keep their vectors in global memory. */
 typedef struct avip_batch* avip_batch_t;
 int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size, avip_batch_t* out);
 /* nsteps steps of every instance; stats[count] (may be NULL) receives per-instance statistics. */

@@ -44,22 +44,15 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Steps per batch of the streamed products: 16 with FP32 values, 8 with FP64.
-template <typename T>
-struct StreamDepth {
-  static constexpr int value = 8;
-};
-
 // Down phase of level l: xp = Q b on the rows of level l (Q = omega D^-1 is diagonal: an
 // elementwise pass) and b' = Rf b on the rows of level l + 1 (a streamed product), b given by
 // `src` (complete on entry).  `hook` takes part in every row i of level l: hook.begin(i) loads
 // the row's own operands, hook.end(i, pre) runs with them (the CG update folded into the
 // finest level's phase).  The elementwise pass takes kRowBatch rows per thread at a time, their
 // loads all issued before their use; then every warp streams a contiguous share of Rf.
-template <typename T, class Src, class Hook>
+template <typename T, int U, class Src, class Hook>
 __device__ __forceinline__ void amg_down(const AmgDevT<T>* __restrict__ H, int l, Src src, Hook hook, int gwarp,
                                          int nwarps, int lane) {
-  constexpr int U = StreamDepth<T>::value;
   constexpr int kRowBatch = 4;
   const AmgLevelT<T>& L = H->L[l];
   T* __restrict__ bn = H->L[l + 1].b;
@@ -97,10 +90,9 @@ __device__ __forceinline__ void amg_down(const AmgDevT<T>* __restrict__ H, int l
 // Up phase of level l: x = U xp + Pf x' = [U | Pf] [xp; x'] on the rows of level l (x' = the
 // next level's solution, complete on entry), each row handed to out.end(i, value, pre) with the
 // operands out.begin(i) fetched ahead.
-template <typename T, class Out>
+template <typename T, int U, class Out>
 __device__ __forceinline__ void amg_up(const AmgDevT<T>* __restrict__ H, int l, Out out, int gwarp, int nwarps,
                                        int lane) {
-  constexpr int U = StreamDepth<T>::value;
   const AmgLevelT<T>& L = H->L[l];
   const T* __restrict__ xp = L.xp;
   const T* __restrict__ xn = H->L[l + 1].x;
@@ -160,7 +152,7 @@ __device__ bool amg_inner(const AmgDevT<T>* __restrict__ H, Ops& ops, int gwarp,
   const int nl = H->nlev;
   for (int l = 1; l + 1 < nl; ++l) {
     const T* __restrict__ b = H->L[l].b;
-    amg_down(H, l, [b](int c) { return __ldca(b + c); }, NoHook(), gwarp, nwarps, lane);
+    amg_down<T, Ops::kStream>(H, l, [b](int c) { return __ldca(b + c); }, NoHook(), gwarp, nwarps, lane);
     if (!ops.barrier()) return false;
   }
   {
@@ -170,7 +162,7 @@ __device__ bool amg_inner(const AmgDevT<T>* __restrict__ H, Ops& ops, int gwarp,
     if (!ops.barrier()) return false;
   }
   for (int l = nl - 2; l >= 1; --l) {
-    amg_up(H, l, StoreOut<T>{H->L[l].x}, gwarp, nwarps, lane);
+    amg_up<T, Ops::kStream>(H, l, StoreOut<T>{H->L[l].x}, gwarp, nwarps, lane);
     if (!ops.barrier()) return false;
   }
   return true;
@@ -197,10 +189,10 @@ __device__ bool vcycle(const AmgDevT<T>* __restrict__ H, const TB* __restrict__ 
   if (H->nlev == 1) {
     amg_coarse(H, src, [&](int row, T v) { out.end(row, v, out.begin(row)); }, gwarp, nwarps, lane);
   } else {
-    amg_down(H, 0, src, NoHook(), gwarp, nwarps, lane);
+    amg_down<T, Ops::kStream>(H, 0, src, NoHook(), gwarp, nwarps, lane);
     if (!ops.barrier()) return false;
     if (!amg_inner(H, ops, gwarp, nwarps, lane)) return false;
-    amg_up(H, 0, out, gwarp, nwarps, lane);
+    amg_up<T, Ops::kStream>(H, 0, out, gwarp, nwarps, lane);
   }
   if (want_dot) {
     double v[1] = {acc.value()};
@@ -282,7 +274,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
             const double* __restrict__ bv = a.b;
             double* __restrict__ rw = rc;
             T* __restrict__ tw = tc;
-            spmv_stream<double, 8>(
+            spmv_stream<double, Ops::kStream64>(
                 A0, ma, mb, lane, [xv](int c) { return __ldca(xv + c); }, [bv](int i) { return bv[i]; },
                 [&](int i, double ax, double bi) {
                   const double r = bi - ax;
@@ -349,7 +341,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
               if (i < N) hook.end(i, hook.begin(i));
             }
           } else {
-            amg_down(H, 0, [res](int c) { return (T)res(c); }, hook, gwarp, nwarps, lane);
+            amg_down<T, Ops::kStream>(H, 0, [res](int c) { return (T)res(c); }, hook, gwarp, nwarps, lane);
           }
           if (upd) {
             double v[1] = {rr};
@@ -388,7 +380,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
                        [&](int row, T v) { out.end(row, v, out.begin(row)); }, gwarp, nwarps, lane);
           } else {
             if (!amg_inner(H, ops, gwarp, nwarps, lane)) return false;
-            amg_up(H, 0, out, gwarp, nwarps, lane);
+            amg_up<T, Ops::kStream>(H, 0, out, gwarp, nwarps, lane);
           }
           rzv[0] = acc.value();
           if (!ops.sum(rzv)) return false;
@@ -415,7 +407,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
           struct PreA {
             double z, q, p;
           };
-          spmv_stream<double, 8>(
+          spmv_stream<double, Ops::kStream64>(
               A0, ma, mb, lane, [zc](int c) { return __ldca(zc + c); },
               [=](int i) { return PreA{__ldca(zc + i), qv[i], pv[i]}; },
               [&](int i, double w, const PreA& o) {
@@ -545,7 +537,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
         struct PreA {
           float z, q, p;
         };
-        spmv_stream<float, 16>(
+        spmv_stream<float, Ops::kStream>(
             A32, ma, mb, lane, [z32](int c) { return __ldca(z32 + c); },
             [=](int i) { return PreA{__ldca(z32 + i), q32[i], p32[i]}; },
             [&](int i, float w, const PreA& o) {
@@ -604,7 +596,11 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
 
 
 // Grid-wide synchronisation of a cooperative launch (counter barrier of grid_sync.cuh).
+// kStream / kStream64: steps per batch of the streamed products with FP32 / FP64 values (8 and 8
+// for the whole-GPU kernels, measured fastest with their 24 warps per SM, and for the cluster
+// solves).
 struct GridOps {
+  static constexpr int kStream = 8, kStream64 = 8;
   FlagSync& fs;
   double* smem;
   __device__ bool barrier() { return grid_barrier(fs); }
@@ -620,6 +616,7 @@ struct GridOps {
 // `part` (2 x 4 doubles), `wsum` (32 x 4 doubles) and `res` (4 doubles) are the calling CTA's
 // shared scratch.
 struct ClusterOps {
+  static constexpr int kStream = 8, kStream64 = 8;
   cooperative_groups::cluster_group cl;
   double* part;  // [2][4]: this CTA's partials, double-buffered
   double* wsum;  // [32][4]: warp partials

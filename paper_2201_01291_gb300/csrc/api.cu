@@ -1213,10 +1213,17 @@ bool batch_configure(avip_batch* b, int C) {
   size_t smem = 0;
   for (int k = 0; k < n; ++k) {
     ClusterHost hd;
-    PcgPlan p = pcg_cluster_plan_fixed(b->m[k]->hm, C, &lays[k], &hd,
-                                       b->m[k]->opts.precision == AVIP_PREC_MIXED ? 1 : 0);
-    if (p.kind == 0) return false;
-    smem = std::max(smem, (size_t)p.maxs);
+    if (b->m[k]->amg || b->m[k]->amg32) {
+      // an AMG instance keeps its vectors in global memory: no shared-memory layout to fit
+      std::memset(&lays[k], 0, sizeof(ClusterLayout));
+      hd.colL.assign(1, 0);
+      hd.push_ptr.assign(1, 0);
+    } else {
+      PcgPlan p = pcg_cluster_plan_fixed(b->m[k]->hm, C, &lays[k], &hd,
+                                         b->m[k]->opts.precision == AVIP_PREC_MIXED ? 1 : 0);
+      if (p.kind == 0) return false;
+      smem = std::max(smem, (size_t)p.maxs);
+    }
     lays[k].colL = batch_upload(b, hd.colL);
     lays[k].push_ptr = batch_upload(b, hd.push_ptr);
     std::vector<int32_t> pd = hd.push_dst;
@@ -1272,7 +1279,8 @@ cudaError_t batch_snapshot(avip_batch* b, std::vector<void*>& buf, int dir) {
 extern "C" {
 
 int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size, avip_batch_t* out) {
-  if (!meshes || count < 1 || !out || (cluster_size != 0 && cluster_size != 8 && cluster_size != 16))
+  if (!meshes || count < 1 || !out ||
+      (cluster_size != 0 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16))
     return AVIP_EINVAL;
   *out = nullptr;
   avip_batch* b = new (std::nothrow) avip_batch();
@@ -1328,7 +1336,8 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
   if (cluster_size != 0) {
     ok = batch_configure(b, cluster_size);
   } else {
-    // autotune: time two steps per feasible cluster size on the batch itself, then restore
+    // autotune: time two steps per feasible cluster size (16, 8, 4 or 2 CTAs: fewer, faster
+    // clusters or more, smaller ones) on the batch itself, then restore
     std::vector<void*> snap;
     cudaError_t e = batch_snapshot(b, snap, 0);
     float best = 0.f;
@@ -1336,7 +1345,7 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int C : {16, 8}) {
+    for (int C : {16, 8, 4, 2}) {
       if (e != cudaSuccess || !batch_configure(b, C)) continue;
       e = cudaEventRecord(e0, b->stream);
       for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = batch_enqueue_step(b);

@@ -1,14 +1,17 @@
 """Serving loop for discharge solves (continuous batching on one GPU).
 
 Requests (a discharge problem and a number of explicit steps) arrive over time.  The server
-admits a request as soon as it has arrived, a slot is free and its device-memory estimate fits
-the HBM budget still available; the request then keeps its whole state resident on the device
-(one mesh handle with its own CUDA stream) until its last step, and releases slot and memory
-when done, which admits the requests waiting behind it.  Admitted requests advance in chunks of
-steps on worker threads; the CUDA work of concurrent requests overlaps on the device (small
-meshes run on one thread-block cluster each, so many run side by side).  Requests whose
-Poisson solve uses the whole-GPU cooperative kernel run their chunks exclusively, because a
-cooperative launch must have the whole grid resident.
+admits a request as soon as it has arrived, a slot is free and its device memory fits: the
+request's estimate must fit both the server's HBM budget and the device memory free at that
+moment (cudaMemGetInfo) minus the reservations of admitted requests whose handle is not built
+yet.  The request then keeps its whole state resident on the device (one mesh handle with its
+own CUDA stream) until its last step, and releases slot and memory when done, which admits the
+requests waiting behind it.  Admitted requests advance in chunks of steps on worker threads;
+the CUDA work of concurrent requests overlaps on the device: every request of up to
+SHARED_MAX_NODES nodes solves its Poisson problem on one thread-block cluster (the Jacobi or
+AMG-preconditioned cluster solvers), so up to nine of them run side by side on the 152 SMs.
+Larger requests use the whole-GPU cooperative kernel and run their chunks exclusively, because
+a cooperative launch must have its whole grid resident.
 
 The numerics are the library's: a request gives the same result alone and in the mix.
 Latency of a request = completion time - arrival time; the report gives p50/p99 latency and
@@ -29,12 +32,26 @@ from . import avip
 # per-node vectors of the solver and of the drift-diffusion stage); used for admission.
 BYTES_PER_NODE = 1400
 BYTES_PER_TRI = 24
-CLUSTER_NODES = 20000  # meshes up to this size use the cluster-resident solver (shared slots)
+SHARED_MAX_NODES = 300000  # requests up to this size solve on one thread-block cluster (shared)
+AUTO_CLUSTER_NODES = 20000  # below this the library's automatic choice is already a cluster solver
 CLUSTER_KINDS = (5, 6, 11)  # solver kinds that occupy one thread-block cluster, not the whole GPU
+FREE_MARGIN = 512 << 20  # device memory kept free for the CUDA runtime and the caching allocator
 
 
 def estimate_bytes(problem) -> int:
     return int(problem.n_nodes * BYTES_PER_NODE + problem.n_tris * BYTES_PER_TRI) + (1 << 20)
+
+
+def solver_kind(problem) -> int:
+    """pcg_kind for a served request: the AMG solve on one cluster (11) for the mid-size meshes
+    the library would give the whole GPU, the library's choice (0) otherwise."""
+    return 11 if AUTO_CLUSTER_NODES < problem.n_nodes <= SHARED_MAX_NODES else 0
+
+
+def device_free_bytes() -> int:
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return int(free)
 
 
 @dataclasses.dataclass
@@ -86,12 +103,11 @@ class _GpuLock:
 
 class Server:
     def __init__(self, hbm_budget: Optional[int] = None, max_slots: int = 32, chunk: int = 50,
-                 rtol: float = 1e-12, keep_state: bool = True):
+                 rtol: float = 1e-12, keep_state: bool = True, free_bytes=device_free_bytes):
         if hbm_budget is None:
-            import torch
-            free, _ = torch.cuda.mem_get_info()
-            hbm_budget = int(free * 0.8)
+            hbm_budget = int(free_bytes() * 0.8)
         self.budget = hbm_budget
+        self.free_bytes = free_bytes  # live free device memory (a callable, replaceable in tests)
         self.max_slots = max_slots
         self.chunk = chunk
         self.rtol = rtol
@@ -99,9 +115,11 @@ class Server:
         self.lock = _GpuLock()
         self.admit_log: List[tuple] = []
 
-    def _work(self, req: Request, t0: float, release):
+    def _work(self, req: Request, t0: float, release, built):
+        m = None
         try:
-            m = avip.Mesh(req.problem, rtol=self.rtol)
+            m = avip.Mesh(req.problem, rtol=self.rtol, pcg_kind=solver_kind(req.problem))
+            built()  # the handle's memory is now part of what the device reports as used
             # cluster-resident solves share the GPU; whole-GPU cooperative solves run exclusively
             ex = m.info["pcg_kind"] not in CLUSTER_KINDS
             left = req.nsteps
@@ -120,6 +138,8 @@ class Server:
             m.close()
         except Exception:
             req.status = avip.AVIP_ECUDA
+            if m is None:
+                built()
         req.done = time.perf_counter() - t0
         release()
 
@@ -127,7 +147,8 @@ class Server:
         """Serve the requests (arrival times relative to now).  With realtime=False every
         request is considered arrived at t = 0 (throughput mode)."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        used = [0]
+        used = [0]       # estimates of the requests in service (the server's budget)
+        reserved = [0]   # estimates of admitted requests whose handle is not built yet
         slots = [0]
         cv = threading.Condition()
         threads = []
@@ -140,6 +161,13 @@ class Server:
                     slots[0] -= 1
                     cv.notify_all()
             return _rel
+
+        def built_for(req):
+            def _built():
+                with cv:
+                    reserved[0] -= estimate_bytes(req.problem)
+                    cv.notify_all()
+            return _built
 
         i = 0
         while i < len(pending):
@@ -158,11 +186,22 @@ class Server:
                 if slots[0] >= self.max_slots or used[0] + need > self.budget:
                     cv.wait(timeout=0.05)
                     continue
+                free = self.free_bytes() - reserved[0] - FREE_MARGIN
+                if need > free:
+                    if slots[0] == 0 and reserved[0] == 0:  # nothing of ours to wait for: never fits
+                        req.status = avip.AVIP_ENOMEM
+                        req.done = req.arrival
+                        i += 1
+                        continue
+                    cv.wait(timeout=0.05)
+                    continue
                 used[0] += need
+                reserved[0] += need
                 slots[0] += 1
                 req.admitted = time.perf_counter() - t0
-                self.admit_log.append((req.rid, req.admitted, used[0]))
-            th = threading.Thread(target=self._work, args=(req, t0, release_for(req)), daemon=True)
+                self.admit_log.append((req.rid, req.admitted, used[0], free))
+            th = threading.Thread(target=self._work, args=(req, t0, release_for(req), built_for(req)),
+                                  daemon=True)
             th.start()
             threads.append(th)
             i += 1

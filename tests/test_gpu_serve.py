@@ -53,4 +53,45 @@ def test_admission_respects_budget(mods):
     srv = serve.Server(hbm_budget=budget, max_slots=8, chunk=6, keep_state=False)
     rep = srv.run(reqs, realtime=False)
     assert rep["rejected"] == 1 and rep["completed"] == len(reqs) - 1
-    assert all(used <= budget for _, _, used in srv.admit_log)
+    assert all(used <= budget for _, _, used, _ in srv.admit_log)
+
+
+def test_admission_follows_free_device_memory(mods):
+    """With the device reporting little free memory, a request waits (it is admitted only while
+    its estimate fits what is free minus the other admitted requests' reservations) and one that
+    could never fit is rejected instead of attempted."""
+    avip, serve = mods
+    reqs = _requests(serve, n=3)
+    need = max(serve.estimate_bytes(r.problem) for r in reqs)
+    fake_free = [serve.FREE_MARGIN + need]        # room for one request at a time
+    srv = serve.Server(hbm_budget=1 << 34, max_slots=8, chunk=5, keep_state=False,
+                       free_bytes=lambda: fake_free[0])
+    rep = srv.run(reqs, realtime=False)
+    assert rep["completed"] == 3
+    assert all(free >= 0 for *_, free in srv.admit_log)
+    fake_free[0] = serve.FREE_MARGIN // 2           # nothing fits: rejected, not run
+    rep = serve.Server(hbm_budget=1 << 34, max_slots=8, chunk=5, keep_state=False,
+                       free_bytes=lambda: fake_free[0]).run(_requests(serve, n=2), realtime=False)
+    assert rep["rejected"] == 2 and rep["completed"] == 0
+
+
+def test_served_matches_oracle(mods):
+    """Three small requests served together (one above the library's automatic cluster size, so
+    it takes the served AMG cluster solve) against the FP64 oracle (norm-wise 1e-10)."""
+    import avip_oracle as O
+    avip, serve = mods
+    reqs = []
+    for k, (nx, ny) in enumerate([(21, 27), (33, 25), (151, 141)]):
+        p = W.plates_problem(nx, ny, 1e-2, 1e-2, 1.2e4 + 3e3 * k, seed=300 + k, field_dependent=True,
+                             source=W.SRC_TOWNSEND)
+        reqs.append(serve.Request(k, 0.01 * k, p, 6 + k))
+    assert serve.solver_kind(reqs[2].problem) == 11
+    rep = serve.Server(hbm_budget=1 << 30, max_slots=3, chunk=3, rtol=1e-13).run(reqs)
+    assert rep["completed"] == 3
+    for r in reqs:
+        n_ref, phi_ref, dts = O.Oracle(r.problem).run(r.nsteps)
+        N = r.problem.n_nodes
+        ns = len(r.problem.species)
+        for s_ in range(ns):
+            assert normwise(r.state[s_ * N:(s_ + 1) * N], n_ref[s_]) <= 1e-10, (r.rid, s_)
+        assert normwise(r.state[ns * N:(ns + 1) * N], phi_ref) <= 1e-10, r.rid
