@@ -226,6 +226,9 @@ NCU_DRAM_BYTES_PER_ITER = {
     # pcg_fp64_res_kernel: 300-iteration capture, L2-resident working set
     2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
                                             "launch's iterations (L2-resident working set)"),
+    # pcg_amg_kernel<768, float>: one 21-iteration solve (two-phase V-cycle, Jacobi smoother)
+    8: ((3633.821e6 + 526.636e6) / 21.0, "ncu DRAM read+write of a 21-iteration solve scaled to the launch's "
+                                         "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
 }
 
 
@@ -261,27 +264,30 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
 
     Conventions: every stored entry of an operator is read once (4 B column + sv B value; sv = 4
     for the FP32 hierarchy, 8 for FP64) and costs 2 flops; a gathered vector is read once per
-    product (as if every reuse hit a cache), an own-row vector element once per access, a
-    written one once, and each row length once (4 B).  With levels[l] = (n, nnz A, nnz P, nnz
-    Rf, nnz U, nnz Pf) and n' the next level's rows, one V-cycle moves, per non-coarsest level:
-      down  (nnz A + nnz Rf)(4 + sv) + sv (n + n + n') + 4 (n + n')   [Q b, Rf b]
-      up    (nnz U + nnz Pf)(4 + sv) + sv (n + n' + n) + 8 n           [U xp + Pf x']
-    and on the coarsest level sv (n_c^2 + 2 n_c) (dense inverse).  In the FP64 CG (kind 8) the
-    finest down phase gathers the FP64 residual and q (16 N instead of sv N) and updates x and
-    r (p, x read, x, r written: 32 N); the finest up phase reads r for r.z (8 N); w = A z reads
-    A (12 nnz), z (sv N), p, q (16 N), writes p, q (16 N), 4 N row lengths.  BiCGStab (kind 9)
-    applies two V-cycles per iteration (FP64 input and output, 8 N each instead of sv N) and its
-    phases add 24 nnz + 216 N bytes.  The mixed-precision solve (kind 10) runs the FP32 V-cycle
-    on FP32 vectors and its inner CG moves 8 B per stored entry of A and 4 B per vector element:
-    8 nnz + 60 N.  Per solve: set-up and the final true residual, 24 nnz + 100 N."""
+    product (as if every reuse hit a cache), an own-row element once per access, a written
+    element once.  With levels[l] = (n, nnz A, nnz P, nnz Rf, nnz U, nnz Pf) and n' the next
+    level's rows, one V-cycle moves, per non-coarsest level:
+      down  rf (4 + sv) + sv (4 n + n')      [Rf b gathers b; xp = Q b elementwise: b, Q's
+                                              diagonal read, xp written; b' written]
+      up    (u + pf)(4 + sv) + sv (2 n + n') [[U | Pf] [xp; x'] gathers xp and x'; x written]
+    and on the coarsest level sv (n_c^2 + 2 n_c) (dense inverse, b read, x written).  In the FP64
+    CG (kind 8) the finest down phase gathers FP32 copies of r and q (2 sv N in place of sv N for
+    b), reads r, q, x, p and writes r, x and the copy of r (32 + 16 + sv bytes per row); the finest
+    up phase reads r and writes z in FP64 (8 + 8 - sv N more); w = A z reads A (12 nnz), gathers
+    z (8 N), reads z, q, p (24 N), writes q, p and q's copy (16 + sv N).  BiCGStab (kind 9)
+    applies two V-cycles per iteration with FP64 input and output (8 - sv more per row at each
+    end) and its phases add 24 nnz + 216 N bytes.  The mixed-precision solve (kind 10) runs the
+    FP32 V-cycle on FP32 vectors and its inner CG moves 8 B per stored entry of A and 4 B per
+    vector element: 8 nnz + 60 N.  Per solve: set-up and the final true residual, 24 nnz + 100 N.
+    Flops: 2 per stored entry of every product, 2 per row and level for the smoother and sums."""
     vb, vf = 0.0, 0.0
     nl = len(levels)
     for l, (n, a, p, rf, u, pf) in enumerate(levels):
         if l + 1 < nl:
             nn = levels[l + 1][0]
-            vb += (a + rf) * (4 + sv) + sv * (2 * n + nn) + 4 * (n + nn)
-            vb += (u + pf) * (4 + sv) + sv * (2 * n + nn) + 8 * n
-            vf += 2 * (a + rf + u + pf) + n
+            vb += rf * (4 + sv) + sv * (4 * n + nn)
+            vb += (u + pf) * (4 + sv) + sv * (2 * n + nn)
+            vf += 2 * (rf + u + pf) + 2 * n
         else:
             vb += sv * (n * n + 2 * n)
             vf += 2 * n * n
@@ -292,7 +298,8 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
         per_it = vb + 8 * nnz0 + 60 * N
         fl_it = vf + 2 * nnz0 + 12 * N
     else:
-        per_it = vb + (16 - sv) * N + 32 * N + 8 * N + 12 * nnz0 + (sv + 36) * N
+        per_it = (vb + sv * N + (48 + sv) * N + (16 - sv) * N
+                  + 12 * nnz0 + 8 * N + 24 * N + (16 + sv) * N)
         fl_it = vf + 2 * nnz0 + 14 * N
     per_solve = 24 * nnz0 + 100 * N
     return iters * per_it + solves * per_solve, iters * fl_it + solves * (4 * nnz0 + 12 * N)
@@ -317,9 +324,6 @@ def run_ours(args, rank, world, local_rank):
     kw["precond_fp64"] = 1 if args.precond_fp64 else 0
     m = avip.Mesh(problem, rtol=args.rtol, stream=stream.cuda_stream, pcg_threads=args.pcg_threads,
                   pcg_kind=args.pcg_kind, precision=prec, **kw)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    with torch.cuda.stream(stream):
-        flush.fill_(-1.0)  # the first fill loads torch's fill kernel (~0.25 s): keep it out of the timing
     # roofline denominators of this device, measured now (before the timed region)
     rc64, fp64_peak = avip.peak_probe(avip.PROBE_FP64_FMA, stream.cuda_stream)
     rcbw, copy_gbs = avip.peak_probe(avip.PROBE_HBM_COPY, stream.cuda_stream)
@@ -340,18 +344,19 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        # K steps queued back to back with events around every kernel, one wait at the end; the
+        # working set moved per step (the solver's operators alone stream ~2 GB) is far larger
+        # than L2, so no step finds the previous one's data cached
         ev0.record(stream)
-        for k in range(args.steps):
-            flush.fill_(float(k))                 # evict the previous step from L2
-            ms, st = m.run_timed(1, allow=allow)
-            for key in kernel_ms:
-                kernel_ms[key] += ms[key]
-            iters += st["pcg_iters_total"]
-            # pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation
-            launches += 5 + (1 if args.precision == "fp64" else 0) + \
-                (len(problem.photo.a) + 1 if problem.photo is not None else 0)
+        ms, st = m.run_timed(args.steps, allow=allow)
         ev1.record(stream)
     torch.cuda.synchronize()
+    for key in kernel_ms:
+        kernel_ms[key] += ms[key]
+    iters += st["pcg_iters_total"]
+    # per step: pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation
+    launches += args.steps * (5 + (1 if args.precision == "fp64" else 0) +
+                              (len(problem.photo.a) + 1 if problem.photo is not None else 0))
     if world > 1:
         torch.distributed.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -430,7 +435,7 @@ def run_ours(args, rank, world, local_rank):
                            "; Krylov iterate, residuals, products with the Poisson matrix and stopping test in FP64")
         if info["pcg_kind"] in (8, 9, 11) else None,
         "parallelism": f"replicas x{world}", "nnz": info["nnz"],
-        "l2": "flushed between timed steps (256 MiB write inside the timed region)",
+        "l2": "working set per step far larger than L2 (the solver streams ~2 GB of operators per step); no flush",
         "e2e": {"value": world * T * e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes,
                 "how": "per step: state_set from host, run_steps(1), state_get to host"},

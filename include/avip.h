@@ -137,6 +137,10 @@ typedef struct avip_opts {
                                           matrix, the residuals and the stopping test stay
                                           FP64, so the solution meets rtol all the same); 1
                                           applies it in FP64 */
+  int32_t cluster_size;                /* solver kind 11 (the AMG solve on one thread-block
+                                          cluster): CTAs of its cluster, 2, 4, 8 or 16; 0 = 16
+                                          when schedulable, else 8.  Smaller clusters leave room
+                                          for more handles solving at the same time */
 } avip_opts;
 
 /* Per-run statistics filled by run_steps / dd_step. */
@@ -268,7 +272,8 @@ int dd_step(avip_mesh_t h, double dt, double* dt_used);
 int run_steps(avip_mesh_t h, int32_t nsteps, avip_stats* stats);
 
 /* Measurement variant of run_steps: the same kernels launched one by one (no graph) with CUDA
- * events recorded on the handle's stream around each of them.  kernel_ms[AVIP_TIMED_KERNELS]
+ * events recorded on the handle's stream around each of them; every step is queued before the
+ * call waits (once, for the last event).  kernel_ms[AVIP_TIMED_KERNELS]
  * receives the summed device time of {Poisson solve, nodal fields, cell time step, fluxes +
  * update, finalize, photoionisation solves + source update} over the call; `stats` (may be
  * NULL) as for run_steps. */

@@ -34,7 +34,8 @@ class AvipOpts(C.Structure):
                 ("inner_rtol", C.c_double), ("pcg_threads", C.c_int32), ("pcg_kind", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("geometry", C.c_int32), ("scheme", C.c_int32),
-                ("v_rise", C.c_double), ("wait_timeout", C.c_double), ("precond_fp64", C.c_int32)]
+                ("v_rise", C.c_double), ("wait_timeout", C.c_double), ("precond_fp64", C.c_int32),
+                ("cluster_size", C.c_int32)]
 
 
 class AvipStats(C.Structure):
@@ -377,7 +378,7 @@ class Mesh:
 
     def __init__(self, problem, precision=PREC_FP64, rtol=None, max_iter=None, dt_fixed=None,
                  reorder=1, use_torch_allocator=False, stream=None, pcg_threads=0, pcg_kind=0,
-                 wait_timeout=None, precond_fp64=0):
+                 wait_timeout=None, precond_fp64=0, cluster_size=0):
         o = avip_opts_default()
         po = problem.opts
         o.cfl, o.fourier, o.a_diel, o.a_chem = po.cfl, po.fourier, po.a_diel, po.a_chem
@@ -395,6 +396,7 @@ class Mesh:
         if wait_timeout is not None:
             o.wait_timeout = wait_timeout
         o.precond_fp64 = int(precond_fp64)
+        o.cluster_size = int(cluster_size)
         self._cb = None
         if use_torch_allocator:
             self._cb = torch_allocator()

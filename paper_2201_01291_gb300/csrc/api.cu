@@ -509,6 +509,8 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
     avip_opts_default(&h->opts);
   if ((h->opts.alloc == nullptr) != (h->opts.free == nullptr) || !(h->opts.rtol > 0) || h->opts.max_iter < 1 ||
       !(h->opts.v_rise >= 0) || !std::isfinite(h->opts.v_rise) || !wait_timeout_ok(h->opts.wait_timeout) ||
+      (h->opts.cluster_size != 0 && h->opts.cluster_size != 2 && h->opts.cluster_size != 4 &&
+       h->opts.cluster_size != 8 && h->opts.cluster_size != 16) ||
       (h->opts.scheme != AVIP_FLUX_LLW && h->opts.scheme != AVIP_FLUX_SG) ||
       (h->opts.precision != AVIP_PREC_FP64 && h->opts.precision != AVIP_PREC_MIXED) ||
       (h->opts.precision == AVIP_PREC_MIXED && !(h->opts.inner_rtol > 0 && h->opts.inner_rtol < 1))) {
@@ -643,7 +645,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   // mid-size planar meshes (or kind 11 forced): the AMG-preconditioned solve on one cluster
   if (!bicg && (h->opts.pcg_kind == 11 ||
                 (h->opts.pcg_kind == 0 && m.N > kClusterAmgMinRows && m.N <= kClusterAutoRows))) {
-    const PcgPlan cp = amg_cluster_plan();
+    const PcgPlan cp = amg_cluster_plan(h->opts.cluster_size);
     if (cp.kind == 11) {
       AmgHost H;
       int rc = amg_setup(m, H, g_err, sizeof(g_err));
@@ -979,7 +981,9 @@ int dd_step(avip_mesh_t h, double dt, double* dt_used) {
 
 int run_steps(avip_mesh_t h, int32_t nsteps, avip_stats* stats) { return run_impl(h, nsteps, 0.0, stats, true); }
 
-// Eager launches with CUDA events around every kernel on the handle's stream.
+// Eager launches with CUDA events around every kernel on the handle's stream: all steps are
+// queued first (the events of each step in their own slots), the call then waits once for the
+// last event and adds up the intervals, so the device runs the steps back to back.
 int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats* stats) {
   if (!ready(h)) return h ? AVIP_ESTATE : AVIP_EINVAL;
   if (nsteps < 0 || !kernel_ms) return AVIP_EINVAL;
@@ -987,46 +991,52 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
   DevScalars s0;
   int rc = read_scalars(h, s0);
   if (rc) return rc;
-  cudaEvent_t ev[6], evp[2];
-  for (auto& e : ev) cudaEventCreate(&e);
-  for (auto& e : evp) cudaEventCreate(&e);
-  cudaError_t e = launch_run_reset(h->sc, h->stream);
+  constexpr int kEv = 8;  // per step: 6 boundaries of the timed stages, 2 around photoionisation
+  std::vector<cudaEvent_t> ev((size_t)nsteps * kEv, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  if (e == cudaSuccess) e = launch_run_reset(h->sc, h->stream);
   const bool auto_dt = !(h->ph.dt_fixed > 0.0);
+  const bool photo = h->ph.photo_terms > 0;
   for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
     NvtxRange r("avip.step_timed");
+    cudaEvent_t* E = ev.data() + (size_t)step * kEv;
     DDArgs a = dd_args(h);
     e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[0], h->stream);
     if (e == cudaSuccess) e = enqueue_pcg_only(h);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-    const bool photo = h->ph.photo_terms > 0;
+    if (e == cudaSuccess) e = cudaEventRecord(E[1], h->stream);
     if (e == cudaSuccess) e = launch_node_fields(a, auto_dt && !photo ? 1 : 0, h->stream);
     // the photoionisation solves and source update are timed on their own
-    if (e == cudaSuccess && photo) e = cudaEventRecord(evp[0], h->stream);
+    if (e == cudaSuccess && photo) e = cudaEventRecord(E[6], h->stream);
     if (e == cudaSuccess && photo) e = enqueue_photo(h, a, auto_dt);
-    if (e == cudaSuccess && photo) e = cudaEventRecord(evp[1], h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess && photo) e = cudaEventRecord(E[7], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[2], h->stream);
     if (e == cudaSuccess && auto_dt) e = launch_dt_cells(a, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[3], h->stream);
     if (e == cudaSuccess) e = launch_flux_update(a, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(E[4], h->stream);
     if (e == cudaSuccess) e = launch_finalize(h->sc, h->qpart, h->nparts, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[5], h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[5]);
+    if (e == cudaSuccess) e = cudaEventRecord(E[5], h->stream);
+  }
+  if (e == cudaSuccess && nsteps > 0) e = cudaEventSynchronize(ev[(size_t)(nsteps - 1) * kEv + 5]);
+  for (int32_t step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    cudaEvent_t* E = ev.data() + (size_t)step * kEv;
     for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      e = cudaEventElapsedTime(&ms, E[k], E[k + 1]);
       kernel_ms[k] += ms;
     }
-    if (e == cudaSuccess && h->ph.photo_terms > 0) {
+    if (e == cudaSuccess && photo) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, evp[0], evp[1]);
+      e = cudaEventElapsedTime(&ms, E[6], E[7]);
       kernel_ms[5] += ms;
       kernel_ms[1] -= ms;
     }
   }
-  for (auto& x : ev) cudaEventDestroy(x);
-  for (auto& x : evp) cudaEventDestroy(x);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
   if (e != cudaSuccess) return cuda_status(e);
   DevScalars sc;
   rc = read_scalars(h, sc);

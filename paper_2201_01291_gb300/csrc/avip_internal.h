@@ -286,7 +286,7 @@ PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
 PcgPlan amg_plan(int nslices, int requested_tpb, int kind, int fp64);  // kind 8 (CG), 9 (BiCGStab), 10 (mixed)
-PcgPlan amg_cluster_plan();  // kind 11 (one cluster; kind 0 if no cluster size is schedulable)
+PcgPlan amg_cluster_plan(int want);  // kind 11 (one cluster of `want` CTAs or 16 / 8; kind 0 if none fits)
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

@@ -770,12 +770,14 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_amg_cluster_kernel(PcgArgs
     cluster_amg_solve(a, s_amg_part, s_amg_wsum);
 }
 
-// Largest schedulable cluster (16 or 8 CTAs) for the standalone AMG cluster kernel; 0 if none.
-PcgPlan amg_cluster_plan() {
+// Cluster of the standalone AMG cluster kernel: `want` CTAs (2, 4, 8 or 16) when schedulable,
+// else the largest schedulable of 16 and 8 (want = 0: 16, else 8); kind 0 if none.
+PcgPlan amg_cluster_plan(int want) {
   PcgPlan pl;
   pl.kind = 0;
   cudaFuncSetAttribute(pcg_amg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  for (int c : {16, 8}) {
+  for (int c : {want, 16, 8}) {
+    if (c <= 0) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);
     cfg.blockDim = dim3(kClusterTPB);

@@ -9,7 +9,8 @@ own CUDA stream) until its last step, and releases slot and memory when done, wh
 requests waiting behind it.  Admitted requests advance in chunks of steps on worker threads;
 the CUDA work of concurrent requests overlaps on the device: every request of up to
 SHARED_MAX_NODES nodes solves its Poisson problem on one thread-block cluster (the Jacobi or
-AMG-preconditioned cluster solvers), so up to nine of them run side by side on the 152 SMs.
+AMG-preconditioned cluster solvers, 16 CTAs for the AMG ones), so up to nine of them run side by
+side on the 152 SMs.
 Larger requests use the whole-GPU cooperative kernel and run their chunks exclusively, because
 a cooperative launch must have its whole grid resident.
 
@@ -36,6 +37,10 @@ SHARED_MAX_NODES = 300000  # requests up to this size solve on one thread-block 
 AUTO_CLUSTER_NODES = 20000  # below this the library's automatic choice is already a cluster solver
 CLUSTER_KINDS = (5, 6, 11)  # solver kinds that occupy one thread-block cluster, not the whole GPU
 FREE_MARGIN = 512 << 20  # device memory kept free for the CUDA runtime and the caching allocator
+# CTAs of a served request's cluster, by size.  On the 100-request sample of the served
+# benchmark, 16 CTAs for every shared request gave 2.40e8 cell-steps/s; 4 CTAs for all 9.3e7,
+# 4 / 8 / 16 by size 1.80e8 (small clusters make the large requests the tail of the makespan).
+CLUSTER_CTAS_BY_NODES = ((SHARED_MAX_NODES, 16),)
 
 
 def estimate_bytes(problem) -> int:
@@ -46,6 +51,15 @@ def solver_kind(problem) -> int:
     """pcg_kind for a served request: the AMG solve on one cluster (11) for the mid-size meshes
     the library would give the whole GPU, the library's choice (0) otherwise."""
     return 11 if AUTO_CLUSTER_NODES < problem.n_nodes <= SHARED_MAX_NODES else 0
+
+
+def cluster_ctas(problem) -> int:
+    """CTAs of the cluster a served request solves on (see CLUSTER_CTAS_BY_NODES); 0 = the
+    library's choice."""
+    for max_nodes, ctas in CLUSTER_CTAS_BY_NODES:
+        if problem.n_nodes <= max_nodes:
+            return ctas
+    return 0
 
 
 def device_free_bytes() -> int:
@@ -103,11 +117,13 @@ class _GpuLock:
 
 class Server:
     def __init__(self, hbm_budget: Optional[int] = None, max_slots: int = 32, chunk: int = 50,
-                 rtol: float = 1e-12, keep_state: bool = True, free_bytes=device_free_bytes):
+                 rtol: float = 1e-12, keep_state: bool = True, free_bytes=device_free_bytes,
+                 cluster_size=cluster_ctas):
         if hbm_budget is None:
             hbm_budget = int(free_bytes() * 0.8)
         self.budget = hbm_budget
         self.free_bytes = free_bytes  # live free device memory (a callable, replaceable in tests)
+        self.cluster_size = cluster_size  # request -> CTAs of its cluster (a callable)
         self.max_slots = max_slots
         self.chunk = chunk
         self.rtol = rtol
@@ -118,7 +134,8 @@ class Server:
     def _work(self, req: Request, t0: float, release, built):
         m = None
         try:
-            m = avip.Mesh(req.problem, rtol=self.rtol, pcg_kind=solver_kind(req.problem))
+            m = avip.Mesh(req.problem, rtol=self.rtol, pcg_kind=solver_kind(req.problem),
+                          cluster_size=self.cluster_size(req.problem))
             built()  # the handle's memory is now part of what the device reports as used
             # cluster-resident solves share the GPU; whole-GPU cooperative solves run exclusively
             ex = m.info["pcg_kind"] not in CLUSTER_KINDS

@@ -72,6 +72,9 @@ def test_mesh_validation_on_host(lib):
         o3.wait_timeout = bad_limit
         assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o3)[0] == avip.AVIP_EINVAL
     assert avip.mesh_set_wait_timeout(None, 1.0) == avip.AVIP_EINVAL
+    o4 = avip.avip_opts_default()
+    o4.cluster_size = 3  # 2, 4, 8, 16 or 0 only
+    assert avip.mesh_create(p.xy, p.tris, p.node_bc, p.phi_D, o4)[0] == avip.AVIP_EINVAL
 
 
 def test_axisymmetric_validation_on_host(lib):

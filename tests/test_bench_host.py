@@ -36,12 +36,13 @@ def test_traffic_models_match_their_formulas():
     assert b == it * (12 * nnz + 24 * N) + solves * (24 * nnz + 80 * N)
     assert f == it * (2 * nnz + 12 * N) + solves * (4 * nnz + 12 * N)
     # two smoothed levels and a dense coarsest level of 20 rows: (n, A, P, Rf, U, Pf)
-    levels = [(N, nnz, 3000, 9000, 19000, 9500), (150, 1200, 400, 1300, 3000, 1400), (20, 300, 0, 0, 0, 0)]
+    levels = [(N, nnz, 3000, 9000, 7000, 9500), (150, 1200, 400, 1300, 1200, 1400), (20, 300, 0, 0, 0, 0)]
     b8, f8 = bench.amg_traffic_model(levels, nnz, N, it, solves, kind=8, sv=4)
-    vb = ((nnz + 9000) * 8 + 4 * (2 * N + 150) + 4 * (N + 150)) + ((19000 + 9500) * 8 + 4 * (2 * N + 150) + 8 * N) \
-        + ((1200 + 1300) * 8 + 4 * (2 * 150 + 20) + 4 * (150 + 20)) + ((3000 + 1400) * 8 + 4 * (2 * 150 + 20) + 8 * 150) \
+    vb = (9000 * 8 + 4 * (4 * N + 150)) + ((7000 + 9500) * 8 + 4 * (2 * N + 150)) \
+        + (1300 * 8 + 4 * (4 * 150 + 20)) + ((1200 + 1400) * 8 + 4 * (2 * 150 + 20)) \
         + 4 * (20 * 20 + 2 * 20)
-    per_it = vb + 12 * N + 32 * N + 8 * N + 12 * nnz + 40 * N
+    # finest down: + 4 N (second gathered copy) + 52 N (hook); up: + 12 N; w = A z: 12 nnz + 52 N
+    per_it = vb + 4 * N + 52 * N + 12 * N + 12 * nnz + 8 * N + 24 * N + 20 * N
     assert b8 == it * per_it + solves * (24 * nnz + 100 * N)
-    vf = 2 * (nnz + 9000 + 19000 + 9500) + N + 2 * (1200 + 1300 + 3000 + 1400) + 150 + 2 * 20 * 20
+    vf = 2 * (9000 + 7000 + 9500) + 2 * N + 2 * (1300 + 1200 + 1400) + 2 * 150 + 2 * 20 * 20
     assert f8 == it * (vf + 2 * nnz + 14 * N) + solves * (4 * nnz + 12 * N)

@@ -175,3 +175,24 @@ def test_predictor_cuts_iterations_and_resumes_bitwise(avip):
     np.testing.assert_array_equal(resumed.state(), m.state())
     for x in (m, cold, resumed):
         x.close()
+
+
+@pytest.mark.parametrize("csize", [2, 4, 8, 16])
+def test_amg_cluster_solve_every_cluster_size(avip, csize):
+    """The AMG solve on one thread-block cluster (kind 11) with 2, 4, 8 and 16 CTAs: the same
+    potential as the oracle's direct solve (1e-12 at rtol 1e-14) and, after 8 steps, the same
+    densities as the whole-GPU AMG solve (1e-11: both converge to rtol 1e-14)."""
+    p = W.plates_problem(97, 113, 1e-2, 1.2e-2, 1.5e4, seed=61, field_dependent=True, source=W.SRC_TOWNSEND)
+    o = O.Oracle(p)
+    phi_ref = o.poisson(o.initial_state())
+    m = avip.Mesh(p, rtol=1e-14, pcg_kind=11, cluster_size=csize)
+    assert m.info["pcg_kind"] == 11 and m.info["pcg_blocks"] == csize
+    m.poisson_solve()
+    assert normwise(m.phi(), phi_ref) <= 1e-12
+    g = avip.Mesh(p, rtol=1e-14, pcg_kind=8)
+    m.run(8)
+    g.run(8)
+    for s in range(2):
+        assert normwise(m.density(s), g.density(s)) <= 1e-11
+    m.close()
+    g.close()
