@@ -279,7 +279,9 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
     end) and its phases add 24 nnz + 216 N bytes.  The mixed-precision solve (kind 10) runs the
     FP32 V-cycle on FP32 vectors and its inner CG moves 8 B per stored entry of A and 4 B per
     vector element: 8 nnz + 60 N.  Per solve: set-up and the final true residual, 24 nnz + 100 N.
-    Flops: 2 per stored entry of every product, 2 per row and level for the smoother and sums."""
+    Flops (returned: FP64 operations only, the unit the FP64 roofline compares): 2 per stored
+    entry of every FP64 product and per-row vector operations; the V-cycle's own 2 per stored
+    entry and 2 per row and level count only with an FP64 hierarchy (sv = 8)."""
     vb, vf = 0.0, 0.0
     nl = len(levels)
     for l, (n, a, p, rf, u, pf) in enumerate(levels):
@@ -291,12 +293,14 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
         else:
             vb += sv * (n * n + 2 * n)
             vf += 2 * n * n
+    if sv != 8:
+        vf = 0.0  # the V-cycle runs in FP32
     if kind == 9:
         per_it = 2 * (vb + 2 * (8 - sv) * N) + 24 * nnz0 + 216 * N
         fl_it = 2 * vf + 4 * nnz0 + 32 * N
     elif kind == 10:
         per_it = vb + 8 * nnz0 + 60 * N
-        fl_it = vf + 2 * nnz0 + 12 * N
+        fl_it = 0.0  # FP32 inner solve; the few FP64 outer residuals are counted per solve
     else:
         per_it = (vb + sv * N + (48 + sv) * N + (16 - sv) * N
                   + 12 * nnz0 + 8 * N + 24 * N + (16 + sv) * N)

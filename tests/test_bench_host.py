@@ -44,5 +44,8 @@ def test_traffic_models_match_their_formulas():
     # finest down: + 4 N (second gathered copy) + 52 N (hook); up: + 12 N; w = A z: 12 nnz + 52 N
     per_it = vb + 4 * N + 52 * N + 12 * N + 12 * nnz + 8 * N + 24 * N + 20 * N
     assert b8 == it * per_it + solves * (24 * nnz + 100 * N)
+    # FP32 hierarchy: only the CG's FP64 work counts as FP64 flops
+    assert f8 == it * (2 * nnz + 14 * N) + solves * (4 * nnz + 12 * N)
+    b64, f64 = bench.amg_traffic_model(levels, nnz, N, it, solves, kind=8, sv=8)
     vf = 2 * (9000 + 7000 + 9500) + 2 * N + 2 * (1300 + 1200 + 1400) + 2 * 150 + 2 * 20 * 20
-    assert f8 == it * (vf + 2 * nnz + 14 * N) + solves * (4 * nnz + 12 * N)
+    assert f64 == it * (vf + 2 * nnz + 14 * N) + solves * (4 * nnz + 12 * N)
