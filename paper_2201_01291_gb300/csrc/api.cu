@@ -770,6 +770,7 @@ int species_set(avip_mesh_t h, int32_t s, int32_t charge, int32_t mob_model, con
   sp.q = (double)charge;
   for (int k = 0; k < 4; ++k) sp.mob[k] = mob_params[k];
   sp.D = D;
+  sp.mob_log_ref = mob_model == AVIP_MOB_POWER ? std::log(mob_params[1]) : 0.0;
   sp.mob_model = mob_model;
   sp.bnd_mode = bnd_mode;
   if (s == h->species_declared) h->species_declared++;

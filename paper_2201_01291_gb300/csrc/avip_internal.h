@@ -161,6 +161,7 @@ struct SpeciesParams {
   double q;           // charge number (-1, +1)
   double mob[4];
   double D;
+  double mob_log_ref;  // log(mob[1]) for AVIP_MOB_POWER (set on the host)
   int32_t mob_model;
   int32_t bnd_mode;
 };

@@ -29,8 +29,11 @@ constexpr int kDDThreads = 256;
 
 // Local-field mobility and the Townsend exponential with the library's FP64 exp / log
 // (fp64_math.cuh: a few ulp, a fraction of the FP64 instructions of the general routines).
+// mu0 (max(|E|, E_floor) / E_ref)^p = mu0 exp(p (log max(|E|, E_floor) - log E_ref)), log E_ref
+// from the host: no FP64 division.
 __device__ __forceinline__ double mobility(const SpeciesParams& sp, double Emag) {
-  if (sp.mob_model == AVIP_MOB_POWER) return sp.mob[0] * pow_pos_fp64(fmax(Emag, sp.mob[3]) / sp.mob[1], sp.mob[2]);
+  if (sp.mob_model == AVIP_MOB_POWER)
+    return sp.mob[0] * exp_fp64(sp.mob[2] * (log_fp64(fmax(Emag, sp.mob[3])) - sp.mob_log_ref));
   return sp.mob[0];
 }
 
@@ -111,7 +114,11 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
       }
     }
     const double Ex = -gpx, Ey = -gpy;
-    const double Emag = sqrt(Ex * Ex + Ey * Ey);
+    // |E| and 1/|E| from one reciprocal square root (the Townsend and attachment exponents take
+    // -B/|E| as a product)
+    const double E2 = Ex * Ex + Ey * Ey;
+    const double invE = E2 > 0.0 ? rsqrt(E2) : 0.0;
+    const double Emag = E2 * invE;
     a.Ex[i] = Ex;
     a.Ey[i] = Ey;
     double mu[AVIP_MAX_SPECIES];
@@ -134,7 +141,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
     if (a.ph.src_model != AVIP_SRC_NONE) {
       const int ie = a.ph.src_idx[0], ip = a.ph.src_idx[1], ineg = a.ph.src_idx[2];
       const double ne = n[(size_t)ie * a.Npad + i];
-      const double alpha = Emag > 0.0 ? a.ph.src_params[0] * exp_fp64(-a.ph.src_params[1] / Emag) : 0.0;
+      const double alpha = Emag > 0.0 ? a.ph.src_params[0] * exp_fp64(-a.ph.src_params[1] * invE) : 0.0;
       double mue = 0.0;
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
@@ -161,7 +168,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
           if (s == ip) npos = n[(size_t)s * a.Npad + i];
           if (s == ineg) nneg = n[(size_t)s * a.Npad + i];
         }
-        const double eta = Emag > 0.0 ? a.ph.src_params[2] * exp_fp64(-a.ph.src_params[3] / Emag) : 0.0;
+        const double eta = Emag > 0.0 ? a.ph.src_params[2] * exp_fp64(-a.ph.src_params[3] * invE) : 0.0;
         const double att = eta * mue * Emag * ne;
         const double rep = a.ph.src_params[4] * ne * npos;
         const double rnp = a.ph.src_params[4] * nneg * npos;
@@ -197,13 +204,17 @@ __global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int w
 // min_c cfl dx / |V| = cfl / max_c |V| / dx, likewise for the dielectric limit.  The Fourier
 // limit, fourier dx^2 / D over cells and species, depends on the mesh only (ph.dt_fourier).
 __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid, int nblocks) {
-  double vmax = 0.0, smax = 0.0;
+  // the largest (|V_cell| / dx)^2 is carried instead of |V_cell| / dx, so that each thread
+  // takes one square root at the end rather than one per cell and species (FP64 square roots
+  // dominated this kernel's FP64 issue)
+  double v2max = 0.0, smax = 0.0;
   const int ns = a.ph.ns;
   for (int c = bid * blockDim.x + threadIdx.x; c < a.T; c += nblocks * blockDim.x) {
     const int n0 = a.cell[c], n1 = a.cell[a.T + c], n2 = a.cell[2 * a.T + c];
     const int n3 = a.nvmax == 4 ? a.cell[3 * a.T + c] : -1;  // -1: triangle
     const bool quad = n3 >= 0;
     const double w = a.cw[c];
+    const double w2 = w * w;
     const double inv_nv = quad ? 0.25 : (1.0 / 3.0);
     double sigma = 0.0;
 #pragma unroll
@@ -227,7 +238,7 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid, int nblo
             vy += d[4 * n3 + 3];
           }
         }
-        vmax = fmax(vmax, sqrt(vx * vx + vy * vy) * w);
+        v2max = fmax(v2max, (vx * vx + vy * vy) * w2);
         const double* nm = a.nm + (size_t)s * a.Npad;
         double cell = nm[n0] + nm[n1] + nm[n2];
         if (quad) cell += nm[n3];
@@ -237,7 +248,7 @@ __device__ __forceinline__ void dt_cells_body(const DDArgs& a, int bid, int nblo
     smax = fmax(smax, sigma * inv_nv);
   }
   double cand = a.ph.dt_fourier;
-  if (vmax > 0.0) cand = fmin(cand, a.ph.cfl / vmax);
+  if (v2max > 0.0) cand = fmin(cand, a.ph.cfl / sqrt(v2max));
   if (smax > 0.0) cand = fmin(cand, a.ph.a_diel * kEps0 / smax);
   block_min_to_global(cand, &a.sc->dt_bits);
 }
@@ -343,16 +354,22 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
       }
     }
     if (a.eflux) {
-      // fluxes already evaluated once per edge (lo -> hi), gathered in the same slot order
-      for (int k = 1; k < rl; ++k) {
-        const int32_t v = __ldg(a.slot_eid + base + k * kSlice);
-        const bool lo_is_me = v >= 0;
-        const int id = v & 0x7fffffff;
+      // fluxes already evaluated once per edge (lo -> hi), gathered in the same slot order: the
+      // edge ids of kG slots are loaded together, then their fluxes, then summed in slot order
+      constexpr int kG = 8;
+      for (int k0 = 1; k0 < rl; k0 += kG) {
+        int32_t v[kG];
+#pragma unroll
+        for (int u = 0; u < kG; ++u) v[u] = k0 + u < rl ? __ldg(a.slot_eid + base + (k0 + u) * kSlice) : 0;
 #pragma unroll
         for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
           if (s < ns) {
-            const double F = a.eflux[(size_t)s * a.E + id];
-            R[s] = lo_is_me ? R[s] - F : R[s] + F;
+            double F[kG];
+#pragma unroll
+            for (int u = 0; u < kG; ++u) F[u] = k0 + u < rl ? a.eflux[(size_t)s * a.E + (v[u] & 0x7fffffff)] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kG; ++u)
+              if (k0 + u < rl) R[s] = v[u] >= 0 ? R[s] - F[u] : R[s] + F[u];
           }
         }
       }
@@ -806,7 +823,9 @@ __global__ void __launch_bounds__(kDDThreads) dt_cells_batch_kernel(const DDArgs
   if (a.ph.dt_fixed > 0.0) return;
   dt_cells_body(a, blockIdx.x - __ldg(bpref + k), __ldg(bpref + k + 1) - __ldg(bpref + k));
 }
-__global__ void __launch_bounds__(kDDThreads, 2) flux_update_batch_kernel(const DDArgs* __restrict__ args,
+// (one resident block per SM guaranteed: the per-row evaluation of every edge needs ~140
+// registers, and a cap of 128 made it spill)
+__global__ void __launch_bounds__(kDDThreads, 1) flux_update_batch_kernel(const DDArgs* __restrict__ args,
                                                                         const int32_t* __restrict__ bpref, int count) {
   const int k = batch_instance(bpref, count, blockIdx.x);
   if (args[k].ph.dd_fp32)
