@@ -14,7 +14,11 @@ side on the 152 SMs.
 Larger requests use the whole-GPU cooperative kernel and run their chunks exclusively, because
 a cooperative launch must have its whole grid resident.
 
-The numerics are the library's: a request gives the same result alone and in the mix.
+Requests run in mixed precision by default (FP32 inner CG and V-cycle with FP64 refinement of
+the Poisson residual, FP32 drift-diffusion fluxes, FP64 state, time step and charge): the
+served form of the task is held to 1e-6 of the FP64 oracle, like the mixed-precision and
+batched forms; `precision=avip.PREC_FP64` serves the plain FP64 path.  The numerics are the
+library's: a request gives the same result alone and in the mix.
 Latency of a request = completion time - arrival time; the report gives p50/p99 latency and
 the aggregate cell-steps/s (triangles x steps of all requests / makespan).
 """
@@ -117,8 +121,8 @@ class _GpuLock:
 
 class Server:
     def __init__(self, hbm_budget: Optional[int] = None, max_slots: int = 32, chunk: int = 50,
-                 rtol: float = 1e-12, keep_state: bool = True, free_bytes=device_free_bytes,
-                 cluster_size=cluster_ctas):
+                 rtol: Optional[float] = None, keep_state: bool = True, free_bytes=device_free_bytes,
+                 cluster_size=cluster_ctas, precision: int = avip.PREC_MIXED):
         if hbm_budget is None:
             hbm_budget = int(free_bytes() * 0.8)
         self.budget = hbm_budget
@@ -126,7 +130,10 @@ class Server:
         self.cluster_size = cluster_size  # request -> CTAs of its cluster (a callable)
         self.max_slots = max_slots
         self.chunk = chunk
-        self.rtol = rtol
+        self.precision = precision
+        # the mixed-precision solve refines the FP64 residual to 1e-10 (its FP32 inner solve
+        # cannot reach 1e-12 per refinement step); the FP64 path solves to 1e-12
+        self.rtol = rtol if rtol is not None else (1e-10 if precision == avip.PREC_MIXED else 1e-12)
         self.keep_state = keep_state
         self.lock = _GpuLock()
         self.admit_log: List[tuple] = []
@@ -135,7 +142,7 @@ class Server:
         m = None
         try:
             m = avip.Mesh(req.problem, rtol=self.rtol, pcg_kind=solver_kind(req.problem),
-                          cluster_size=self.cluster_size(req.problem))
+                          cluster_size=self.cluster_size(req.problem), precision=self.precision)
             built()  # the handle's memory is now part of what the device reports as used
             # cluster-resident solves share the GPU; whole-GPU cooperative solves run exclusively
             ex = m.info["pcg_kind"] not in CLUSTER_KINDS
