@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=256, help="batch256: number of instances")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests in the sample")
     ap.add_argument("--req-steps", type=int, nargs=2, default=[20, 60], help="served: step-count range")
+    ap.add_argument("--served-fp64", action="store_true", help="served: serve on the FP64 path (default mixed)")
     ap.add_argument("--rtol", type=float, default=1e-12)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed = FP32 inner PCG with FP64 refinement of the Poisson residual")
@@ -358,9 +359,11 @@ def run_ours(args, rank, world, local_rank):
     for key in kernel_ms:
         kernel_ms[key] += ms[key]
     iters += st["pcg_iters_total"]
-    # per step: pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation
-    launches += args.steps * (5 + (1 if args.precision == "fp64" else 0) +
-                              (len(problem.photo.a) + 1 if problem.photo is not None else 0))
+    photo = m.photo_stats() if problem.photo is not None else None
+    # per step: pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation:
+    # the solves (one launch side by side, else one per term) and the source update
+    n_photo = 0 if photo is None else (1 if photo["side_by_side"] else len(problem.photo.a)) + 1
+    launches += args.steps * (5 + (1 if args.precision == "fp64" else 0) + n_photo)
     if world > 1:
         torch.distributed.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -447,6 +450,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "clocks": clocks,
     }
+    if photo is not None:
+        out["photoionisation"] = {"solves": "side by side in one launch" if photo["side_by_side"] else "one by one",
+                                  "iters_last_step": photo["iters"],
+                                  "ms_per_step": round(kernel_ms["photo"] / args.steps, 4)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], ref = cpu_baseline(problem, args.cpu_steps)
         n_gpu, phi_gpu = check
@@ -554,11 +561,13 @@ def run_served(args, rank, world, local_rank):
     reqs = serve.poisson_requests(args.requests, 50.0, seed=5 + 1000 * rank, steps_min=lo, steps_max=hi)
     # warm-up: compile paths, first-touch
     warm = serve.poisson_requests(2, 50.0, seed=999, t_max=2e4, steps_min=5, steps_max=5)
-    serve.Server(keep_state=False).run(warm, realtime=False)
+    serve.Server(keep_state=False, precision=avip.PREC_FP64 if args.served_fp64 else avip.PREC_MIXED).run(
+        warm, realtime=False)
     sampler = ClockSampler(local_rank) if rank == 0 and not args.no_clocks else None
     if sampler:
         sampler.start()
-    srv = serve.Server(chunk=25, keep_state=False)
+    prec = avip.PREC_FP64 if args.served_fp64 else avip.PREC_MIXED
+    srv = serve.Server(chunk=25, keep_state=False, precision=prec)
     served = srv.run(reqs)
     clocks = sampler.stop() if sampler else None
     seq_reqs = serve.poisson_requests(args.requests, 50.0, seed=5 + 1000 * rank, steps_min=lo, steps_max=hi)
@@ -569,11 +578,13 @@ def run_served(args, rank, world, local_rank):
     return {
         "metric": METRIC, "value": served["cell_steps_per_s"] * world, "unit": UNIT, "n_gpus": world,
         "steps": sum(r.nsteps for r in reqs), "warmup": 1, "ms_per_step": None,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.served_fp64 else "f32+f64", "data": "synthetic",
         "config": {"workload": f"served: {args.requests} Poisson arrivals at 50 req/s, triangles lognormal "
                                f"(median 1e5, clipped to [5e3, 2e6]; this sample {T} in total), 5-25 kV, "
-                               f"steps uniform in [{lo}, {hi}], mixed precision",
-                   "requests": args.requests, "precision": "mixed (FP32 solve and fluxes, FP64 refinement "
+                               f"steps uniform in [{lo}, {hi}], " + ("FP64" if args.served_fp64 else "mixed precision"),
+                   "requests": args.requests,
+                   "precision": "fp64" if args.served_fp64 else "mixed (FP32 solve and fluxes, FP64 refinement "
                    "and state)", "parallelism": f"replicas x{world}"},
         "served": served, "sequential_fp64": seq,
         "p50_latency_s": served["p50_latency_s"], "p99_latency_s": served["p99_latency_s"],

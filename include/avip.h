@@ -243,7 +243,8 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
  *     zero normal derivative on the other boundaries,
  * are solved (vertex-centred: (K + kappa_j^2 V) S_j = a_j c V I_ion with the Poisson matrix K and
  * the dual volumes V) by the handle's own solver kind with the term's own diagonal scaling and,
- * for the AMG kinds, its own hierarchy (built here, once), started from the quadratic
+ * for the AMG kinds, its own hierarchy (built here, once; with the whole-GPU AMG kinds the
+ * terms are solved side by side in one launch, see photo_stats), started from the quadratic
  * extrapolation of its last three solutions; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
  * source_set) before the time step and the update, and enters the chemical time-step limit.
  *   a[n_terms]     A_j p_O2^2 (1/m^2)  — with A_j, lambda_j the coefficients of the fit;
@@ -255,6 +256,14 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
  * handle with photoionisation cannot join a batch.  The solves' iteration counts are not part
  * of avip_stats (those count the Poisson solves); a solve that fails sets the run status. */
 int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kappa, double c);
+
+/* The photoionisation solves of the last step (waits for the handle's stream): *n_terms the
+ * number of terms (0 without photo_set); per term j, iters[j] its iterations and relres[j] its
+ * final true relative residual (arrays of AVIP_MAX_PHOTO_TERMS entries, either may be NULL);
+ * *side_by_side 1 when the terms are solved at the same time in one launch, each on its own
+ * share of the grid (the whole-GPU AMG solver kinds 8 and 9), 0 when one after another.
+ * AVIP_EINVAL for a NULL handle, n_terms or side_by_side. */
+int photo_stats(avip_mesh_t h, int32_t* n_terms, int32_t* iters, double* relres, int32_t* side_by_side);
 
 /* Solve the Poisson problem for the current densities, starting from the quadratic
  * extrapolation of the last potentials (the last one alone after mesh_create or a state with

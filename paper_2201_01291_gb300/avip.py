@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libavip.so")
 AVIP_OK, AVIP_EINVAL, AVIP_ENOMEM, AVIP_ENOTCONV, AVIP_ENAN, AVIP_ECUDA, AVIP_ETIMEOUT, AVIP_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 FIELD_PHI, FIELD_EX, FIELD_EY, FIELD_DENSITY, FIELD_VOLUME, FIELD_PHOTO = 0, 1, 2, 3, 4, 5
+MAX_PHOTO_TERMS = 3
 PREC_FP64, PREC_MIXED = 0, 1
 GEOM_PLANAR, GEOM_AXISYMMETRIC = 0, 1
 FLUX_LLW, FLUX_SG = 0, 1
@@ -73,6 +74,7 @@ _SIGS = {
     "species_set": (C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, _D, C.c_double, C.c_int32, _D]),
     "source_set": (C.c_int, [_H, C.c_int32, _D, _I]),
     "photo_set": (C.c_int, [_H, C.c_int32, _D, _D, C.c_double]),
+    "photo_stats": (C.c_int, [_H, _I, _I, _D, _I]),
     "poisson_solve": (C.c_int, [_H, _I, _D]),
     "dd_step": (C.c_int, [_H, C.c_double, _D]),
     "run_steps": (C.c_int, [_H, C.c_int32, _P(AvipStats)]),
@@ -217,6 +219,18 @@ def photo_set(h, a, kappa, c):
     a = np.ascontiguousarray(a, dtype=np.float64)
     kappa = np.ascontiguousarray(kappa, dtype=np.float64)
     return load().photo_set(h, int(a.size), _dptr(a), _dptr(kappa), float(c))
+
+
+def photo_stats(h):
+    """(rc, {"iters": [...], "relres": [...], "side_by_side": bool}) of the last step's
+    photoionisation solves."""
+    n = C.c_int32(0)
+    sbs = C.c_int32(0)
+    it = (C.c_int32 * MAX_PHOTO_TERMS)()
+    rr = (C.c_double * MAX_PHOTO_TERMS)()
+    rc = load().photo_stats(h, C.byref(n), it, rr, C.byref(sbs))
+    k = n.value
+    return rc, {"iters": list(it)[:k], "relres": list(rr)[:k], "side_by_side": bool(sbs.value)}
 
 
 def poisson_solve(h):
@@ -476,6 +490,11 @@ class Mesh:
     def photo(self):
         """Photoionisation source S_ph of the last step."""
         return self.field(FIELD_PHOTO)
+
+    def photo_stats(self):
+        rc, st = photo_stats(self.h)
+        _check(rc, "photo_stats")
+        return st
 
     def state(self):
         rc, st = state_get(self.h)

@@ -27,6 +27,7 @@ cudaError_t launch_pcg_fp64(const PcgArgs& args, const PcgPlan& pl, cudaStream_t
 cudaError_t launch_pcg_mixed(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_bicgstab(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
+cudaError_t launch_amg_group(const AmgGroupArgs& g, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_amg_cluster(const PcgArgs& args, const PcgPlan& pl, cudaStream_t st);
 cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const ClusterLayout& L, cudaStream_t st);
 cudaError_t launch_node_fields(const DDArgs& a, int with_dt, cudaStream_t st);
@@ -86,7 +87,14 @@ struct avip_mesh {
   std::vector<PhotoTerm> photo;
   double *photo_psi = nullptr, *photo_I = nullptr, *photo_S = nullptr, *photo_zero = nullptr;
   int32_t* photo_hist = nullptr;  // per term: earlier solutions kept for the predictor
-  DevScalars* sc_aux = nullptr;
+  DevScalars* sc_aux = nullptr;   // per term: the solve's statistics
+  // whole-GPU AMG solvers (kinds 8, 9): the terms are solved side by side in one launch, each on
+  // its own group of blocks, with per term its own Krylov vectors (kPhotoWork x Npad doubles),
+  // FP32 residual copies (3 x Npad floats, FP32 hierarchy) and barrier state
+  bool photo_group = false;
+  double* photo_work = nullptr;
+  float* photo_rq32 = nullptr;
+  GridSync* photo_gs = nullptr;
   int32_t Npad = 0;
   PcgPlan plan;
   ClusterLayout clay{};
@@ -285,6 +293,15 @@ cudaError_t enqueue_poisson(avip_mesh* h) {
   return enqueue_pcg_only(h);
 }
 
+// Per photoionisation term, the Krylov vectors of a side-by-side solve: x, b, r, p, q, r2, z
+// and the five of BiCGStab.
+constexpr int kPhotoWork = 12;
+
+// First block of term j's group in the side-by-side solve (the grid split as evenly as possible).
+int photo_group_start(const avip_mesh* h, int j) {
+  return (int)((int64_t)j * h->plan.blocks / h->ph.photo_terms);
+}
+
 // Arguments of the solve of photoionisation term j: the same solver and sparsity as the
 // Poisson problem, the term's scaled Helmholtz values, b = rhs_j * (ionisation rate), zero
 // Dirichlet values, results reported to the auxiliary block.
@@ -301,19 +318,50 @@ PcgArgs photo_args(const avip_mesh* h, int j) {
   a.phi1 = h->photo_psi + (size_t)(h->ph.photo_terms + 2 * j) * h->Npad;  // own history
   a.phi2 = a.phi1 + h->Npad;
   a.hist = h->photo_hist + j;
-  a.res = h->sc_aux;
+  a.res = h->sc_aux + j;
   a.v_rise = 0.0;
   a.amg = t.amg;
   a.amg32 = t.amg32;
+  if (h->photo_group) {  // own vectors and barrier state: the terms run at the same time
+    const size_t Np = (size_t)h->Npad;
+    double* w = h->photo_work + (size_t)j * kPhotoWork * Np;
+    a.x = w;
+    a.b = w + Np;
+    a.r = w + 2 * Np;
+    a.p = w + 3 * Np;
+    a.q_ap = w + 4 * Np;
+    a.r2 = w + 5 * Np;
+    a.z = w + 6 * Np;
+    a.bcg = w + 7 * Np;  // 5 vectors
+    a.rq32 = h->photo_rq32 ? h->photo_rq32 + (size_t)j * 3 * Np : nullptr;
+    a.sync = h->photo_gs + j;
+    a.flags = &h->photo_gs[j].count;
+    a.parts = h->parts + (size_t)8 * photo_group_start(h, j);
+  }
   return a;
 }
 
-// The photoionisation solves and the source update that follows them.
+// The photoionisation solves and the source update that follows them: side by side in one
+// launch (whole-GPU AMG solvers), else one after another.
 cudaError_t enqueue_photo(avip_mesh* h, const DDArgs& a, bool auto_dt) {
   cudaError_t e = cudaSuccess;
-  for (int j = 0; j < h->ph.photo_terms && e == cudaSuccess; ++j) {
-    e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
-    if (e == cudaSuccess) e = enqueue_solver(h, photo_args(h, j));
+  const int n = h->ph.photo_terms;
+  if (h->photo_group) {
+    AmgGroupArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.n = n;
+    for (int j = 0; j < n; ++j) {
+      g.a[j] = photo_args(h, j);
+      g.start[j] = photo_group_start(h, j);
+    }
+    g.start[n] = h->plan.blocks;
+    e = cudaMemsetAsync(h->photo_gs, 0, (size_t)n * sizeof(GridSync), h->stream);
+    if (e == cudaSuccess) e = launch_amg_group(g, h->plan, h->stream);
+  } else {
+    for (int j = 0; j < n && e == cudaSuccess; ++j) {
+      e = cudaMemsetAsync(h->sync, 0, h->sync_bytes, h->stream);
+      if (e == cudaSuccess) e = enqueue_solver(h, photo_args(h, j));
+    }
   }
   if (e == cudaSuccess) e = launch_photo_add(a, auto_dt ? 1 : 0, h->stream);
   return e;
@@ -833,7 +881,13 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
   // solutions of the terms, then two history vectors per term
   bool ok = zalloc(h, h->photo_psi, (size_t)3 * n_terms * Np) && zalloc(h, h->photo_hist, n_terms) &&
             zalloc(h, h->photo_I, Np) &&
-            zalloc(h, h->photo_S, Np) && zalloc(h, h->photo_zero, Np) && zalloc(h, h->sc_aux, 1);
+            zalloc(h, h->photo_S, Np) && zalloc(h, h->photo_zero, Np) && zalloc(h, h->sc_aux, n_terms);
+  // side by side on the whole-GPU AMG solvers, when every term gets a group of blocks
+  const bool group = (kind == 8 || kind == 9) && n_terms > 1 && h->plan.blocks >= n_terms;
+  if (ok && group) {
+    ok = zalloc(h, h->photo_work, (size_t)kPhotoWork * n_terms * Np) && zalloc(h, h->photo_gs, n_terms) &&
+         (h->amg || kind == 9 || zalloc(h, h->photo_rq32, (size_t)3 * n_terms * Np));
+  }
   for (int j = 0; j < n_terms && ok; ++j) {
     // (K + kappa_j^2 V) S_j = c a_j V I with S_j = 0 on the Dirichlet nodes: the unscaled
     // Poisson values are recovered from the scaled ones, the diagonal of the free rows gains
@@ -887,8 +941,26 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
   }
   if (!ok) return AVIP_ENOMEM;
   h->ph.photo_terms = n_terms;
+  h->photo_group = group;
   invalidate_graph(h);
   return cudaStreamSynchronize(h->stream) == cudaSuccess ? AVIP_OK : AVIP_ECUDA;
+}
+
+int photo_stats(avip_mesh_t h, int32_t* n_terms, int32_t* iters, double* relres, int32_t* side_by_side) {
+  if (!h || !n_terms || !side_by_side) return AVIP_EINVAL;
+  const int n = h->ph.photo_terms;
+  *n_terms = n;
+  *side_by_side = h->photo_group ? 1 : 0;
+  if (n == 0) return AVIP_OK;
+  DevScalars st[AVIP_MAX_PHOTO_TERMS];
+  cudaError_t e = cudaMemcpyAsync(st, h->sc_aux, (size_t)n * sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int j = 0; j < n; ++j) {
+    if (iters) iters[j] = st[j].pcg_iters;
+    if (relres) relres[j] = st[j].pcg_relres;
+  }
+  return AVIP_OK;
 }
 
 int poisson_solve(avip_mesh_t h, int32_t* iters_out, double* relres_out) {

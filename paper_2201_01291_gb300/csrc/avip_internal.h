@@ -271,6 +271,15 @@ struct PcgArgs {
   int32_t amg_mixed;      // 1: FP32 inner CG + FP64 refinement (kind 10); 0: FP64 CG
 };
 
+// Systems solved side by side in one cooperative launch (the photoionisation terms): system j
+// by the blocks start[j] .. start[j+1] - 1, with its own arguments (vectors, hierarchy, barrier
+// state flags / parts / sync, statistics block res).
+struct AmgGroupArgs {
+  PcgArgs a[AVIP_MAX_PHOTO_TERMS];
+  int32_t n;
+  int32_t start[AVIP_MAX_PHOTO_TERMS + 1];
+};
+
 // Kernel and grid of a PCG launch.
 struct PcgPlan {
   int kind = 1;    // 1 streaming, 2 register-resident, 4 mixed precision, 5 cluster-resident,

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBcgTPB, 1) bicgstab_fp64_kernel(PcgArgs a) {
   double* __restrict__ sv = a.bcg;
   double* __restrict__ tv = a.bcg + Np;
   double* __restrict__ rh = a.bcg + 2 * Np;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
 
   // ---- x = D^1/2 phi (warm start) and b'
   const double gain = dirichlet_gain(a);

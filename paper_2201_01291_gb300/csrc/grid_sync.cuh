@@ -8,10 +8,13 @@
 // Every wait is bounded: after FlagSync::spin_ns of polling (the handle's wait_timeout) a block
 // raises `abort`, every waiter leaves, and the kernel reports a timeout instead of hanging.
 //
-// The arrival counter is a 32-bit value that only grows (mod 2^32); a block waits for barrier
-// seq until counter - seq * gridDim.x, taken as a signed difference, is no longer negative.  The
-// counter never runs more than gridDim.x arrivals ahead of or behind the barrier a block waits
-// for, so the test stays right when seq * gridDim.x wraps past 2^32 on very long solves.
+// The blocks taking part are the whole grid, or one contiguous group of it (solves that run side
+// by side in one launch, each with its own barrier state): FlagSync::nb blocks, this block being
+// number FlagSync::rank among them.  The arrival counter is a 32-bit value that only grows
+// (mod 2^32); a block waits for barrier seq until counter - seq * nb, taken as a signed
+// difference, is no longer negative.  The counter never runs more than nb arrivals ahead of or
+// behind the barrier a block waits for, so the test stays right when seq * nb wraps past 2^32 on
+// very long solves.
 #pragma once
 #include <cstdint>
 
@@ -72,14 +75,16 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
   for (int k = 0; k < NV; ++k) v[k] = smem[32 * NV + k];
 }
 
-// Barrier state of one cooperative launch.  `flags[0]` (the arrival counter) must be zero at
-// launch; `parts` holds 2 * gridDim.x * 4 doubles.
+// Barrier state of the blocks of one solve.  `flags[0]` (the arrival counter) must be zero at
+// launch; `parts` holds 2 * nb * 4 doubles.
 struct FlagSync {
   unsigned* flags;
-  double* parts;  // [2][gridDim.x][4]
+  double* parts;  // [2][nb][4]
   GridSync* gs;   // abort flag
   unsigned seq;   // reductions passed so far (identical in every thread)
   unsigned long long spin_ns;  // give up a wait after this long (0: at the first unsatisfied poll)
+  int nb;         // blocks taking part (gridDim.x for a whole-grid solve)
+  int rank;       // this block's index among them (blockIdx.x for a whole-grid solve)
 };
 
 // True while the arrival counter has not reached `target` (wrap-safe, see above).
@@ -123,7 +128,7 @@ __device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide sum of NV (<= 4) values; NE (<= 4) scalars are then derived from the totals by
+// Sum of NV (<= 4) values over the participating blocks; NE (<= 4) scalars are then derived from the totals by
 // `epi` on one thread per block.  On return v[] holds the totals and out[] the epilogue
 // results, identical in every thread of the grid.  Returns false if the wait was abandoned
 // (timeout or another block aborted); the caller must leave.
@@ -131,14 +136,14 @@ __device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
 // Protocol (measured fastest on GB300 among flag-per-block, last-block and counter schemes):
 // warp sums -> shared memory -> warp 0 adds the block partial, stores it in the block's slot
 // and announces it with one release reduction on a monotone arrival counter; every lane of
-// warp 0 waits (acquire) until the counter reaches seq * gridDim.x and then reads all
-// partials in block order.  Partials are double-buffered by the parity of seq because a fast
+// warp 0 waits (acquire) until the counter reaches seq * nb and then reads all partials in
+// block order.  Partials are double-buffered by the parity of seq because a fast
 // block may publish reduction k+1 while a slow one is still reading reduction k.
 template <int NV, int NE, typename Epi>
 __device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 0 ? NE : 1], FlagSync& fs,
                                             double* smem, Epi epi) {
   static_assert(NV <= 4 && NE <= 4, "grid_allsum: at most 4 sums and 4 derived scalars");
-  const int nb = gridDim.x;
+  const int nb = fs.nb;
   const unsigned seq = ++fs.seq;
   const int par = seq & 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -167,7 +172,7 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], double (&out)[NE > 
     int ok = 1;
     if (nb > 1) {
       if (lane == 0) {
-        double* mine = fs.parts + ((size_t)par * nb + blockIdx.x) * 4;
+        double* mine = fs.parts + ((size_t)par * nb + fs.rank) * 4;
 #pragma unroll
         for (int k = 0; k < NV; ++k) __stcg(mine + k, bt[k]);
         red_add_release_u32(fs.flags, 1u);
@@ -234,7 +239,7 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[NV], FlagSync& fs, doubl
 
 // Grid barrier without a sum: the block's writes are ordered before one release increment of
 // the same monotone arrival counter by thread 0, which then waits (acquire, bounded) for
-// seq * gridDim.x arrivals.  It shares the counter and the sequence number with grid_allsum,
+// seq * nb arrivals.  It shares the counter and the sequence number with grid_allsum,
 // whose partials it does not touch; a reduction k and the next one of the same buffer parity,
 // k + 2, are then separated by this barrier k + 1, which no block passes before every block has
 // finished reading reduction k.  Returns false if the wait was abandoned.
@@ -244,7 +249,7 @@ __device__ __forceinline__ bool grid_barrier(FlagSync& fs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const int nb = gridDim.x;
+    const int nb = fs.nb;
     if (nb > 1) {
       red_add_release_u32(fs.flags, 1u);
       if (!wait_arrivals(fs, seq * (unsigned)nb)) ok = 0;

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_fp64_k
   const int nwarps = gridDim.x * wpb;
   const int N = a.A.N, nsl = a.A.nslices;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
   double one[1];
 
   // ---- x = D^1/2 phi (warm start) and b'
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(TPB, 1) pcg_fp64_res_kernel(PcgArgs a) {
   const int gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
   const int N = a.A.N, nsl = a.A.nslices;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
   double one[1];
 
   int base[MAXS], wid[MAXS], rl[MAXS];

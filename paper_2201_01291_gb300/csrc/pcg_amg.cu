@@ -46,20 +46,24 @@ template <>
 __device__ __forceinline__ const AmgDevT<float>* amg_of<float>(const PcgArgs& a) { return a.amg32; }
 template <>
 __device__ __forceinline__ const AmgDevT<double>* amg_of<double>(const PcgArgs& a) { return a.amg; }
+// A wait was abandoned: make every other waiter of this solve leave, report the timeout.
+__device__ __forceinline__ void report_timeout(const PcgArgs& a) {
+  atomicExch(&a.sync->abort, 1);
+  a.res->pcg_status = AVIP_ETIMEOUT;
+  atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
+}
+
 template <int TPB, typename T>
 __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   constexpr int wpb = TPB / 32;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
   GridOps ops{fs, smem};
   if (!amg_cg_solve<T>(a, amg_of<T>(a), a.z, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb,
                        threadIdx.x & 31, blockIdx.x == 0 && threadIdx.x == 0) &&
-      threadIdx.x == 0) {
-    atomicExch(&a.sync->abort, 1);
-    a.res->pcg_status = AVIP_ETIMEOUT;
-    atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
-  }
+      threadIdx.x == 0)
+    report_timeout(a);
 }
 
 // BiCGStab right-preconditioned by the same V-cycle, for the non-symmetric axisymmetric
@@ -70,18 +74,14 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
 // (van der Vorst's iteration with M^-1 applied on the right, so x is updated directly and the
 // stopping test stays on the true scaled residual of the free rows).  Two V-cycles per
 // iteration; breakdowns and a true residual still too large restart from the true residual.
-template <int TPB, typename T>
-__global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
-  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
-  __shared__ double smem[2 * 32 * 4];
-  const int lane = threadIdx.x & 31;
-  constexpr int wpb = TPB / 32;
-  const int gwarp = blockIdx.x * wpb + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * wpb;
+// The solve of one system by the blocks taking part in `fs` (gwarp / nwarps number their warps,
+// `leader` is the one thread that writes the statistics); false if a wait was abandoned.
+template <typename T>
+__device__ bool amg_bicgstab_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H, FlagSync& fs, double* smem,
+                                   int gwarp, int nwarps, int lane, bool leader) {
   const int N = a.A.N, nsl = a.A.nslices;
   const size_t Np = (size_t)a.Npad;
   const double* nb = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * Np;
-  const AmgDevT<T>* __restrict__ H = amg_of<T>(a);
   double* __restrict__ x = a.x;
   double* __restrict__ r = a.r;
   double* __restrict__ p = a.p;
@@ -91,7 +91,6 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
   double* __restrict__ rh = a.bcg + 2 * Np;
   double* __restrict__ ph = a.bcg + 3 * Np;
   double* __restrict__ sh = a.bcg + 4 * Np;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
   GridOps ops{fs, smem};
   double dummy = 0.0;
 
@@ -117,7 +116,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
     if (a.rhs_scale[i] != 0.0) bb[0] = fma(b, b, bb[0]);  // free rows only: a Dirichlet row holds its value exactly
     else x[i] = b;  // a Dirichlet unit row takes its (possibly ramped) value exactly
   }
-  if (!grid_allsum<1>(bb, fs, smem)) goto timeout;
+  if (!grid_allsum<1>(bb, fs, smem)) return false;
   {
     const double thresh = a.rtol * a.rtol * bb[0];
     double rr_true = 0.0, rho = 0.0;
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
             p[i] = ri;
             r2[0] = fma(ri, ri, r2[0]);
           }
-          if (!grid_allsum<1>(r2, fs, smem)) goto timeout;
+          if (!grid_allsum<1>(r2, fs, smem)) return false;
           rr_true = r2[0];
           if (rr_true <= thresh) break;
           if (!isfinite(rr_true)) {
@@ -158,7 +157,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           restart = false;
         }
         // ---- p^ = M p, then P1: v = A p^
-        if (!vcycle(H, (const double*)p, ph, ops, gwarp, nwarps, lane, false, dummy)) goto timeout;
+        if (!vcycle(H, (const double*)p, ph, ops, gwarp, nwarps, lane, false, dummy)) return false;
         double rv[1] = {0.0};
         for (int sl = gwarp; sl < nsl; sl += nwarps) {
           const int i = sl * kSlice + lane;
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
         if (!grid_allsum<1, 1>(rv, al, fs, smem, [rho_now](const double* t, double* e) {
               e[0] = t[0] != 0.0 ? rho_now / t[0] : 0.0;
             }))
-          goto timeout;
+          return false;
         if (rv[0] == 0.0 || !isfinite(rv[0])) {  // breakdown
           if (it == 0) {
             status = AVIP_ENOTCONV;
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           sv[i] = si;
           ss[0] = fma(si, si, ss[0]);
         }
-        if (!grid_allsum<1>(ss, fs, smem)) goto timeout;
+        if (!grid_allsum<1>(ss, fs, smem)) return false;
         if (ss[0] <= thresh) {  // s small enough: x += alpha p^, confirm on the true residual
           for (int sl = gwarp; sl < nsl; sl += nwarps) {
             const int i = sl * kSlice + lane;
@@ -200,11 +199,11 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           ++it;
           restart = true;
           double z0[1] = {0.0};
-          if (!grid_allsum<1>(z0, fs, smem)) goto timeout;
+          if (!grid_allsum<1>(z0, fs, smem)) return false;
           continue;
         }
         // ---- s^ = M s, then P3: t = A s^
-        if (!vcycle(H, (const double*)sv, sh, ops, gwarp, nwarps, lane, false, dummy)) goto timeout;
+        if (!vcycle(H, (const double*)sv, sh, ops, gwarp, nwarps, lane, false, dummy)) return false;
         double d4[4] = {0.0, 0.0, 0.0, 0.0};  // t.s, t.t, rh.s, rh.t
         for (int sl = gwarp; sl < nsl; sl += nwarps) {
           const int i = sl * kSlice + lane;
@@ -225,7 +224,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
               e[1] = rn;
               e[2] = (om != 0.0 && rn != 0.0) ? (rn / rho_now) * (alpha / om) : 0.0;
             }))
-          goto timeout;
+          return false;
         const double omega = e3[0], rho_new = e3[1], beta = e3[2];
         // ---- P4: x, r, p; first V-cycle direction of the new p
         double rn2[1] = {0.0};
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
           p[i] = pn;
           rn2[0] = fma(ri, ri, rn2[0]);
         }
-        if (!grid_allsum<1>(rn2, fs, smem)) goto timeout;
+        if (!grid_allsum<1>(rn2, fs, smem)) return false;
         ++it;
         rho = rho_new;
         if (rn2[0] <= thresh || !isfinite(rn2[0]) || omega == 0.0 || rho_new == 0.0 || it >= a.max_iter)
@@ -251,7 +250,7 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
       const int i = sl * kSlice + lane;
       if (i < N) a.phi[i] = a.dsqinv[i] * x[i];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader) {
       a.res->pcg_iters = it;
       if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
       a.res->pcg_status = status;
@@ -259,15 +258,63 @@ __global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
       a.res->pcg_bnorm = sqrt(bb[0]);
       if (status != AVIP_OK && a.sc->status == AVIP_OK) a.sc->status = status;
     }
-    return;
   }
-timeout:
-  if (threadIdx.x == 0) {
-    atomicExch(&a.sync->abort, 1);
-    a.res->pcg_status = AVIP_ETIMEOUT;
-    atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
-  }
+  return true;
 }
+
+template <int TPB, typename T>
+__global__ void __launch_bounds__(TPB, 1) bicgstab_amg_kernel(PcgArgs a) {
+  if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
+  __shared__ double smem[2 * 32 * 4];
+  constexpr int wpb = TPB / 32;
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
+  if (!amg_bicgstab_solve<T>(a, amg_of<T>(a), fs, smem, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb,
+                             threadIdx.x & 31, blockIdx.x == 0 && threadIdx.x == 0) &&
+      threadIdx.x == 0)
+    report_timeout(a);
+}
+
+// Several systems solved side by side in one cooperative launch (the photoionisation terms):
+// the grid is split into contiguous groups of blocks, start[j] .. start[j+1] - 1 solving
+// system j with its own arguments, hierarchy, vectors and barrier state, so the systems share
+// no barrier and each group stops when its own system has converged.  The blocks of a group
+// first agree on whether an earlier stage failed (a group that has finished may already have
+// reported a failure when another group's block starts).
+template <int TPB, typename T, bool kBicg>
+__global__ void __launch_bounds__(TPB, 1) amg_group_kernel(const __grid_constant__ AmgGroupArgs g) {
+  int j = 0;
+  while (j + 1 < g.n && (int)blockIdx.x >= g.start[j + 1]) ++j;
+  // the group's arguments, copied to shared memory (a runtime index into the parameters would
+  // keep every field the solve reads in registers)
+  __shared__ PcgArgs s_args;
+  {
+    static_assert(sizeof(PcgArgs) % sizeof(unsigned long long) == 0, "PcgArgs: whole 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&g.a[j]);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_args);
+    for (int k = threadIdx.x; k < (int)(sizeof(PcgArgs) / 8); k += TPB) dst[k] = src[k];
+  }
+  __syncthreads();
+  const PcgArgs& a = s_args;
+  __shared__ double smem[2 * 32 * 4];
+  constexpr int wpb = TPB / 32;
+  const int nb = g.start[j + 1] - g.start[j], rank = (int)blockIdx.x - g.start[j];
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, nb, rank};
+  const int gwarp = rank * wpb + (int)(threadIdx.x >> 5), nwarps = nb * wpb, lane = threadIdx.x & 31;
+  const bool leader = rank == 0 && threadIdx.x == 0;
+  double skip[1] = {solve_skipped(a.sc) ? 1.0 : 0.0};
+  bool ok = grid_allsum<1>(skip, fs, smem);
+  if (ok && skip[0] > 0.0) return;
+  if (ok) {
+    if constexpr (kBicg) {
+      ok = amg_bicgstab_solve<T>(a, amg_of<T>(a), fs, smem, gwarp, nwarps, lane, leader);
+    } else {
+      GridOps ops{fs, smem};
+      ok = amg_cg_solve<T>(a, amg_of<T>(a), a.z, ops, gwarp, nwarps, lane, leader);
+    }
+  }
+  if (!ok && threadIdx.x == 0) report_timeout(a);
+}
+
 
 // Mixed precision with the AMG preconditioner (solver kind 10): FP64 outer residual
 // r = b' - A x and correction x += ||r|| e; the inner solve A e = r / ||r|| runs CG in FP32
@@ -279,15 +326,12 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_mixed_kernel(PcgArgs a) {
   if (solve_skipped(a.sc)) return;  // an earlier stage of this run failed beyond repair
   __shared__ double smem[2 * 32 * 4];
   constexpr int wpb = TPB / 32;
-  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns};
+  FlagSync fs{a.flags, a.parts, a.sync, 0u, a.spin_ns, (int)gridDim.x, (int)blockIdx.x};
   GridOps ops{fs, smem};
   if (!amg_mixed_solve(a, ops, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb, threadIdx.x & 31,
                        blockIdx.x == 0 && threadIdx.x == 0) &&
-      threadIdx.x == 0) {
-    atomicExch(&a.sync->abort, 1);
-    a.res->pcg_status = AVIP_ETIMEOUT;
-    atomicCAS(&a.sc->status, AVIP_OK, AVIP_ETIMEOUT);
-  }
+      threadIdx.x == 0)
+    report_timeout(a);
 }
 
 template <typename T>
@@ -350,6 +394,35 @@ cudaError_t launch_pcg_amg(const PcgArgs& args, const PcgPlan& pl, cudaStream_t 
   cfg.numAttrs = 1;
   void* kargs[] = {const_cast<PcgArgs*>(&args)};
   return cudaLaunchKernelExC(&cfg, amg_kernel_ptr(pl.kind, pl.tpb, pl.maxs), kargs);
+}
+
+template <typename T, bool kBicg>
+static const void* amg_group_ptr_t(int tpb) {
+  switch (tpb) {
+    case 768: return (const void*)amg_group_kernel<768, T, kBicg>;
+    case 1024: return (const void*)amg_group_kernel<1024, T, kBicg>;
+    default: return (const void*)amg_group_kernel<512, T, kBicg>;
+  }
+}
+
+// The side-by-side solves of g.n systems of solver kind pl.kind (8: CG, 9: BiCGStab) over the
+// grid of pl (the grid of the single solve: one block per SM).
+cudaError_t launch_amg_group(const AmgGroupArgs& g, const PcgPlan& pl, cudaStream_t st) {
+  const bool bicg = pl.kind == 9;
+  const void* fn = pl.maxs ? (bicg ? amg_group_ptr_t<double, true>(pl.tpb) : amg_group_ptr_t<double, false>(pl.tpb))
+                           : (bicg ? amg_group_ptr_t<float, true>(pl.tpb) : amg_group_ptr_t<float, false>(pl.tpb));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl.blocks);
+  cfg.blockDim = dim3(pl.tpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* kargs[] = {const_cast<AmgGroupArgs*>(&g)};
+  return cudaLaunchKernelExC(&cfg, fn, kargs);
 }
 
 }  // namespace avip

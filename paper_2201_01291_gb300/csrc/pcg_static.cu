@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kStaticTPB) pcg_csr_static_kernel(StaticPcgArg
   double* z = r + kStaticMaxRows;
   double* p = z + kStaticMaxRows;
   double* q = p + kStaticMaxRows;
-  FlagSync fs{flags, parts, gs, 0u, kSpinLimitNs};
+  FlagSync fs{flags, parts, gs, 0u, kSpinLimitNs, (int)gridDim.x, (int)blockIdx.x};
   const int n = a.n;
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;

@@ -52,6 +52,11 @@ def test_photo_source_one_step(avip, geom, kind):
     assert normwise(m.photo(), o.last_photo) <= TOL
     for s in range(2):
         assert normwise(m.density(s), n1[s]) <= TOL, s
+    ps = m.photo_stats()
+    # the whole-GPU AMG kinds solve the three terms side by side, each on its own blocks
+    assert ps["side_by_side"] == (kind in (8, 9) and m.info["pcg_blocks"] >= 3)
+    assert len(ps["iters"]) == 3 and all(k > 0 for k in ps["iters"])
+    assert all(r <= 1e-14 for r in ps["relres"]), ps
     m.close()
 
 
@@ -82,6 +87,8 @@ def test_photo_large_axisymmetric_amg(avip):
     assert m.info["pcg_kind"] == 9
     st = m.run(6)
     assert st["status"] == 0
+    ps = m.photo_stats()
+    assert ps["side_by_side"] and all(r <= 1e-13 for r in ps["relres"]), ps
     for s in range(2):
         assert normwise(m.density(s), n_ref[s]) <= TOL, s
     assert normwise(m.phi(), phi_ref) <= TOL
@@ -123,4 +130,28 @@ def test_photo_on_hybrid_mesh_with_chemistry_and_ramp(avip):
     for s in range(3):
         assert normwise(m.density(s), n_ref[s]) <= TOL, s
     assert normwise(m.photo(), o.last_photo) <= TOL
+    m.close()
+
+
+def test_photo_side_by_side_skips_after_timeout_then_recovers(avip):
+    """With a wait limit of zero the Poisson solve gives up; the side-by-side photoionisation
+    launch that follows sees the failed run and every group leaves together (none waits for a
+    group that skipped).  With a normal limit the same handle matches the oracle."""
+    p = planar(121, 117)
+    m = avip.Mesh(p, rtol=1e-13, pcg_kind=8, wait_timeout=0.0)
+    assert m.photo_stats()["side_by_side"]
+    s0 = m.state()
+    st = m.run(1, allow=(avip.AVIP_ETIMEOUT,))
+    assert st["status"] == avip.AVIP_ETIMEOUT
+    m.set_wait_timeout(2.0)
+    m.set_state(s0)
+    st = m.run(2)
+    assert st["status"] == avip.AVIP_OK
+    o = O.Oracle(p)
+    n_ref, phi_ref, _ = o.run(2)
+    for s in range(2):
+        assert normwise(m.density(s), n_ref[s]) <= TOL, s
+    assert normwise(m.phi(), phi_ref) <= TOL
+    # S_ph is the output of solves stopped at rtol 1e-13: the solve's accuracy
+    assert normwise(m.photo(), o.last_photo) <= 1e-9
     m.close()
