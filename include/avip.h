@@ -244,8 +244,8 @@ int source_set(avip_mesh_t h, int32_t model, const double* params, const int32_t
  * are solved (vertex-centred: (K + kappa_j^2 V) S_j = a_j c V I_ion with the Poisson matrix K and
  * the dual volumes V) by the handle's own solver kind with the term's own diagonal scaling and,
  * for the AMG kinds, its own hierarchy (built here, once; with the whole-GPU AMG kinds the
- * terms are solved side by side in one launch, see photo_stats), started from the quadratic
- * extrapolation of its last three solutions; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
+ * terms are solved side by side in one launch, see photo_stats), started from the cubic
+ * extrapolation of its last four solutions; S_ph = sum_j S_j is added to the electron and positive-ion sources (idx[0], idx[1] of
  * source_set) before the time step and the update, and enters the chemical time-step limit.
  *   a[n_terms]     A_j p_O2^2 (1/m^2)  — with A_j, lambda_j the coefficients of the fit;
  *   kappa[n_terms] lambda_j p_O2 (1/m), > 0;
@@ -265,7 +265,7 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
  * AVIP_EINVAL for a NULL handle, n_terms or side_by_side. */
 int photo_stats(avip_mesh_t h, int32_t* n_terms, int32_t* iters, double* relres, int32_t* side_by_side);
 
-/* Solve the Poisson problem for the current densities, starting from the quadratic
+/* Solve the Poisson problem for the current densities, starting from the cubic
  * extrapolation of the last potentials (the last one alone after mesh_create or a state with
  * no history).  Every call advances that history.
  * iters_out / relres_out (may be NULL) receive the PCG iteration count and the final true
@@ -294,13 +294,13 @@ int run_steps_timed(avip_mesh_t h, int32_t nsteps, double* kernel_ms, avip_stats
 int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out);
 
 /* Checkpoint / resume.  state layout, caller numbering: [n_species * n_nodes densities]
- * [n_nodes phi][t][n_nodes phi_{n-1}][n_nodes phi_{n-2}][h], where phi_{n-1}, phi_{n-2} and
- * h (0, 1 or 2 of them valid) are the history of the Poisson solver's initial-guess predictor
- * (quadratic extrapolation of the last potentials), so that a resumed run repeats the
- * uninterrupted one bit for bit (with photoionisation the Helmholtz solutions and their
- * histories are not part of the state: a resumed run then agrees within the solve
- * tolerance); size = (n_species + 3) * n_nodes + 2 doubles.  state_set
- * returns AVIP_EINVAL for h outside {0, 1, 2}, AVIP_ENAN for a non-finite entry. */
+ * [n_nodes phi][t][n_nodes phi_{n-1}][n_nodes phi_{n-2}][n_nodes phi_{n-3}][h], where
+ * phi_{n-1}, phi_{n-2}, phi_{n-3} and h (0 .. 3 of them valid) are the history of the Poisson
+ * solver's initial-guess predictor (cubic extrapolation of the last potentials), so that a
+ * resumed run repeats the uninterrupted one bit for bit (with photoionisation the Helmholtz
+ * solutions and their histories are not part of the state: a resumed run then agrees within
+ * the solve tolerance); size = (n_species + 4) * n_nodes + 2 doubles.  state_set
+ * returns AVIP_EINVAL for h outside {0, 1, 2, 3}, AVIP_ENAN for a non-finite entry. */
 int state_size(avip_mesh_t h, int64_t* n_doubles);
 int state_get(avip_mesh_t h, double* host_state);
 int state_set(avip_mesh_t h, const double* host_state);

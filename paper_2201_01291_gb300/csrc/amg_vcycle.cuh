@@ -430,7 +430,7 @@ __device__ bool amg_cg_solve(const PcgArgs& a, const AmgDevT<T>* __restrict__ H,
     }
     if (leader) {
       a.res->pcg_iters = it;
-      if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
+      advance_history(a);
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);
@@ -583,7 +583,7 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
     }
     if (leader) {
       a.res->pcg_iters = it;
-      if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
+      advance_history(a);
       a.res->pcg_outer = outer;
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;

@@ -56,7 +56,7 @@ struct avip_mesh {
   double* cw = nullptr;
   int32_t *e_lo = nullptr, *e_hi = nullptr, *slot_eid = nullptr;  // edge list (flux once per edge)
   double *e_sx = nullptr, *e_sy = nullptr, *eflux = nullptr;
-  double *phi1 = nullptr, *phi2 = nullptr;  // the two previous potentials (predictor)
+  double *phi1 = nullptr, *phi2 = nullptr, *phi3 = nullptr;  // the three previous potentials (predictor)
   double *phi = nullptr, *xs = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
   double *nbuf = nullptr, *ndat = nullptr, *nm = nullptr, *src = nullptr, *Ex = nullptr, *Ey = nullptr;
   double* qpart = nullptr;      // per-block charge partials of the flux kernel
@@ -189,6 +189,7 @@ PcgArgs pcg_args(const avip_mesh* h) {
   a.phi = h->phi;
   a.phi1 = h->phi1;
   a.phi2 = h->phi2;
+  a.phi3 = h->phi3;
   a.hist = &h->sc->phi_hist;
   a.x = h->xs;
   a.b = h->b;
@@ -315,8 +316,9 @@ PcgArgs photo_args(const avip_mesh* h, int j) {
   a.lift = h->photo_zero;
   a.rhs_src = h->photo_I;
   a.phi = h->photo_psi + (size_t)j * h->Npad;
-  a.phi1 = h->photo_psi + (size_t)(h->ph.photo_terms + 2 * j) * h->Npad;  // own history
+  a.phi1 = h->photo_psi + (size_t)(h->ph.photo_terms + kPredictorHistory * j) * h->Npad;  // own history
   a.phi2 = a.phi1 + h->Npad;
+  a.phi3 = a.phi2 + h->Npad;
   a.hist = h->photo_hist + j;
   a.res = h->sc_aux + j;
   a.v_rise = 0.0;
@@ -612,7 +614,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   std::vector<double> phi0(Np, 0.0);
   for (int32_t i = 0; i < m.N; ++i)
     if (m.bc[i] == 1) phi0[i] = h->opts.v_rise > 0 ? 0.0 : m.lift[i];  // a ramp starts at 0 V
-  ok = ok && upload(h, h->phi, phi0) && upload(h, h->phi1, phi0) && upload(h, h->phi2, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
+  ok = ok && upload(h, h->phi, phi0) && upload(h, h->phi1, phi0) && upload(h, h->phi2, phi0) && upload(h, h->phi3, phi0) && zalloc(h, h->b, Np) && zalloc(h, h->r, Np) && zalloc(h, h->xs, Np) &&
        zalloc(h, h->p, Np) && zalloc(h, h->q, Np) && zalloc(h, h->nbuf, 2 * AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->ndat, 4 * AVIP_MAX_SPECIES * Np) && zalloc(h, h->nm, AVIP_MAX_SPECIES * Np) &&
        zalloc(h, h->src, AVIP_MAX_SPECIES * Np) && zalloc(h, h->Ex, Np) && zalloc(h, h->Ey, Np);
@@ -879,7 +881,7 @@ int photo_set(avip_mesh_t h, int32_t n_terms, const double* a, const double* kap
   const size_t Np = (size_t)h->Npad;
   const bool amg = kind == 8 || kind == 9 || kind == 11;
   // solutions of the terms, then two history vectors per term
-  bool ok = zalloc(h, h->photo_psi, (size_t)3 * n_terms * Np) && zalloc(h, h->photo_hist, n_terms) &&
+  bool ok = zalloc(h, h->photo_psi, (size_t)(1 + kPredictorHistory) * n_terms * Np) && zalloc(h, h->photo_hist, n_terms) &&
             zalloc(h, h->photo_I, Np) &&
             zalloc(h, h->photo_S, Np) && zalloc(h, h->photo_zero, Np) && zalloc(h, h->sc_aux, n_terms);
   // side by side on the whole-GPU AMG solvers, when every term gets a group of blocks
@@ -1161,7 +1163,7 @@ int field_get(avip_mesh_t h, int32_t which, int32_t s, double* host_out) {
 
 int state_size(avip_mesh_t h, int64_t* n) {
   if (!h || !n) return AVIP_EINVAL;
-  *n = (int64_t)(h->ph.ns + 3) * h->hm.N + 2;
+  *n = (int64_t)(h->ph.ns + 1 + kPredictorHistory) * h->hm.N + 2;
   return AVIP_OK;
 }
 
@@ -1178,11 +1180,12 @@ int state_get(avip_mesh_t h, double* out) {
   rc = read_scalars(h, sc);
   if (rc) return rc;
   out[(size_t)(h->ph.ns + 1) * N] = sc.t;
-  // the predictor's history: phi_{n-1}, phi_{n-2} and how many of them are valid
+  // the predictor's history: phi_{n-1}, phi_{n-2}, phi_{n-3} and how many of them are valid
   double* hist = out + (size_t)(h->ph.ns + 1) * N + 1;
   if ((rc = to_host_perm(h, h->phi1, hist)) != AVIP_OK) return rc;
   if ((rc = to_host_perm(h, h->phi2, hist + N)) != AVIP_OK) return rc;
-  hist[2 * (size_t)N] = (double)sc.phi_hist;
+  if ((rc = to_host_perm(h, h->phi3, hist + 2 * (size_t)N)) != AVIP_OK) return rc;
+  hist[kPredictorHistory * (size_t)N] = (double)sc.phi_hist;
   return AVIP_OK;
 }
 
@@ -1207,16 +1210,16 @@ int state_set(avip_mesh_t h, const double* in) {
   if (e != cudaSuccess) return cuda_status(e);
   const double t = in[(size_t)(h->ph.ns + 1) * N];
   const double* hist = in + (size_t)(h->ph.ns + 1) * N + 1;
-  const double hn = hist[2 * (size_t)N];
-  if (!(hn == 0.0 || hn == 1.0 || hn == 2.0)) return AVIP_EINVAL;
+  const double hn = hist[kPredictorHistory * (size_t)N];
+  if (!(hn >= 0.0 && hn <= (double)kPredictorHistory && hn == std::floor(hn))) return AVIP_EINVAL;
   const int32_t hv = (int32_t)hn;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  double* const dst_hist[kPredictorHistory] = {h->phi1, h->phi2, h->phi3};
+  for (int k = 0; k < kPredictorHistory && e == cudaSuccess; ++k) {
     for (int32_t i = 0; i < N; ++i) {
       tmp[i] = hist[(size_t)k * N + h->hm.perm[i]];
       if (!std::isfinite(tmp[i])) return AVIP_ENAN;
     }
-    e = cudaMemcpyAsync(k == 0 ? h->phi1 : h->phi2, tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice,
-                        h->stream);
+    e = cudaMemcpyAsync(dst_hist[k], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);

@@ -269,7 +269,7 @@ __device__ void cluster_solve(const PcgArgs& a, const ClusterLayout& L, ClusterS
   }
   if (rank == 0 && threadIdx.x == 0) {
     a.res->pcg_iters = it;
-    if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
+    advance_history(a);
     a.res->pcg_status = status;
     a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr_true / bb[0]) : 0.0;
     a.res->pcg_bnorm = sqrt(bb[0]);
@@ -545,7 +545,7 @@ __device__ void cluster_solve_mixed(const PcgArgs& a, const ClusterLayout& L, Cl
   }
   if (rank == 0 && threadIdx.x == 0) {
     a.res->pcg_iters = it;
-    if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
+    advance_history(a);
     a.res->pcg_outer = outer;
     a.res->pcg_status = status;
     a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;

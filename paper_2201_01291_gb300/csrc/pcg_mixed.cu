@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(TPB, (TPB <= 512 ? 1024 / TPB : 1)) pcg_mixed_
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.res->pcg_iters = it;
-      if (a.phi1) *a.hist = *a.hist < 2 ? *a.hist + 1 : 2;
+      advance_history(a);
       a.res->pcg_status = status;
       a.res->pcg_relres = bb[0] > 0.0 ? sqrt(rr64 / bb[0]) : 0.0;
       a.res->pcg_bnorm = sqrt(bb[0]);

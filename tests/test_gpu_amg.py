@@ -156,7 +156,7 @@ def test_predictor_cuts_iterations_and_resumes_bitwise(avip):
     m = avip.Mesh(p, rtol=1e-12, pcg_kind=8)
     m.run(20)
     snap = m.state()
-    assert snap[-1] == 2.0
+    assert snap[-1] == 3.0
     it_pred = m.run(10)["pcg_iters_total"]
     cold = avip.Mesh(p, rtol=1e-12, pcg_kind=8)
     cold.set_state(snap)
