@@ -106,7 +106,8 @@ typedef struct avip_opts {
   int32_t reorder;                     /* 1 = Morton renumbering (default), 0 = keep order    */
   double dt_fixed;                     /* > 0: use this time step instead of the automatic one */
   double inner_rtol;                   /* mixed precision: FP32 inner reduction per refinement */
-  int32_t pcg_threads;                 /* streaming PCG block size (256/512/768/1024; 0 = 768) */
+  int32_t pcg_threads;                 /* solver block size (256/512/768/1024; 0 = the kind's default:
+                                          768, 1024 for the AMG-preconditioned CG) */
   int32_t pcg_kind;                    /* solver kernel: 0 auto, 1 streaming, 2 register-resident,
                                           5 cluster, 7 BiCGStab (the only one for AXISYMMETRIC),
                                           8 CG preconditioned by an AMG V-cycle (auto for planar

@@ -48,39 +48,24 @@ struct DotAcc<float> {
 // elementwise pass) and b' = Rf b on the rows of level l + 1 (a streamed product), b given by
 // `src` (complete on entry).  `hook` takes part in every row i of level l: hook.begin(i) loads
 // the row's own operands, hook.end(i, pre) runs with them (the CG update folded into the
-// finest level's phase).  The elementwise pass takes kRowBatch rows per thread at a time, their
-// loads all issued before their use; then every warp streams a contiguous share of Rf.
+// finest level's phase).  The elementwise pass takes one row per thread at a time (issuing the
+// loads of several rows before their use kept more registers live than the 64 - 80 a thread has
+// at 768 - 1024 threads per block: the spills cost more than the extra loads in flight saved);
+// then every warp streams a contiguous share of Rf.
 template <typename T, int U, class Src, class Hook>
 __device__ __forceinline__ void amg_down(const AmgDevT<T>* __restrict__ H, int l, Src src, Hook hook, int gwarp,
                                          int nwarps, int lane) {
-  constexpr int kRowBatch = 4;
   const AmgLevelT<T>& L = H->L[l];
   T* __restrict__ bn = H->L[l + 1].b;
   T* __restrict__ xp = L.xp;
   const T* __restrict__ qd = L.qd;
   const int n = L.n;
-  const int stride = nwarps * kSlice;
-  using Pre = decltype(hook.begin(0));
-  for (int i0 = gwarp * kSlice + lane; i0 < n; i0 += kRowBatch * stride) {
-    Pre pre[kRowBatch];
-    T bi[kRowBatch], qi[kRowBatch];
-#pragma unroll
-    for (int k = 0; k < kRowBatch; ++k) {
-      const int i = i0 + k * stride;
-      if (i < n) {
-        pre[k] = hook.begin(i);
-        bi[k] = src(i);
-        qi[k] = __ldg(qd + i);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kRowBatch; ++k) {
-      const int i = i0 + k * stride;
-      if (i < n) {
-        hook.end(i, pre[k]);
-        xp[i] = qi[k] * bi[k];
-      }
-    }
+  for (int i = gwarp * kSlice + lane; i < n; i += nwarps * kSlice) {
+    const auto pre = hook.begin(i);
+    const T bi = src(i);
+    const T qi = __ldg(qd + i);
+    hook.end(i, pre);
+    xp[i] = qi * bi;
   }
   int sa, sb;
   warp_slices(L.Rf.nslices, gwarp, nwarps, sa, sb);
@@ -600,7 +585,11 @@ __device__ bool amg_mixed_solve(const PcgArgs& a, Ops& ops, int gwarp, int nwarp
 // for the whole-GPU kernels, measured fastest with their 24 warps per SM, and for the cluster
 // solves).
 struct GridOps {
-  static constexpr int kStream = 8, kStream64 = 8;
+  // steps of 32 elements loaded ahead by the streamed products: FP32 operators, FP64 matrix.
+  // Measured on the pin-plane solve (500k rows, 1024 threads): 6 / 4 gave 99.9 us per CG
+  // iteration, 8 / 4 101.2, 4 / 4 104.9, 12 / 4 139 (register spills), 8 / 8 (with row batches
+  // of 4 in the down phase) 127
+  static constexpr int kStream = 6, kStream64 = 4;
   FlagSync& fs;
   double* smem;
   __device__ bool barrier() { return grid_barrier(fs); }
