@@ -604,8 +604,11 @@ struct GridOps {
 // distributed shared memory (at most 32 CTAs; deterministic: fixed shuffle tree over the ranks).
 // `part` (2 x 4 doubles), `wsum` (32 x 4 doubles) and `res` (4 doubles) are the calling CTA's
 // shared scratch.
-struct ClusterOps {
-  static constexpr int kStream = 8, kStream64 = 8;
+// S, S64: steps loaded ahead by the streamed FP32 / FP64 products (8 / 8 at 512 threads per CTA,
+// 6 / 4 at 768, where fewer registers are left per thread).
+template <int S, int S64>
+struct ClusterOpsT {
+  static constexpr int kStream = S, kStream64 = S64;
   cooperative_groups::cluster_group cl;
   double* part;  // [2][4]: this CTA's partials, double-buffered
   double* wsum;  // [32][4]: warp partials
@@ -653,5 +656,6 @@ struct ClusterOps {
     return true;
   }
 };
+using ClusterOps = ClusterOpsT<8, 8>;
 
 }  // namespace avip

@@ -695,7 +695,7 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   // mid-size planar meshes (or kind 11 forced): the AMG-preconditioned solve on one cluster
   if (!bicg && (h->opts.pcg_kind == 11 ||
                 (h->opts.pcg_kind == 0 && m.N > kClusterAmgMinRows && m.N <= kClusterAutoRows))) {
-    const PcgPlan cp = amg_cluster_plan(h->opts.cluster_size);
+    const PcgPlan cp = amg_cluster_plan(h->opts.cluster_size, m.N);
     if (cp.kind == 11) {
       AmgHost H;
       int rc = amg_setup(m, H, g_err, sizeof(g_err));

@@ -297,7 +297,7 @@ PcgPlan pcg_plan(int nslices, int kind, int requested_tpb);
 PcgPlan pcg_mixed_plan(int nslices, int requested_tpb);
 PcgPlan bicgstab_plan(int nslices, int requested_tpb);
 PcgPlan amg_plan(int nslices, int requested_tpb, int kind, int fp64);  // kind 8 (CG), 9 (BiCGStab), 10 (mixed)
-PcgPlan amg_cluster_plan(int want);  // kind 11 (one cluster of `want` CTAs or 16 / 8; kind 0 if none fits)
+PcgPlan amg_cluster_plan(int want, int n);  // kind 11 for n rows (one cluster of `want` CTAs or 16 / 8; kind 0 if none fits)
 
 // Cluster-resident solve (kind 5): rows, halo and matrix slices per CTA of the cluster.
 struct ClusterLayout {

@@ -568,10 +568,11 @@ __global__ void __launch_bounds__(kClusterTPB, 1) pcg_cluster_kernel(PcgArgs a, 
 // AMG-preconditioned CG of one instance on one cluster: the rows of every level are shared by
 // the cluster's warps, barriers are cluster barriers and sums go through distributed shared
 // memory (the same V-cycle and CG as the whole-GPU kernel, solver kind 8).
+template <class Ops = ClusterOps>
 __device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) {
   if (solve_skipped(a.sc)) return;  // every CTA of the cluster reads the same status
   cg::cluster_group cl = cg::this_cluster();
-  ClusterOps ops{cl, part, wsum, wsum + 32 * 4, 0u};
+  Ops ops{cl, part, wsum, wsum + 32 * 4, 0u};
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
   const int gw = rank * wpb + (int)(threadIdx.x >> 5), nw = (int)cl.num_blocks() * wpb, lane = (int)(threadIdx.x & 31);
   if (a.amg32)  // FP32 hierarchy (default), else FP64
@@ -584,10 +585,11 @@ __device__ void cluster_amg_solve(const PcgArgs& a, double* part, double* wsum) 
 // (wsum holds 32 x 4 warp partials followed by the 4 totals.)
 
 // The same for a mixed-precision instance with an FP32 hierarchy (solver kind 10).
+template <class Ops = ClusterOps>
 __device__ void cluster_amg_mixed_solve(const PcgArgs& a, double* part, double* wsum) {
   if (solve_skipped(a.sc)) return;
   cg::cluster_group cl = cg::this_cluster();
-  ClusterOps ops{cl, part, wsum, wsum + 32 * 4, 0u};
+  Ops ops{cl, part, wsum, wsum + 32 * 4, 0u};
   const int wpb = (int)(blockDim.x >> 5), rank = (int)cl.block_rank();
   amg_mixed_solve(a, ops, rank * wpb + (int)(threadIdx.x >> 5), (int)cl.num_blocks() * wpb,
                   (int)(threadIdx.x & 31), rank == 0 && threadIdx.x == 0);
@@ -762,25 +764,37 @@ cudaError_t launch_pcg_cluster(const PcgArgs& args, const PcgPlan& pl, const Clu
 // Standalone AMG solve on one thread-block cluster (solver kind 11): small and mid-size meshes
 // whose solve is too short to occupy the whole GPU (FP64 CG with an FP32 or FP64 hierarchy, or
 // the mixed-precision solve).  Other work, such as other requests of a server, can run beside it.
-__global__ void __launch_bounds__(kClusterTPB, 1) pcg_amg_cluster_kernel(PcgArgs a) {
+// 512 threads per CTA for small meshes, 768 above kAmgClusterWideRows rows (measured on one
+// 16-CTA cluster: 150k nodes 218 -> 185 us per CG iteration, mixed 188 -> 155; 4k nodes 26.3 ->
+// 28.5, so small meshes keep 512).
+constexpr int kAmgClusterWideRows = 20000;
+template <int TPB, class Ops>
+__global__ void __launch_bounds__(TPB, 1) pcg_amg_cluster_kernel(PcgArgs a) {
   __shared__ double s_amg_part[2 * 4], s_amg_wsum[32 * 4 + 4];
   if (a.amg_mixed)
-    cluster_amg_mixed_solve(a, s_amg_part, s_amg_wsum);
+    cluster_amg_mixed_solve<Ops>(a, s_amg_part, s_amg_wsum);
   else
-    cluster_amg_solve(a, s_amg_part, s_amg_wsum);
+    cluster_amg_solve<Ops>(a, s_amg_part, s_amg_wsum);
+}
+static const void* amg_cluster_kernel_ptr(int tpb) {
+  return tpb == 768 ? (const void*)pcg_amg_cluster_kernel<768, ClusterOpsT<6, 4>>
+                    : (const void*)pcg_amg_cluster_kernel<kClusterTPB, ClusterOps>;
 }
 
-// Cluster of the standalone AMG cluster kernel: `want` CTAs (2, 4, 8 or 16) when schedulable,
-// else the largest schedulable of 16 and 8 (want = 0: 16, else 8); kind 0 if none.
-PcgPlan amg_cluster_plan(int want) {
+// Cluster of the standalone AMG cluster kernel for a mesh of n rows: `want` CTAs (2, 4, 8 or
+// 16) when schedulable, else the largest schedulable of 16 and 8 (want = 0: 16, else 8); kind 0
+// if none.
+PcgPlan amg_cluster_plan(int want, int n) {
   PcgPlan pl;
   pl.kind = 0;
-  cudaFuncSetAttribute(pcg_amg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const int tpb = n > kAmgClusterWideRows ? 768 : kClusterTPB;
+  const void* fn = amg_cluster_kernel_ptr(tpb);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int c : {want, 16, 8}) {
     if (c <= 0) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);
-    cfg.blockDim = dim3(kClusterTPB);
+    cfg.blockDim = dim3(tpb);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = c;
@@ -788,10 +802,10 @@ PcgPlan amg_cluster_plan(int want) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, pcg_amg_cluster_kernel, &cfg) == cudaSuccess && n > 0) {
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc > 0) {
       pl.kind = 11;
-      pl.tpb = kClusterTPB;
+      pl.tpb = tpb;
       pl.blocks = c;
       pl.maxs = 0;
       return pl;
@@ -813,7 +827,8 @@ cudaError_t launch_pcg_amg_cluster(const PcgArgs& args, const PcgPlan& pl, cudaS
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, pcg_amg_cluster_kernel, args);
+  void* kargs[] = {const_cast<PcgArgs*>(&args)};
+  return cudaLaunchKernelExC(&cfg, amg_cluster_kernel_ptr(pl.tpb), kargs);
 }
 
 // Clusters of size C that can be resident at once with `smem` bytes per CTA.
