@@ -227,9 +227,10 @@ NCU_DRAM_BYTES_PER_ITER = {
     # pcg_fp64_res_kernel: 300-iteration capture, L2-resident working set
     2: ((72.372224e6 + 2.023936e6) / 300.0, "ncu DRAM read+write of a 300-iteration capture scaled to the "
                                             "launch's iterations (L2-resident working set)"),
-    # pcg_amg_kernel<768, float>: one 21-iteration solve (two-phase V-cycle, Jacobi smoother)
-    8: ((3633.821e6 + 526.636e6) / 21.0, "ncu DRAM read+write of a 21-iteration solve scaled to the launch's "
-                                         "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
+    # pcg_amg_kernel<1024, float>: one 21-iteration solve (two-phase V-cycle, Jacobi smoother,
+    # spill-free streams)
+    8: ((3574.051e6 + 28.363e6) / 21.0, "ncu DRAM read+write of a 21-iteration solve scaled to the launch's "
+                                        "iterations (profiles/pcg_amg_kernel_pin_plane_500x1000.md)"),
 }
 
 
