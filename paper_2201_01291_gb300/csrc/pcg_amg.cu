@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(TPB, 1) pcg_amg_kernel(PcgArgs a) {
 // (van der Vorst's iteration with M^-1 applied on the right, so x is updated directly and the
 // stopping test stays on the true scaled residual of the free rows).  Two V-cycles per
 // iteration; breakdowns and a true residual still too large restart from the true residual.
+// The products with A stream the matrix by contiguous slice shares (spmv_stream, each row's own
+// operands fetched ahead), the elementwise phases take slices round-robin.
 // The solve of one system by the blocks taking part in `fs` (gwarp / nwarps number their warps,
 // `leader` is the one thread that writes the statistics); false if a wait was abandoned.
 template <typename T>
@@ -97,6 +99,13 @@ __device__ bool amg_bicgstab_solve(const PcgArgs& a, const AmgDevT<T>* __restric
   double* __restrict__ sh = a.bcg + 4 * Np;
   GridOps ops{fs, smem};
   double dummy = 0.0;
+  // the matrix as a streamed operator (products by contiguous slice shares, see spmv_stream)
+  const SellMatT<double> A0{a.A.sl_ptr, a.A.sl_w, a.A.rlen, a.A.col, a.A.aval, N, nsl, 1};
+  int ma, mb;
+  warp_slices(nsl, gwarp, nwarps, ma, mb);
+  struct Two {
+    double u, w;
+  };
 
   const double gain = dirichlet_gain(a);
   const int hist = history_length(a);
@@ -136,14 +145,18 @@ __device__ bool amg_bicgstab_solve(const PcgArgs& a, const AmgDevT<T>* __restric
         if (restart) {
           // ---- true residual; rh = p = r; first V-cycle direction of p
           double r2[1] = {0.0};
-          for (int sl = gwarp; sl < nsl; sl += nwarps) {
-            const int i = sl * kSlice + lane;
-            if (i >= N) continue;
-            const double ri = a.b[i] - sell_row_dot(a.A, sl, lane, i, x);
-            r[i] = ri;
-            rh[i] = ri;
-            p[i] = ri;
-            r2[0] = fma(ri, ri, r2[0]);
+          {
+            const double* __restrict__ bv = a.b;
+            const double* __restrict__ xv = x;
+            spmv_stream<double, GridOps::kStream64>(
+                A0, ma, mb, lane, [xv](int c) { return __ldca(xv + c); }, [bv](int i) { return bv[i]; },
+                [&](int i, double ax, double bi) {
+                  const double ri = bi - ax;
+                  r[i] = ri;
+                  rh[i] = ri;
+                  p[i] = ri;
+                  r2[0] = fma(ri, ri, r2[0]);
+                });
           }
           if (!grid_allsum<1>(r2, fs, smem)) return false;
           rr_true = r2[0];
@@ -163,12 +176,15 @@ __device__ bool amg_bicgstab_solve(const PcgArgs& a, const AmgDevT<T>* __restric
         // ---- p^ = M p, then P1: v = A p^
         if (!vcycle(H, (const double*)p, ph, ops, gwarp, nwarps, lane, false, dummy)) return false;
         double rv[1] = {0.0};
-        for (int sl = gwarp; sl < nsl; sl += nwarps) {
-          const int i = sl * kSlice + lane;
-          if (i >= N) continue;
-          const double w = sell_row_dot(a.A, sl, lane, i, ph);
-          v[i] = w;
-          rv[0] = fma(rh[i], w, rv[0]);
+        {
+          const double* __restrict__ phv = ph;
+          const double* __restrict__ rhv = rh;
+          spmv_stream<double, GridOps::kStream64>(
+              A0, ma, mb, lane, [phv](int c) { return __ldca(phv + c); }, [rhv](int i) { return rhv[i]; },
+              [&](int i, double w, double rhi) {
+                v[i] = w;
+                rv[0] = fma(rhi, w, rv[0]);
+              });
         }
         double al[1];
         const double rho_now = rho;
@@ -209,16 +225,21 @@ __device__ bool amg_bicgstab_solve(const PcgArgs& a, const AmgDevT<T>* __restric
         // ---- s^ = M s, then P3: t = A s^
         if (!vcycle(H, (const double*)sv, sh, ops, gwarp, nwarps, lane, false, dummy)) return false;
         double d4[4] = {0.0, 0.0, 0.0, 0.0};  // t.s, t.t, rh.s, rh.t
-        for (int sl = gwarp; sl < nsl; sl += nwarps) {
-          const int i = sl * kSlice + lane;
-          if (i >= N) continue;
-          const double ti = sell_row_dot(a.A, sl, lane, i, sh);
-          const double si = sv[i], rhi = rh[i];
-          tv[i] = ti;
-          d4[0] = fma(ti, si, d4[0]);
-          d4[1] = fma(ti, ti, d4[1]);
-          d4[2] = fma(rhi, si, d4[2]);
-          d4[3] = fma(rhi, ti, d4[3]);
+        {
+          const double* __restrict__ shv = sh;
+          const double* __restrict__ svv = sv;
+          const double* __restrict__ rhv = rh;
+          spmv_stream<double, GridOps::kStream64>(
+              A0, ma, mb, lane, [shv](int c) { return __ldca(shv + c); },
+              [svv, rhv](int i) { return Two{svv[i], rhv[i]}; },
+              [&](int i, double ti, const Two& o) {
+                const double si = o.u, rhi = o.w;
+                tv[i] = ti;
+                d4[0] = fma(ti, si, d4[0]);
+                d4[1] = fma(ti, ti, d4[1]);
+                d4[2] = fma(rhi, si, d4[2]);
+                d4[3] = fma(rhi, ti, d4[3]);
+              });
         }
         double e3[3];
         if (!grid_allsum<4, 3>(d4, e3, fs, smem, [rho_now, alpha](const double* t, double* e) {
