@@ -334,7 +334,9 @@ int solver_levels(avip_mesh_t h, int64_t* out, int32_t max_levels);
  *                  not be stepped on their own while the batch runs;
  *   cluster_size:  2, 4, 8 or 16 CTAs per cluster, or 0 to pick by timing each on the batch
  *                  (the instances' state is saved and restored around the trial): fewer, larger
- *                  clusters solve each instance faster, more, smaller ones run more at once.
+ *                  clusters solve each instance faster, more, smaller ones run more at once; with
+ *                  0 the block of the drift-diffusion stages (256 or 128 threads, i.e. the rows
+ *                  and edges each block takes) is then timed the same way (256 otherwise).
  * AVIP_EINVAL if an instance solved by the shared-memory Jacobi-PCG does not fit one cluster's
  * shared memory (it holds every vector of its instance there; about 100k nodes at most with 16
  * CTAs); instances with an AMG hierarchy keep their vectors in global memory. */
@@ -342,8 +344,12 @@ typedef struct avip_batch* avip_batch_t;
 int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size, avip_batch_t* out);
 /* nsteps steps of every instance; stats[count] (may be NULL) receives per-instance statistics. */
 int batch_run_steps(avip_batch_t b, int32_t nsteps, avip_stats* stats);
-/* info[4] = {cluster size, resident clusters, dynamic shared memory bytes per CTA, count}. */
+/* info[5] = {cluster size, resident clusters, dynamic shared memory bytes per CTA, count,
+ * threads per block of the drift-diffusion stages}. */
 int batch_info(avip_batch_t b, int64_t* info);
+/* Set the block of the batch's drift-diffusion stages (128 or 256 threads; AVIP_EINVAL
+ * otherwise), overriding the autotuner's choice; results do not depend on it. */
+int batch_set_dd_threads(avip_batch_t b, int32_t threads);
 int batch_destroy(avip_batch_t b);
 
 /* No-allocation Jacobi-preconditioned CG for callers that cannot allocate device memory.

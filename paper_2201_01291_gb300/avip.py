@@ -86,6 +86,7 @@ _SIGS = {
     "batch_create": (C.c_int, [_P(_H), C.c_int32, C.c_int32, _P(_H)]),
     "batch_run_steps": (C.c_int, [_H, C.c_int32, C.c_void_p]),
     "batch_info": (C.c_int, [_H, _P(C.c_int64)]),
+    "batch_set_dd_threads": (C.c_int, [_H, C.c_int32]),
     "batch_destroy": (C.c_int, [_H]),
     "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_int32, C.c_void_p, _I, _D]),
@@ -357,9 +358,14 @@ def batch_run_steps(b, nsteps, count):
 
 
 def batch_info(b):
-    info = np.zeros(4, dtype=np.int64)
+    info = np.zeros(5, dtype=np.int64)
     _check(load().batch_info(b, info.ctypes.data_as(_P(C.c_int64))), "batch_info")
-    return dict(cluster_size=int(info[0]), clusters=int(info[1]), smem_bytes=int(info[2]), count=int(info[3]))
+    return dict(cluster_size=int(info[0]), clusters=int(info[1]), smem_bytes=int(info[2]), count=int(info[3]),
+                dd_threads=int(info[4]))
+
+
+def batch_set_dd_threads(b, threads):
+    return load().batch_set_dd_threads(b, int(threads))
 
 
 def batch_destroy(b):

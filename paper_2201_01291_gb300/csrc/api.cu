@@ -37,6 +37,7 @@ cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st);
 cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st);
 int flux_blocks(int N);
+int flux_partials_max(int N);
 }  // namespace avip
 
 using namespace avip;
@@ -711,7 +712,8 @@ int mesh_create_hybrid(const double* xy, int32_t n_nodes, const int32_t* tris, i
   }
   h->nparts = flux_blocks(m.N);
   h->sync_bytes = sizeof(GridSync) + sizeof(unsigned) * (size_t)(h->plan.blocks + 1);
-  ok = ok && zalloc(h, h->parts, (size_t)h->plan.blocks * 8) && zalloc(h, h->qpart, (size_t)h->nparts) &&
+  ok = ok && zalloc(h, h->parts, (size_t)h->plan.blocks * 8) &&
+       zalloc(h, h->qpart, (size_t)std::max(h->nparts, flux_partials_max(m.N))) &&
        zalloc(h, h->sync, (h->sync_bytes + sizeof(GridSync) - 1) / sizeof(GridSync)) && zalloc(h, h->sc, 1);
   if (ok) h->flags = reinterpret_cast<unsigned*>(h->sync + 1);
   if (!ok) {
@@ -1244,7 +1246,7 @@ PcgPlan pcg_cluster_plan_fixed(const HostMesh& m, int C, ClusterLayout* out, Clu
 cudaError_t launch_pcg_cluster_batch(const PcgArgs* args, const ClusterLayout* lays, const int32_t* order, int count,
                                      int C, int nclusters, size_t smem, cudaStream_t st);
 cudaError_t launch_dd_batch(const DDArgs* args, const int32_t* node_pref, const int32_t* cell_pref, int count,
-                            int node_blocks, int cell_blocks, cudaStream_t st);
+                            int node_blocks, int cell_blocks, int threads, cudaStream_t st);
 cudaError_t launch_run_reset_batch(const DDArgs* args, int count, cudaStream_t st);
 int dd_threads();
 }  // namespace avip
@@ -1260,6 +1262,7 @@ struct avip_batch {
   DDArgs* d_dargs = nullptr;
   int32_t *d_order = nullptr, *d_npref = nullptr, *d_cpref = nullptr;
   int node_blocks = 0, cell_blocks = 0;
+  int dd_threads = 256;  // threads per block of the drift-diffusion stages (autotuned)
   cudaGraphExec_t graph = nullptr;
   // per candidate cluster size: layouts (device arrays owned by the batch)
   std::vector<ClusterLayout> lays;
@@ -1329,22 +1332,49 @@ bool batch_configure(avip_batch* b, int C) {
   return b->d_lays != nullptr;
 }
 
+// Partition of the drift-diffusion stages: T threads per block, each instance's nodes and cells
+// in whole blocks (block prefix sums in instance order); false if the tables cannot be written.
+bool batch_set_dd(avip_batch* b, int T) {
+  const int count = (int)b->m.size();
+  std::vector<int32_t> npref(count + 1, 0), cpref(count + 1, 0);
+  for (int k = 0; k < count; ++k) {
+    npref[k + 1] = npref[k] + (b->m[k]->hm.N + T - 1) / T;
+    cpref[k + 1] = cpref[k] + (b->m[k]->hm.T + T - 1) / T;
+  }
+  if (cudaMemcpyAsync(b->d_npref, npref.data(), npref.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_cpref, cpref.data(), cpref.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b->node_blocks = npref[count];
+  b->cell_blocks = cpref[count];
+  b->dd_threads = T;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  return true;
+}
+
 cudaError_t batch_enqueue_step(avip_batch* b) {
   cudaError_t e = launch_pcg_cluster_batch(b->d_pargs, b->d_lays, b->d_order, (int)b->m.size(), b->C, b->nclusters,
                                            b->smem, b->stream);
   if (e != cudaSuccess) return e;
   return launch_dd_batch(b->d_dargs, b->d_npref, b->d_cpref, (int)b->m.size(), b->node_blocks, b->cell_blocks,
-                         b->stream);
+                         b->dd_threads, b->stream);
 }
 
-// Save (dir = 0) or restore (dir = 1) every instance's densities, potential and scalars.
+// Save (dir = 0) or restore (dir = 1) every instance's densities, potential, predictor history
+// and scalars.
 cudaError_t batch_snapshot(avip_batch* b, std::vector<void*>& buf, int dir) {
   cudaError_t e = cudaSuccess;
   size_t j = 0;
   for (avip_mesh* h : b->m) {
     const size_t nb = (size_t)2 * AVIP_MAX_SPECIES * h->Npad * sizeof(double);
     const size_t pb = (size_t)h->Npad * sizeof(double);
-    struct Item { void* dev; size_t bytes; } items[3] = {{h->nbuf, nb}, {h->phi, pb}, {h->sc, sizeof(DevScalars)}};
+    struct Item { void* dev; size_t bytes; } items[6] = {{h->nbuf, nb},  {h->phi, pb},  {h->phi1, pb},
+                                                        {h->phi2, pb}, {h->phi3, pb}, {h->sc, sizeof(DevScalars)}};
     for (auto& it : items) {
       if (dir == 0) {
         void* p = batch_alloc(b, it.bytes);
@@ -1394,25 +1424,20 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
   std::vector<PcgArgs> pa(count);
   std::vector<DDArgs> da(count);
   std::vector<int32_t> order(count), npref(count + 1, 0), cpref(count + 1, 0);
-  const int T = dd_threads();
   for (int k = 0; k < count; ++k) {
     pa[k] = pcg_args(b->m[k]);
     da[k] = dd_args(b->m[k]);
     da[k].eflux = nullptr;  // batched flux kernel: each row evaluates its edges
     da[k].partials = b->m[k]->qpart;
     order[k] = k;
-    npref[k + 1] = npref[k] + (b->m[k]->hm.N + T - 1) / T;
-    cpref[k + 1] = cpref[k] + (b->m[k]->hm.T + T - 1) / T;
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->m[x]->hm.N > b->m[y]->hm.N; });
-  b->node_blocks = npref[count];
-  b->cell_blocks = cpref[count];
   b->d_pargs = batch_upload(b, pa);
   b->d_dargs = batch_upload(b, da);
   b->d_order = batch_upload(b, order);
   b->d_npref = batch_upload(b, npref);
   b->d_cpref = batch_upload(b, cpref);
-  if (!b->d_pargs || !b->d_dargs || !b->d_order || !b->d_npref || !b->d_cpref) {
+  if (!b->d_pargs || !b->d_dargs || !b->d_order || !b->d_npref || !b->d_cpref || !batch_set_dd(b, dd_threads())) {
     batch_free(b);
     cudaStreamDestroy(b->stream);
     delete b;
@@ -1422,32 +1447,51 @@ int batch_create(const avip_mesh_t* meshes, int32_t count, int32_t cluster_size,
   if (cluster_size != 0) {
     ok = batch_configure(b, cluster_size);
   } else {
-    // autotune: time two steps per feasible cluster size (16, 8, 4 or 2 CTAs: fewer, faster
-    // clusters or more, smaller ones) on the batch itself, then restore
+    // autotune on the batch itself, then restore its state: the cluster size of the solves
+    // (16, 8, 4 or 2 CTAs: fewer, faster clusters or more, smaller ones), timed over two steps,
+    // then for that size the block (node and cell partition) of the drift-diffusion stages,
+    // 256 or 128 threads, timed over the stages alone
     std::vector<void*> snap;
     cudaError_t e = batch_snapshot(b, snap, 0);
-    float best = 0.f;
-    int bestC = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int C : {16, 8, 4, 2}) {
-      if (e != cudaSuccess || !batch_configure(b, C)) continue;
+    auto timed = [&](auto&& body, float& ms) {
       e = cudaEventRecord(e0, b->stream);
-      for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = batch_enqueue_step(b);
+      for (int s = 0; s < 2 && e == cudaSuccess; ++s) e = body();
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
+      ms = 0.f;
       if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess) e = batch_snapshot(b, snap, 1);
+    };
+    float best = 0.f;
+    int bestC = 0;
+    for (int C : {16, 8, 4, 2}) {
+      if (e != cudaSuccess || !batch_configure(b, C)) continue;
+      float ms = 0.f;
+      timed([&] { return batch_enqueue_step(b); }, ms);
       if (e == cudaSuccess && (bestC == 0 || ms < best)) {
         best = ms;
         bestC = C;
       }
-      if (e == cudaSuccess) e = batch_snapshot(b, snap, 1);
+    }
+    if (e == cudaSuccess && bestC != 0) ok = batch_configure(b, bestC);
+    float bestT_ms = 0.f;
+    int bestT = 0;
+    for (int T : {256, 128}) {
+      if (!ok || e != cudaSuccess || !batch_set_dd(b, T)) continue;
+      float ms = 0.f;
+      timed([&] { return launch_dd_batch(b->d_dargs, b->d_npref, b->d_cpref, (int)b->m.size(), b->node_blocks,
+                                         b->cell_blocks, b->dd_threads, b->stream); }, ms);
+      if (e == cudaSuccess && (bestT == 0 || ms < bestT_ms)) {
+        bestT_ms = ms;
+        bestT = T;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (e == cudaSuccess && bestC != 0) ok = batch_configure(b, bestC);
+    if (ok && e == cudaSuccess && bestT != 0) ok = batch_set_dd(b, bestT);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) ok = false;
   }
@@ -1478,7 +1522,13 @@ int batch_info(avip_batch_t b, int64_t* info) {
   info[1] = b->nclusters;
   info[2] = (int64_t)b->smem;
   info[3] = (int64_t)b->m.size();
+  info[4] = b->dd_threads;
   return AVIP_OK;
+}
+
+int batch_set_dd_threads(avip_batch_t b, int32_t threads) {
+  if (!b || (threads != 128 && threads != 256)) return AVIP_EINVAL;
+  return batch_set_dd(b, threads) ? AVIP_OK : AVIP_ECUDA;
 }
 
 int batch_run_steps(avip_batch_t b, int32_t nsteps, avip_stats* stats) {

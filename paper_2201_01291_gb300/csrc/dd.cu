@@ -26,6 +26,7 @@
 namespace avip {
 
 constexpr int kDDThreads = 256;
+constexpr int kDDMinThreads = 128;  // smallest block of the batched stages (autotuned)
 
 // Local-field mobility and the Townsend exponential with the library's FP64 exp / log
 // (fp64_math.cuh: a few ulp, a fraction of the FP64 instructions of the general routines).
@@ -841,9 +842,9 @@ __global__ void __launch_bounds__(kDDThreads, 1) flux_update_batch_kernel(const 
   else
     flux_update_body(args[k], blockIdx.x - __ldg(bpref + k));
 }
-__global__ void finalize_batch_kernel(const DDArgs* __restrict__ args, int count) {
+__global__ void finalize_batch_kernel(const DDArgs* __restrict__ args, int count, int threads) {
   const DDArgs& a = args[blockIdx.x];
-  finalize_body(a.sc, a.partials, (a.A.N + kDDThreads - 1) / kDDThreads);
+  finalize_body(a.sc, a.partials, (a.A.N + threads - 1) / threads);
 }
 __global__ void run_reset_batch_kernel(const DDArgs* __restrict__ args, int count) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -897,13 +898,18 @@ cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st) {
   return cudaGetLastError();
 }
 int flux_blocks(int N) { return nblk(N); }
+// Charge partials a handle must hold: one per block at the smallest batched block size.
+int flux_partials_max(int N) { return (N + kDDMinThreads - 1) / kDDMinThreads; }
 
+// The drift-diffusion stages of a batch with `threads` threads per block (kDDMinThreads ..
+// kDDThreads, a multiple of 32; the block prefix sums node_pref / cell_pref were made for it).
 cudaError_t launch_dd_batch(const DDArgs* args, const int32_t* node_pref, const int32_t* cell_pref, int count,
-                            int node_blocks, int cell_blocks, cudaStream_t st) {
-  node_fields_batch_kernel<<<node_blocks, kDDThreads, 0, st>>>(args, node_pref, count);
-  dt_cells_batch_kernel<<<cell_blocks, kDDThreads, 0, st>>>(args, cell_pref, count);
-  flux_update_batch_kernel<<<node_blocks, kDDThreads, 0, st>>>(args, node_pref, count);
-  finalize_batch_kernel<<<count, 256, 0, st>>>(args, count);
+                            int node_blocks, int cell_blocks, int threads, cudaStream_t st) {
+  if (threads < kDDMinThreads || threads > kDDThreads || threads % 32) return cudaErrorInvalidValue;
+  node_fields_batch_kernel<<<node_blocks, threads, 0, st>>>(args, node_pref, count);
+  dt_cells_batch_kernel<<<cell_blocks, threads, 0, st>>>(args, cell_pref, count);
+  flux_update_batch_kernel<<<node_blocks, threads, 0, st>>>(args, node_pref, count);
+  finalize_batch_kernel<<<count, 256, 0, st>>>(args, count, threads);
   return cudaGetLastError();
 }
 cudaError_t launch_run_reset_batch(const DDArgs* args, int count, cudaStream_t st) {

@@ -30,6 +30,13 @@ def test_batch_equals_alone(avip, cluster_size):
     nsteps = 8
     batch_meshes = [avip.Mesh(p, rtol=1e-13, pcg_kind=5) for p in ps]  # the shared-memory Jacobi solver
     b = avip.Batch(batch_meshes, cluster_size=cluster_size)
+    # the drift-diffusion block: tuned with cluster_size 0, else 256; set to 128 for 8 CTAs so
+    # that both partitions are exercised
+    assert b.info["dd_threads"] in ((128, 256) if cluster_size == 0 else (256,))
+    if cluster_size == 8:
+        assert avip.batch_set_dd_threads(b.b, 128) == avip.AVIP_OK
+        assert avip.batch_set_dd_threads(b.b, 96) == avip.AVIP_EINVAL
+        assert avip.batch_info(b.b)["dd_threads"] == 128
     st = b.run(nsteps)
     assert all(s["steps"] == nsteps for s in st)
     C = b.info["cluster_size"]
