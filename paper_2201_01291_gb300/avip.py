@@ -302,10 +302,15 @@ def solver_levels(h, max_levels=12):
     return [tuple(int(v) for v in out[LEVEL_STATS * l:LEVEL_STATS * (l + 1)]) for l in range(min(nl, max_levels))]
 
 
-def state_get(h):
+def state_get(h, out=None):
+    """(rc, state); `out` (float64, contiguous, state_size long, e.g. a view of pinned host
+    memory) receives the state when given."""
     n = C.c_int64()
     _check(load().state_size(h, C.byref(n)), "state_size")
-    out = np.empty(n.value)
+    if out is None:
+        out = np.empty(n.value)
+    elif out.dtype != np.float64 or out.size != n.value or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("state_get: out must be a contiguous float64 array of state_size entries")
     return load().state_get(h, _dptr(out)), out
 
 
@@ -502,8 +507,8 @@ class Mesh:
         _check(rc, "photo_stats")
         return st
 
-    def state(self):
-        rc, st = state_get(self.h)
+    def state(self, out=None):
+        rc, st = state_get(self.h, out)
         _check(rc, "state_get")
         return st
 

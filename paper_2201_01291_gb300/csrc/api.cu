@@ -37,6 +37,9 @@ cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st);
 cudaError_t launch_finalize(DevScalars* sc, const double* partials, int nparts, cudaStream_t st);
 cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st);
 int flux_blocks(int N);
+cudaError_t launch_state_take(const StateArgs& s, cudaStream_t st);
+cudaError_t launch_state_check(const StateArgs& s, cudaStream_t st);
+cudaError_t launch_state_put(const StateArgs& s, cudaStream_t st);
 int flux_partials_max(int N);
 }  // namespace avip
 
@@ -92,6 +95,11 @@ struct avip_mesh {
   // whole-GPU AMG solvers (kinds 8, 9): the terms are solved side by side in one launch, each on
   // its own group of blocks, with per term its own Krylov vectors (kPhotoWork x Npad doubles),
   // FP32 residual copies (3 x Npad floats, FP32 hierarchy) and barrier state
+  // checkpoint copies (allocated at the first state_get / state_set): the node permutation and
+  // the state in the caller's layout on the device, and a validation flag
+  int32_t* d_perm = nullptr;
+  double* d_stage = nullptr;
+  int32_t* d_state_flag = nullptr;
   bool photo_group = false;
   double* photo_work = nullptr;
   float* photo_rq32 = nullptr;
@@ -1169,64 +1177,67 @@ int state_size(avip_mesh_t h, int64_t* n) {
   return AVIP_OK;
 }
 
-int state_get(avip_mesh_t h, double* out) {
-  if (!ready(h) || !out) return AVIP_EINVAL;
-  const int32_t N = h->hm.N;
-  for (int s = 0; s < h->ph.ns; ++s) {
-    int rc = field_get(h, AVIP_FIELD_DENSITY, s, out + (size_t)s * N);
-    if (rc) return rc;
-  }
-  int rc = field_get(h, AVIP_FIELD_PHI, 0, out + (size_t)h->ph.ns * N);
-  if (rc) return rc;
-  DevScalars sc;
-  rc = read_scalars(h, sc);
-  if (rc) return rc;
-  out[(size_t)(h->ph.ns + 1) * N] = sc.t;
-  // the predictor's history: phi_{n-1}, phi_{n-2}, phi_{n-3} and how many of them are valid
-  double* hist = out + (size_t)(h->ph.ns + 1) * N + 1;
-  if ((rc = to_host_perm(h, h->phi1, hist)) != AVIP_OK) return rc;
-  if ((rc = to_host_perm(h, h->phi2, hist + N)) != AVIP_OK) return rc;
-  if ((rc = to_host_perm(h, h->phi3, hist + 2 * (size_t)N)) != AVIP_OK) return rc;
-  hist[kPredictorHistory * (size_t)N] = (double)sc.phi_hist;
-  return AVIP_OK;
+// Device buffers of the checkpoint copies; false if they cannot be allocated.
+static bool state_buffers(avip_mesh* h) {
+  if (h->d_stage) return true;
+  int64_t n = 0;
+  state_size(h, &n);
+  return upload(h, h->d_perm, h->hm.perm) && zalloc(h, h->d_stage, (size_t)n) && zalloc(h, h->d_state_flag, 1);
 }
 
+static StateArgs state_args(avip_mesh* h) {
+  StateArgs s;
+  std::memset(&s, 0, sizeof(s));
+  s.N = h->hm.N;
+  s.ns = h->ph.ns;
+  s.Npad = h->Npad;
+  s.perm = h->d_perm;
+  s.stage = h->d_stage;
+  s.nbuf = h->nbuf;
+  s.phi = h->phi;
+  s.phi1 = h->phi1;
+  s.phi2 = h->phi2;
+  s.phi3 = h->phi3;
+  s.sc = h->sc;
+  s.flag = h->d_state_flag;
+  return s;
+}
+
+// One kernel writes the state in the caller's layout to device memory, one copy brings it to
+// `out` (pinned host memory makes that copy a direct transfer).
+int state_get(avip_mesh_t h, double* out) {
+  if (!ready(h) || !out) return AVIP_EINVAL;
+  if (!state_buffers(h)) return AVIP_ENOMEM;
+  int64_t n = 0;
+  state_size(h, &n);
+  cudaError_t e = launch_state_take(state_args(h), h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->d_stage, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+// One copy brings the caller's state to device memory, a kernel checks that every entry is
+// finite (AVIP_ENAN, and nothing installed, otherwise), another installs it.
 int state_set(avip_mesh_t h, const double* in) {
   if (!ready(h) || !in) return AVIP_EINVAL;
-  const int32_t N = h->hm.N;
-  DevScalars sc;
-  int rc = read_scalars(h, sc);
-  if (rc) return rc;
-  std::vector<double> tmp(N);
-  cudaError_t e = cudaSuccess;
-  for (int s = 0; s <= h->ph.ns && e == cudaSuccess; ++s) {
-    const double* src = in + (size_t)s * N;
-    for (int32_t i = 0; i < N; ++i) {
-      tmp[i] = src[h->hm.perm[i]];
-      if (!std::isfinite(tmp[i])) return AVIP_ENAN;
-    }
-    double* dst = s < h->ph.ns ? h->nbuf + ((size_t)sc.parity * AVIP_MAX_SPECIES + s) * h->Npad : h->phi;
-    e = cudaMemcpyAsync(dst, tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  }
-  if (e != cudaSuccess) return cuda_status(e);
-  const double t = in[(size_t)(h->ph.ns + 1) * N];
-  const double* hist = in + (size_t)(h->ph.ns + 1) * N + 1;
-  const double hn = hist[kPredictorHistory * (size_t)N];
+  const size_t N = (size_t)h->hm.N;
+  const double hn = in[(size_t)(h->ph.ns + 1) * N + 1 + kPredictorHistory * N];
   if (!(hn >= 0.0 && hn <= (double)kPredictorHistory && hn == std::floor(hn))) return AVIP_EINVAL;
-  const int32_t hv = (int32_t)hn;
-  double* const dst_hist[kPredictorHistory] = {h->phi1, h->phi2, h->phi3};
-  for (int k = 0; k < kPredictorHistory && e == cudaSuccess; ++k) {
-    for (int32_t i = 0; i < N; ++i) {
-      tmp[i] = hist[(size_t)k * N + h->hm.perm[i]];
-      if (!std::isfinite(tmp[i])) return AVIP_ENAN;
-    }
-    e = cudaMemcpyAsync(dst_hist[k], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&h->sc->phi_hist, &hv, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+  if (!state_buffers(h)) return AVIP_ENOMEM;
+  int64_t n = 0;
+  state_size(h, &n);
+  StateArgs sa = state_args(h);
+  sa.t = in[(size_t)(h->ph.ns + 1) * N];
+  sa.hist = (int32_t)hn;
+  int32_t flag = 0;
+  cudaError_t e = cudaMemcpyAsync(h->d_stage, in, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_state_flag, 0, sizeof(int32_t), h->stream);
+  if (e == cudaSuccess) e = launch_state_check(sa, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, h->d_state_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (flag) return AVIP_ENAN;
+  e = launch_state_put(sa, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return cuda_status(e);
 }

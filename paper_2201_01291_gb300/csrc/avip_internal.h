@@ -365,6 +365,20 @@ __device__ __forceinline__ bool solve_skipped(const DevScalars* sc) {
 }
 #endif
 
+// Checkpoint copies between the caller's layout (caller numbering: densities, phi, t, the
+// predictor history, its count) and the device state: perm[i] is the caller index of internal
+// node i, stage the state in the caller's layout (device memory).
+struct StateArgs {
+  int32_t N, ns, Npad;
+  const int32_t* perm;
+  double* stage;
+  double *nbuf, *phi, *phi1, *phi2, *phi3;
+  DevScalars* sc;
+  int32_t* flag;  // state_check: set to 1 when an entry is not finite
+  double t;       // state_put: simulated time and predictor history count to install
+  int32_t hist;
+};
+
 struct DDArgs {
   SellView A;
   Physics ph;

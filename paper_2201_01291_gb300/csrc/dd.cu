@@ -897,6 +897,64 @@ cudaError_t launch_run_reset(DevScalars* sc, cudaStream_t st) {
   run_reset_kernel<<<1, 1, 0, st>>>(sc);
   return cudaGetLastError();
 }
+// ------------------------------------------------------------------ checkpoint copies
+// state_get: the device state in the caller's layout (one coalesced read per field, a scattered
+// write to the caller positions); state_put: the reverse, after state_check has found every
+// entry finite.  Values are copied, never recomputed, so a checkpoint round trip is exact.
+__global__ void state_take_kernel(StateArgs s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N = (size_t)s.N;
+  const size_t hb = (size_t)(s.ns + 1) * N + 1;  // first predictor-history entry
+  if (i == 0) {
+    s.stage[(size_t)(s.ns + 1) * N] = s.sc->t;
+    s.stage[hb + 3 * N] = (double)s.sc->phi_hist;
+  }
+  if (i >= s.N) return;
+  const size_t c = (size_t)__ldg(s.perm + i);
+  const double* n = s.nbuf + (size_t)s.sc->parity * AVIP_MAX_SPECIES * s.Npad;
+  for (int k = 0; k < s.ns; ++k) s.stage[k * N + c] = n[(size_t)k * s.Npad + i];
+  s.stage[s.ns * N + c] = s.phi[i];
+  s.stage[hb + c] = s.phi1[i];
+  s.stage[hb + N + c] = s.phi2[i];
+  s.stage[hb + 2 * N + c] = s.phi3[i];
+}
+__global__ void state_check_kernel(StateArgs s) {
+  const size_t total = (size_t)(s.ns + 4) * s.N + 2;
+  bool bad = false;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(s.stage[k]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(s.flag, 1);
+}
+__global__ void state_put_kernel(StateArgs s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N = (size_t)s.N;
+  const size_t hb = (size_t)(s.ns + 1) * N + 1;
+  if (i == 0) {
+    s.sc->t = s.t;
+    s.sc->phi_hist = s.hist;
+  }
+  if (i >= s.N) return;
+  const size_t c = (size_t)__ldg(s.perm + i);
+  double* n = s.nbuf + (size_t)s.sc->parity * AVIP_MAX_SPECIES * s.Npad;
+  for (int k = 0; k < s.ns; ++k) n[(size_t)k * s.Npad + i] = s.stage[k * N + c];
+  s.phi[i] = s.stage[s.ns * N + c];
+  s.phi1[i] = s.stage[hb + c];
+  s.phi2[i] = s.stage[hb + N + c];
+  s.phi3[i] = s.stage[hb + 2 * N + c];
+}
+cudaError_t launch_state_take(const StateArgs& s, cudaStream_t st) {
+  state_take_kernel<<<nblk(s.N), kDDThreads, 0, st>>>(s);
+  return cudaGetLastError();
+}
+cudaError_t launch_state_check(const StateArgs& s, cudaStream_t st) {
+  state_check_kernel<<<nblk(s.N), kDDThreads, 0, st>>>(s);
+  return cudaGetLastError();
+}
+cudaError_t launch_state_put(const StateArgs& s, cudaStream_t st) {
+  state_put_kernel<<<nblk(s.N), kDDThreads, 0, st>>>(s);
+  return cudaGetLastError();
+}
+
 int flux_blocks(int N) { return nblk(N); }
 // Charge partials a handle must hold: one per block at the smallest batched block size.
 int flux_partials_max(int N) { return (N + kDDMinThreads - 1) / kDDMinThreads; }

@@ -125,6 +125,30 @@ def test_checkpoint_resume_bitwise(avip):
     np.testing.assert_array_equal(a.state(), b.state())
 
 
+def test_checkpoint_rejects_bad_state_and_fills_given_buffer(avip):
+    """state_set refuses a non-finite entry (AVIP_ENAN) or a history count outside 0..3
+    (AVIP_EINVAL) and installs nothing; state_get fills a caller buffer (here pinned host memory)
+    with the same values as a fresh array."""
+    import torch
+    p = W.config_small(nx=23, ny=19, seed=14)
+    m = avip.Mesh(p)
+    m.run(4)
+    good = m.state()
+    pinned = torch.empty(good.size, dtype=torch.float64, pin_memory=True).numpy()
+    assert m.state(out=pinned) is pinned
+    np.testing.assert_array_equal(pinned, good)
+    with pytest.raises(ValueError):
+        m.state(out=np.empty(good.size - 1))
+    bad = good.copy()
+    bad[7] = np.nan
+    assert avip.state_set(m.h, bad) == avip.AVIP_ENAN
+    bad = good.copy()
+    bad[-1] = 4.0
+    assert avip.state_set(m.h, bad) == avip.AVIP_EINVAL
+    np.testing.assert_array_equal(m.state(), good)
+    m.close()
+
+
 def test_reorder_does_not_change_results(avip):
     p = W.config_small(nx=30, ny=22, seed=5)
     a = avip.Mesh(p, rtol=1e-14, reorder=1)
