@@ -251,8 +251,10 @@ def pcg_traffic_model(info, iters, solves):
     if kind in (8, 9, 10):
         return amg_traffic_model(info["levels"], nnz, N, iters, solves, kind, sv=info.get("precond_bytes", 4))
     per_it = {1: 12 * nnz + 92 * N, 2: 12 * nnz + 24 * N, 4: 8 * nnz + 48 * N, 7: 24 * nnz + 160 * N}.get(kind, 0)
-    per_solve = {1: 24 * nnz + 100 * N, 2: 24 * nnz + 80 * N, 4: 24 * nnz + 100 * N,
-                 7: 24 * nnz + 170 * N}.get(kind, 0)
+    # per solve: the set-up (the cubic predictor reads four potentials and shifts three, the
+    # right-hand side) and the final true residual
+    per_solve = {1: 24 * nnz + 116 * N, 2: 24 * nnz + 96 * N, 4: 24 * nnz + 116 * N,
+                 7: 24 * nnz + 186 * N}.get(kind, 0)
     bytes_ = iters * per_it + solves * per_solve
     if kind == 7:
         flops = iters * (4 * nnz + 32 * N) + solves * (4 * nnz + 20 * N)
@@ -280,7 +282,8 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
     applies two V-cycles per iteration with FP64 input and output (8 - sv more per row at each
     end) and its phases add 24 nnz + 216 N bytes.  The mixed-precision solve (kind 10) runs the
     FP32 V-cycle on FP32 vectors and its inner CG moves 8 B per stored entry of A and 4 B per
-    vector element: 8 nnz + 60 N.  Per solve: set-up and the final true residual, 24 nnz + 100 N.
+    vector element: 8 nnz + 60 N.  Per solve: set-up (the cubic predictor reads four potentials
+    and shifts three) and the final true residual, 24 nnz + 116 N.
     Flops (returned: FP64 operations only, the unit the FP64 roofline compares): 2 per stored
     entry of every FP64 product and per-row vector operations; the V-cycle's own 2 per stored
     entry and 2 per row and level count only with an FP64 hierarchy (sv = 8)."""
@@ -307,7 +310,7 @@ def amg_traffic_model(levels, nnz0, N, iters, solves, kind=8, sv=4):
         per_it = (vb + sv * N + (48 + sv) * N + (16 - sv) * N
                   + 12 * nnz0 + 8 * N + 24 * N + (16 + sv) * N)
         fl_it = vf + 2 * nnz0 + 14 * N
-    per_solve = 24 * nnz0 + 100 * N
+    per_solve = 24 * nnz0 + 116 * N
     return iters * per_it + solves * per_solve, iters * fl_it + solves * (4 * nnz0 + 12 * N)
 
 
