@@ -389,12 +389,13 @@ int pcg_csr_static(int32_t n, const int32_t* row_ptr, const int32_t* col, const 
 #define AVIP_PROBE_HBM_COPY 1
 int peak_probe(int32_t which, void* stream, double* value_out);
 
-/* Accuracy check of the library's own FP64 exponential, logarithm and power (used by the
- * local-field mobility and Townsend closures of the FP64 path; the paper has no counterpart):
- * max_rel_err[3] receives the largest relative difference from the CUDA math library's exp,
- * log and pow over 65,536 log-spaced arguments (exp on [-700, 700], log on positive arguments
- * from 1e-300 to 1e300, pow on bases from 1e-6 to 1e6 with exponents -0.2, 0.5, -1.7, 2.3).  Runs
- * one kernel on the current device and waits for it.  AVIP_EINVAL, AVIP_ENOMEM, AVIP_ECUDA. */
+/* Accuracy check of the library's own FP64 exponential, logarithm, power and reciprocal (used by
+ * the local-field mobility and Townsend closures and by the limiter ratio of the FP64 path; the
+ * paper has no counterpart): max_rel_err[4] receives the largest relative difference from the
+ * CUDA math library's exp, log, pow and from the IEEE quotient 1/x over 65,536 log-spaced
+ * arguments (exp on [-700, 700], log on positive arguments from 1e-300 to 1e300, pow on bases
+ * from 1e-6 to 1e6 with exponents -0.2, 0.5, -1.7, 2.3, the reciprocal on +-1e-300 to +-1e300).
+ * Runs one kernel on the current device and waits for it.  AVIP_EINVAL, AVIP_ENOMEM, AVIP_ECUDA. */
 int fp64_math_check(double* max_rel_err);
 
 /* Human-readable text of a status code (static storage). */

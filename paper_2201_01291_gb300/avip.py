@@ -342,9 +342,9 @@ def peak_probe(which, stream=0):
 
 
 def fp64_math_check():
-    """Largest relative differences (exp, log, pow) of the library's FP64 closures' math from
-    the CUDA math library."""
-    out = np.zeros(3)
+    """Largest relative differences (exp, log, pow, reciprocal) of the library's FP64 math from
+    the CUDA math library (the IEEE quotient for the reciprocal)."""
+    out = np.zeros(4)
     rc = load().fp64_math_check(_dptr(out))
     return rc, out
 

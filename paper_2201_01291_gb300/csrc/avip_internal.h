@@ -385,6 +385,7 @@ struct DDArgs {
   const double* x;        // node coordinates
   const double* y;
   const double* vol;
+  const double* ivol;     // 1 / V_i
   const double* phi;
   double* nbuf;           // density ping-pong buffers
   double* ndat;           // per species per node: gx, gy, vx, vy (4 doubles)

@@ -327,7 +327,8 @@ __device__ __forceinline__ double edge_flux(const EdgeEnd& lo, const EdgeEnd& hi
   double psi = 0.0;
   if (delta != 0.0) {
     const double dx = W.x - U.x, dy = W.y - U.y;
-    const double r = (2.0 * (U.gx * dx + U.gy * dy) - delta) / delta;
+    // the ratio of the upwind to the local difference
+    const double r = (2.0 * (U.gx * dx + U.gy * dy) - delta) * recip_nr(delta);
     psi = (lim == AVIP_LIM_SWEBY && beta == 1.0) ? fmax(0.0, fmin(r, 1.0))  // min-mod: the same value
                                                  : limiter(r, beta, lim);
   }
@@ -411,7 +412,7 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
     }
     // boundary closure through the boundary nodal normal kept in the diagonal slot
     const double Sbx = __ldg(a.A.sx + base), Sby = __ldg(a.A.sy + base);
-    const double Vi = a.vol[i];
+    const double Vi = a.vol[i], iVi = a.ivol[i];
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s) {
@@ -423,7 +424,7 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
           Fy -= sp.D * me[s].gy;
         }
         const double rs = R[s] - (Fx * Sbx + Fy * Sby);
-        const double un = me[s].u + dt * (rs / Vi + a.src[(size_t)s * a.Npad + i]);
+        const double un = me[s].u + dt * fma(rs, iVi, a.src[(size_t)s * a.Npad + i]);
         nn[(size_t)s * a.Npad + i] = un;
         bad |= !isfinite(un);
         qsum += sp.q * (Vi * un);

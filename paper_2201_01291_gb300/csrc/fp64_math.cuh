@@ -83,4 +83,19 @@ __device__ __forceinline__ double log_fp64(double x) {
 
 __device__ __forceinline__ double pow_pos_fp64(double x, double p) { return exp_fp64(p * log_fp64(x)); }
 
+// 1 / d for a nonzero d: the hardware's approximate reciprocal refined by two Newton-Raphson
+// steps y <- y + y (1 - d y) (each squares the relative error: about 2^-20 -> 2^-40 -> the FP64
+// rounding), within a few ulp of the rounded quotient, for 5 FP64 instructions against about
+// twice that for an IEEE division.  A subnormal d (exponent field zero; the approximation
+// flushes it) takes the division.
+__device__ __forceinline__ double recip_nr(double d) {
+  if ((__double2hiint(d) & 0x7ff00000) == 0) return 1.0 / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
 }  // namespace avip

@@ -67,9 +67,10 @@ cudaError_t best_ms(cudaStream_t st, F launch, float& best) {
   return e;
 }
 
-// Largest relative difference between this library's FP64 exp / log / pow (fp64_math.cuh) and
-// the CUDA math library over log-spaced arguments: exp on [-700, 700], log on 1e-300 .. 1e300,
-// pow (exponents -0.2, 0.5, -1.7, 2.3) on bases 1e-6 .. 1e6.
+// Largest relative difference between this library's FP64 exp / log / pow / reciprocal
+// (fp64_math.cuh) and the CUDA math library (the IEEE quotient for the reciprocal) over
+// log-spaced arguments: exp on [-700, 700], log on 1e-300 .. 1e300, pow (exponents -0.2, 0.5,
+// -1.7, 2.3) on bases 1e-6 .. 1e6, the reciprocal on +-(1e-300 .. 1e300).
 constexpr int kCheckPoints = 1 << 16;
 __global__ void fp64_math_check_kernel(unsigned long long* worst) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,16 +79,18 @@ __global__ void fp64_math_check_kernel(unsigned long long* worst) {
   const double xe = -700.0 + 1400.0 * t;
   const double xl = exp10(-300.0 + 600.0 * t) * (1.0 + 0.3 * sin(37.0 * k));
   auto rel = [](double a, double b) { return b != 0.0 ? fabs(a - b) / fabs(b) : fabs(a); };
-  double e[3];
+  double e[4];
   e[0] = rel(exp_fp64(xe), exp(xe));
   e[1] = rel(log_fp64(xl), log(xl));
   e[2] = 0.0;
+  const double xr = (k & 1 ? -1.0 : 1.0) * xl;
+  e[3] = rel(recip_nr(xr), 1.0 / xr);
   const double ps[4] = {-0.2, 0.5, -1.7, 2.3};
   for (double pp : ps) {
     const double xb = exp10(-6.0 + 12.0 * t) * (1.0 + 0.3 * sin(11.0 * k));
     e[2] = fmax(e[2], rel(pow_pos_fp64(xb, pp), pow(xb, pp)));
   }
-  for (int j = 0; j < 3; ++j) atomicMax(worst + j, (unsigned long long)__double_as_longlong(e[j]));
+  for (int j = 0; j < 4; ++j) atomicMax(worst + j, (unsigned long long)__double_as_longlong(e[j]));
 }
 
 }  // namespace
@@ -98,11 +101,11 @@ using namespace avip;
 extern "C" int fp64_math_check(double* max_rel_err) {
   if (!max_rel_err) return AVIP_EINVAL;
   unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return AVIP_ENOMEM;
   }
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemset(d, 0, sizeof(h));
   if (e == cudaSuccess) {
     fp64_math_check_kernel<<<kCheckPoints / 256, 256>>>(d);
@@ -114,7 +117,7 @@ extern "C" int fp64_math_check(double* max_rel_err) {
     cudaGetLastError();
     return AVIP_ECUDA;
   }
-  for (int j = 0; j < 3; ++j) std::memcpy(max_rel_err + j, h + j, sizeof(double));
+  for (int j = 0; j < 4; ++j) std::memcpy(max_rel_err + j, h + j, sizeof(double));
   return AVIP_OK;
 }
 

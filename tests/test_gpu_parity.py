@@ -322,10 +322,12 @@ def test_neumann_marker_same_as_free(avip):
 
 def test_fp64_closure_math_matches_cuda_math_library(avip):
     """The library's own FP64 exp / log / pow (the local-field mobility and Townsend closures)
-    against the CUDA math library: exp and log within a few ulp; pow within 4e-16 (1 + |p ln x|)
-    with |p ln x| <= 2.3 ln(1.3e6) here, i.e. about 1.5e-14."""
+    and reciprocal (the limiter ratio) against the CUDA math library and the IEEE quotient: exp
+    and log within a few ulp; pow within 4e-16 (1 + |p ln x|) with |p ln x| <= 2.3 ln(1.3e6)
+    here, i.e. about 1.5e-14; the reciprocal within two ulp."""
     rc, err = avip.fp64_math_check()
     assert rc == avip.AVIP_OK
     assert err[0] <= 1.2e-15, err
     assert err[1] <= 1.2e-15, err
     assert err[2] <= 4e-16 * (1.0 + 2.3 * np.log(1.3e6)), err
+    assert err[3] <= 4.5e-16, err  # two Newton steps: within two ulp of the quotient
