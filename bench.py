@@ -367,7 +367,8 @@ def run_ours(args, rank, world, local_rank):
     # per step: pcg, node_fields, dt_cells, (edge_flux in FP64,) flux_update, finalize; photoionisation:
     # the solves (one launch side by side, else one per term) and the source update
     n_photo = 0 if photo is None else (1 if photo["side_by_side"] else len(problem.photo.a)) + 1
-    launches += args.steps * (5 + (1 if args.precision == "fp64" else 0) + n_photo)
+    # plus one statistics reset per call (memsets are not kernels and are not counted)
+    launches += 1 + args.steps * (5 + (1 if args.precision == "fp64" else 0) + n_photo)
     if world > 1:
         torch.distributed.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -547,7 +548,7 @@ def run_batch(args, rank, world, local_rank):
         "pcg_iters_per_step": iters / args.steps,
         "e2e": {"value": world * T * e2e_steps / e2e_t if e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 1 + 5 * args.steps,  # statistics reset, then per step the solve and 4 stages
         "clocks": clocks,
     }
 

@@ -184,7 +184,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
 #pragma unroll
       for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
         if (s == ie) se = src[s];
-      if (se != 0.0) chem = a.ph.a_chem * fabs(ne) / fabs(se);
+      if (se != 0.0) chem = a.ph.a_chem * fabs(ne) * recip_nr(fabs(se));
     }
 #pragma unroll
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s)
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kDDThreads) photo_add_kernel(DDArgs a, int wit
     a.src[(size_t)ip * a.Npad + i] += S;
     if (with_dt && se != 0.0) {
       const double* n = a.nbuf + (size_t)a.sc->parity * AVIP_MAX_SPECIES * a.Npad;
-      chem = a.ph.a_chem * fabs(n[(size_t)ie * a.Npad + i]) / fabs(se);
+      chem = a.ph.a_chem * fabs(n[(size_t)ie * a.Npad + i]) * recip_nr(fabs(se));
     }
   }
   if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
