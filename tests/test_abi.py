@@ -2,6 +2,7 @@
 include/avip.h declares; host-only entry points behave.  No GPU compute is called."""
 import os
 
+import numpy as np
 import pytest
 
 from helpers import header_functions
@@ -37,6 +38,10 @@ def test_host_only_entry_points(lib):
     assert avip.status_str(avip.AVIP_ENOTCONV).startswith("PCG")
     assert avip.status_str(12345) == "unknown status"
     assert lib.mesh_destroy(None) == 0
+    # null handles are rejected before any device work
+    assert avip.batch_set_dd_threads(None, 128) == avip.AVIP_EINVAL
+    assert avip.photo_stats(None)[0] == avip.AVIP_EINVAL
+    assert avip.state_set(None, np.zeros(4)) == avip.AVIP_EINVAL
 
 
 def test_mesh_validation_on_host(lib):

@@ -113,6 +113,9 @@ def test_photo_error_paths(avip):
     with pytest.raises(avip.AvipError):
         avip.Batch([m])
     m.close()
+    plain = avip.Mesh(q)  # no photoionisation: no terms, nothing side by side
+    assert plain.photo_stats() == {"iters": [], "relres": [], "side_by_side": False}
+    plain.close()
 
 
 def test_photo_on_hybrid_mesh_with_chemistry_and_ramp(avip):
