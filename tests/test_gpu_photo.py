@@ -158,3 +158,19 @@ def test_photo_side_by_side_skips_after_timeout_then_recovers(avip):
     # S_ph is the output of solves stopped at rtol 1e-13: the solve's accuracy
     assert normwise(m.photo(), o.last_photo) <= 1e-9
     m.close()
+
+
+def test_photo_side_by_side_on_the_whole_grid(avip):
+    """A planar mesh large enough for the whole-GPU AMG grid (one block per SM): the three terms
+    run side by side on groups of about a third of the SMs each, every term converges to the
+    handle's tolerance and the run status stays OK (no group waits on another)."""
+    p = planar(421, 421)
+    m = avip.Mesh(p, rtol=1e-12)
+    assert m.info["pcg_kind"] == 8
+    st = m.run(2)
+    assert st["status"] == avip.AVIP_OK and st["steps"] == 2
+    ps = m.photo_stats()
+    assert ps["side_by_side"] and m.info["pcg_blocks"] >= 100, (ps, m.info)
+    assert all(k > 0 for k in ps["iters"]) and all(r <= 1e-12 for r in ps["relres"]), ps
+    assert np.all(np.isfinite(m.photo())) and m.photo().max() > 0
+    m.close()
