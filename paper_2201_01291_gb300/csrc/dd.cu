@@ -338,7 +338,11 @@ __device__ __forceinline__ double edge_flux(const EdgeEnd& lo, const EdgeEnd& hi
   return fc + fd;
 }
 
-__device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
+// kGather: the edge fluxes were evaluated once per edge (edge_flux_kernel) and are gathered;
+// otherwise every row evaluates its own edges (batches).  Specialised so that the single-instance
+// kernel carries none of the per-row evaluation's registers.
+template <bool kGather>
+__device__ __forceinline__ void flux_update_body_t(const DDArgs& a, int bid) {
   const int i = bid * blockDim.x + threadIdx.x;
   const int N = a.A.N;
   const int ns = a.ph.ns;
@@ -363,10 +367,10 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
         me[s] = EdgeEnd{n[(size_t)s * a.Npad + i], g.x, g.y, v.x, v.y, xi, yi};
       }
     }
-    if (a.eflux) {
+    if (kGather) {
       // fluxes already evaluated once per edge (lo -> hi), gathered in the same slot order: the
       // edge ids of kG slots are loaded together, then their fluxes, then summed in slot order
-      constexpr int kG = 8;
+      constexpr int kG = 4;
       for (int k0 = 1; k0 < rl; k0 += kG) {
         int32_t v[kG];
 #pragma unroll
@@ -384,7 +388,7 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
         }
       }
     }
-    for (int k = 1; k < (a.eflux ? 0 : rl); ++k) {
+    for (int k = 1; k < (kGather ? 0 : rl); ++k) {
       const int e = base + k * kSlice;
       const int j = __ldg(a.A.col + e);
       const double Sx = __ldg(a.A.sx + e), Sy = __ldg(a.A.sy + e);
@@ -448,7 +452,10 @@ __device__ __forceinline__ void flux_update_body(const DDArgs& a, int bid) {
   if (bid == 0 && threadIdx.x == 0) a.sc->dt = dt;
 }
 
-__global__ void __launch_bounds__(kDDThreads, 2) flux_update_kernel(DDArgs a) { flux_update_body(a, blockIdx.x); }
+template <bool kGather>
+__global__ void __launch_bounds__(kDDThreads, kGather ? 3 : 2) flux_update_kernel(DDArgs a) {
+  flux_update_body_t<kGather>(a, blockIdx.x);
+}
 
 // One thread per edge (lo, hi): the flux of every species from lo to hi through the edge's dual
 // face, the same function of the same operands as in flux_update_body's per-row evaluation, so
@@ -841,7 +848,7 @@ __global__ void __launch_bounds__(kDDThreads, 1) flux_update_batch_kernel(const 
   if (args[k].ph.dd_fp32)
     flux_update32_body(args[k], blockIdx.x - __ldg(bpref + k));
   else
-    flux_update_body(args[k], blockIdx.x - __ldg(bpref + k));
+    flux_update_body_t<false>(args[k], blockIdx.x - __ldg(bpref + k));  // batches evaluate each edge per row
 }
 __global__ void finalize_batch_kernel(const DDArgs* __restrict__ args, int count, int threads) {
   const DDArgs& a = args[blockIdx.x];
@@ -885,8 +892,12 @@ cudaError_t launch_flux_update(const DDArgs& a, cudaStream_t st) {
   if (a.ph.dd_fp32) {
     flux_update32_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
   } else {
-    if (a.eflux && a.E > 0) edge_flux_kernel<<<nblk(a.E), kDDThreads, 0, st>>>(a);
-    flux_update_kernel<<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+    if (a.eflux && a.E > 0) {
+      edge_flux_kernel<<<nblk(a.E), kDDThreads, 0, st>>>(a);
+      flux_update_kernel<true><<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+    } else {
+      flux_update_kernel<false><<<nblk(a.A.N), kDDThreads, 0, st>>>(a);
+    }
   }
   return cudaGetLastError();
 }
