@@ -76,7 +76,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
     for (int s = 0; s < AVIP_MAX_SPECIES; ++s) gnx[s] = gny[s] = 0.0;
     // neighbours in groups of kG: the column and weight loads of a group are issued together,
     // then its potential and density gathers, then the sums (in slot order, as one at a time)
-    constexpr int kG = 8;
+    constexpr int kG = 4;
     for (int k0 = 0; k0 < rl; k0 += kG) {
       int c[kG];
       double wx[kG], wy[kG];
@@ -193,7 +193,7 @@ __device__ __forceinline__ void node_fields_body(const DDArgs& a, int with_dt, i
   if (with_dt) block_min_to_global(chem, &a.sc->dt_bits);
 }
 
-__global__ void __launch_bounds__(kDDThreads) node_fields_kernel(DDArgs a, int with_dt) {
+__global__ void __launch_bounds__(kDDThreads, 3) node_fields_kernel(DDArgs a, int with_dt) {
   node_fields_body(a, with_dt, blockIdx.x);
 }
 
