@@ -810,7 +810,7 @@ __device__ __forceinline__ void flux_update32_body(const DDArgs& a, int bid) {
   if (bid == 0 && threadIdx.x == 0) a.sc->dt = dt;
 }
 
-__global__ void __launch_bounds__(kDDThreads, 2) flux_update32_kernel(DDArgs a) { flux_update32_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(kDDThreads, 3) flux_update32_kernel(DDArgs a) { flux_update32_body(a, blockIdx.x); }
 
 // ------------------------------------------------------------------------ batched forms
 // One launch covers every instance of a batch: block b belongs to the instance k with
