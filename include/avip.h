@@ -350,6 +350,13 @@ int batch_info(avip_batch_t b, int64_t* info);
 /* Set the block of the batch's drift-diffusion stages (128 or 256 threads; AVIP_EINVAL
  * otherwise), overriding the autotuner's choice; results do not depend on it. */
 int batch_set_dd_threads(avip_batch_t b, int32_t threads);
+/* Checkpoint of a whole batch: the states of its instances concatenated in the order the
+ * handles were given to batch_create, each laid out as state_get lays it out (the sum of their
+ * state_size entries).  One wait per call whatever the number of instances.  batch_state_set
+ * installs nothing when an entry is not finite (AVIP_ENAN) or a history count is outside 0..3
+ * (AVIP_EINVAL). */
+int batch_state_get(avip_batch_t b, double* host_state);
+int batch_state_set(avip_batch_t b, const double* host_state);
 int batch_destroy(avip_batch_t b);
 
 /* No-allocation Jacobi-preconditioned CG for callers that cannot allocate device memory.

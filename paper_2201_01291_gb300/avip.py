@@ -87,6 +87,8 @@ _SIGS = {
     "batch_run_steps": (C.c_int, [_H, C.c_int32, C.c_void_p]),
     "batch_info": (C.c_int, [_H, _P(C.c_int64)]),
     "batch_set_dd_threads": (C.c_int, [_H, C.c_int32]),
+    "batch_state_get": (C.c_int, [_H, _D]),
+    "batch_state_set": (C.c_int, [_H, _D]),
     "batch_destroy": (C.c_int, [_H]),
     "pcg_csr_static": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_double, C.c_int32, C.c_void_p, _I, _D]),
@@ -373,6 +375,19 @@ def batch_set_dd_threads(b, threads):
     return load().batch_set_dd_threads(b, int(threads))
 
 
+def batch_state_get(b, out):
+    """Fill `out` (float64, contiguous, the sum of the instances' state sizes) with the batch's
+    concatenated states; returns the status."""
+    if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("batch_state_get: out must be a contiguous float64 array")
+    return load().batch_state_get(b, _dptr(out))
+
+
+def batch_state_set(b, state):
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    return load().batch_state_set(b, _dptr(s))
+
+
 def batch_destroy(b):
     return load().batch_destroy(b)
 
@@ -531,6 +546,24 @@ class Batch:
         rc, st = batch_run_steps(self.b, nsteps, len(self.meshes))
         _check(rc, "batch_run_steps", allow)
         return st
+
+    def state_size(self):
+        total = 0
+        for m in self.meshes:
+            n = C.c_int64()
+            _check(load().state_size(m.h, C.byref(n)), "state_size")
+            total += n.value
+        return total
+
+    def state(self, out=None):
+        """The instances' states concatenated (see batch_state_get); `out` may be given."""
+        if out is None:
+            out = np.empty(self.state_size())
+        _check(batch_state_get(self.b, out), "batch_state_get")
+        return out
+
+    def set_state(self, st):
+        _check(batch_state_set(self.b, st), "batch_state_set")
 
     def close(self):
         if getattr(self, "b", None):

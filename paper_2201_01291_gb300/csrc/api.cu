@@ -1536,6 +1536,68 @@ int batch_destroy(avip_batch_t b) {
   return AVIP_OK;
 }
 
+// The states of every instance of a batch, concatenated in the order the handles were given
+// (each instance's block as state_get lays it out): every instance's copy is queued on the
+// batch's stream and the call waits once, instead of once per instance.
+int batch_state_get(avip_batch_t b, double* out) {
+  if (!b || !out) return AVIP_EINVAL;
+  size_t off = 0;
+  cudaError_t e = cudaSuccess;
+  for (avip_mesh* h : b->m) {
+    if (!state_buffers(h)) return AVIP_ENOMEM;
+    int64_t n = 0;
+    state_size(h, &n);
+    if (e == cudaSuccess) e = launch_state_take(state_args(h), b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + off, h->d_stage, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    off += (size_t)n;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return cuda_status(e);
+}
+
+// Install the concatenated states of batch_state_get: AVIP_EINVAL (a history count outside
+// 0..3) or AVIP_ENAN (a non-finite entry) install nothing.
+int batch_state_set(avip_batch_t b, const double* in) {
+  if (!b || !in) return AVIP_EINVAL;
+  const size_t count = b->m.size();
+  std::vector<size_t> off(count + 1, 0);
+  for (size_t k = 0; k < count; ++k) {
+    avip_mesh* h = b->m[k];
+    int64_t n = 0;
+    state_size(h, &n);
+    off[k + 1] = off[k] + (size_t)n;
+    const double hn = in[off[k + 1] - 1];
+    if (!(hn >= 0.0 && hn <= (double)kPredictorHistory && hn == std::floor(hn))) return AVIP_EINVAL;
+    if (!state_buffers(h)) return AVIP_ENOMEM;
+  }
+  std::vector<int32_t> flags(count, 0);
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < count && e == cudaSuccess; ++k) {
+    avip_mesh* h = b->m[k];
+    e = cudaMemcpyAsync(h->d_stage, in + off[k], (off[k + 1] - off[k]) * sizeof(double), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_state_flag, 0, sizeof(int32_t), b->stream);
+    if (e == cudaSuccess) e = launch_state_check(state_args(h), b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&flags[k], h->d_state_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int32_t f : flags)
+    if (f) return AVIP_ENAN;
+  for (size_t k = 0; k < count && e == cudaSuccess; ++k) {
+    avip_mesh* h = b->m[k];
+    StateArgs sa = state_args(h);
+    const size_t N = (size_t)h->hm.N;
+    sa.t = in[off[k] + (size_t)(h->ph.ns + 1) * N];
+    sa.hist = (int32_t)in[off[k + 1] - 1];
+    e = launch_state_put(sa, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return cuda_status(e);
+}
+
 int batch_info(avip_batch_t b, int64_t* info) {
   if (!b || !info) return AVIP_EINVAL;
   info[0] = b->C;

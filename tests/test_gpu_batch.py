@@ -137,3 +137,24 @@ def test_mixed_batch_with_amg_instances(avip):
         assert normwise(meshes[k].phi(), phi_ref) <= 1e-6
         alone.close()
     b.close()
+
+
+def test_batch_checkpoint_round_trip(avip):
+    """batch_state_get equals the instances' own states concatenated; batch_state_set restores
+    them (the batch then repeats its steps bit for bit) and refuses a non-finite entry."""
+    ps = _instances()[:4]
+    meshes = [avip.Mesh(p, rtol=1e-13, pcg_kind=5) for p in ps]
+    b = avip.Batch(meshes, cluster_size=16)
+    b.run(2)
+    snap = b.state()
+    np.testing.assert_array_equal(snap, np.concatenate([m.state() for m in meshes]))
+    b.run(3)
+    after = b.state()
+    bad = snap.copy()
+    bad[5] = np.inf
+    assert avip.batch_state_set(b.b, bad) == avip.AVIP_ENAN
+    np.testing.assert_array_equal(b.state(), after)  # nothing installed
+    b.set_state(snap)
+    b.run(3)
+    np.testing.assert_array_equal(b.state(), after)
+    b.close()
